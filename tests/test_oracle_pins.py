@@ -1,0 +1,303 @@
+"""Pins of the oracle against references other than itself (CPU only).
+
+Each test would fail for a plausible mistake in the oracle: a dropped or
+sign-flipped term, a transposed A, a wrong stage index, a wrong step rule.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+import pins
+from paper_2209_13049_b300 import inputs
+from paper_2209_13049_b300.inputs import Plant
+
+
+def _tiny(seed, ns=2, nu=1, N=3, xb=0.5, ub=0.4, dense_q=True):
+    return inputs.random_small(ns, nu, N, seed, xb=xb, ub=ub, dense_q=dense_q)
+
+
+# ---------------------------------------------------------------- IPM optimum
+
+
+def _double_integrator(N=3, ub=0.5, r=0.1):
+    A = np.array([[1.0, 0.5], [0.0, 1.0]])
+    B = np.array([[0.125], [0.5]])
+    return Plant(2, 1, N, A, B, np.eye(2), np.array([[r]]), np.eye(2),
+                 -np.ones(2), np.ones(2), -ub * np.ones(1), ub * np.ones(1))
+
+
+def _feasible_cases(make, draws, count):
+    """(plant, x0, brute-force optimum, active rows) for the first `count`
+    feasible draws; infeasible draws (no KKT point) are skipped."""
+    out = []
+    for p, x0 in draws:
+        bf = pins.brute_force(p, x0)
+        if bf is not None:
+            out.append((p, x0, bf[0], bf[1]))
+        if len(out) == count:
+            break
+    return out
+
+
+def _di_draws():
+    rng = np.random.default_rng(0)
+    for _ in range(40):
+        yield _double_integrator(), rng.uniform([0.3, 0.2], [0.95, 0.9])
+
+
+def _random_draws():
+    for seed in range(40):
+        p = _tiny(seed)
+        yield p, np.random.default_rng(100 + seed).uniform(-0.45, 0.45, size=p.ns)
+
+
+def test_ipm_matches_brute_force_active_bounds():
+    """Brute-force active-set enumeration gives the exact minimiser; these
+    double-integrator cases have state and input bounds that bind."""
+    cases = _feasible_cases(None, _di_draws(), 8)
+    assert len(cases) == 8
+    assert sum(len(c[3]) for c in cases) >= 10
+    for p, x0, ubf, _ in cases:
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        assert r["status"] == oracle.STATUS_OK
+        np.testing.assert_allclose(r["u"], ubf, rtol=0, atol=1e-8)
+
+
+def test_ipm_matches_brute_force_random_dense():
+    """Random non-symmetric A, dense Q, Qf, R (a transposed A or a wrong Qf
+    stage would change the optimum)."""
+    cases = _feasible_cases(None, _random_draws(), 8)
+    assert len(cases) == 8
+    for p, x0, ubf, _ in cases:
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        assert r["status"] == oracle.STATUS_OK
+        np.testing.assert_allclose(r["u"], ubf, rtol=0, atol=1e-8)
+
+
+def test_ipm_matches_brute_force_two_inputs():
+    draws = ((inputs.random_small(2, 2, 2, 50 + s, xb=0.4, ub=0.3, dense_q=True),
+              np.random.default_rng(s).uniform(-0.35, 0.35, size=2)) for s in range(20))
+    cases = _feasible_cases(None, draws, 3)
+    assert len(cases) == 3
+    for p, x0, ubf, _ in cases:
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        np.testing.assert_allclose(r["u"], ubf, rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_ipm_unbounded_equals_lqr(seed):
+    """With every bound absent the QP is the finite-horizon LQR problem."""
+    p = inputs.random_small(4, 2, 6, seed, dense_q=True)
+    p.xl, p.xu = np.full(4, -np.inf), np.full(4, np.inf)
+    p.ul, p.uu = np.full(2, -np.inf), np.full(2, np.inf)
+    x0 = np.random.default_rng(seed).standard_normal(4)
+    r = oracle.ipm_solve(p, x0, tol=1e-12)
+    assert r["stats"]["m"] == 0
+    np.testing.assert_allclose(r["u"], pins.lqr(p, x0), rtol=0, atol=1e-11)
+
+
+def test_ipm_inactive_bounds_equal_lqr_heat1d():
+    """1-D heat plant with loose finite bounds: the optimum is the LQR law."""
+    p = inputs.heat1d(20, 3, 8, xb=50.0, ub=50.0)
+    x0 = inputs.x0_uniform(20, 3)
+    r = oracle.ipm_solve(p, x0, tol=1e-13)
+    assert r["status"] == 0
+    np.testing.assert_allclose(r["u"], pins.lqr(p, x0), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("case", [
+    (0.9, 0.5, 2.0, 0.1, 1.0, -0.5, 0.5, -1.0, 1.0),    # state bound active
+    (0.9, -0.5, 2.0, 0.1, 1.0, -0.8, 0.8, -0.3, 0.3),   # input bound active, b < 0
+    (0.5, 1.0, 1.0, 1.0, 0.2, -1.0, 1.0, -1.0, 1.0),    # interior optimum
+])
+def test_ipm_scalar_closed_form(case):
+    a, b, qf, r_, xbar, xl, xu, ul, uu = case
+    p = Plant(1, 1, 1, np.array([[a]]), np.array([[b]]), np.array([[1.0]]), np.array([[r_]]),
+              np.array([[qf]]), np.array([xl]), np.array([xu]), np.array([ul]), np.array([uu]))
+    r = oracle.ipm_solve(p, np.array([xbar]), tol=1e-13)
+    ref = pins.scalar_closed_form(a, b, qf, r_, xbar, xl, xu, ul, uu)
+    assert abs(r["u"][0] - ref) < 1e-10
+
+
+def test_ipm_kkt_invariants_heat1d():
+    """Stationarity, feasibility, nonnegative duals and complementarity at the
+    returned point of the ns=50 1-D configuration."""
+    p, x0 = inputs.config_1d_small(0)
+    r = oracle.ipm_solve(p, x0, tol=1e-10)
+    k = oracle.kkt_check(p, x0, r["u"], r["z"])
+    assert r["status"] == 0
+    assert k["primal_violation"] <= 1e-12
+    assert k["stationarity"] <= 1e-9
+    assert k["dual_min"] >= 0.0
+    assert k["complementarity"] <= 1e-8
+
+
+def test_ipm_kkt_invariants_active_heat2d_small():
+    """A small 2-D plant where the lower state bound binds."""
+    p = inputs.heat2d(6, 4, 8)
+    x0 = inputs.x0_gaussians(6, 1)
+    r = oracle.ipm_solve(p, x0, tol=1e-11)
+    k = oracle.kkt_check(p, x0, r["u"], r["z"])
+    x = oracle.simulate(p, x0, r["u"])
+    assert r["status"] == 0
+    assert np.sum(x < 1e-7) > 0
+    assert k["primal_violation"] <= 1e-12 and k["stationarity"] <= 1e-9
+    assert k["complementarity"] <= 1e-9
+
+
+def test_ipm_trace_monotone_and_steps_valid():
+    p, x0 = inputs.config_1d_small(2)
+    r = oracle.ipm_solve(p, x0, want_trace=True)
+    tr = r["trace"]
+    assert np.all(tr[:-1, 5] > 0) and np.all(tr[:-1, 5] <= 1)
+    assert np.all(tr[:-1, 3] > 0) and np.all(tr[:-1, 3] <= 1)
+    assert np.all(np.diff(tr[:, 0]) < 0)          # mu decreases every iteration
+
+
+def test_ipm_status_codes_match_abi_numbering():
+    """The oracle's status numbers equal the C-ABI's (documented values)."""
+    assert (oracle.STATUS_OK, oracle.STATUS_NOT_PD, oracle.STATUS_MAXITER, oracle.STATUS_NAN) == (0, 3, 4, 6)
+
+
+def test_ipm_maxiter_on_infeasible():
+    """x0 far outside what the inputs can correct: the QP is infeasible and the
+    iteration must end with MAXITER or NAN, never a false OK."""
+    p = _tiny(0, xb=0.1, ub=0.01)
+    r = oracle.ipm_solve(p, np.array([5.0, -5.0]), max_iter=40)
+    assert r["status"] in (oracle.STATUS_MAXITER, oracle.STATUS_NAN)
+
+
+# ------------------------------------------------------ condensed operators
+
+
+def test_gstack_is_toeplitz_expansion_of_impulse_response():
+    """Gamma's block (r, t) equals A^{r-t} B (the structure the paper notes in
+    its conclusions: all data of J sits in its first nu columns)."""
+    p = inputs.heat2d(5, 3, 6)
+    G = oracle.gstack(p)
+    Gam, _, _, _ = oracle.condensed(p, np.zeros(p.ns))
+    for r in range(p.N):
+        for t in range(p.N):
+            blk = Gam[r * p.ns:(r + 1) * p.ns, t * p.nu:(t + 1) * p.nu]
+            if t <= r:
+                np.testing.assert_allclose(blk, G[r - t], rtol=1e-14, atol=1e-300)
+            else:
+                assert not blk.any()
+
+
+def test_condensed_reproduces_dynamics():
+    """Phi xbar + Gamma u equals a direct simulation of the dynamics."""
+    p = inputs.random_small(3, 2, 5, 7)
+    x0 = np.array([0.3, -0.2, 0.1])
+    u = np.random.default_rng(1).standard_normal(p.n)
+    Gam, y, _, _ = oracle.condensed(p, x0)
+    np.testing.assert_allclose(y + Gam @ u, oracle.simulate(p, x0, u).reshape(-1), rtol=1e-13, atol=1e-14)
+
+
+@pytest.mark.parametrize("dense_q", [False, True])
+def test_condensed_objective_identity(dense_q):
+    """1/2 u'Hu + h'u + c equals the sparse objective of Eq. 1 for any u;
+    checked at several u so H and h are both pinned (with the constant c
+    from u = 0)."""
+    p = inputs.random_small(3, 2, 5, 11, dense_q=dense_q)
+    x0 = np.array([0.4, 0.1, -0.3])
+    Gam, y, H, h = oracle.condensed(p, x0)
+    Q, Qf, R = p.dense("Q"), p.dense("Qf"), np.asarray(p.R)
+
+    def sparse_obj(u):
+        x = oracle.simulate(p, x0, u)
+        uu = u.reshape(p.N, p.nu)
+        v = sum(0.5 * x[t] @ (Qf if t == p.N - 1 else Q) @ x[t] for t in range(p.N))
+        return v + sum(0.5 * uu[t] @ R @ uu[t] for t in range(p.N))
+
+    c = sparse_obj(np.zeros(p.n))
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        u = rng.standard_normal(p.n)
+        assert abs(0.5 * u @ H @ u + h @ u + c - sparse_obj(u)) < 1e-11 * (1 + abs(c))
+
+
+def test_condensed_matches_independent_dense_build():
+    p = inputs.random_small(3, 2, 4, 3, dense_q=True)
+    x0 = np.array([0.2, 0.5, -0.1])
+    G1, y1, H1, h1 = oracle.condensed(p, x0)
+    G2, y2, H2, h2 = pins.dense_qp(p, x0)
+    np.testing.assert_allclose(G1, G2, rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(H1, H2, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(h1, h2, rtol=1e-12, atol=1e-14)
+
+
+def test_kkt_matrix_matches_matrix_free_product():
+    """M v = H v + Gamma'(Sigma_x (Gamma v)) + Sigma_u v, with Gamma v by
+    simulation and Gamma' w by the adjoint recursion (no explicit Gamma)."""
+    p = inputs.heat2d(4, 3, 5)
+    rng = np.random.default_rng(4)
+    sigx = rng.uniform(0, 10, p.ns * p.N)
+    sigu = rng.uniform(0, 10, p.n)
+    M = oracle.kkt_matrix(p, sigx, sigu)
+    Gam, _, H, _ = oracle.condensed(p, np.zeros(p.ns))
+    for _ in range(3):
+        v = rng.standard_normal(p.n)
+        Gv = oracle.simulate(p, np.zeros(p.ns), v).reshape(-1)
+        mv = H @ v + oracle.adjoint_gradient(p, None, sigx * Gv) + sigu * v
+        np.testing.assert_allclose(M @ v, mv, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(M, M.T, rtol=0, atol=1e-12)
+    np.linalg.cholesky(M)          # positive definite (Eq. 7)
+
+
+def test_kkt_entries_match_dense_definition():
+    p = inputs.heat1d(12, 2, 5)
+    rng = np.random.default_rng(5)
+    sigx = rng.uniform(0, 3, p.ns * p.N)
+    sigu = rng.uniform(0, 3, p.n)
+    Gam, _, H, _ = oracle.condensed(p, np.zeros(p.ns))
+    M = oracle.kkt_matrix(p, sigx, sigu, Gam, H)
+    pairs = [(j, k) for j in range(p.n) for k in range(p.n)]
+    e = oracle.kkt_entries(p, sigx, sigu, pairs, H=H)
+    np.testing.assert_allclose(e, M.reshape(-1), rtol=1e-13, atol=1e-14)
+    hq = oracle.hessian_entries(p, pairs)
+    np.testing.assert_allclose(hq, H.reshape(-1), rtol=1e-13, atol=1e-15)
+
+
+def test_dimensions_of_figure1_instance():
+    """Fig. 1's instance (nx=5, nu=3, T=5): the condensed system is n_u T = 15
+    square, J has (n_x + n_u) T two-sided rows (conclusions), and the dense QP
+    has 2 T (n_x + n_u) one-sided inequalities (Section II)."""
+    p = inputs.random_small(5, 3, 5, 0)
+    Gam, y, H, h = oracle.condensed(p, np.zeros(5))
+    M = oracle.kkt_matrix(p, np.ones(25), np.ones(15), Gam, H)
+    assert M.shape == (15, 15)
+    assert Gam.shape[0] + p.n == (5 + 3) * 5
+    r = oracle.ipm_solve(p, np.zeros(5))
+    assert r["stats"]["m"] == 2 * 5 * (5 + 3)
+
+
+# ----------------------------------------- planted mistakes are caught (CPU)
+
+
+def test_planted_transpose_is_caught_by_objective_identity():
+    """Plant a transposed A in the oracle's condensing step: the objective
+    identity against the true dynamics must fail."""
+    p = inputs.random_small(3, 2, 4, 9)
+    x0 = np.array([0.4, 0.1, -0.3])
+    wrong = inputs.random_small(3, 2, 4, 9)
+    wrong.A = p.A.T.copy()
+    _, _, H, h = oracle.condensed(wrong, x0)
+    Q, R = p.dense("Q"), np.asarray(p.R)
+    u = np.random.default_rng(0).standard_normal(p.n)
+    x = oracle.simulate(p, x0, u)
+    true = sum(0.5 * x[t] @ Q @ x[t] for t in range(p.N)) + 0.5 * u @ np.kron(np.eye(p.N), R) @ u
+    x00 = oracle.simulate(p, x0, np.zeros(p.n))
+    c = sum(0.5 * x00[t] @ Q @ x00[t] for t in range(p.N))
+    assert abs(0.5 * u @ H @ u + h @ u + c - true) > 1e-6
+
+
+def test_planted_sign_error_is_caught_by_brute_force():
+    """Flip the sign of A's off-diagonal in the oracle's input: its optimum no
+    longer matches the brute-force optimum of the true problem."""
+    p, x0, ubf, _ = _feasible_cases(None, _di_draws(), 1)[0]
+    bad = _double_integrator()
+    bad.A = np.array([[1.0, -0.5], [0.0, 1.0]])
+    r = oracle.ipm_solve(bad, x0, tol=1e-12)
+    assert np.max(np.abs(r["u"] - ubf)) > 1e-4
