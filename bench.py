@@ -1,0 +1,311 @@
+#!/usr/bin/env python
+"""Benchmark: LQ-MPC interior-point solves/s and per-iteration KKT time at a
+1e-8 scaled KKT residual, mixed precision (BF16 tensor-core SYRK + FP32
+Cholesky + FP64 refinement) versus FP64, on the 2-D heat plant of a 32 x 32
+grid (ns = 1024, nu = 10, N = 50; condensed M is 500 x 500).
+
+One step = one full IPM solve (all per-iteration steps of the hot path) for
+one seeded initial state x0.  Inputs sit in device memory before the timed
+region; L2 is flushed (512 MB write) between steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU runs are independent replicas (one process per GPU, disjoint x0
+seeds, no collective in the data path): value = all solves / max-over-ranks
+time.  The reference arm is the CPU oracle (FP64 Riccati-Mehrotra), timed on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2209_13049_b300 import inputs  # noqa: E402
+
+METRIC = "LQ-MPC IPM solves/s & per-iter KKT ms at 1e-8 residual, mixed vs FP64"
+WORKLOAD = "heat2d 32x32 (ns=1024, nu=10, N=50), x0 = seeded 8-Gaussian fields, tol 1e-8"
+GOLD = os.path.join(ROOT, "tests", "golden", "heat2d_g32_nu10_N50.npz")
+NS, NU, N = 1024, 10, 50
+
+
+def syrk_alg_flops(ns, nu, N):
+    """Algorithmic flops of one KKT-matrix formation exploiting the block
+    lower-triangular Toeplitz structure of Gamma: the lower-triangle blocks
+    (j >= k) each need N - j products G_p' D G_q of 2 ns nu^2 flops."""
+    return 2.0 * ns * nu * nu * N * (N + 1) * (N + 2) / 6.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_baseline(seconds_budget: float = 30.0):
+    """The oracle as it stands, single-threaded, on one full solve of the
+    workload (seed 0): about 25 s on one host core."""
+    import oracle
+    plant, x0 = inputs.config_2d_32(0)
+    t = time.perf_counter()
+    r = oracle.ipm_solve(plant, x0, tol=1e-8)
+    dt = time.perf_counter() - t
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 full solve (x0 seed 0, {r['stats']['iters']} iterations) of the workload, "
+                      f"{dt:.1f} s on 1 host core ({len(os.sched_getaffinity(0))} available)"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    plant, x0s = inputs.heat2d(32, 10, 50), None
+    full_iters = None
+    if os.path.exists(GOLD):
+        full_iters = len(np.load(GOLD)["heat2d_32_s0_trace8"]) - 1
+    per_iter = []
+    sample_iters = 2
+    for step in range(args.warmup + args.steps):
+        x0 = inputs.x0_gaussians(32, step)
+        t = time.perf_counter()
+        r = oracle.ipm_solve(plant, x0, tol=1e-8, max_iter=sample_iters)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            per_iter.append(dt / max(1, r["stats"]["iters"]))
+    if full_iters is None:
+        full_iters = oracle.ipm_solve(plant, inputs.x0_gaussians(32, 0), tol=1e-8)["stats"]["iters"]
+    t_iter = float(np.mean(per_iter))
+    value = 1.0 / (t_iter * full_iters)
+    ms_per_step = t_iter * sample_iters * 1e3
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "ns": NS, "nu": NU, "N": N},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {sample_iters} IPM iterations of the oracle on one x0; "
+                                       f"solves/s = 1/(time per iteration x {full_iters} iterations of a full "
+                                       f"solve of x0 seed 0)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2209_13049_b300 import binding, build
+    build.build()
+    binding.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    plant = inputs.heat2d(32, 10, 50)
+    K, W = args.steps, args.warmup
+    seeds = [rank * 100000 + i for i in range(W + K)]
+    x0_host = [inputs.x0_gaussians(32, s) for s in seeds]
+    x0_dev = [torch.tensor(x, dtype=torch.float64, device=dev) for x in x0_host]
+    u_dev = [torch.zeros(plant.n, dtype=torch.float64, device=dev) for _ in seeds]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed_solves(solver, idx, use_host=False):
+        """Per-step CUDA-event times (ms) on the solver's stream; L2 flushed between steps."""
+        times, stats = [], []
+        for i in idx:
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if use_host:
+                u, st = solver.solve(x0_host[i], check=False)
+            else:
+                st = solver.solve_device(x0_dev[i], u_dev[i], check=False)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(st)
+        return times, stats
+
+    mixed = binding.Solver(plant, precision=args.precision, stream=stream)
+    fp64 = binding.Solver(plant, precision="fp64", stream=stream)
+
+    # warm-up
+    timed_solves(mixed, range(W))
+    timed_solves(fp64, range(min(W, 1)))
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = binding.kernel_launches()
+    barrier()
+    t_mixed, st_mixed = timed_solves(mixed, range(W, W + K))
+    barrier()
+    launches = binding.kernel_launches() - launches0
+    clocks = sampler.stop()
+    # FP64 comparison (fewer steps: each FP64 solve is ~10x longer)
+    kf = max(1, min(K, args.fp64_steps))
+    t_fp64, st_fp64 = timed_solves(fp64, range(W, W + kf))
+    # end-to-end through the host API (x0 from host, u back to host, inside the call)
+    t_e2e, _ = timed_solves(mixed, range(W, W + K), use_host=True)
+    barrier()
+
+    total_ms = float(sum(t_mixed))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms, float(sum(t_e2e))], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, e2e_ms = float(tt[0]), float(tt[1])
+    else:
+        e2e_ms = float(sum(t_e2e))
+    value = world * K / (total_ms / 1e3)
+    e2e_value = world * K / (e2e_ms / 1e3)
+
+    # parity of the timed solves' first instance against the stored oracle result
+    errs = {}
+    if os.path.exists(GOLD):
+        g = np.load(GOLD)
+        ref = g["heat2d_32_s0_u12"]
+        u_m, _ = mixed.solve(g["heat2d_32_s0_x0"], check=False)
+        u_f, _ = fp64.solve(g["heat2d_32_s0_x0"], check=False)
+        scale = max(1.0, float(np.max(np.abs(ref))))
+        errs = {"mixed": float(np.max(np.abs(u_m - ref)) / scale), "fp64": float(np.max(np.abs(u_f - ref)) / scale)}
+
+    def summary(times, stats):
+        iters = [s["iters"] for s in stats]
+        kkt = [s["t_kkt_ms"] / max(1, s["iters"]) for s in stats]
+        return {"solves_per_s": len(times) / (sum(times) / 1e3), "ms_per_solve": float(np.mean(times)),
+                "iters_mean": float(np.mean(iters)), "kkt_ms_per_iter": float(np.mean(kkt)),
+                "refine_steps_mean": float(np.mean([s["refine_steps"] for s in stats])),
+                "fallbacks_total": int(sum(s["fallbacks"] for s in stats)),
+                "status": sorted({int(s["status"]) for s in stats})}
+
+    # roofline of the tensor-core SYRK (a4), from events around its launches in the timed region
+    n_tc = sum(s["syrk_tc_launches"] for s in st_mixed)
+    t_tc = sum(s["t_syrk_tc_ms"] for s in st_mixed)
+    peaks, which = measured_peaks()
+    flops = syrk_alg_flops(NS, NU, N)
+    achieved = flops / (t_tc / max(1, n_tc) / 1e3) / 1e12 if n_tc else None
+    peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    roofline = {"kernel": "k_syrk_tc<bf16> (tcgen05 KKT-matrix formation)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": f"{which} bf16_tflops_sustained", "flops_per_launch": flops,
+                "launches": n_tc, "avg_launch_us": (t_tc / max(1, n_tc) * 1e3) if n_tc else None}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
+                "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "mixed-bf16 (bf16 SYRK, fp32 Cholesky, fp64 refinement)",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "ns": NS, "nu": NU, "N": N,
+                           "l2": "flushed between steps (512 MB write, outside the timed events)",
+                           "parallelism": f"replicas x{world}", "precision": args.precision},
+                "mixed": summary(t_mixed, st_mixed), "fp64": summary(t_fp64, st_fp64),
+                "speedup_mixed_vs_fp64": (value / world) / (kf / (sum(t_fp64) / 1e3)),
+                "u_rel_err_vs_oracle": errs, "roofline": roofline, "clocks": clocks,
+                "gpu_launches": int(launches),
+                "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": NS * 8,
+                        "d2h_bytes_per_step": plant.n * 8}}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_baseline()
+        print(json.dumps(line), flush=True)
+    mixed.close()
+    fp64.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * lqmpc: condensed-space interior-point solver for box-constrained
+ * linear-quadratic MPC on one B300 GPU (sm_103a).
+ *
+ * The problem (the paper's Eq. 1 with S = 0, no general constraints, w = 0):
+ *     min  1/2 sum_{t=1}^{N-1} x_t' Q x_t + 1/2 x_N' Qf x_N + 1/2 sum_{t=0}^{N-1} u_t' R u_t
+ *     s.t. x_0 = x0,  x_{t+1} = A x_t + B u_t          (t = 0..N-1)
+ *          xl <= x_t <= xu  (t = 1..N),  ul <= u_t <= uu  (t = 0..N-1).
+ * The states are eliminated once (Section II: x = Phi x0 + Gamma u, Gamma the
+ * block lower-triangular Toeplitz matrix of the blocks A^k B), giving the
+ * dense QP of Eq. 3 in u (n = nu*N variables).  Each interior-point iteration
+ * (Section III, Algorithm 1) forms the condensed KKT matrix of Eq. 7,
+ *     M = H + Gamma' Sigma_x Gamma + Sigma_u,
+ * factors it by Cholesky, solves for the input step and recovers the slack
+ * and dual steps by products with Gamma.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major unless stated.  Sparse matrices are CSR with
+ *    int32 row pointers (rows+1), int32 column indices and double values.
+ *  - Input vectors are u_t stacked (u[t*nu + c]); state vectors x_1..x_N
+ *    stacked (x[(t-1)*ns + i]).
+ *  - Pointers are host memory unless the name says "device".  The caller owns
+ *    every buffer it passes; the context owns all device memory it allocates.
+ *  - No function throws across this boundary or aborts the process.  Errors
+ *    are reported as an lqmpc_status; on failure, output buffers hold the best
+ *    available values (the last iterate for a solve) or are left untouched
+ *    for argument errors.
+ *  - Bounds may be -INFINITY / +INFINITY; an infinite bound is absent.
+ *  - All device work runs on the stream given at setup (NULL = legacy default
+ *    stream).  Calls on one context are not thread-safe.
+ *  - There is no CPU fallback: if the CUDA device or kernels are unavailable
+ *    the calls return LQMPC_ERR_CUDA.
+ */
+#ifndef LQMPC_H
+#define LQMPC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqmpc_ctx lqmpc_ctx;
+
+typedef enum {
+    LQMPC_OK = 0,
+    LQMPC_ERR_ARG = 1,          /* invalid argument (sizes, NULL pointers, NaN data) */
+    LQMPC_ERR_CUDA = 2,         /* CUDA runtime error or no usable device */
+    LQMPC_ERR_NOT_PD = 3,       /* Cholesky of M failed even in FP64 (Eq. 7 requires M > 0) */
+    LQMPC_ERR_MAXITER = 4,      /* iteration limit reached before the stop test */
+    LQMPC_ERR_INFEASIBLE = 5,   /* x0 outside its bounds or detected infeasibility */
+    LQMPC_ERR_NAN = 6,          /* non-finite iterate */
+    LQMPC_ERR_STALL = 7,        /* iterative refinement stalled and fallback disabled */
+    LQMPC_ERR_TIMEOUT = 8,      /* a bounded device-side wait gave up */
+    LQMPC_ERR_UNSUPPORTED = 9   /* option or size not supported by this build */
+} lqmpc_status;
+
+/* Arithmetic of the KKT step (the M formation, factorisation and solves). */
+enum {
+    LQMPC_FP64 = 0,         /* FP64 SYRK, FP64 Cholesky and solves */
+    LQMPC_MIXED_BF16 = 1,   /* BF16 tensor-core SYRK (FP32 accumulate), FP32 Cholesky,
+                               FP64 iterative refinement, FP64 fallback */
+    LQMPC_MIXED_TF32 = 2,   /* as above with TF32 tensor-core SYRK */
+    LQMPC_FP32 = 3          /* FP32 CUDA-core SYRK, FP32 Cholesky, FP64 refinement */
+};
+
+typedef struct {
+    double tol;          /* stop: max(||r_d||/(1+||h||), ||r_p||/(1+||d||), mu) <= tol; 1e-8 */
+    int max_iter;        /* iteration limit; 100 */
+    int precision;       /* LQMPC_FP64 (default) / LQMPC_MIXED_BF16 / LQMPC_MIXED_TF32 / LQMPC_FP32 */
+    int refine_max;      /* refinement steps per solve in the mixed modes; 6 */
+    double refine_tol;   /* refinement stops at ||b - M du||_inf <= refine_tol ||b||_inf; 1e-10 */
+    int fallback;        /* 1: switch to FP64 for the rest of the solve when refinement stalls */
+    double tau;          /* fraction to the boundary; 0.995 */
+    int verbose;         /* 1: keep the per-iteration trace of the last solve */
+} lqmpc_options;
+
+typedef struct {
+    int iters;           /* interior-point iterations taken */
+    int refine_steps;    /* total refinement steps (mixed modes) */
+    int fallbacks;       /* iterations that fell back to FP64 */
+    int status;          /* lqmpc_status of the solve */
+    double mu;           /* final complementarity s'z/m */
+    double res_primal;   /* final ||r_p||_inf/(1+||d||_inf) */
+    double res_dual;     /* final ||r_d||_inf/(1+||h||_inf) */
+    double t_total_ms;   /* device time of the whole solve (CUDA events) */
+    double t_kkt_ms;     /* device time of the KKT steps (form M, factor, solve) */
+    double t_syrk_tc_ms; /* device time of the tensor-core SYRK launches (CUDA events) */
+    double t_syrk_cc_ms; /* device time of the CUDA-core (FP64/FP32) SYRK launches */
+    int syrk_tc_launches;
+    int syrk_cc_launches;
+} lqmpc_stats;
+
+/* Default options (values in the comments above). */
+lqmpc_options lqmpc_default_options(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* lqmpc_status_str(int status);
+
+/*
+ * Build a solver context for one plant: uploads the data, runs the one-time
+ * state elimination (Section II: the blocks A^k B of Gamma, in FP64 because
+ * powers of A may grow) and forms H = Gamma' Qbar Gamma + Rbar (Eq. 3a).
+ *  ns, nu, N   : states, inputs, horizon (all >= 1).
+ *  a_*         : A (ns x ns) in CSR.
+ *  B           : ns x nu dense column-major.
+ *  q_*, qf_*   : Q and Qf (ns x ns) in CSR, symmetric positive semidefinite;
+ *                qf_* all NULL means Qf = Q.
+ *  R           : nu x nu dense column-major, symmetric positive definite.
+ *  xl, xu      : ns state bounds; ul, uu: nu input bounds (+-INFINITY allowed).
+ *  opts        : NULL for defaults; copied.
+ *  stream      : a cudaStream_t (NULL for the default stream).
+ * Returns LQMPC_ERR_ARG for bad sizes/pointers/NaNs or crossed bounds,
+ * LQMPC_ERR_CUDA if the device is unusable.  *out is NULL on failure.
+ */
+lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N,
+                         const int* a_ptr, const int* a_idx, const double* a_val,
+                         const double* B,
+                         const int* q_ptr, const int* q_idx, const double* q_val,
+                         const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                         const double* R,
+                         const double* xl, const double* xu, const double* ul, const double* uu,
+                         const lqmpc_options* opts, void* stream);
+
+/* Replace the options of a context (takes effect at the next solve). */
+lqmpc_status lqmpc_set_options(lqmpc_ctx* ctx, const lqmpc_options* opts);
+
+/*
+ * Solve the QP for initial state x0 (ns, host) and write the optimal input
+ * sequence to u_out (nu*N, host).  Host-to-device and device-to-host copies
+ * are part of the call.  stats may be NULL.  Returns the solve status
+ * (LQMPC_ERR_INFEASIBLE if the problem has no interior iterate that
+ * converges, LQMPC_ERR_MAXITER, LQMPC_ERR_NAN, LQMPC_ERR_NOT_PD).
+ */
+lqmpc_status lqmpc_solve(lqmpc_ctx* ctx, const double* x0, double* u_out, lqmpc_stats* stats);
+
+/* As lqmpc_solve with x0_device (ns doubles) and u_device (nu*N doubles) in
+ * device memory of the context's GPU; no host copies except 'stats'. */
+lqmpc_status lqmpc_solve_device(lqmpc_ctx* ctx, const double* x0_device, double* u_device,
+                                lqmpc_stats* stats);
+
+/*
+ * Solve `count` independent problems (contexts may differ in ns, nu, N and
+ * options other than precision, which is taken from ctxs[0]) in lockstep:
+ * every kernel launch of an iteration covers all unfinished instances.
+ * x0s[i] / u_outs[i] are host pointers for instance i; stats may be NULL or
+ * an array of `count`.  All contexts must share the stream of ctxs[0].
+ * Returns LQMPC_OK if every instance converged, otherwise the first failing
+ * instance's status.
+ */
+lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                               double* const* u_outs, lqmpc_stats* stats);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts); differences around a region count its launches. */
+unsigned long long lqmpc_kernel_launches(void);
+
+/* Release a context and all device memory it owns.  NULL is a no-op. */
+void lqmpc_free(lqmpc_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Stage-level entry points: each runs one step of the hot path on the GPU on
+ * host-provided data and copies the result back (host buffers).  They exist
+ * for inspection and parity testing of the individual steps.
+ * ------------------------------------------------------------------------ */
+
+/* The blocks G_k = A^k B (k = 0..N-1) built at setup (Section II).  G is
+ * N*ns*nu doubles: G_k[i, c] at G[(k*nu + c)*ns + i]. */
+lqmpc_status lqmpc_get_gstack(lqmpc_ctx* ctx, double* G);
+
+/* H = Gamma' Qbar Gamma + Rbar (n x n, column-major, FP64) built at setup. */
+lqmpc_status lqmpc_get_hessian(lqmpc_ctx* ctx, double* H);
+
+/* out = Gamma v (v: n, out: ns*N) and out = Gamma' w (w: ns*N, out: n), FP64,
+ * using only the G-stack (the implicit Jacobian of the paper's conclusions). */
+lqmpc_status lqmpc_gamma_mv(lqmpc_ctx* ctx, const double* v, double* out);
+lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out);
+
+/* Form M = H + Gamma' diag(sigx) Gamma + diag(sigu) (Eq. 7) in the given
+ * precision (LQMPC_FP64, LQMPC_MIXED_BF16, LQMPC_MIXED_TF32, LQMPC_FP32) and
+ * return it as n x n doubles (full symmetric).  sigx: ns*N, sigu: n, >= 0. */
+lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* sigu,
+                            int precision, double* M);
+
+/* Form M as above, Cholesky-factor it and solve M x = b (mixed precisions
+ * with FP64 iterative refinement).  L (nullable) receives the lower factor
+ * as n x n doubles (upper triangle zero).  refine_steps (nullable) receives
+ * the refinement steps taken.  Returns LQMPC_ERR_NOT_PD if a pivot is not
+ * positive, LQMPC_ERR_STALL if refinement did not reach refine_tol. */
+lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* sigu,
+                             int precision, const double* b, double* x, double* L,
+                             int* refine_steps);
+
+/* Per-iteration trace of the last solve (requires opts.verbose = 1): rows of
+ * 6 doubles (mu, res_dual, res_primal, alpha_aff, sigma, alpha); writes at
+ * most max_rows rows and returns the row count in *rows. */
+lqmpc_status lqmpc_get_trace(lqmpc_ctx* ctx, double* trace, int max_rows, int* rows);
+
+/* Final duals of the last solve: [z_xu (ns*N), z_xl (ns*N), z_uu (n), z_ul (n)]. */
+lqmpc_status lqmpc_get_duals(lqmpc_ctx* ctx, double* z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQMPC_H */

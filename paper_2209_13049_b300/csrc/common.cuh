@@ -1,0 +1,164 @@
+// Shared device-side definitions of the lqmpc CUDA path.
+//
+// Every kernel processes a batch of independent problem instances: blockIdx.y
+// selects the instance, blockIdx.x the work item inside it, so a single solve
+// is a batch of one and a batched solve uses the same launches (one launch
+// per phase covers every instance; finished instances skip their work).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lqmpc {
+
+// Every kernel launch of the library goes through LQ_LAUNCH so the process-wide
+// launch count (lqmpc_kernel_launches) is exact.
+void note_launches(int k);
+#define LQ_LAUNCH(...)          \
+    do {                        \
+        __VA_ARGS__;            \
+        ::lqmpc::note_launches(1); \
+    } while (0)
+
+constexpr int kMaxParts = 1024;     // max blocks of a reduction launch per instance
+constexpr int kParts = 8;           // reduction slots per instance
+constexpr int kTraceW = 6;          // mu, res_d, res_p, alpha_aff, sigma, alpha
+
+// Per-instance scalars living in device memory.
+struct Scal {
+    double mu, mu_aff, sigma, alpha, alpha_aff;
+    double hnorm, dnorm, res_d, res_p, res;
+    double tol, tau, refine_tol;
+    double rnorm0, rnorm, rnorm_prev;   // refinement: ||b||, current and previous ||rho||
+    int m;              // number of finite one-sided constraints
+    int done;           // 1 once the stop test passed or the solve failed
+    int status;         // lqmpc_status of the solve
+    int iter;           // iterations taken
+    int max_iter;
+    int info;           // Cholesky: first non-positive pivot + 1 (0 = ok)
+    int refine_ok;      // refinement converged for the current right-hand side
+    int refine_steps;   // refinement steps in total
+    int refine_cur;     // refinement steps for the current right-hand side
+    int stalled;        // refinement stalled (current right-hand side)
+    int fallbacks;      // iterations that fell back to FP64
+    int use_fp64;       // sticky: remaining iterations in FP64
+    int err;            // device-side error flags (bounded wait timeouts etc.)
+    int pad;
+};
+
+// Device descriptor of one instance (all pointers are device memory).
+struct Inst {
+    int ns, nu, N, n, SX, ldg;
+    int q_diag;                       // Q and Qf diagonal
+    int pad0;
+    // plant
+    const int* a_ptr; const int* a_idx; const double* a_val;
+    const int* q_ptr; const int* q_idx; const double* q_val;
+    const int* qf_ptr; const int* qf_idx; const double* qf_val;
+    const double* B;                  // ns x nu
+    const double* R;                  // nu x nu
+    const double *xl, *xu, *ul, *uu;
+    const double* qd;                 // diag(Q) (ns), when q_diag
+    const double* qfd;                // diag(Qf) (ns), when q_diag
+    // state elimination (G-stack in reversed block order, column-major, ld = ldg):
+    // column (N-1-k)*nu + c holds (A^k B)[:, c]
+    double* G64;
+    float* G32;
+    __nv_bfloat16* G16;
+    double* H64;                      // n x n
+    float* H32;                       // n x n
+    // per solve
+    double *xbar, *y, *h;
+    double *u, *x;                    // n, SX (x_1..x_N)
+    double *s1, *z1, *s2, *z2;        // SX: upper / lower state bound slacks and duals
+    double *s3, *z3, *s4, *z4;        // n:  upper / lower input bound slacks and duals
+    double *sigx, *sigu;              // SX, n
+    float* sigx32;                    // SX
+    double *wz, *wx;                  // SX: vectors for Gamma' products
+    double *wzu, *wxu;                // n
+    double *gz, *gw;                  // n: Gamma' outputs
+    double *rd, *b, *du, *dx, *du_aff, *dx_aff;
+    double *ds1, *dz1, *ds2, *dz2;    // SX
+    double *ds3, *dz3, *ds4, *dz4;    // n
+    double* M64; float* M32;          // n x n
+    double *rho, *dcorr;              // refinement: residual, correction (n)
+    double* mv;                       // n: Gamma' output of matrix-free products
+    double* tmpx;                     // SX scratch
+    double* gpart;                    // Gamma' stage-1 partial sums
+    float* r32;                       // n FP32 right-hand side
+    void* syrk_ws;                    // split-K partial tiles
+    size_t syrk_ws_bytes;
+    double* part;                     // kParts x kMaxParts reduction partials
+    Scal* sc;
+    double* trace;                    // (max_iter+1) x kTraceW
+};
+
+// Vectors addressed by role, so one launch can name "the same vector" of
+// every instance of a batch.
+enum Role : int {
+    R_U = 0, R_X, R_Y, R_H, R_TMPX, R_WZ, R_WX, R_GZ, R_GW, R_DU, R_DX, R_DU_AFF, R_DX_AFF,
+    R_RHO, R_DCORR, R_B, R_RD, R_MV, R_NONE
+};
+
+__device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
+    switch (r) {
+        case R_U: return I.u;        case R_X: return I.x;        case R_Y: return I.y;
+        case R_H: return I.h;        case R_TMPX: return I.tmpx;  case R_WZ: return I.wz;
+        case R_WX: return I.wx;      case R_GZ: return I.gz;      case R_GW: return I.gw;
+        case R_DU: return I.du;      case R_DX: return I.dx;      case R_DU_AFF: return I.du_aff;
+        case R_DX_AFF: return I.dx_aff; case R_RHO: return I.rho; case R_DCORR: return I.dcorr;
+        case R_B: return I.b;        case R_RD: return I.rd;      case R_MV: return I.mv;
+        default: return nullptr;
+    }
+}
+
+// Launch predicates: F_FORCE runs even after the instance finished (setup and
+// stage-level calls); F_SKIP_REFINED skips instances whose refinement converged.
+enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2 };
+
+__device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
+    if (!(flags & F_FORCE) && I.sc->done) return true;
+    if ((flags & F_SKIP_REFINED) && I.sc->refine_ok) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide reduction (blockDim.x multiple of 32, <= 1024); result valid in thread 0.
+template <int OP>   // 0 sum, 1 max, 2 min
+__device__ __forceinline__ double block_reduce(double v, double* smem32) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = OP == 0 ? warp_sum(v) : OP == 1 ? warp_max(v) : warp_min(v);
+    __syncthreads();
+    if (lane == 0) smem32[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (w == 0) {
+        double t = lane < nw ? smem32[lane]
+                             : (OP == 0 ? 0.0 : OP == 1 ? -INFINITY : INFINITY);
+        t = OP == 0 ? warp_sum(t) : OP == 1 ? warp_max(t) : warp_min(t);
+        v = t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+}  // namespace lqmpc

@@ -1,0 +1,282 @@
+// State elimination and products with the condensed Jacobian (Section II).
+//
+// Gamma (ns*N x nu*N) has block (r, t) = A^{r-t} B for t <= r (state x_{r+1},
+// input u_t) and zero above.  The paper's conclusions note that all of its
+// data sits in its first nu columns; the build stores only the G-stack
+//   G[:, (N-1-k)*nu + c] = (A^k B)[:, c],   column-major, leading dim ldg,
+// i.e. in reversed block order, so that row block r of Gamma is the
+// contiguous column window G[:, (N-1-r)*nu : (N-1-r)*nu + n] with every column
+// index >= n reading as zero.  The tensor-core SYRK exploits the same window
+// through TMA coordinates.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lqmpc {
+
+// G_0 = B into its column block (N-1)*nu.
+__global__ void k_gstack_init(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    const int total = I.ns * I.nu;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int i = q % I.ns, c = q / I.ns;
+        I.G64[(size_t)I.ldg * ((I.N - 1) * I.nu + c) + i] = I.B[(size_t)c * I.ns + i];
+    }
+}
+
+// G_k = A G_{k-1} (CSR A).  One thread per (row i, input c).
+__global__ void k_gstack_step(const Inst* __restrict__ insts, int k) {
+    const Inst& I = insts[blockIdx.y];
+    if (k >= I.N) return;
+    const int total = I.ns * I.nu;
+    const double* src = I.G64 + (size_t)I.ldg * ((I.N - k) * I.nu);
+    double* dst = I.G64 + (size_t)I.ldg * ((I.N - 1 - k) * I.nu);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        int i = q % I.ns, c = q / I.ns;
+        const double* sc = src + (size_t)I.ldg * c;
+        double acc = 0.0;
+        for (int p = I.a_ptr[i]; p < I.a_ptr[i + 1]; ++p) acc += I.a_val[p] * sc[I.a_idx[p]];
+        dst[(size_t)I.ldg * c + i] = acc;
+    }
+}
+
+// Working copies of the G-stack in FP32 and BF16 (padding rows stay zero).
+__global__ void k_gstack_cast(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    const size_t total = (size_t)I.ldg * I.n;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        double g = I.G64[q];
+        if (I.G32) I.G32[q] = (float)g;
+        if (I.G16) I.G16[q] = __double2bfloat16(g);
+    }
+}
+
+// out[r*ns + i] = sum_{t < (r+1) nu} G[i, (N-1-r) nu + t] v[t]   (out = Gamma v).
+// Each thread owns one state i and RB consecutive row blocks; a G element
+// loaded once serves every row block of the group (each is the same column
+// window shifted by nu).
+template <int RB>
+__global__ void k_gamma_mv(const Inst* __restrict__ insts, int in_role, int out_role, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const double* v = role_ptr(I, in_role);
+    double* out = role_ptr(I, out_role);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r0 = blockIdx.z * RB;
+    if (i >= I.ns || r0 >= I.N) return;
+    const int nu = I.nu, N = I.N, n = I.n;
+    const int rlast = min(r0 + RB, N) - 1;
+    double acc[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) acc[q] = 0.0;
+    const int col0 = (N - 1 - rlast) * nu;       // smallest window start in the group
+    const double* g = I.G64 + i;
+    for (int col = col0; col < n; ++col) {
+        double gv = g[(size_t)I.ldg * col];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            int r = r0 + q;
+            int off = (N - 1 - r) * nu;
+            int t = col - off;
+            if (r <= rlast && t >= 0) acc[q] += gv * __ldg(v + t);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+        if (r0 + q <= rlast) out[(size_t)(r0 + q) * I.ns + i] = acc[q];
+}
+
+// Gamma' w, two-level.  Stage 1: block (t, chunk) computes for input block t
+// and a chunk of states the partial sums
+//     P[chunk][t*nu + c] = sum_{r >= t} sum_{i in chunk} G[i, (N-1-r+t) nu + c] w_r[i]
+// for NV vectors at once.  Stage 2 adds the chunks in order (deterministic).
+constexpr int kTmvChunk = 256;
+constexpr int kTmvMaxNu = 32;
+
+template <int NV>
+__global__ void k_gamma_tmv_part(const Inst* __restrict__ insts, int w0_role, int w1_role,
+                                 int scale0, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int t = blockIdx.x;
+    const int chunk = blockIdx.z;
+    const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
+    if (t >= I.N || chunk >= nchunks) return;
+    const int nu = I.nu, N = I.N;
+    const double* w0 = role_ptr(I, w0_role);
+    const double* w1 = NV > 1 ? role_ptr(I, w1_role) : nullptr;
+    double* part = I.gpart;
+    __shared__ double red[NV][kTmvMaxNu][33];
+    const int i = chunk * kTmvChunk + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < nu; c0 += kTmvMaxNu) {
+        const int cn = min(kTmvMaxNu, nu - c0);
+        double acc[NV][kTmvMaxNu];
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int c = 0; c < kTmvMaxNu; ++c) acc[a][c] = 0.0;
+        if (i < I.ns) {
+            for (int r = t; r < N; ++r) {
+                double wa = w0[(size_t)r * I.ns + i];
+                if (scale0) wa *= I.sigx[(size_t)r * I.ns + i];
+                double wb = NV > 1 ? w1[(size_t)r * I.ns + i] : 0.0;
+                const double* g = I.G64 + (size_t)I.ldg * ((N - 1 - r + t) * nu + c0) + i;
+#pragma unroll
+                for (int c = 0; c < kTmvMaxNu; ++c) {
+                    if (c < cn) {
+                        double gv = g[(size_t)I.ldg * c];
+                        acc[0][c] += gv * wa;
+                        if (NV > 1) acc[NV - 1][c] += gv * wb;
+                    }
+                }
+            }
+        }
+        // block reduction of each (vector, c)
+#pragma unroll
+        for (int a = 0; a < NV; ++a)
+#pragma unroll
+            for (int c = 0; c < kTmvMaxNu; ++c) {
+                double v = warp_sum(acc[a][c]);
+                if (lane == 0) red[a][c][warp] = v;
+            }
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        for (int q = threadIdx.x; q < NV * cn; q += blockDim.x) {
+            int a = q / cn, c = q % cn;
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += red[a][c][w];
+            part[((size_t)a * nchunks + chunk) * I.n + t * nu + c0 + c] = s;
+        }
+        __syncthreads();
+    }
+}
+
+template <int NV>
+__global__ void k_gamma_tmv_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
+    const double* part = I.gpart;
+    double* o0 = role_ptr(I, o0_role);
+    double* o1 = NV > 1 ? role_ptr(I, o1_role) : nullptr;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+            double s = 0.0;
+            for (int q = 0; q < nchunks; ++q) s += part[((size_t)a * nchunks + q) * I.n + j];
+            (a == 0 ? o0 : o1)[j] = s;
+        }
+    }
+}
+
+// y_t = A^t xbar for t = 1..N (one block per instance, sequential in t).
+__global__ void k_ychain(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    const double* prev = I.xbar;
+    for (int t = 0; t < I.N; ++t) {
+        double* cur = I.y + (size_t)t * I.ns;
+        for (int i = threadIdx.x; i < I.ns; i += blockDim.x) {
+            double acc = 0.0;
+            for (int p = I.a_ptr[i]; p < I.a_ptr[i + 1]; ++p) acc += I.a_val[p] * prev[I.a_idx[p]];
+            cur[i] = acc;
+        }
+        __syncthreads();
+        prev = cur;
+    }
+}
+
+// w = Qbar y (Q on blocks 0..N-2, Qf on block N-1), CSR, into tmpx.
+__global__ void k_qbar_y(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
+        int r = k / I.ns, i = k % I.ns;
+        bool last = r == I.N - 1;
+        const int* ptr = last ? I.qf_ptr : I.q_ptr;
+        const int* idx = last ? I.qf_idx : I.q_idx;
+        const double* val = last ? I.qf_val : I.q_val;
+        const double* yr = I.y + (size_t)r * I.ns;
+        double acc = 0.0;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) acc += val[p] * yr[idx[p]];
+        I.tmpx[k] = acc;
+    }
+}
+
+// Dense-Q operand for H: GQ = Q * G (columns of the G-stack), or Qf * G.
+__global__ void k_q_times_g(const Inst* __restrict__ insts, int use_qf, double* out) {
+    const Inst& I = insts[blockIdx.y];
+    const int* ptr = use_qf ? I.qf_ptr : I.q_ptr;
+    const int* idx = use_qf ? I.qf_idx : I.q_idx;
+    const double* val = use_qf ? I.qf_val : I.q_val;
+    const size_t total = (size_t)I.ns * I.n;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (size_t)gridDim.x * blockDim.x) {
+        int i = (int)(q % I.ns);
+        size_t col = q / I.ns;
+        const double* g = I.G64 + (size_t)I.ldg * col;
+        double acc = 0.0;
+        for (int p = ptr[i]; p < ptr[i + 1]; ++p) acc += val[p] * g[idx[p]];
+        out[(size_t)I.ldg * col + i] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st) {
+    int tot = h.ns * h.nu;
+    int nb = (tot + 255) / 256;
+    nb = nb > 4096 ? 4096 : nb;
+    LQ_LAUNCH(k_gstack_init<<<dim3(nb, 1), 256, 0, st>>>(d_inst));
+    LQ_LAUNCH(for (int k = 1; k < h.N; ++k) k_gstack_step<<<dim3(nb, 1), 256, 0, st>>>(d_inst, k));
+    size_t tot2 = (size_t)h.ldg * h.n;
+    int nb2 = (int)((tot2 + 255) / 256);
+    nb2 = nb2 > 8192 ? 8192 : nb2;
+    LQ_LAUNCH(k_gstack_cast<<<dim3(nb2, 1), 256, 0, st>>>(d_inst));
+}
+
+void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int in_role,
+                     int out_role, int flags, cudaStream_t st) {
+    constexpr int RB = 8;
+    dim3 grid((max_ns + 127) / 128, count, (max_N + RB - 1) / RB);
+    LQ_LAUNCH(k_gamma_mv<RB><<<grid, 128, 0, st>>>(d_insts, in_role, out_role, flags));
+}
+
+size_t gamma_tmv_part_doubles(int ns, int n) {
+    return (size_t)2 * ((ns + kTmvChunk - 1) / kTmvChunk) * n;
+}
+
+void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
+                      int w0_role, int w1_role, int o0_role, int o1_role, int scale0, int flags,
+                      cudaStream_t st) {
+    int nchunks = (max_ns + kTmvChunk - 1) / kTmvChunk;
+    dim3 grid(max_N, count, nchunks);
+    int nbs = (max_n + 255) / 256;
+    if (w1_role != R_NONE) {
+        LQ_LAUNCH(k_gamma_tmv_part<2><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
+        LQ_LAUNCH(k_gamma_tmv_sum<2><<<dim3(nbs, count), 256, 0, st>>>(d_insts, o0_role, o1_role, flags));
+    } else {
+        LQ_LAUNCH(k_gamma_tmv_part<1><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags));
+        LQ_LAUNCH(k_gamma_tmv_sum<1><<<dim3(nbs, count), 256, 0, st>>>(d_insts, o0_role, R_NONE, flags));
+    }
+}
+
+void launch_ychain(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_ychain<<<dim3(1, count), 1024, 0, st>>>(d_insts));
+}
+
+void launch_qbar_y(const Inst* d_insts, int count, int max_sx, cudaStream_t st) {
+    int nb = (max_sx + 255) / 256;
+    nb = nb > 4096 ? 4096 : nb;
+    LQ_LAUNCH(k_qbar_y<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+}
+
+void launch_q_times_g(const Inst* d_inst, const Inst& h, int use_qf, double* out, cudaStream_t st) {
+    size_t tot = (size_t)h.ns * h.n;
+    int nb = (int)((tot + 255) / 256);
+    nb = nb > 8192 ? 8192 : nb;
+    LQ_LAUNCH(k_q_times_g<<<dim3(nb, 1), 256, 0, st>>>(d_inst, use_qf, out));
+}
+
+}  // namespace lqmpc

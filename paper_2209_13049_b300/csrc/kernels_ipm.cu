@@ -1,0 +1,453 @@
+// Interior-point vector kernels: initial point, residuals and Sigma, Mehrotra
+// predictor/corrector right-hand sides, fraction-to-boundary step lengths and
+// the iterate update (Section III, Eqs. 5-7 and Algorithm 1).
+//
+// Notation.  The dense QP (Eq. 3) has variables u (n = nu*N) and the
+// constraint J u <= d with J = [Gamma; -Gamma; I; -I]: four families of
+// one-sided rows, each with a slack s and a dual z:
+//   family 1 (state upper):  x + s1 = xu     family 2 (state lower): -x + s2 = -xl
+//   family 3 (input upper):  u + s3 = uu     family 4 (input lower): -u + s4 = -ul
+// where x = Phi xbar + Gamma u is kept as an iterate.  A two-sided row is one
+// row of Gamma with two slacks.  Rows whose bound is infinite are absent:
+// their s = 1, z = 0 never change and they are left out of every sum.
+//
+// Reductions are deterministic: every block writes one partial per slot and a
+// one-block finaliser combines them in block order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace lqmpc {
+
+// ---------------------------------------------------------------------------
+// Per-row helpers
+// ---------------------------------------------------------------------------
+
+struct RowView {
+    double* s_u; double* z_u; double* s_l; double* z_l;   // upper / lower slack, dual
+    double* ds_u; double* dz_u; double* ds_l; double* dz_l;
+    double lo, hi;        // bounds of this row
+    double v;             // current value (x_k or u_j)
+    bool fu, fl;          // bounds finite
+};
+
+__device__ __forceinline__ RowView row_view(const Inst& I, int k) {
+    RowView r;
+    if (k < I.SX) {
+        int i = k % I.ns;
+        r.s_u = I.s1 + k; r.z_u = I.z1 + k; r.s_l = I.s2 + k; r.z_l = I.z2 + k;
+        r.ds_u = I.ds1 + k; r.dz_u = I.dz1 + k; r.ds_l = I.ds2 + k; r.dz_l = I.dz2 + k;
+        r.lo = I.xl[i]; r.hi = I.xu[i]; r.v = I.x[k];
+    } else {
+        int j = k - I.SX, c = j % I.nu;
+        r.s_u = I.s3 + j; r.z_u = I.z3 + j; r.s_l = I.s4 + j; r.z_l = I.z4 + j;
+        r.ds_u = I.ds3 + j; r.dz_u = I.dz3 + j; r.ds_l = I.ds4 + j; r.dz_l = I.dz4 + j;
+        r.lo = I.ul[c]; r.hi = I.uu[c]; r.v = I.u[j];
+    }
+    r.fu = isfinite(r.hi); r.fl = isfinite(r.lo);
+    return r;
+}
+
+// Write one partial per slot for this block.
+__device__ __forceinline__ void put_part(const Inst& I, int slot, double v) {
+    if (threadIdx.x == 0) I.part[slot * kMaxParts + blockIdx.x] = v;
+}
+
+// ---------------------------------------------------------------------------
+// Initial point.  u0 = box midpoint (lo+1 / hi-1 for one-sided boxes, 0 for
+// none); x0 = y + Gamma u0 (Gamma u0 precomputed into tmpx); s0 = max(slack, 1)
+// and z0 = 1 for present rows.  Also the norms ||d|| and ||h|| of the stop
+// test and the row count m.
+// ---------------------------------------------------------------------------
+
+__global__ void k_set_u0(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x) {
+        int c = j % I.nu;
+        double lo = I.ul[c], hi = I.uu[c];
+        bool fl = isfinite(lo), fh = isfinite(hi);
+        I.u[j] = (fl && fh) ? 0.5 * (lo + hi) : fl ? lo + 1.0 : fh ? hi - 1.0 : 0.0;
+    }
+}
+
+__global__ void k_init_slacks(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    const int total = I.SX + I.n;
+    double cnt = 0.0, dmax = 0.0, hmax = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        if (k < I.SX) {
+            int i = k % I.ns;
+            double xk = I.y[k] + I.tmpx[k];
+            I.x[k] = xk;
+            double hi = I.xu[i], lo = I.xl[i];
+            bool fu = isfinite(hi), fl = isfinite(lo);
+            I.s1[k] = fu ? fmax(hi - xk, 1.0) : 1.0; I.z1[k] = fu ? 1.0 : 0.0;
+            I.s2[k] = fl ? fmax(xk - lo, 1.0) : 1.0; I.z2[k] = fl ? 1.0 : 0.0;
+            cnt += (double)fu + (double)fl;
+            double yk = I.y[k];
+            if (fu) dmax = fmax(dmax, fabs(hi - yk));
+            if (fl) dmax = fmax(dmax, fabs(yk - lo));
+        } else {
+            int j = k - I.SX, c = j % I.nu;
+            double uj = I.u[j], hi = I.uu[c], lo = I.ul[c];
+            bool fu = isfinite(hi), fl = isfinite(lo);
+            I.s3[j] = fu ? fmax(hi - uj, 1.0) : 1.0; I.z3[j] = fu ? 1.0 : 0.0;
+            I.s4[j] = fl ? fmax(uj - lo, 1.0) : 1.0; I.z4[j] = fl ? 1.0 : 0.0;
+            cnt += (double)fu + (double)fl;
+            if (fu) dmax = fmax(dmax, fabs(hi));
+            if (fl) dmax = fmax(dmax, fabs(lo));
+            hmax = fmax(hmax, fabs(I.h[j]));
+        }
+    }
+    double v = block_reduce<0>(cnt, red); put_part(I, 0, v);
+    v = block_reduce<1>(dmax, red); put_part(I, 1, v);
+    v = block_reduce<1>(hmax, red); put_part(I, 2, v);
+}
+
+__global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double tol, double tau,
+                           int max_iter, double refine_tol) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    double c = 0, d = 0, h = 0;
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+        c += I.part[0 * kMaxParts + p];
+        d = fmax(d, I.part[1 * kMaxParts + p]);
+        h = fmax(h, I.part[2 * kMaxParts + p]);
+    }
+    c = block_reduce<0>(c, red);
+    d = block_reduce<1>(d, red);
+    h = block_reduce<1>(h, red);
+    if (threadIdx.x == 0) {
+        Scal* S = I.sc;
+        S->m = (int)(c + 0.5);
+        S->dnorm = d; S->hnorm = h;
+        S->tol = tol; S->tau = tau; S->max_iter = max_iter; S->refine_tol = refine_tol;
+        S->done = 0; S->status = 0; S->iter = 0; S->info = 0;
+        S->refine_steps = 0; S->fallbacks = 0; S->use_fp64 = 0; S->err = 0;
+        S->mu = S->sigma = S->alpha = S->alpha_aff = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residuals (Eq. 5), Sigma = S^{-1} Z (Eq. 6) and the predictor vectors.
+//   r_p per family; Sigma_x = z1/s1 + z2/s2 per state row, Sigma_u likewise;
+//   wz = z1 - z2 (for the Gamma' z term of r_d);
+//   predictor w_i = z_i - Sigma_i r_p,i, combined wx = w1 - w2 (for Gamma').
+// Partials: slot 0 max|r_p|, slot 1 sum s.z.
+// ---------------------------------------------------------------------------
+
+__global__ void k_resid(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const int total = I.SX + I.n;
+    double rpmax = 0.0, sz = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        RowView r = row_view(I, k);
+        double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
+        double rpu = r.fu ? r.v + su - r.hi : 0.0;
+        double rpl = r.fl ? -r.v + sl + r.lo : 0.0;
+        double sgu = zu / su, sgl = zl / sl;
+        rpmax = fmax(rpmax, fmax(fabs(rpu), fabs(rpl)));
+        if (r.fu) sz += su * zu;
+        if (r.fl) sz += sl * zl;
+        double wz = zu - zl;
+        double wx = (zu - sgu * rpu) - (zl - sgl * rpl);
+        if (k < I.SX) {
+            I.sigx[k] = sgu + sgl; I.sigx32[k] = (float)(sgu + sgl);
+            I.wz[k] = wz; I.wx[k] = wx;
+        } else {
+            int j = k - I.SX;
+            I.sigu[j] = sgu + sgl; I.wzu[j] = wz; I.wxu[j] = wx;
+        }
+    }
+    double v = block_reduce<1>(rpmax, red); put_part(I, 0, v);
+    v = block_reduce<0>(sz, red); put_part(I, 1, v);
+}
+
+// r_d = H u + h + Gamma'(z1 - z2) + z3 - z4 (Eq. 5a with lambda = z) and the
+// predictor right-hand side b = -r_d + J' w (Eq. 7, read with J' r2, see
+// the design notes).  One warp per input row; H column j = row j (symmetric).
+// Partial: slot 2 max|r_d|.
+__global__ void k_rd(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    double rdmax = 0.0;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < I.n; j += gridDim.x * wpb) {
+        const double* hc = I.H64 + (size_t)j * I.n;
+        double acc = 0.0;
+        for (int k = lane; k < I.n; k += 32) acc += hc[k] * I.u[k];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+            double rd = acc + I.h[j] + I.gz[j] + I.wzu[j];
+            I.rd[j] = rd;
+            I.b[j] = -rd + I.gw[j] + I.wxu[j];
+            rdmax = fmax(rdmax, fabs(rd));
+        }
+    }
+    double v = block_reduce<1>(rdmax, red); put_part(I, 2, v);
+}
+
+// Stop test and trace.  nb1: partial count of k_resid, nb2: of k_rd.
+__global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int trace_on) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    Scal* S = I.sc;
+    if (S->done) return;
+    double rp = 0, sz = 0, rd = 0;
+    for (int p = threadIdx.x; p < nb1; p += blockDim.x) {
+        rp = fmax(rp, I.part[0 * kMaxParts + p]);
+        sz += I.part[1 * kMaxParts + p];
+    }
+    for (int p = threadIdx.x; p < nb2; p += blockDim.x) rd = fmax(rd, I.part[2 * kMaxParts + p]);
+    rp = block_reduce<1>(rp, red);
+    sz = block_reduce<0>(sz, red);
+    rd = block_reduce<1>(rd, red);
+    if (threadIdx.x == 0) {
+        double mu = S->m > 0 ? sz / S->m : 0.0;
+        double res_d = rd / (1.0 + S->hnorm);
+        double res_p = rp / (1.0 + S->dnorm);
+        double res = fmax(fmax(res_d, res_p), mu);
+        S->mu = mu; S->res_d = res_d; S->res_p = res_p; S->res = res;
+        if (trace_on && S->iter <= S->max_iter) {
+            double* t = I.trace + (size_t)S->iter * kTraceW;
+            t[0] = mu; t[1] = res_d; t[2] = res_p; t[3] = 0; t[4] = 0; t[5] = 0;
+        }
+        if (!(res == res)) { S->done = 1; S->status = 6; }
+        else if (res <= S->tol) { S->done = 1; S->status = 0; }
+        else if (S->iter >= S->max_iter) { S->done = 1; S->status = 4; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Affine (predictor) step: ds = -r_p - J du, dz = -z - Sigma ds per family.
+// Stored in ds*/dz*.  Partials: slot 3 largest step to the boundary,
+// slot 4 sum(s dz + z ds), slot 5 sum(ds dz) -- so that
+// mu_aff = (sum s z + a S4 + a^2 S5)/m in closed form.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void ratio(double v, double dv, double& amax) {
+    if (dv < 0.0) amax = fmin(amax, -v / dv);
+}
+
+__global__ void k_aff(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const int total = I.SX + I.n;
+    double amax = INFINITY, s4 = 0.0, s5 = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        RowView r = row_view(I, k);
+        double d = k < I.SX ? I.dx_aff[k] : I.du_aff[k - I.SX];
+        double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
+        double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
+        if (r.fu) {
+            double rp = r.v + su - r.hi;
+            dsu = -rp - d; dzu = -zu - (zu / su) * dsu;
+            ratio(su, dsu, amax); ratio(zu, dzu, amax);
+            s4 += su * dzu + zu * dsu; s5 += dsu * dzu;
+        }
+        if (r.fl) {
+            double rp = -r.v + sl + r.lo;
+            dsl = -rp + d; dzl = -zl - (zl / sl) * dsl;
+            ratio(sl, dsl, amax); ratio(zl, dzl, amax);
+            s4 += sl * dzl + zl * dsl; s5 += dsl * dzl;
+        }
+        *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
+    }
+    double v = block_reduce<2>(amax, red); put_part(I, 3, v);
+    v = block_reduce<0>(s4, red); put_part(I, 4, v);
+    v = block_reduce<0>(s5, red); put_part(I, 5, v);
+}
+
+// alpha_aff = min(1, max step); mu_aff; sigma = (mu_aff/mu)^3 (Mehrotra).
+__global__ void k_aff_fin(const Inst* __restrict__ insts, int nb) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    Scal* S = I.sc;
+    if (S->done) return;
+    double a = INFINITY, sz = 0, s4 = 0, s5 = 0;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
+        a = fmin(a, I.part[3 * kMaxParts + p]);
+        sz += I.part[1 * kMaxParts + p];
+        s4 += I.part[4 * kMaxParts + p];
+        s5 += I.part[5 * kMaxParts + p];
+    }
+    a = block_reduce<2>(a, red);
+    sz = block_reduce<0>(sz, red);
+    s4 = block_reduce<0>(s4, red);
+    s5 = block_reduce<0>(s5, red);
+    if (threadIdx.x == 0) {
+        double al = fmin(1.0, a);
+        double mu_aff = S->m > 0 ? (sz + al * s4 + al * al * s5) / S->m : 0.0;
+        double ratio_ = S->mu > 0.0 ? mu_aff / S->mu : 0.0;
+        S->alpha_aff = al; S->mu_aff = mu_aff;
+        S->sigma = ratio_ * ratio_ * ratio_;
+    }
+}
+
+// Corrector: r_c = s.z + ds_aff.dz_aff - sigma mu; w = (r_c - z r_p)/s per
+// family; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).
+__global__ void k_corr(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const double smu = I.sc->sigma * I.sc->mu;
+    const int total = I.SX + I.n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        RowView r = row_view(I, k);
+        double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
+        double wu = 0, wl = 0;
+        if (r.fu) {
+            double rp = r.v + su - r.hi;
+            double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
+            wu = (rc - zu * rp) / su;
+        }
+        if (r.fl) {
+            double rp = -r.v + sl + r.lo;
+            double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
+            wl = (rc - zl * rp) / sl;
+        }
+        if (k < I.SX) I.wx[k] = wu - wl;
+        else I.wxu[k - I.SX] = wu - wl;
+    }
+}
+
+// b = -r_d + Gamma' wx + wxu
+__global__ void k_rhs(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x)
+        I.b[j] = -I.rd[j] + I.gw[j] + I.wxu[j];
+}
+
+// Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with r_c from the
+// stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.
+__global__ void k_step(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const double smu = I.sc->sigma * I.sc->mu;
+    const int total = I.SX + I.n;
+    double amax = INFINITY;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        RowView r = row_view(I, k);
+        double d = k < I.SX ? I.dx[k] : I.du[k - I.SX];
+        double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
+        double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
+        if (r.fu) {
+            double rp = r.v + su - r.hi;
+            double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
+            dsu = -rp - d; dzu = -(rc + zu * dsu) / su;
+            ratio(su, dsu, amax); ratio(zu, dzu, amax);
+        }
+        if (r.fl) {
+            double rp = -r.v + sl + r.lo;
+            double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
+            dsl = -rp + d; dzl = -(rc + zl * dsl) / sl;
+            ratio(sl, dsl, amax); ratio(zl, dzl, amax);
+        }
+        *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
+    }
+    double v = block_reduce<2>(amax, red); put_part(I, 3, v);
+}
+
+// alpha = min(1, tau * max step); trace; iteration count.
+__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    Scal* S = I.sc;
+    if (S->done) return;
+    double a = INFINITY;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) a = fmin(a, I.part[3 * kMaxParts + p]);
+    a = block_reduce<2>(a, red);
+    if (threadIdx.x == 0) {
+        double al = fmin(1.0, S->tau * a);
+        S->alpha = al;
+        if (trace_on && S->iter <= S->max_iter) {
+            double* t = I.trace + (size_t)S->iter * kTraceW;
+            t[3] = S->alpha_aff; t[4] = S->sigma; t[5] = al;
+        }
+    }
+}
+
+// One step length for every variable (u, x, s, z).
+__global__ void k_update(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    const Scal* S = I.sc;
+    if (S->done) return;
+    const double al = S->alpha;
+    const int total = I.SX + I.n;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        RowView r = row_view(I, k);
+        if (k < I.SX) I.x[k] += al * I.dx[k];
+        else I.u[k - I.SX] += al * I.du[k - I.SX];
+        *r.s_u += al * (*r.ds_u); *r.z_u += al * (*r.dz_u);
+        *r.s_l += al * (*r.ds_l); *r.z_l += al * (*r.dz_l);
+    }
+}
+
+__global__ void k_iter_inc(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    if (threadIdx.x == 0 && !I.sc->done) I.sc->iter += 1;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+static int ew_blocks(int total_max, int threads) {
+    int b = (total_max + threads - 1) / threads;
+    return b < 1 ? 1 : (b > kMaxParts ? kMaxParts : b);
+}
+
+void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
+                       double tau, int max_iter, double refine_tol, cudaStream_t st) {
+    int nb = ew_blocks(max_total, 256);
+    LQ_LAUNCH(k_init_slacks<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_init_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, tol, tau, max_iter, refine_tol));
+}
+
+void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
+    LQ_LAUNCH(k_set_u0<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
+}
+
+void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
+                        cudaStream_t st, bool do_resid, bool do_rd) {
+    int nb1 = ew_blocks(max_total, 256);
+    if (do_resid) LQ_LAUNCH(k_resid<<<dim3(nb1, count), 256, 0, st>>>(d_insts));
+    int wpb = 8;
+    int nb2 = (max_n + wpb - 1) / wpb;
+    nb2 = nb2 > kMaxParts ? kMaxParts : nb2;
+    if (do_rd) {
+        LQ_LAUNCH(k_rd<<<dim3(nb2, count), wpb * 32, 0, st>>>(d_insts));
+        LQ_LAUNCH(k_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb1, nb2, trace_on));
+    }
+}
+
+void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
+    int nb = ew_blocks(max_total, 256);
+    LQ_LAUNCH(k_aff<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_aff_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb));
+}
+
+void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
+    LQ_LAUNCH(k_corr<<<dim3(ew_blocks(max_total, 256), count), 256, 0, st>>>(d_insts));
+}
+
+void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
+    LQ_LAUNCH(k_rhs<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
+}
+
+void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
+                        cudaStream_t st) {
+    int nb = ew_blocks(max_total, 256);
+    LQ_LAUNCH(k_step<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on));
+    LQ_LAUNCH(k_update<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_iter_inc<<<dim3(1, count), 32, 0, st>>>(d_insts));
+}
+
+}  // namespace lqmpc

@@ -1,0 +1,865 @@
+// Host side of the lqmpc C ABI: context and device-arena management, the
+// one-time setup (state elimination and H), and the interior-point driver.
+//
+// One solve is the paper's Algorithm 1 with Mehrotra's predictor-corrector
+// step: per iteration
+//   residuals and Sigma -> stop test -> form M = H + Gamma' Sigma_x Gamma +
+//   Sigma_u -> Cholesky -> predictor solve -> affine step length and sigma ->
+//   corrector right-hand side -> corrector solve -> step length -> update.
+// Every launch covers a batch of instances (grid.y); a single solve is a
+// batch of one.  The host waits on the device once per iteration (to learn
+// whether every instance has finished) and, in the mixed-precision modes,
+// once after each refined solve (to decide on the FP64 fallback).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lqmpc.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace lqmpc;
+
+#include <atomic>
+
+namespace lqmpc {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+}  // namespace lqmpc
+
+struct lqmpc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lqmpc_options opts;
+    Inst h;                     // host copy of the descriptor
+    Inst* d_inst = nullptr;     // device copy
+    unsigned char* arena = nullptr;
+    size_t arena_bytes = 0;
+    Scal* h_scal = nullptr;     // pinned host mirror of the Scal
+    double* h_trace = nullptr;
+    int trace_rows = 0;
+    int cc_splits = 1;          // CUDA-core SYRK split-K factor
+    int tc_splits = 1;          // tensor-core SYRK split-K factor
+    int tc_ok = 0;              // tensor maps built
+    void* d_maps = nullptr;     // 2 CUtensorMap (BF16, TF32), 64-byte aligned, device
+    cudaEvent_t ev[4];
+    cudaEvent_t evk[4];         // around the SYRK launch: tensor-core pair, CUDA-core pair
+    bool events = false;
+    // per-solve SYRK timing
+    double t_tc = 0, t_cc = 0;
+    int n_tc = 0, n_cc = 0;
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Carver {
+    unsigned char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool all_finite(const double* v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+bool csr_ok(int n, const int* ptr, const int* idx, const double* val) {
+    if (!ptr || (!idx && ptr[n] > 0) || (!val && ptr[n] > 0) || ptr[0] != 0) return false;
+    for (int r = 0; r < n; ++r)
+        if (ptr[r + 1] < ptr[r]) return false;
+    for (int k = 0; k < ptr[n]; ++k)
+        if (idx[k] < 0 || idx[k] >= n || !std::isfinite(val[k])) return false;
+    return true;
+}
+
+bool csr_diag(int n, const int* ptr, const int* idx, const double* val, std::vector<double>& d) {
+    d.assign(n, 0.0);
+    for (int r = 0; r < n; ++r)
+        for (int k = ptr[r]; k < ptr[r + 1]; ++k) {
+            if (idx[k] != r) {
+                if (val[k] != 0.0) return false;
+            } else {
+                d[r] += val[k];
+            }
+        }
+    return true;
+}
+
+#define CK(x)                                                                        \
+    do {                                                                             \
+        cudaError_t e_ = (x);                                                        \
+        if (e_ != cudaSuccess) {                                                     \
+            if (getenv("LQMPC_DEBUG"))                                               \
+                fprintf(stderr, "lqmpc: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return LQMPC_ERR_CUDA;                                                   \
+        }                                                                            \
+    } while (0)
+
+// Lay out every device array of an instance in one arena.
+template <bool kAssign>
+size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int max_iter,
+              int cc_splits, int tc_splits) {
+    Carver c{base};
+    const int ns = I.ns, nu = I.nu, n = I.n, SX = I.SX;
+    const size_t G = (size_t)I.ldg * n;
+    auto a_ptr = c.take<int>(ns + 1); auto a_idx = c.take<int>(nnzA); auto a_val = c.take<double>(nnzA);
+    auto q_ptr = c.take<int>(ns + 1); auto q_idx = c.take<int>(nnzQ); auto q_val = c.take<double>(nnzQ);
+    auto qf_ptr = c.take<int>(ns + 1); auto qf_idx = c.take<int>(nnzQf); auto qf_val = c.take<double>(nnzQf);
+    auto B = c.take<double>((size_t)ns * nu); auto R = c.take<double>((size_t)nu * nu);
+    auto xl = c.take<double>(ns); auto xu = c.take<double>(ns);
+    auto ul = c.take<double>(nu); auto uu = c.take<double>(nu);
+    auto qd = c.take<double>(ns); auto qfd = c.take<double>(ns);
+    auto G64 = c.take<double>(G); auto G32 = c.take<float>(G); auto G16 = c.take<__nv_bfloat16>(G);
+    auto H64 = c.take<double>((size_t)n * n); auto H32 = c.take<float>((size_t)n * n);
+    auto xbar = c.take<double>(ns); auto y = c.take<double>(SX); auto h = c.take<double>(n);
+    auto u = c.take<double>(n); auto x = c.take<double>(SX);
+    auto s1 = c.take<double>(SX); auto z1 = c.take<double>(SX);
+    auto s2 = c.take<double>(SX); auto z2 = c.take<double>(SX);
+    auto s3 = c.take<double>(n); auto z3 = c.take<double>(n);
+    auto s4 = c.take<double>(n); auto z4 = c.take<double>(n);
+    auto sigx = c.take<double>(SX); auto sigu = c.take<double>(n); auto sigx32 = c.take<float>(SX);
+    auto wz = c.take<double>(SX); auto wx = c.take<double>(SX);
+    auto wzu = c.take<double>(n); auto wxu = c.take<double>(n);
+    auto gz = c.take<double>(n); auto gw = c.take<double>(n);
+    auto rd = c.take<double>(n); auto b = c.take<double>(n); auto du = c.take<double>(n);
+    auto dx = c.take<double>(SX); auto du_aff = c.take<double>(n); auto dx_aff = c.take<double>(SX);
+    auto ds1 = c.take<double>(SX); auto dz1 = c.take<double>(SX);
+    auto ds2 = c.take<double>(SX); auto dz2 = c.take<double>(SX);
+    auto ds3 = c.take<double>(n); auto dz3 = c.take<double>(n);
+    auto ds4 = c.take<double>(n); auto dz4 = c.take<double>(n);
+    auto M64 = c.take<double>((size_t)n * n); auto M32 = c.take<float>((size_t)n * n);
+    auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
+    auto tmpx = c.take<double>(SX);
+    auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n));
+    auto r32 = c.take<float>(n);
+    size_t ws_cc = (size_t)syrk_cc_tiles(n) * cc_splits * 64 * 64 * sizeof(double);
+    size_t ws_tc = (size_t)syrk_tc_tiles(n) * tc_splits * 128 * 128 * sizeof(float);
+    size_t ws = std::max(ws_cc, ws_tc);
+    auto syrk_ws = c.take<unsigned char>(ws);
+    auto part = c.take<double>((size_t)kParts * kMaxParts);
+    auto sc = c.take<Scal>(1);
+    auto trace = c.take<double>((size_t)(max_iter + 1) * kTraceW);
+    if (kAssign) {
+        I.a_ptr = a_ptr; I.a_idx = a_idx; I.a_val = a_val;
+        I.q_ptr = q_ptr; I.q_idx = q_idx; I.q_val = q_val;
+        I.qf_ptr = qf_ptr; I.qf_idx = qf_idx; I.qf_val = qf_val;
+        I.B = B; I.R = R; I.xl = xl; I.xu = xu; I.ul = ul; I.uu = uu; I.qd = qd; I.qfd = qfd;
+        I.G64 = G64; I.G32 = G32; I.G16 = G16; I.H64 = H64; I.H32 = H32;
+        I.xbar = xbar; I.y = y; I.h = h; I.u = u; I.x = x;
+        I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
+        I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32;
+        I.wz = wz; I.wx = wx; I.wzu = wzu; I.wxu = wxu; I.gz = gz; I.gw = gw;
+        I.rd = rd; I.b = b; I.du = du; I.dx = dx; I.du_aff = du_aff; I.dx_aff = dx_aff;
+        I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;
+        I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
+        I.M64 = M64; I.M32 = M32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
+        I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
+        I.part = part; I.sc = sc; I.trace = trace;
+    }
+    return c.off;
+}
+
+bool is_mixed(int p) { return p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32 || p == LQMPC_FP32; }
+
+// A batch view over one or more contexts.
+struct Batch {
+    std::vector<lqmpc_ctx*> ctxs;
+    Inst* d_insts = nullptr;        // device array
+    bool own = false;
+    int count = 0, max_ns = 0, max_N = 0, max_n = 0, max_sx = 0, max_total = 0;
+    int cc_splits = 1, tc_splits = 1;
+    cudaStream_t st = nullptr;
+    const void* d_maps = nullptr;   // tensor maps (batch of one only)
+};
+
+void batch_dims(Batch& b) {
+    b.count = (int)b.ctxs.size();
+    b.max_ns = b.max_N = b.max_n = b.max_sx = b.max_total = 0;
+    b.cc_splits = b.tc_splits = 1 << 30;
+    for (auto* c : b.ctxs) {
+        b.max_ns = std::max(b.max_ns, c->h.ns);
+        b.max_N = std::max(b.max_N, c->h.N);
+        b.max_n = std::max(b.max_n, c->h.n);
+        b.max_sx = std::max(b.max_sx, c->h.SX);
+        b.max_total = std::max(b.max_total, c->h.SX + c->h.n);
+        b.cc_splits = std::min(b.cc_splits, c->cc_splits);
+        b.tc_splits = std::min(b.tc_splits, c->tc_splits);
+    }
+    b.st = b.ctxs[0]->stream;
+}
+
+// ---- one KKT solve M du = b (in role R_B) into R_DU, and R_TMPX = Gamma du.
+// Returns false if the mixed-precision refinement did not converge for some
+// instance (the caller then falls back to FP64).
+// SYRK timing: the events of ctxs[0] bracket the SYRK launch itself.
+struct SyrkTimer {
+    bool tc = false, cc = false;
+};
+
+void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr) {
+    lqmpc_ctx* c0 = b.ctxs[0];
+    if (prec == LQMPC_FP64) {
+        if (tm) cudaEventRecord(c0->evk[2], b.st);
+        launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
+        if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; }
+        launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
+        launch_potrf(b.d_insts, b.count, b.max_n, 1, F_NONE, b.st);
+    } else {
+        if (prec == LQMPC_FP32) {
+            if (tm) cudaEventRecord(c0->evk[2], b.st);
+            launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
+            if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; }
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st);
+        } else {
+            if (tm) cudaEventRecord(c0->evk[0], b.st);
+            launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
+                           F_NONE, b.st);
+            if (tm) { cudaEventRecord(c0->evk[1], b.st); tm->tc = true; }
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st);
+        }
+        launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st);
+    }
+}
+
+void kkt_solve_fp64(const Batch& b) {
+    launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
+    launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_DU, R_TMPX, F_NONE, b.st);
+}
+
+void kkt_solve_mixed(const Batch& b, int refine_max) {
+    launch_refine_begin(b.d_insts, b.count, b.max_n, b.st);
+    launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_B, R_DU, F_NONE, b.st);
+    for (int s = 0; s <= refine_max; ++s) {
+        launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_DU, R_TMPX, F_SKIP_REFINED, b.st);
+        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_TMPX, R_NONE, R_MV, R_NONE,
+                         1, F_SKIP_REFINED, b.st);
+        launch_refine_residual(b.d_insts, b.count, b.max_n, b.st);
+        if (s == refine_max) break;
+        launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+        launch_refine_update(b.d_insts, b.count, b.max_n, 0, b.st);
+    }
+}
+
+lqmpc_status read_scals(Batch& b) {
+    for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
+    CK(cudaStreamSynchronize(b.st));
+    return LQMPC_OK;
+}
+
+// Per-solve preparation: y = Phi xbar, h = Gamma' Qbar y, initial point.
+void prepare(const Batch& b, const lqmpc_options& o) {
+    for (auto* c : b.ctxs) cudaMemsetAsync(c->h.sc, 0, sizeof(Scal), b.st);
+    launch_ychain(b.d_insts, b.count, b.st);
+    launch_qbar_y(b.d_insts, b.count, b.max_sx, b.st);
+    launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_TMPX, R_NONE, R_H, R_NONE, 0,
+                     F_FORCE, b.st);
+    launch_set_u0(b.d_insts, b.count, b.max_n, b.st);
+    launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_U, R_TMPX, F_FORCE, b.st);
+    launch_init_point(b.d_insts, b.count, b.max_total, b.max_n, o.tol, o.tau, o.max_iter, o.refine_tol,
+                      b.st);
+}
+
+// Mixed-precision refinement failed for some unfinished instance: either
+// finish those instances with a status (no fallback) or switch the whole
+// batch to FP64 for the rest of the solve.  Returns true if FP64 is needed.
+bool handle_refine_failure(Batch& b, const lqmpc_options& o) {
+    bool need = false;
+    for (auto* c : b.ctxs)
+        if (!c->h_scal->done && (c->h_scal->info || !c->h_scal->refine_ok)) need = true;
+    if (!need) return false;
+    for (auto* c : b.ctxs) {
+        Scal fix = *c->h_scal;
+        if (fix.done) continue;
+        if (!o.fallback) {
+            if (fix.info || !fix.refine_ok) {
+                fix.done = 1;
+                fix.status = fix.info ? LQMPC_ERR_NOT_PD : LQMPC_ERR_STALL;
+            }
+        } else {
+            fix.info = 0;
+            fix.fallbacks += 1;
+            fix.use_fp64 = 1;
+        }
+        *c->h_scal = fix;
+        cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
+    }
+    return o.fallback != 0;
+}
+
+lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* t_kkt) {
+    const int prec = o.precision;
+    const bool mixed = is_mixed(prec);
+    if (mixed && prec != LQMPC_FP32 && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
+    lqmpc_ctx* c0 = b.ctxs[0];
+    c0->t_tc = c0->t_cc = 0.0;
+    c0->n_tc = c0->n_cc = 0;
+    cudaEventRecord(c0->ev[0], b.st);
+    prepare(b, o);
+    bool fp64_now = !mixed;
+    double kkt_ms = 0.0;
+    for (int it = 0; it <= o.max_iter; ++it) {
+        SyrkTimer tm;
+        // residuals, Sigma, stop test
+        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
+        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_WZ, R_WX, R_GZ, R_GW, 0,
+                         F_NONE, b.st);
+        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
+        cudaEventRecord(c0->ev[2], b.st);
+        // predictor: M du_aff = b
+        if (fp64_now) {
+            kkt_form(b, LQMPC_FP64, &tm);
+            kkt_solve_fp64(b);
+        } else {
+            kkt_form(b, prec, &tm);
+            kkt_solve_mixed(b, o.refine_max);
+            lqmpc_status s = read_scals(b);
+            if (s != LQMPC_OK) return s;
+            if (handle_refine_failure(b, o)) {
+                fp64_now = true;
+                kkt_form(b, LQMPC_FP64, &tm);
+                kkt_solve_fp64(b);
+            }
+        }
+        launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX_AFF, 0, F_NONE, b.st);
+        // affine step, sigma, corrector right-hand side
+        launch_aff(b.d_insts, b.count, b.max_total, b.st);
+        launch_corr(b.d_insts, b.count, b.max_total, b.st);
+        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_WX, R_NONE, R_GW, R_NONE, 0,
+                         F_NONE, b.st);
+        launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+        // corrector: M du = b with the same factor
+        if (fp64_now) {
+            kkt_solve_fp64(b);
+        } else {
+            kkt_solve_mixed(b, o.refine_max);
+            lqmpc_status s = read_scals(b);
+            if (s != LQMPC_OK) return s;
+            if (handle_refine_failure(b, o)) {
+                fp64_now = true;
+                kkt_form(b, LQMPC_FP64, &tm);
+                kkt_solve_fp64(b);
+            }
+        }
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX, 0, F_NONE, b.st);
+        cudaEventRecord(c0->ev[3], b.st);
+        launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st);
+        lqmpc_status s = read_scals(b);
+        if (s != LQMPC_OK) return s;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]) == cudaSuccess) kkt_ms += ms;
+        if (tm.tc && cudaEventElapsedTime(&ms, c0->evk[0], c0->evk[1]) == cudaSuccess) { c0->t_tc += ms; c0->n_tc++; }
+        if (tm.cc && cudaEventElapsedTime(&ms, c0->evk[2], c0->evk[3]) == cudaSuccess) { c0->t_cc += ms; c0->n_cc++; }
+        bool all_done = true;
+        for (auto* c : b.ctxs) {
+            if (c->h_scal->err) return LQMPC_ERR_TIMEOUT;
+            if (!c->h_scal->done) all_done = false;
+        }
+        if (all_done) break;
+    }
+    cudaEventRecord(c0->ev[1], b.st);
+    lqmpc_status s = read_scals(b);
+    if (s != LQMPC_OK) return s;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c0->ev[0], c0->ev[1]);
+    *t_total = ms;
+    *t_kkt = kkt_ms;
+    if (cudaGetLastError() != cudaSuccess) return LQMPC_ERR_CUDA;
+    return LQMPC_OK;
+}
+
+void fill_stats(lqmpc_ctx* c, lqmpc_stats* st, double t_total, double t_kkt) {
+    const Scal& S = *c->h_scal;
+    if (!st) return;
+    st->iters = S.iter;
+    st->refine_steps = S.refine_steps;
+    st->fallbacks = S.fallbacks;
+    st->status = S.done ? S.status : LQMPC_ERR_MAXITER;
+    st->mu = S.mu;
+    st->res_primal = S.res_p;
+    st->res_dual = S.res_d;
+    st->t_total_ms = t_total;
+    st->t_kkt_ms = t_kkt;
+    st->t_syrk_tc_ms = c->t_tc;
+    st->t_syrk_cc_ms = c->t_cc;
+    st->syrk_tc_launches = c->n_tc;
+    st->syrk_cc_launches = c->n_cc;
+}
+
+lqmpc_status final_status(lqmpc_ctx* c) {
+    const Scal& S = *c->h_scal;
+    if (!S.done) return LQMPC_ERR_MAXITER;
+    return (lqmpc_status)S.status;
+}
+
+lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double* u, bool u_dev,
+                          lqmpc_stats* st) {
+    if (!ctx || !x0 || !u) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    if (!x0_dev) {
+        if (!all_finite(x0, I.ns)) return LQMPC_ERR_ARG;
+        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    Batch b;
+    b.ctxs = {ctx};
+    b.d_insts = ctx->d_inst;
+    batch_dims(b);
+    b.d_maps = ctx->tc_ok ? ctx->d_maps : nullptr;
+    double tt = 0, tk = 0;
+    lqmpc_status s = run_ipm(b, ctx->opts, &tt, &tk);
+    if (s != LQMPC_OK) return s;
+    CK(cudaMemcpyAsync(u, I.u, sizeof(double) * I.n, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    fill_stats(ctx, st, tt, tk);
+    return final_status(ctx);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+lqmpc_options lqmpc_default_options(void) {
+    lqmpc_options o;
+    o.tol = 1e-8;
+    o.max_iter = 100;
+    o.precision = LQMPC_FP64;
+    o.refine_max = 6;
+    o.refine_tol = 1e-10;
+    o.fallback = 1;
+    o.tau = 0.995;
+    o.verbose = 0;
+    return o;
+}
+
+const char* lqmpc_status_str(int s) {
+    switch (s) {
+        case LQMPC_OK: return "ok";
+        case LQMPC_ERR_ARG: return "invalid argument";
+        case LQMPC_ERR_CUDA: return "CUDA error";
+        case LQMPC_ERR_NOT_PD: return "KKT matrix not positive definite";
+        case LQMPC_ERR_MAXITER: return "iteration limit reached";
+        case LQMPC_ERR_INFEASIBLE: return "infeasible";
+        case LQMPC_ERR_NAN: return "non-finite iterate";
+        case LQMPC_ERR_STALL: return "iterative refinement stalled";
+        case LQMPC_ERR_TIMEOUT: return "device wait timed out";
+        case LQMPC_ERR_UNSUPPORTED: return "unsupported option or size";
+        default: return "unknown status";
+    }
+}
+
+static bool opts_ok(const lqmpc_options& o) {
+    return o.tol > 0 && o.max_iter >= 1 && o.max_iter <= 100000 && o.precision >= 0 && o.precision <= 3 &&
+           o.refine_max >= 0 && o.refine_max <= 100 && o.refine_tol > 0 && o.tau > 0 && o.tau < 1;
+}
+
+lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_ptr, const int* a_idx,
+                         const double* a_val, const double* Bh, const int* q_ptr, const int* q_idx,
+                         const double* q_val, const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                         const double* Rh, const double* xl, const double* xu, const double* ul,
+                         const double* uu, const lqmpc_options* opts, void* stream) {
+    if (!out) return LQMPC_ERR_ARG;
+    *out = nullptr;
+    if (ns < 1 || nu < 1 || N < 1 || (long long)nu * N > 30000 || (long long)ns * N > (1LL << 31) - 1)
+        return LQMPC_ERR_ARG;
+    if (!Bh || !Rh || !xl || !xu || !ul || !uu) return LQMPC_ERR_ARG;
+    if (!csr_ok(ns, a_ptr, a_idx, a_val) || !csr_ok(ns, q_ptr, q_idx, q_val)) return LQMPC_ERR_ARG;
+    const bool qf_given = qf_ptr != nullptr;
+    if (qf_given && !csr_ok(ns, qf_ptr, qf_idx, qf_val)) return LQMPC_ERR_ARG;
+    if (!all_finite(Bh, (size_t)ns * nu) || !all_finite(Rh, (size_t)nu * nu)) return LQMPC_ERR_ARG;
+    for (int i = 0; i < ns; ++i)
+        if (std::isnan(xl[i]) || std::isnan(xu[i]) || xl[i] > xu[i] || xl[i] == INFINITY || xu[i] == -INFINITY)
+            return LQMPC_ERR_ARG;
+    for (int j = 0; j < nu; ++j)
+        if (std::isnan(ul[j]) || std::isnan(uu[j]) || ul[j] > uu[j] || ul[j] == INFINITY || uu[j] == -INFINITY)
+            return LQMPC_ERR_ARG;
+    lqmpc_options o = opts ? *opts : lqmpc_default_options();
+    if (!opts_ok(o)) return LQMPC_ERR_ARG;
+    if (!qf_given) { qf_ptr = q_ptr; qf_idx = q_idx; qf_val = q_val; }
+
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) return LQMPC_ERR_CUDA;
+    lqmpc_ctx* ctx = new (std::nothrow) lqmpc_ctx();
+    if (!ctx) return LQMPC_ERR_CUDA;
+    cudaGetDevice(&ctx->device);
+    ctx->stream = (cudaStream_t)stream;
+    ctx->opts = o;
+    Inst& I = ctx->h;
+    memset(&I, 0, sizeof(I));
+    I.ns = ns; I.nu = nu; I.N = N; I.n = nu * N; I.SX = ns * N;
+    I.ldg = (int)align_up(ns, 64);
+    std::vector<double> qd, qfd;
+    bool qdiag = csr_diag(ns, q_ptr, q_idx, q_val, qd) && csr_diag(ns, qf_ptr, qf_idx, qf_val, qfd);
+    I.q_diag = qdiag ? 1 : 0;
+    const int nnzA = a_ptr[ns], nnzQ = q_ptr[ns], nnzQf = qf_ptr[ns];
+    ctx->cc_splits = syrk_cc_splits(ns, nu, N);
+    ctx->tc_splits = syrk_tc_splits(ns, nu, N);
+    size_t bytes = layout<false>(I, nullptr, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits);
+    auto fail = [&](lqmpc_status s) {
+        lqmpc_free(ctx);
+        return s;
+    };
+    if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+    ctx->arena_bytes = bytes;
+    if (cudaMemsetAsync(ctx->arena, 0, bytes, ctx->stream) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+    layout<true>(I, ctx->arena, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits);
+    if (cudaMallocHost(&ctx->h_scal, sizeof(Scal)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+    memset(ctx->h_scal, 0, sizeof(Scal));
+    for (int e = 0; e < 4; ++e)
+        if (cudaEventCreate(&ctx->ev[e]) != cudaSuccess || cudaEventCreate(&ctx->evk[e]) != cudaSuccess)
+            return fail(LQMPC_ERR_CUDA);
+    ctx->events = true;
+    cudaStream_t st = ctx->stream;
+    auto up = [&](const void* dst, const void* src, size_t n) {
+        return cudaMemcpyAsync((void*)dst, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    bool ok = up(I.a_ptr, a_ptr, sizeof(int) * (ns + 1)) && up(I.a_idx, a_idx, sizeof(int) * nnzA) &&
+              up(I.a_val, a_val, sizeof(double) * nnzA) && up(I.q_ptr, q_ptr, sizeof(int) * (ns + 1)) &&
+              up(I.q_idx, q_idx, sizeof(int) * nnzQ) && up(I.q_val, q_val, sizeof(double) * nnzQ) &&
+              up(I.qf_ptr, qf_ptr, sizeof(int) * (ns + 1)) && up(I.qf_idx, qf_idx, sizeof(int) * nnzQf) &&
+              up(I.qf_val, qf_val, sizeof(double) * nnzQf) && up(I.B, Bh, sizeof(double) * ns * nu) &&
+              up(I.R, Rh, sizeof(double) * nu * nu) && up(I.xl, xl, sizeof(double) * ns) &&
+              up(I.xu, xu, sizeof(double) * ns) && up(I.ul, ul, sizeof(double) * nu) &&
+              up(I.uu, uu, sizeof(double) * nu);
+    if (qdiag) ok = ok && up(I.qd, qd.data(), sizeof(double) * ns) && up(I.qfd, qfd.data(), sizeof(double) * ns);
+    if (!ok) return fail(LQMPC_ERR_CUDA);
+    if (cudaMalloc(&ctx->d_inst, sizeof(Inst)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+    if (!up(ctx->d_inst, &I, sizeof(Inst))) return fail(LQMPC_ERR_CUDA);
+    // the solve's Scal starts "not done" for the setup-time launches
+    cudaMemsetAsync(I.sc, 0, sizeof(Scal), st);
+
+    // one-time state elimination and H (FP64)
+    launch_gstack(ctx->d_inst, I, st);
+    if (qdiag) {
+        launch_syrk_cc(ctx->d_inst, 1, I.n, ctx->cc_splits, 1, 1, nullptr, nullptr, F_FORCE, st);
+    } else {
+        double *gq = nullptr, *gqf = nullptr;
+        size_t gb = sizeof(double) * (size_t)I.ldg * I.n;
+        if (cudaMalloc(&gq, gb) != cudaSuccess || cudaMalloc(&gqf, gb) != cudaSuccess) {
+            cudaFree(gq);
+            return fail(LQMPC_ERR_CUDA);
+        }
+        cudaMemsetAsync(gq, 0, gb, st);
+        cudaMemsetAsync(gqf, 0, gb, st);
+        launch_q_times_g(ctx->d_inst, I, 0, gq, st);
+        launch_q_times_g(ctx->d_inst, I, 1, gqf, st);
+        launch_syrk_cc(ctx->d_inst, 1, I.n, ctx->cc_splits, 1, 2, gq, gqf, F_FORCE, st);
+        cudaStreamSynchronize(st);
+        cudaFree(gq);
+        cudaFree(gqf);
+    }
+    launch_syrk_reduce(ctx->d_inst, 1, I.n, ctx->cc_splits, 0, 1, 1, 0, F_FORCE, I.H64, st);
+    launch_h_to_f32(ctx->d_inst, I.n, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return fail(LQMPC_ERR_CUDA);
+    // tensor maps for the tcgen05 SYRK (BF16 and TF32 views of the G-stack)
+    {
+        alignas(64) unsigned char maps[256];
+        bool m0 = syrk_tc_make_maps(I, 0, maps);
+        bool m1 = syrk_tc_make_maps(I, 1, maps + 128);
+        if (m0 && m1) {
+            if (cudaMalloc(&ctx->d_maps, 256) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+            if (cudaMemcpy(ctx->d_maps, maps, 256, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(LQMPC_ERR_CUDA);
+            ctx->tc_ok = 1;
+        }
+    }
+    *out = ctx;
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_set_options(lqmpc_ctx* ctx, const lqmpc_options* opts) {
+    if (!ctx || !opts || !opts_ok(*opts)) return LQMPC_ERR_ARG;
+    if (opts->max_iter > ctx->opts.max_iter) return LQMPC_ERR_ARG;  // trace buffer sized at setup
+    ctx->opts = *opts;
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_solve(lqmpc_ctx* ctx, const double* x0, double* u_out, lqmpc_stats* stats) {
+    return solve_common(ctx, x0, false, u_out, false, stats);
+}
+
+lqmpc_status lqmpc_solve_device(lqmpc_ctx* ctx, const double* x0_device, double* u_device,
+                                lqmpc_stats* stats) {
+    return solve_common(ctx, x0_device, true, u_device, true, stats);
+}
+
+lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                               double* const* u_outs, lqmpc_stats* stats) {
+    if (!ctxs || count < 1 || !x0s || !u_outs) return LQMPC_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i] || !x0s[i] || !u_outs[i] || ctxs[i]->stream != ctxs[0]->stream ||
+            ctxs[i]->device != ctxs[0]->device)
+            return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctxs[0]->device));
+    Batch b;
+    b.ctxs.assign(ctxs, ctxs + count);
+    batch_dims(b);
+    lqmpc_options o = ctxs[0]->opts;
+    for (int i = 0; i < count; ++i) {
+        if (!all_finite(x0s[i], ctxs[i]->h.ns)) return LQMPC_ERR_ARG;
+        if (ctxs[i]->opts.max_iter < o.max_iter) o.max_iter = ctxs[i]->opts.max_iter;
+    }
+    if (o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32) {
+        if (count > 1) o.precision = LQMPC_FP32;  // per-instance tensor maps: single instance only
+        else b.d_maps = ctxs[0]->tc_ok ? ctxs[0]->d_maps : nullptr;
+    }
+    std::vector<Inst> hosts(count);
+    for (int i = 0; i < count; ++i) hosts[i] = ctxs[i]->h;
+    Inst* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(Inst) * count));
+    b.d_insts = d;
+    lqmpc_status s = LQMPC_OK;
+    if (cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess)
+        s = LQMPC_ERR_CUDA;
+    for (int i = 0; i < count && s == LQMPC_OK; ++i)
+        if (cudaMemcpyAsync(ctxs[i]->h.xbar, x0s[i], sizeof(double) * ctxs[i]->h.ns, cudaMemcpyHostToDevice,
+                            b.st) != cudaSuccess)
+            s = LQMPC_ERR_CUDA;
+    double tt = 0, tk = 0;
+    if (s == LQMPC_OK) s = run_ipm(b, o, &tt, &tk);
+    if (s == LQMPC_OK) {
+        for (int i = 0; i < count; ++i)
+            if (cudaMemcpyAsync(u_outs[i], ctxs[i]->h.u, sizeof(double) * ctxs[i]->h.n, cudaMemcpyDeviceToHost,
+                                b.st) != cudaSuccess)
+                s = LQMPC_ERR_CUDA;
+        if (cudaStreamSynchronize(b.st) != cudaSuccess) s = LQMPC_ERR_CUDA;
+    }
+    cudaFree(d);
+    if (s != LQMPC_OK) return s;
+    lqmpc_status first = LQMPC_OK;
+    for (int i = 0; i < count; ++i) {
+        if (stats) fill_stats(ctxs[i], &stats[i], tt, tk);
+        lqmpc_status si = final_status(ctxs[i]);
+        if (si != LQMPC_OK && first == LQMPC_OK) first = si;
+    }
+    return first;
+}
+
+unsigned long long lqmpc_kernel_launches(void) { return g_launches.load(); }
+
+void lqmpc_free(lqmpc_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->events)
+        for (int e = 0; e < 4; ++e) {
+            cudaEventDestroy(ctx->ev[e]);
+            cudaEventDestroy(ctx->evk[e]);
+        }
+    cudaFree(ctx->arena);
+    cudaFree(ctx->d_inst);
+    cudaFree(ctx->d_maps);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// Stage-level entry points
+// ---------------------------------------------------------------------------
+
+lqmpc_status lqmpc_get_gstack(lqmpc_ctx* ctx, double* G) {
+    if (!ctx || !G) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    std::vector<double> raw((size_t)I.ldg * I.n);
+    CK(cudaMemcpy(raw.data(), I.G64, sizeof(double) * raw.size(), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < I.N; ++k)
+        for (int c = 0; c < I.nu; ++c)
+            memcpy(G + ((size_t)k * I.nu + c) * I.ns, raw.data() + (size_t)I.ldg * ((I.N - 1 - k) * I.nu + c),
+                   sizeof(double) * I.ns);
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_get_hessian(lqmpc_ctx* ctx, double* H) {
+    if (!ctx || !H) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaMemcpy(H, ctx->h.H64, sizeof(double) * ctx->h.n * ctx->h.n, cudaMemcpyDeviceToHost));
+    return LQMPC_OK;
+}
+
+static lqmpc_status reset_scal(lqmpc_ctx* ctx) {
+    Scal s;
+    memset(&s, 0, sizeof(s));
+    s.refine_tol = ctx->opts.refine_tol;
+    s.tol = ctx->opts.tol;
+    s.tau = ctx->opts.tau;
+    s.max_iter = ctx->opts.max_iter;
+    CK(cudaMemcpyAsync(ctx->h.sc, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_gamma_mv(lqmpc_ctx* ctx, const double* v, double* out) {
+    if (!ctx || !v || !out) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    lqmpc_status s = reset_scal(ctx);
+    if (s) return s;
+    CK(cudaMemcpyAsync(I.du, v, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_gamma_mv(ctx->d_inst, 1, I.ns, I.N, R_DU, R_TMPX, F_FORCE, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, I.tmpx, sizeof(double) * I.SX, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out) {
+    if (!ctx || !w || !out) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    lqmpc_status s = reset_scal(ctx);
+    if (s) return s;
+    CK(cudaMemcpyAsync(I.tmpx, w, sizeof(double) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
+    launch_gamma_tmv(ctx->d_inst, 1, I.ns, I.N, I.n, R_TMPX, R_NONE, R_MV, R_NONE, 0, F_FORCE, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, I.mv, sizeof(double) * I.n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LQMPC_OK;
+}
+
+static lqmpc_status upload_sigma(lqmpc_ctx* ctx, const double* sigx, const double* sigu) {
+    const Inst& I = ctx->h;
+    if (!all_finite(sigx, I.SX) || !all_finite(sigu, I.n)) return LQMPC_ERR_ARG;
+    for (int k = 0; k < I.SX; ++k)
+        if (sigx[k] < 0) return LQMPC_ERR_ARG;
+    for (int k = 0; k < I.n; ++k)
+        if (sigu[k] < 0) return LQMPC_ERR_ARG;
+    std::vector<float> s32(sigx, sigx + I.SX);
+    CK(cudaMemcpyAsync(I.sigx, sigx, sizeof(double) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(I.sigx32, s32.data(), sizeof(float) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(I.sigu, sigu, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LQMPC_OK;
+}
+
+static lqmpc_status download_matrix(lqmpc_ctx* ctx, bool fp64, double* out, bool lower_only) {
+    const Inst& I = ctx->h;
+    size_t nn = (size_t)I.n * I.n;
+    if (fp64) {
+        CK(cudaMemcpy(out, I.M64, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> t(nn);
+        CK(cudaMemcpy(t.data(), I.M32, sizeof(float) * nn, cudaMemcpyDeviceToHost));
+        for (size_t q = 0; q < nn; ++q) out[q] = t[q];
+    }
+    if (lower_only)
+        for (int k = 0; k < I.n; ++k)
+            for (int j = 0; j < k; ++j) out[j + (size_t)I.n * k] = 0.0;
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* sigu, int precision,
+                            double* M) {
+    if (!ctx || !sigx || !sigu || !M || precision < 0 || precision > 3) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    if ((precision == LQMPC_MIXED_BF16 || precision == LQMPC_MIXED_TF32) && !ctx->tc_ok)
+        return LQMPC_ERR_UNSUPPORTED;
+    lqmpc_status s = upload_sigma(ctx, sigx, sigu);
+    if (s) return s;
+    s = reset_scal(ctx);
+    if (s) return s;
+    Batch b;
+    b.ctxs = {ctx};
+    b.d_insts = ctx->d_inst;
+    batch_dims(b);
+    b.d_maps = ctx->d_maps;
+    const Inst& I = ctx->h;
+    if (precision == LQMPC_FP64) {
+        launch_syrk_cc(b.d_insts, 1, I.n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
+        launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
+    } else if (precision == LQMPC_FP32) {
+        launch_syrk_cc(b.d_insts, 1, I.n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
+        launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st);
+    } else {
+        launch_syrk_tc(b.d_insts, 1, I.n, b.tc_splits, precision == LQMPC_MIXED_TF32, b.d_maps, F_NONE, b.st);
+        launch_syrk_reduce(b.d_insts, 1, I.n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(b.st));
+    return download_matrix(ctx, precision == LQMPC_FP64, M, false);
+}
+
+lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* sigu, int precision,
+                             const double* rhs, double* x, double* L, int* refine_steps) {
+    if (!ctx || !sigx || !sigu || !rhs || !x || precision < 0 || precision > 3) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    if ((precision == LQMPC_MIXED_BF16 || precision == LQMPC_MIXED_TF32) && !ctx->tc_ok)
+        return LQMPC_ERR_UNSUPPORTED;
+    const Inst& I = ctx->h;
+    if (!all_finite(rhs, I.n)) return LQMPC_ERR_ARG;
+    lqmpc_status s = upload_sigma(ctx, sigx, sigu);
+    if (s) return s;
+    s = reset_scal(ctx);
+    if (s) return s;
+    Batch b;
+    b.ctxs = {ctx};
+    b.d_insts = ctx->d_inst;
+    batch_dims(b);
+    b.d_maps = ctx->d_maps;
+    CK(cudaMemcpyAsync(I.b, rhs, sizeof(double) * I.n, cudaMemcpyHostToDevice, b.st));
+    kkt_form(b, precision);
+    if (precision == LQMPC_FP64) kkt_solve_fp64(b);
+    else kkt_solve_mixed(b, ctx->opts.refine_max);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_scal, I.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
+    CK(cudaStreamSynchronize(b.st));
+    CK(cudaMemcpy(x, I.du, sizeof(double) * I.n, cudaMemcpyDeviceToHost));
+    if (L) {
+        s = download_matrix(ctx, precision == LQMPC_FP64, L, true);
+        if (s) return s;
+    }
+    if (refine_steps) *refine_steps = ctx->h_scal->refine_steps;
+    if (ctx->h_scal->info) return LQMPC_ERR_NOT_PD;
+    if (precision != LQMPC_FP64 && !ctx->h_scal->refine_ok) return LQMPC_ERR_STALL;
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_get_trace(lqmpc_ctx* ctx, double* trace, int max_rows, int* rows) {
+    if (!ctx || !trace || !rows || max_rows < 0) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    Scal S;
+    CK(cudaMemcpy(&S, ctx->h.sc, sizeof(S), cudaMemcpyDeviceToHost));
+    int r = std::min(S.iter + 1, ctx->opts.max_iter + 1);
+    r = std::min(r, max_rows);
+    if (r > 0) CK(cudaMemcpy(trace, ctx->h.trace, sizeof(double) * kTraceW * r, cudaMemcpyDeviceToHost));
+    *rows = r;
+    return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_get_duals(lqmpc_ctx* ctx, double* z) {
+    if (!ctx || !z) return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    CK(cudaMemcpy(z, I.z1, sizeof(double) * I.SX, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(z + I.SX, I.z2, sizeof(double) * I.SX, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(z + 2 * (size_t)I.SX, I.z3, sizeof(double) * I.n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(z + 2 * (size_t)I.SX + I.n, I.z4, sizeof(double) * I.n, cudaMemcpyDeviceToHost));
+    return LQMPC_OK;
+}
+
+}  // extern "C"
