@@ -66,9 +66,12 @@ typedef struct {
     double tol;          /* stop: max(||r_d||/(1+||h||), ||r_p||/(1+||d||), mu) <= tol; 1e-8 */
     int max_iter;        /* iteration limit; 100 */
     int precision;       /* LQMPC_FP64 (default) / LQMPC_MIXED_BF16 / LQMPC_MIXED_TF32 / LQMPC_FP32 */
-    int refine_max;      /* refinement steps per solve in the mixed modes; 6 */
-    double refine_tol;   /* refinement stops at ||b - M du||_inf <= refine_tol ||b||_inf; 1e-10 */
-    int fallback;        /* 1: switch to FP64 for the rest of the solve when refinement stalls */
+    int refine_max;      /* refinement steps per solve in the mixed modes; 10 */
+    double refine_tol;   /* refinement stops at ||b - M du||_inf <= refine_tol ||b||_inf (1e-10)
+                            or <= 0.01 tol (1 + ||h||_inf), whichever is larger */
+    int fallback;        /* 1: when refinement stalls (two steps that do not halve the residual)
+                            or runs out of steps, move to a more accurate factor for the rest of
+                            the solve: BF16/TF32 -> FP32 -> FP64 */
     double tau;          /* fraction to the boundary; 0.995 */
     int verbose;         /* 1: keep the per-iteration trace of the last solve */
 } lqmpc_options;
@@ -189,9 +192,10 @@ lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* s
                              int precision, const double* b, double* x, double* L,
                              int* refine_steps);
 
-/* Per-iteration trace of the last solve (requires opts.verbose = 1): rows of
- * 6 doubles (mu, res_dual, res_primal, alpha_aff, sigma, alpha); writes at
- * most max_rows rows and returns the row count in *rows. */
+/* Per-iteration trace of the last solve: rows of 8 doubles (mu, res_dual,
+ * res_primal, alpha_aff, sigma, alpha, refinement steps, KKT precision code
+ * of the iteration); writes at most max_rows rows and returns the row count
+ * in *rows. */
 lqmpc_status lqmpc_get_trace(lqmpc_ctx* ctx, double* trace, int max_rows, int* rows);
 
 /* Final duals of the last solve: [z_xu (ns*N), z_xl (ns*N), z_uu (n), z_ul (n)]. */

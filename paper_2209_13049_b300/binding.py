@@ -231,7 +231,7 @@ class Solver:
 
     def get_trace(self, max_rows=None):
         max_rows = max_rows or (self.options.max_iter + 1)
-        tr = np.zeros((max_rows, 6))
+        tr = np.zeros((max_rows, 8))
         rows = ctypes.c_int(0)
         _check(load().lqmpc_get_trace(self.h, _p(tr), max_rows, ctypes.byref(rows)), "lqmpc_get_trace")
         return tr[: rows.value].copy()

@@ -15,15 +15,20 @@ namespace lqmpc {
 // Every kernel launch of the library goes through LQ_LAUNCH so the process-wide
 // launch count (lqmpc_kernel_launches) is exact.
 void note_launches(int k);
-#define LQ_LAUNCH(...)          \
-    do {                        \
-        __VA_ARGS__;            \
-        ::lqmpc::note_launches(1); \
+// With LQMPC_CHECK=1 in the environment every launch is followed by a stream
+// synchronisation and an error check that names the failing launch (debug
+// aid; off by default).
+void check_launch(cudaStream_t st, const char* what, const char* file, int line);
+#define LQ_LAUNCH(...)                                               \
+    do {                                                             \
+        __VA_ARGS__;                                                 \
+        ::lqmpc::note_launches(1);                                   \
+        ::lqmpc::check_launch(st, #__VA_ARGS__, __FILE__, __LINE__); \
     } while (0)
 
 constexpr int kMaxParts = 1024;     // max blocks of a reduction launch per instance
 constexpr int kParts = 8;           // reduction slots per instance
-constexpr int kTraceW = 6;          // mu, res_d, res_p, alpha_aff, sigma, alpha
+constexpr int kTraceW = 8;          // mu, res_d, res_p, alpha_aff, sigma, alpha, refine steps, precision
 
 // Per-instance scalars living in device memory.
 struct Scal {
@@ -44,6 +49,9 @@ struct Scal {
     int fallbacks;      // iterations that fell back to FP64
     int use_fp64;       // sticky: remaining iterations in FP64
     int err;            // device-side error flags (bounded wait timeouts etc.)
+    int refine_fail;    // refinement stalled or produced a non-finite residual
+    int refine_iter;    // refinement steps in the current interior-point iteration
+    int prec_used;      // KKT precision of the current iteration (trace)
     int pad;
 };
 
@@ -90,6 +98,7 @@ struct Inst {
     void* syrk_ws;                    // split-K partial tiles
     size_t syrk_ws_bytes;
     double* part;                     // kParts x kMaxParts reduction partials
+    unsigned* bar;                    // grid-barrier state of cooperative launches (2 words)
     Scal* sc;
     double* trace;                    // (max_iter+1) x kTraceW
 };
@@ -119,7 +128,7 @@ enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2 };
 
 __device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
     if (!(flags & F_FORCE) && I.sc->done) return true;
-    if ((flags & F_SKIP_REFINED) && I.sc->refine_ok) return true;
+    if ((flags & F_SKIP_REFINED) && (I.sc->refine_ok || I.sc->refine_fail)) return true;
     return false;
 }
 

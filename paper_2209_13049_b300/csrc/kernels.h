@@ -18,14 +18,14 @@ void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st);
 void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st);
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st);
-void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
+void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, int prec,
                         cudaStream_t st);
 
 // kernels_gamma.cu
 void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st);
 void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int in_role,
                      int out_role, int force, cudaStream_t st);
-size_t gamma_tmv_part_doubles(int ns, int n);
+size_t gamma_tmv_part_doubles(int ns, int n, int N);
 void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
                       int w0_role, int w1_role, int o0_role, int o1_role, int scale0, int force,
                       cudaStream_t st);

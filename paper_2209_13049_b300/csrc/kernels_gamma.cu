@@ -86,29 +86,43 @@ __global__ void k_gamma_mv(const Inst* __restrict__ insts, int in_role, int out_
         if (r0 + q <= rlast) out[(size_t)(r0 + q) * I.ns + i] = acc[q];
 }
 
-// Gamma' w, two-level.  Stage 1: block (t, chunk) computes for input block t
-// and a chunk of states the partial sums
-//     P[chunk][t*nu + c] = sum_{r >= t} sum_{i in chunk} G[i, (N-1-r+t) nu + c] w_r[i]
-// for NV vectors at once.  Stage 2 adds the chunks in order (deterministic).
-constexpr int kTmvChunk = 256;
+// Gamma' w, two-level.  Stage 1: block (t, chunk, rgroup) computes, for input
+// block t, a chunk of kTmvChunk states and kTmvRg consecutive row blocks
+// r >= t of Gamma, the partial sums
+//     P[rgroup][chunk][t*nu + c] = sum_{r in group} sum_{i in chunk} G[i, (N-1-r+t) nu + c] w_r[i]
+// for NV vectors at once.  Stage 2 adds the partials in a fixed order
+// (deterministic).  Small blocks over all three indices keep every SM busy:
+// FP64 throughput per SM is low on this part, so the work must be spread.
+constexpr int kTmvChunk = 128;
+constexpr int kTmvRg = 8;
 constexpr int kTmvMaxNu = 32;
 
+__host__ __device__ inline int tmv_groups(int N) { return (N + kTmvRg - 1) / kTmvRg; }
+
 template <int NV>
-__global__ void k_gamma_tmv_part(const Inst* __restrict__ insts, int w0_role, int w1_role,
-                                 int scale0, int flags) {
+__global__ void __launch_bounds__(kTmvChunk) k_gamma_tmv_part(const Inst* __restrict__ insts, int w0_role,
+                                                              int w1_role, int scale0, int flags) {
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
-    const int t = blockIdx.x;
-    const int chunk = blockIdx.z;
     const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
+    const int ngroups = tmv_groups(I.N);
+    const int t = blockIdx.x / ngroups, g = blockIdx.x % ngroups;
+    const int chunk = blockIdx.z;
     if (t >= I.N || chunk >= nchunks) return;
     const int nu = I.nu, N = I.N;
+    const int r0 = t + g * kTmvRg;
+    double* part = I.gpart + ((size_t)g * nchunks + chunk) * NV * I.n;
+    __shared__ double red[NV][kTmvMaxNu][kTmvChunk / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (r0 >= N) {   // empty group: contributes zeros
+        for (int q = threadIdx.x; q < NV * nu; q += blockDim.x)
+            part[(size_t)(q / nu) * I.n + t * nu + q % nu] = 0.0;
+        return;
+    }
+    const int r1 = min(r0 + kTmvRg, N);
     const double* w0 = role_ptr(I, w0_role);
     const double* w1 = NV > 1 ? role_ptr(I, w1_role) : nullptr;
-    double* part = I.gpart;
-    __shared__ double red[NV][kTmvMaxNu][33];
     const int i = chunk * kTmvChunk + threadIdx.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c0 = 0; c0 < nu; c0 += kTmvMaxNu) {
         const int cn = min(kTmvMaxNu, nu - c0);
         double acc[NV][kTmvMaxNu];
@@ -117,36 +131,37 @@ __global__ void k_gamma_tmv_part(const Inst* __restrict__ insts, int w0_role, in
 #pragma unroll
             for (int c = 0; c < kTmvMaxNu; ++c) acc[a][c] = 0.0;
         if (i < I.ns) {
-            for (int r = t; r < N; ++r) {
+            for (int r = r0; r < r1; ++r) {
                 double wa = w0[(size_t)r * I.ns + i];
                 if (scale0) wa *= I.sigx[(size_t)r * I.ns + i];
                 double wb = NV > 1 ? w1[(size_t)r * I.ns + i] : 0.0;
-                const double* g = I.G64 + (size_t)I.ldg * ((N - 1 - r + t) * nu + c0) + i;
+                const double* gp = I.G64 + (size_t)I.ldg * ((N - 1 - r + t) * nu + c0) + i;
 #pragma unroll
                 for (int c = 0; c < kTmvMaxNu; ++c) {
                     if (c < cn) {
-                        double gv = g[(size_t)I.ldg * c];
+                        double gv = gp[(size_t)I.ldg * c];
                         acc[0][c] += gv * wa;
                         if (NV > 1) acc[NV - 1][c] += gv * wb;
                     }
                 }
             }
         }
-        // block reduction of each (vector, c)
 #pragma unroll
         for (int a = 0; a < NV; ++a)
 #pragma unroll
             for (int c = 0; c < kTmvMaxNu; ++c) {
-                double v = warp_sum(acc[a][c]);
-                if (lane == 0) red[a][c][warp] = v;
+                if (c < cn) {
+                    double v = warp_sum(acc[a][c]);
+                    if (lane == 0) red[a][c][warp] = v;
+                }
             }
         __syncthreads();
         const int nw = blockDim.x >> 5;
         for (int q = threadIdx.x; q < NV * cn; q += blockDim.x) {
             int a = q / cn, c = q % cn;
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red[a][c][w];
-            part[((size_t)a * nchunks + chunk) * I.n + t * nu + c0 + c] = s;
+            double sum = 0.0;
+            for (int w = 0; w < nw; ++w) sum += red[a][c][w];
+            part[(size_t)a * I.n + t * nu + c0 + c] = sum;
         }
         __syncthreads();
     }
@@ -157,15 +172,20 @@ __global__ void k_gamma_tmv_sum(const Inst* __restrict__ insts, int o0_role, int
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
+    const int ngroups = tmv_groups(I.N);
     const double* part = I.gpart;
     double* o0 = role_ptr(I, o0_role);
     double* o1 = NV > 1 ? role_ptr(I, o1_role) : nullptr;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x) {
+        const int t = j / I.nu;
+        const int gmax = tmv_groups(I.N - t);    // groups that hold row blocks of this t
 #pragma unroll
         for (int a = 0; a < NV; ++a) {
-            double s = 0.0;
-            for (int q = 0; q < nchunks; ++q) s += part[((size_t)a * nchunks + q) * I.n + j];
-            (a == 0 ? o0 : o1)[j] = s;
+            double sum = 0.0;
+            for (int g = 0; g < gmax && g < ngroups; ++g)
+                for (int q = 0; q < nchunks; ++q)
+                    sum += part[(((size_t)g * nchunks + q) * NV + a) * I.n + j];
+            (a == 0 ? o0 : o1)[j] = sum;
         }
     }
 }
@@ -238,20 +258,20 @@ void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st) {
 
 void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int in_role,
                      int out_role, int flags, cudaStream_t st) {
-    constexpr int RB = 8;
-    dim3 grid((max_ns + 127) / 128, count, (max_N + RB - 1) / RB);
-    LQ_LAUNCH(k_gamma_mv<RB><<<grid, 128, 0, st>>>(d_insts, in_role, out_role, flags));
+    constexpr int RB = 4;
+    dim3 grid((max_ns + 31) / 32, count, (max_N + RB - 1) / RB);
+    LQ_LAUNCH(k_gamma_mv<RB><<<grid, 32, 0, st>>>(d_insts, in_role, out_role, flags));
 }
 
-size_t gamma_tmv_part_doubles(int ns, int n) {
-    return (size_t)2 * ((ns + kTmvChunk - 1) / kTmvChunk) * n;
+size_t gamma_tmv_part_doubles(int ns, int n, int N) {
+    return (size_t)2 * tmv_groups(N) * ((ns + kTmvChunk - 1) / kTmvChunk) * n;
 }
 
 void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
                       int w0_role, int w1_role, int o0_role, int o1_role, int scale0, int flags,
                       cudaStream_t st) {
     int nchunks = (max_ns + kTmvChunk - 1) / kTmvChunk;
-    dim3 grid(max_N, count, nchunks);
+    dim3 grid(max_N * tmv_groups(max_N), count, nchunks);
     int nbs = (max_n + 255) / 256;
     if (w1_role != R_NONE) {
         LQ_LAUNCH(k_gamma_tmv_part<2><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));

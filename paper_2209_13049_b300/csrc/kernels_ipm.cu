@@ -214,8 +214,9 @@ __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int tr
         S->mu = mu; S->res_d = res_d; S->res_p = res_p; S->res = res;
         if (trace_on && S->iter <= S->max_iter) {
             double* t = I.trace + (size_t)S->iter * kTraceW;
-            t[0] = mu; t[1] = res_d; t[2] = res_p; t[3] = 0; t[4] = 0; t[5] = 0;
+            t[0] = mu; t[1] = res_d; t[2] = res_p; t[3] = 0; t[4] = 0; t[5] = 0; t[6] = 0; t[7] = -1;
         }
+        S->refine_iter = 0;
         if (!(res == res)) { S->done = 1; S->status = 6; }
         else if (res <= S->tol) { S->done = 1; S->status = 0; }
         else if (S->iter >= S->max_iter) { S->done = 1; S->status = 4; }
@@ -355,7 +356,7 @@ __global__ void k_step(const Inst* __restrict__ insts) {
 }
 
 // alpha = min(1, tau * max step); trace; iteration count.
-__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on) {
+__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on, int prec) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -369,6 +370,7 @@ __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on)
         if (trace_on && S->iter <= S->max_iter) {
             double* t = I.trace + (size_t)S->iter * kTraceW;
             t[3] = S->alpha_aff; t[4] = S->sigma; t[5] = al;
+            t[6] = S->refine_iter; t[7] = prec;
         }
     }
 }
@@ -441,11 +443,11 @@ void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
     LQ_LAUNCH(k_rhs<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
 }
 
-void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
+void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, int prec,
                         cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
     LQ_LAUNCH(k_step<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on));
+    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on, prec));
     LQ_LAUNCH(k_update<<<dim3(nb, count), 256, 0, st>>>(d_insts));
     LQ_LAUNCH(k_iter_inc<<<dim3(1, count), 32, 0, st>>>(d_insts));
 }

@@ -21,7 +21,7 @@ __global__ void k_refine_begin(const Inst* __restrict__ insts) {
     m = block_reduce<1>(m, red);
     if (threadIdx.x == 0) {
         S->rnorm0 = m; S->rnorm = INFINITY; S->rnorm_prev = INFINITY;
-        S->refine_ok = 0; S->refine_cur = 0; S->stalled = 0;
+        S->refine_ok = 0; S->refine_fail = 0; S->refine_cur = 0; S->stalled = 0;
     }
 }
 
@@ -31,7 +31,7 @@ __global__ void k_refine_resid(const Inst* __restrict__ insts, int du_role) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     const Scal* S = I.sc;
-    if (S->done || S->refine_ok) return;
+    if (S->done || S->refine_ok || S->refine_fail) return;
     const double* du = role_ptr(I, du_role);
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double rmax = 0.0;
@@ -54,15 +54,20 @@ __global__ void k_refine_check(const Inst* __restrict__ insts, int nb) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done || S->refine_ok) return;
+    if (S->done || S->refine_ok || S->refine_fail) return;
     double m = 0.0;
     for (int p = threadIdx.x; p < nb; p += blockDim.x) m = fmax(m, I.part[6 * kMaxParts + p]);
     m = block_reduce<1>(m, red);
     if (threadIdx.x == 0) {
         S->rnorm = m;
-        if (!(m == m)) { S->stalled = 1 << 20; return; }
-        if (m <= S->refine_tol * S->rnorm0 || S->rnorm0 == 0.0) { S->refine_ok = 1; return; }
+        if (!(m == m)) { S->refine_fail = 1; return; }
+        // converged: relative to ||b||, or small enough that the stationarity
+        // residual it leaves behind is far below the stop tolerance
+        const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
+        if (m <= S->refine_tol * S->rnorm0 || m <= floor_abs || S->rnorm0 == 0.0) { S->refine_ok = 1; return; }
         if (m > 0.5 * S->rnorm_prev) S->stalled += 1;
+        else S->stalled = 0;
+        if (S->stalled >= 2) S->refine_fail = 1;
         S->rnorm_prev = m;
     }
 }
@@ -70,12 +75,14 @@ __global__ void k_refine_check(const Inst* __restrict__ insts, int nb) {
 __global__ void k_refine_update(const Inst* __restrict__ insts, int du_role, int last) {
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done || S->refine_ok) return;
+    if (S->done || S->refine_ok || S->refine_fail) return;
     double* du = role_ptr(I, du_role);
     if (!last)
         for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x)
             du[j] += I.dcorr[j];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !last) { S->refine_cur += 1; S->refine_steps += 1; }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !last) {
+        S->refine_cur += 1; S->refine_steps += 1; S->refine_iter += 1;
+    }
 }
 
 // dst = src over the instance's SX (len_kind 0) or n (len_kind 1) entries.

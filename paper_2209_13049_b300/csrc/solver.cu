@@ -32,6 +32,21 @@ using namespace lqmpc;
 namespace lqmpc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+static int g_check = -1;
+void check_launch(cudaStream_t st, const char* what, const char* file, int line) {
+    if (g_check < 0) {
+        const char* e = getenv("LQMPC_CHECK");
+        g_check = (e && e[0] == '1') ? 1 : 0;
+    }
+    if (!g_check) return;
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        fprintf(stderr, "lqmpc check: %s / %s after %s (%s:%d)\n", cudaGetErrorString(e1), cudaGetErrorString(e2),
+                what, file, line);
+        fflush(stderr);
+    }
+}
 }  // namespace lqmpc
 
 struct lqmpc_ctx {
@@ -146,13 +161,14 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto M64 = c.take<double>((size_t)n * n); auto M32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto tmpx = c.take<double>(SX);
-    auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n));
+    auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n, I.N));
     auto r32 = c.take<float>(n);
     size_t ws_cc = (size_t)syrk_cc_tiles(n) * cc_splits * 64 * 64 * sizeof(double);
     size_t ws_tc = (size_t)syrk_tc_tiles(n) * tc_splits * 128 * 128 * sizeof(float);
     size_t ws = std::max(ws_cc, ws_tc);
     auto syrk_ws = c.take<unsigned char>(ws);
     auto part = c.take<double>((size_t)kParts * kMaxParts);
+    auto bar = c.take<unsigned>(2);
     auto sc = c.take<Scal>(1);
     auto trace = c.take<double>((size_t)(max_iter + 1) * kTraceW);
     if (kAssign) {
@@ -170,12 +186,10 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
-        I.part = part; I.sc = sc; I.trace = trace;
+        I.part = part; I.bar = bar; I.sc = sc; I.trace = trace;
     }
     return c.off;
 }
-
-bool is_mixed(int p) { return p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32 || p == LQMPC_FP32; }
 
 // A batch view over one or more contexts.
 struct Batch {
@@ -242,7 +256,17 @@ void kkt_solve_fp64(const Batch& b) {
     launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_DU, R_TMPX, F_NONE, b.st);
 }
 
-void kkt_solve_mixed(const Batch& b, int refine_max) {
+lqmpc_status read_scals(Batch& b) {
+    for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
+    CK(cudaStreamSynchronize(b.st));
+    return LQMPC_OK;
+}
+
+// Mixed-precision solve of M du = b (R_B -> R_DU, R_TMPX = Gamma du) with the
+// low-precision factor and FP64 iterative refinement.  The host looks at the
+// instance flags every second step and stops launching once every unfinished
+// instance has converged or failed; afterwards each h_scal holds the outcome.
+lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
     launch_refine_begin(b.d_insts, b.count, b.max_n, b.st);
     launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_B, R_DU, F_NONE, b.st);
     for (int s = 0; s <= refine_max; ++s) {
@@ -253,13 +277,17 @@ void kkt_solve_mixed(const Batch& b, int refine_max) {
         if (s == refine_max) break;
         launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
         launch_refine_update(b.d_insts, b.count, b.max_n, 0, b.st);
+        if (s % 2 == 0) {
+            lqmpc_status st = read_scals(b);
+            if (st != LQMPC_OK) return st;
+            bool pending = false;
+            for (auto* c : b.ctxs)
+                if (!c->h_scal->done && !c->h_scal->refine_ok && !c->h_scal->refine_fail && !c->h_scal->info)
+                    pending = true;
+            if (!pending) break;
+        }
     }
-}
-
-lqmpc_status read_scals(Batch& b) {
-    for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
-    CK(cudaStreamSynchronize(b.st));
-    return LQMPC_OK;
+    return read_scals(b);
 }
 
 // Per-solve preparation: y = Phi xbar, h = Gamma' Qbar y, initial point.
@@ -275,18 +303,26 @@ void prepare(const Batch& b, const lqmpc_options& o) {
                       b.st);
 }
 
-// Mixed-precision refinement failed for some unfinished instance: either
-// finish those instances with a status (no fallback) or switch the whole
-// batch to FP64 for the rest of the solve.  Returns true if FP64 is needed.
-bool handle_refine_failure(Batch& b, const lqmpc_options& o) {
-    bool need = false;
+int next_precision(int p) {
+    return (p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32) ? LQMPC_FP32 : LQMPC_FP64;
+}
+
+// After a refined solve: does some unfinished instance need a more accurate
+// factor (pivot failure or refinement that stalled / ran out of steps)?
+bool refine_failed(const Batch& b) {
     for (auto* c : b.ctxs)
-        if (!c->h_scal->done && (c->h_scal->info || !c->h_scal->refine_ok)) need = true;
-    if (!need) return false;
+        if (!c->h_scal->done && (c->h_scal->info || !c->h_scal->refine_ok)) return true;
+    return false;
+}
+
+// Without fallback: finish the failed instances with a status.  With
+// fallback: clear their pivot flag and count the switch (the caller moves the
+// whole batch to the next precision).
+void mark_failures(Batch& b, bool fallback) {
     for (auto* c : b.ctxs) {
         Scal fix = *c->h_scal;
         if (fix.done) continue;
-        if (!o.fallback) {
+        if (!fallback) {
             if (fix.info || !fix.refine_ok) {
                 fix.done = 1;
                 fix.status = fix.info ? LQMPC_ERR_NOT_PD : LQMPC_ERR_STALL;
@@ -294,24 +330,41 @@ bool handle_refine_failure(Batch& b, const lqmpc_options& o) {
         } else {
             fix.info = 0;
             fix.fallbacks += 1;
-            fix.use_fp64 = 1;
         }
         *c->h_scal = fix;
         cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
     }
-    return o.fallback != 0;
+}
+
+// Solve M du = b in the current precision `cur`, escalating BF16/TF32 ->
+// FP32 -> FP64 while refinement fails (if fallback is on).  `formed` says
+// whether M is already formed and factored in `cur`.
+lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, SyrkTimer* tm) {
+    for (;;) {
+        if (!formed) kkt_form(b, cur, tm);
+        if (cur == LQMPC_FP64) {
+            kkt_solve_fp64(b);
+            return LQMPC_OK;
+        }
+        lqmpc_status s = kkt_solve_mixed(b, o.refine_max);
+        if (s != LQMPC_OK) return s;
+        if (!refine_failed(b)) return LQMPC_OK;
+        mark_failures(b, o.fallback != 0);
+        if (!o.fallback) return LQMPC_OK;
+        cur = next_precision(cur);
+        formed = false;
+    }
 }
 
 lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* t_kkt) {
     const int prec = o.precision;
-    const bool mixed = is_mixed(prec);
-    if (mixed && prec != LQMPC_FP32 && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
+    if ((prec == LQMPC_MIXED_BF16 || prec == LQMPC_MIXED_TF32) && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
     lqmpc_ctx* c0 = b.ctxs[0];
     c0->t_tc = c0->t_cc = 0.0;
     c0->n_tc = c0->n_cc = 0;
     cudaEventRecord(c0->ev[0], b.st);
     prepare(b, o);
-    bool fp64_now = !mixed;
+    int cur = prec;          // sticky: once escalated, the rest of the solve stays there
     double kkt_ms = 0.0;
     for (int it = 0; it <= o.max_iter; ++it) {
         SyrkTimer tm;
@@ -321,21 +374,9 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
                          F_NONE, b.st);
         launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
         cudaEventRecord(c0->ev[2], b.st);
-        // predictor: M du_aff = b
-        if (fp64_now) {
-            kkt_form(b, LQMPC_FP64, &tm);
-            kkt_solve_fp64(b);
-        } else {
-            kkt_form(b, prec, &tm);
-            kkt_solve_mixed(b, o.refine_max);
-            lqmpc_status s = read_scals(b);
-            if (s != LQMPC_OK) return s;
-            if (handle_refine_failure(b, o)) {
-                fp64_now = true;
-                kkt_form(b, LQMPC_FP64, &tm);
-                kkt_solve_fp64(b);
-            }
-        }
+        // predictor: form and factor M, solve M du_aff = b
+        lqmpc_status s = kkt_step(b, o, cur, false, &tm);
+        if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX_AFF, 0, F_NONE, b.st);
         // affine step, sigma, corrector right-hand side
@@ -344,23 +385,13 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_WX, R_NONE, R_GW, R_NONE, 0,
                          F_NONE, b.st);
         launch_rhs(b.d_insts, b.count, b.max_n, b.st);
-        // corrector: M du = b with the same factor
-        if (fp64_now) {
-            kkt_solve_fp64(b);
-        } else {
-            kkt_solve_mixed(b, o.refine_max);
-            lqmpc_status s = read_scals(b);
-            if (s != LQMPC_OK) return s;
-            if (handle_refine_failure(b, o)) {
-                fp64_now = true;
-                kkt_form(b, LQMPC_FP64, &tm);
-                kkt_solve_fp64(b);
-            }
-        }
+        // corrector: same factor
+        s = kkt_step(b, o, cur, true, &tm);
+        if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
-        launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st);
-        lqmpc_status s = read_scals(b);
+        launch_step_update(b.d_insts, b.count, b.max_total, 1, cur, b.st);
+        s = read_scals(b);
         if (s != LQMPC_OK) return s;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]) == cudaSuccess) kkt_ms += ms;
@@ -447,7 +478,7 @@ lqmpc_options lqmpc_default_options(void) {
     o.tol = 1e-8;
     o.max_iter = 100;
     o.precision = LQMPC_FP64;
-    o.refine_max = 6;
+    o.refine_max = 10;
     o.refine_tol = 1e-10;
     o.fallback = 1;
     o.tau = 0.995;
@@ -824,7 +855,10 @@ lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* s
     CK(cudaMemcpyAsync(I.b, rhs, sizeof(double) * I.n, cudaMemcpyHostToDevice, b.st));
     kkt_form(b, precision);
     if (precision == LQMPC_FP64) kkt_solve_fp64(b);
-    else kkt_solve_mixed(b, ctx->opts.refine_max);
+    else {
+        lqmpc_status rs = kkt_solve_mixed(b, ctx->opts.refine_max);
+        if (rs != LQMPC_OK) return rs;
+    }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->h_scal, I.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
     CK(cudaStreamSynchronize(b.st));
