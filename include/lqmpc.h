@@ -66,7 +66,8 @@ typedef struct {
     double tol;          /* stop: max(||r_d||/(1+||h||), ||r_p||/(1+||d||), mu) <= tol; 1e-8 */
     int max_iter;        /* iteration limit; 100 */
     int precision;       /* LQMPC_FP64 (default) / LQMPC_MIXED_BF16 / LQMPC_MIXED_TF32 / LQMPC_FP32 */
-    int refine_max;      /* refinement steps per solve in the mixed modes; 10 */
+    int refine_max;      /* conjugate-gradient steps per KKT solve with an FP32 factor (30);
+                            BF16/TF32 factors get min(refine_max, 12) before escalating */
     double refine_tol;   /* refinement stops at ||b - M du||_inf <= refine_tol ||b||_inf (1e-10)
                             or <= 0.01 tol (1 + ||h||_inf), whichever is larger */
     int fallback;        /* 1: when refinement stalls (two steps that do not halve the residual)
@@ -172,8 +173,11 @@ lqmpc_status lqmpc_get_gstack(lqmpc_ctx* ctx, double* G);
 /* H = Gamma' Qbar Gamma + Rbar (n x n, column-major, FP64) built at setup. */
 lqmpc_status lqmpc_get_hessian(lqmpc_ctx* ctx, double* H);
 
-/* out = Gamma v (v: n, out: ns*N) and out = Gamma' w (w: ns*N, out: n), FP64,
- * using only the G-stack (the implicit Jacobian of the paper's conclusions). */
+/* out = Gamma v (v: n, out: ns*N) and out = Gamma' w (w: ns*N, out: n), using
+ * only the G-stack (the implicit Jacobian of the paper's conclusions), in the
+ * arithmetic the context's solves use: FP64 when opts.precision is
+ * LQMPC_FP64, float-float (two FP32 words per value, about 2^-44 relative per
+ * term) in the mixed-precision modes. */
 lqmpc_status lqmpc_gamma_mv(lqmpc_ctx* ctx, const double* v, double* out);
 lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out);
 

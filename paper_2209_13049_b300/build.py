@@ -50,7 +50,7 @@ def build(force: bool = False, jobs: int | None = None, verbose_ptxas: bool = Fa
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [NVCC, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcudart"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

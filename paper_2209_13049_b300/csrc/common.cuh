@@ -19,10 +19,16 @@ void note_launches(int k);
 // synchronisation and an error check that names the failing launch (debug
 // aid; off by default).
 void check_launch(cudaStream_t st, const char* what, const char* file, int line);
+// With LQMPC_PROFILE=1 every launch is bracketed by CUDA events and a
+// per-kernel table is printed to stderr after each solve (debug aid).
+cudaEvent_t prof_start(cudaStream_t st);
+void prof_stop(cudaStream_t st, cudaEvent_t e0, const char* what);
 #define LQ_LAUNCH(...)                                               \
     do {                                                             \
+        cudaEvent_t lq_e0_ = ::lqmpc::prof_start(st);                \
         __VA_ARGS__;                                                 \
         ::lqmpc::note_launches(1);                                   \
+        ::lqmpc::prof_stop(st, lq_e0_, #__VA_ARGS__);                \
         ::lqmpc::check_launch(st, #__VA_ARGS__, __FILE__, __LINE__); \
     } while (0)
 
@@ -36,6 +42,7 @@ struct Scal {
     double hnorm, dnorm, res_d, res_p, res;
     double tol, tau, refine_tol;
     double rnorm0, rnorm, rnorm_prev;   // refinement: ||b||, current and previous ||rho||
+    double pcg_rz, pcg_alpha;           // conjugate-gradient scalars r'z and the step
     int m;              // number of finite one-sided constraints
     int done;           // 1 once the stop test passed or the solve failed
     int status;         // lqmpc_status of the solve
@@ -72,7 +79,8 @@ struct Inst {
     // state elimination (G-stack in reversed block order, column-major, ld = ldg):
     // column (N-1-k)*nu + c holds (A^k B)[:, c]
     double* G64;
-    float* G32;
+    float* G32;                       // FP32 rounding of G64 (also the TF32 operand)
+    float* G32lo;                     // G64 - G32 in FP32 (float-float products)
     __nv_bfloat16* G16;
     double* H64;                      // n x n
     float* H32;                       // n x n
@@ -82,7 +90,7 @@ struct Inst {
     double *s1, *z1, *s2, *z2;        // SX: upper / lower state bound slacks and duals
     double *s3, *z3, *s4, *z4;        // n:  upper / lower input bound slacks and duals
     double *sigx, *sigu;              // SX, n
-    float* sigx32;                    // SX
+    float* sigx32;                    // N x ldg: FP32 Sigma_x, row r at r*ldg, zero padding
     double *wz, *wx;                  // SX: vectors for Gamma' products
     double *wzu, *wxu;                // n
     double *gz, *gw;                  // n: Gamma' outputs
@@ -90,13 +98,19 @@ struct Inst {
     double *ds1, *dz1, *ds2, *dz2;    // SX
     double *ds3, *dz3, *ds4, *dz4;    // n
     double* M64; float* M32;          // n x n
+    float* Xinv32;                    // n x n: inverse of the FP32 Cholesky factor (preconditioner)
+    float* XinvT32;                   // its transpose (coalesced rows)
+    float* Tinv32;                    // n x n scratch of the inversion
     double *rho, *dcorr;              // refinement: residual, correction (n)
     double* mv;                       // n: Gamma' output of matrix-free products
+    double *pp, *qq;                  // n: conjugate-gradient direction p and M p
+    double* dxs;                      // SX: Gamma du of the latest KKT solve
     double* tmpx;                     // SX scratch
     double* gpart;                    // Gamma' stage-1 partial sums
     float* r32;                       // n FP32 right-hand side
     void* syrk_ws;                    // split-K partial tiles
     size_t syrk_ws_bytes;
+    const int* tc_plan;               // tensor-core SYRK: per lower tile (splits, first partial)
     double* part;                     // kParts x kMaxParts reduction partials
     unsigned* bar;                    // grid-barrier state of cooperative launches (2 words)
     Scal* sc;
@@ -107,7 +121,7 @@ struct Inst {
 // every instance of a batch.
 enum Role : int {
     R_U = 0, R_X, R_Y, R_H, R_TMPX, R_WZ, R_WX, R_GZ, R_GW, R_DU, R_DX, R_DU_AFF, R_DX_AFF,
-    R_RHO, R_DCORR, R_B, R_RD, R_MV, R_NONE
+    R_RHO, R_DCORR, R_B, R_RD, R_MV, R_P, R_Q, R_DXS, R_NONE
 };
 
 __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
@@ -118,6 +132,7 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
         case R_DU: return I.du;      case R_DX: return I.dx;      case R_DU_AFF: return I.du_aff;
         case R_DX_AFF: return I.dx_aff; case R_RHO: return I.rho; case R_DCORR: return I.dcorr;
         case R_B: return I.b;        case R_RD: return I.rd;      case R_MV: return I.mv;
+        case R_P: return I.pp;       case R_Q: return I.qq;       case R_DXS: return I.dxs;
         default: return nullptr;
     }
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 namespace lqmpc {
 
 struct Inst;
@@ -29,6 +31,10 @@ size_t gamma_tmv_part_doubles(int ns, int n, int N);
 void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
                       int w0_role, int w1_role, int o0_role, int o1_role, int scale0, int force,
                       cudaStream_t st);
+void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
+                        int out_role, int flags, cudaStream_t st);
+void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
+                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st);
 void launch_ychain(const Inst* d_insts, int count, cudaStream_t st);
 void launch_qbar_y(const Inst* d_insts, int count, int max_sx, cudaStream_t st);
 void launch_q_times_g(const Inst* d_inst, const Inst& h, int use_qf, double* out, cudaStream_t st);
@@ -40,24 +46,31 @@ void launch_syrk_cc(const Inst* d_insts, int count, int max_n, int splits, int f
                     const double* gq, const double* gqf, int force, cudaStream_t st);
 void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, int part_kind,
                         int out_fp64, int base_mode, int add_sigu, int force, void* out_override,
-                        cudaStream_t st);
+                        cudaStream_t st, double shift = 0.0);
 void launch_h_to_f32(const Inst* d_inst, int n, cudaStream_t st);
 
 // kernels_chol.cu
-void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int force, cudaStream_t st);
+void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st,
+                  int want_inv = 0);
+void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
+                       cudaStream_t st);
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,
                        int out_role, int force, cudaStream_t st);
 
-// kernels_refine.cu
-void launch_refine_begin(const Inst* d_insts, int count, int max_n, cudaStream_t st);
-void launch_refine_residual(const Inst* d_insts, int count, int max_n, cudaStream_t st);
-void launch_refine_update(const Inst* d_insts, int count, int max_n, int last, cudaStream_t st);
+// kernels_refine.cu (preconditioned conjugate gradients on M du = b)
+void launch_pcg_begin(const Inst* d_insts, int count, cudaStream_t st);
+void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, cudaStream_t st);
+void launch_pcg_pinit(const Inst* d_insts, int count, cudaStream_t st);
+void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, cudaStream_t st);
+void launch_pcg_beta(const Inst* d_insts, int count, cudaStream_t st);
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
                      int len_kind, int force, cudaStream_t st);
 
 // kernels_tc.cu (tcgen05 tensor-core SYRK)
 int syrk_tc_tiles(int n);
 int syrk_tc_splits(int ns, int nu, int N);
+int syrk_tc_plan_partials(int ns, int nu, int N);
+std::vector<int> syrk_tc_make_plan(int ns, int nu, int N);
 bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out /* 128-byte CUtensorMap */);
 void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int tf32,
                     const void* d_maps, int force, cudaStream_t st);

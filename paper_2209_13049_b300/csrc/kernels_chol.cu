@@ -102,38 +102,63 @@ __device__ bool factor_diag(const Inst& I, T* M, int k, bool owner, T (*Ld)[kNb 
     return *fail_sh == 0;
 }
 
-// Panel k, row tile p (p == k: write the diagonal factor; p > k: solve the
-// tile rows against it).
+// Inverse of the factored 32 x 32 diagonal block (lower triangular), one
+// column per thread of warp 0: Li[c][c] = 1/L[c][c], then forward
+// substitution down the column.
 template <typename T>
-__device__ void panel_tile(const Inst& I, int k, int p, T (*Ld)[kNb + 1], int* fail_sh) {
+__device__ void invert_diag(T (*Ld)[kNb + 1], T (*Li)[kNb + 1]) {
+    __shared__ T rd[kNb];
+    if (threadIdx.x < kNb) rd[threadIdx.x] = T(1) / Ld[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < kNb) {
+        const int c = threadIdx.x;
+        for (int i = 0; i < c; ++i) Li[i][c] = T(0);
+        Li[c][c] = rd[c];
+        for (int i = c + 1; i < kNb; ++i) {
+            T acc = 0;
+            for (int m = c; m < i; ++m) acc += Ld[i][m] * Li[m][c];
+            Li[i][c] = -acc * rd[i];
+        }
+    }
+    __syncthreads();
+}
+
+// Panel k, row tile p.  Every CTA of the panel factors the diagonal block and
+// inverts it; p == k writes L_kk (and L_kk^{-1} into the inverse when one is
+// kept), p > k forms L_pk = A_pk L_kk^{-T} as a 32 x 32 x 32 product.
+template <typename T>
+__device__ void panel_tile(const Inst& I, int k, int p, T (*Ld)[kNb + 1], T (*Li)[kNb + 1], T (*A)[kNb + 1],
+                           int* fail_sh, T* X) {
     T* M = kkt_mat<T>(I);
     const int n = I.n, k0 = k * kNb, kn = min(kNb, n - k0);
     if (!factor_diag<T>(I, M, k, p == k, Ld, fail_sh)) return;
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        if (p == k) {
-            if (lane < kn)
-                for (int c = 0; c <= lane; ++c) M[(size_t)(k0 + lane) + (size_t)n * (k0 + c)] = Ld[lane][c];
-        } else {
-            const int row = p * kNb + lane;
-            if (row < n) {
-                T x[kNb];
-#pragma unroll
-                for (int c = 0; c < kNb; ++c) x[c] = c < kn ? M[(size_t)row + (size_t)n * (k0 + c)] : T(0);
-#pragma unroll
-                for (int c = 0; c < kNb; ++c) {
-                    if (c < kn) {
-                        T v = x[c];
-#pragma unroll
-                        for (int m = 0; m < c; ++m) v -= x[m] * Ld[c][m];
-                        x[c] = v / Ld[c][c];
-                    }
+    invert_diag<T>(Ld, Li);
+    if (p == k) {
+        for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+            const int r = e % kNb, c = e / kNb;
+            if (r < kn && c < kn && c <= r) {
+                M[(size_t)(k0 + r) + (size_t)n * (k0 + c)] = Ld[r][c];
+                if (X) {
+                    X[(size_t)(k0 + r) + (size_t)n * (k0 + c)] = Li[r][c];
+                    I.XinvT32[(size_t)(k0 + c) + (size_t)n * (k0 + r)] = (float)Li[r][c];
                 }
-#pragma unroll
-                for (int c = 0; c < kNb; ++c)
-                    if (c < kn) M[(size_t)row + (size_t)n * (k0 + c)] = x[c];
             }
         }
+        __syncthreads();
+        return;
+    }
+    const int p0 = p * kNb;
+    for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+        const int r = e % kNb, c = e / kNb;
+        A[r][c] = (p0 + r < n && c < kn) ? M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] : T(0);
+    }
+    __syncthreads();
+    // out[r][c] = sum_{m <= c} A[r][m] Li[c][m]
+    for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+        const int r = e % kNb, c = e / kNb;
+        T acc = 0;
+        for (int m = 0; m <= c; ++m) acc += A[r][m] * Li[c][m];
+        if (p0 + r < n && c < kn) M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] = acc;
     }
     __syncthreads();
 }
@@ -169,17 +194,76 @@ __device__ void update_tile(const Inst& I, int k, int p, int q, T (*Lp)[kNb + 1]
     __syncthreads();
 }
 
+// C (32 x 32 tile) = sum_{j in [j0, j1)} A_j B_j for tiles read from global
+// column-major n x n matrices: A_j = tile (ar, j) of Amat, B_j = tile (j, bc)
+// of Bmat (zero outside [0, n)).  The next pair of tiles is fetched into
+// registers while the current pair is multiplied.  Result in registers
+// (thread owns 4 entries: row threadIdx.x % 32, columns threadIdx.x / 32 + 8 e).
+template <typename T>
+__device__ void tile_chain(const T* Amat, const T* Bmat, int n, int ar, int bc, int j0, int j1,
+                           T (*As)[kNb + 1], T (*Bs)[kNb + 1], T acc[4]) {
+    const int r = threadIdx.x % kNb, cb = threadIdx.x / kNb;   // 256 threads: cb in 0..7
+    T pa[4], pb[4];
+    auto fetch = [&](int j) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = cb + 8 * e;
+            const int ra = ar * kNb + r, ca = j * kNb + c;
+            const int rb = j * kNb + r, cbb = bc * kNb + c;
+            pa[e] = (ra < n && ca < n) ? Amat[(size_t)ra + (size_t)n * ca] : T(0);
+            pb[e] = (rb < n && cbb < n) ? Bmat[(size_t)rb + (size_t)n * cbb] : T(0);
+        }
+    };
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = 0;
+    if (j0 >= j1) return;
+    fetch(j0);
+    for (int j = j0; j < j1; ++j) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { As[r][cb + 8 * e] = pa[e]; Bs[r][cb + 8 * e] = pb[e]; }
+        __syncthreads();
+        if (j + 1 < j1) fetch(j + 1);
+#pragma unroll 8
+        for (int m = 0; m < kNb; ++m) {
+            const T a = As[r][m];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] += a * Bs[m][cb + 8 * e];
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__device__ void store_tile(T* Mat, int n, int tr, int tc, const T acc[4], T scale, T* MatT = nullptr) {
+    const int r = threadIdx.x % kNb, cb = threadIdx.x / kNb;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int rr = tr * kNb + r, cc = tc * kNb + cb + 8 * e;
+        if (rr < n && cc < n) {
+            Mat[(size_t)rr + (size_t)n * cc] = scale * acc[e];
+            if (MatT) MatT[(size_t)cc + (size_t)n * rr] = scale * acc[e];
+        }
+    }
+}
+
 // Right-looking blocked Cholesky of every participating instance in one
-// cooperative launch: per panel, a panel phase (diagonal factor + panel
-// solve, one row tile per work item) and an update phase (one trailing tile
-// per work item), separated by grid barriers.  Instances are chosen once at
-// entry (not done, no earlier failure); a pivot failure only stops that
-// instance's own work.
+// cooperative launch: per panel, a panel phase (diagonal factor and inverse,
+// panel product, one row tile per work item) and an update phase (one
+// trailing tile per work item), separated by grid barriers.  Instances are
+// chosen once at entry (not done, no earlier failure); a pivot failure only
+// stops that instance's own work.
+//
+// With want_inv (the mixed-precision preconditioner) the kernel goes on to
+// form X = L^{-1} by recursive 2 x 2 blocking over the 32-tiles: at level l
+// (half size B = 2^l tiles) each pair of diagonal blocks [X11 0; X21 X22]
+// gets X21 = -X22 (L21 X11), computed as T = L21 X11 then X21 = -X22 T (two
+// barriered stages per level).  The diagonal tiles of X come from the panels.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ insts, int count, int max_nt,
-                                                    int flags) {
+                                                    int flags, int want_inv) {
     __shared__ T S1[kNb][kNb + 1];
     __shared__ T S2[kNb][kNb + 1];
+    __shared__ T S3[kNb][kNb + 1];
     __shared__ int fail_sh;
     unsigned* bar = insts[0].bar;
     int* err = &insts[0].sc->err;
@@ -201,7 +285,8 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
                 rem -= c;
             }
             const Inst& I = insts[q];
-            if (!I.sc->info) panel_tile<T>(I, k, k + rem, S1, &fail_sh);
+            T* X = (want_inv && sizeof(T) == 4) ? (T*)I.Xinv32 : nullptr;
+            if (!I.sc->info) panel_tile<T>(I, k, k + rem, S1, S2, S3, &fail_sh, X);
         }
         if (!grid_barrier(bar, err)) return;
         // update phase
@@ -228,6 +313,87 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
             update_tile<T>(I, k, k + 1 + a, k + 1 + b, S1, S2);
         }
         if (!grid_barrier(bar, err)) return;
+    }
+    if (!want_inv || sizeof(T) != 4) return;
+    // ---- X = L^{-1} by recursive doubling over the 32-tiles
+    for (int B = 1; B < max_nt; B <<= 1) {
+        for (int stage = 0; stage < 2; ++stage) {
+            // tasks: for each instance, each pair i (lo1 = 2 i B), each tile (p, c),
+            // p in [lo1 + B, min(lo1 + 2B, nt)), c in [lo1, lo1 + B)
+            int total = 0;
+            for (int q = 0; q < count; ++q) {
+                const Inst& I = insts[q];
+                if (skip_instance(I, flags)) continue;
+                const int nt = (I.n + kNb - 1) / kNb;
+                for (int lo1 = 0; lo1 + B < nt; lo1 += 2 * B) total += B * (min(lo1 + 2 * B, nt) - lo1 - B);
+            }
+            for (int item = blockIdx.x; item < total; item += gridDim.x) {
+                int q = 0, rem = item, lo1 = 0, np = 0;
+                bool found = false;
+                for (; q < count && !found; ++q) {
+                    const Inst& I = insts[q];
+                    if (skip_instance(I, flags)) continue;
+                    const int nt = (I.n + kNb - 1) / kNb;
+                    for (lo1 = 0; lo1 + B < nt; lo1 += 2 * B) {
+                        np = min(lo1 + 2 * B, nt) - lo1 - B;
+                        if (rem < B * np) { found = true; break; }
+                        rem -= B * np;
+                    }
+                    if (found) break;
+                }
+                const Inst& I = insts[q];
+                if (I.sc->info) continue;
+                const int p = lo1 + B + rem / B, c = lo1 + rem % B;
+                const float* L = I.M32;
+                float* X = I.Xinv32;
+                float* Tm = I.Tinv32;
+                T acc[4];
+                if (stage == 0) {   // T_pc = sum_{j = c}^{lo1 + B - 1} L_pj X_jc
+                    tile_chain<T>((const T*)L, (const T*)X, I.n, p, c, c, lo1 + B, S1, S2, acc);
+                    store_tile<T>((T*)Tm, I.n, p, c, acc, T(1));
+                } else {            // X_pc = -sum_{j = lo1 + B}^{p} X_pj T_jc
+                    tile_chain<T>((const T*)X, (const T*)Tm, I.n, p, c, lo1 + B, p + 1, S1, S2, acc);
+                    store_tile<T>((T*)X, I.n, p, c, acc, T(-1), (T*)I.XinvT32);
+                }
+            }
+            if (!grid_barrier(bar, err)) return;
+        }
+    }
+}
+
+// Preconditioner of the mixed-precision conjugate gradients: z = X' (X r)
+// with X = L^{-1} (FP32, lower).  Stage 1: t = X r, one thread per row
+// (coalesced along the column-major rows); stage 2: z = X' t, one warp per
+// column.
+__global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags) || I.sc->info) return;
+    const double* r = role_ptr(I, in_role);
+    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const float* XT = I.XinvT32;   // X' column-major: row i of X is contiguous
+    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
+        const float* row = XT + (size_t)n * i;
+        float acc = 0.f;
+        for (int j = lane; j <= i; j += 32) acc = fmaf(row[j], (float)r[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) I.r32[i] = acc;
+    }
+}
+
+__global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags) || I.sc->info) return;
+    double* z = role_ptr(I, out_role);
+    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const float* X = I.Xinv32;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
+        const float* col = X + (size_t)n * j;
+        float acc = 0.f;
+        for (int i = j + lane; i < n; i += 32) acc = fmaf(col[i], I.r32[i], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) z[j] = (double)acc;
     }
 }
 
@@ -271,14 +437,17 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nworkers = blockDim.x - 32, wid = threadIdx.x - 32;
 
-    // ---- forward: L y = b
+    // ---- forward: L y = b.  Warp 0 holds the current diagonal block in Ld
+    // and loads the next one while the other warps apply the update.
+    T Ld[kNb];
+    if (warp == 0) {
+        const int kn0 = min(kNb, n);
+#pragma unroll
+        for (int j = 0; j < kNb; ++j) Ld[j] = (lane < kn0 && j <= lane) ? L[(size_t)lane + (size_t)n * j] : T(0);
+    }
     for (int kb = 0; kb < nt; ++kb) {
         const int k0 = kb * kNb, kn = min(kNb, n - k0);
         if (warp == 0) {
-            T Ld[kNb];
-#pragma unroll
-            for (int j = 0; j < kNb; ++j)
-                Ld[j] = (lane < kn && j <= lane) ? L[(size_t)(k0 + lane) + (size_t)n * (k0 + j)] : T(0);
             T v = lane < kn ? y[k0 + lane] : T(0);
 #pragma unroll
             for (int j = 0; j < kNb; ++j) {
@@ -290,6 +459,12 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
                 }
             }
             if (lane < kn) y[k0 + lane] = v;
+            if (kb + 1 < nt) {   // prefetch the next diagonal block
+                const int k1 = k0 + kNb, kn1 = min(kNb, n - k1);
+#pragma unroll
+                for (int j = 0; j < kNb; ++j)
+                    Ld[j] = (lane < kn1 && j <= lane) ? L[(size_t)(k1 + lane) + (size_t)n * (k1 + j)] : T(0);
+            }
         }
         // rows below the block: prefetch the block's columns, then wait for y_k
         for (int base = k0 + kn; base < n; base += nworkers) {
@@ -310,25 +485,33 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
         if (k0 + kn >= n) __syncthreads();
         __syncthreads();
     }
-    // ---- backward: L' x = y
+    // ---- backward: L' x = y (columns of the diagonal block, prefetched likewise)
+    if (warp == 0) {
+        const int k0 = (nt - 1) * kNb, kn = n - k0;
+#pragma unroll
+        for (int i = 0; i < kNb; ++i)
+            Ld[i] = (lane < kn && i < kn && i >= lane) ? L[(size_t)(k0 + i) + (size_t)n * (k0 + lane)] : T(0);
+    }
     for (int kb = nt - 1; kb >= 0; --kb) {
         const int k0 = kb * kNb, kn = min(kNb, n - k0);
         if (warp == 0) {
-            T Lc[kNb];   // column 'lane' of the diagonal block: Lc[i] = L(k0+i, k0+lane)
-#pragma unroll
-            for (int i = 0; i < kNb; ++i)
-                Lc[i] = (lane < kn && i < kn && i >= lane) ? L[(size_t)(k0 + i) + (size_t)n * (k0 + lane)] : T(0);
             T v = lane < kn ? y[k0 + lane] : T(0);
 #pragma unroll
             for (int j = kNb - 1; j >= 0; --j) {
                 if (j < kn) {
-                    T diag = __shfl_sync(full, Lc[j], j);
+                    T diag = __shfl_sync(full, Ld[j], j);
                     T xj = __shfl_sync(full, v, j) / diag;
                     if (lane == j) v = xj;
-                    if (lane < j) v -= Lc[j] * xj;
+                    if (lane < j) v -= Ld[j] * xj;
                 }
             }
             if (lane < kn) y[k0 + lane] = v;
+            if (kb > 0) {   // prefetch the previous block's diagonal columns (full block)
+                const int km = k0 - kNb;
+#pragma unroll
+                for (int i = 0; i < kNb; ++i)
+                    Ld[i] = (i >= lane) ? L[(size_t)(km + i) + (size_t)n * (km + lane)] : T(0);
+            }
         }
         for (int base = 0; base < k0; base += nworkers) {
             const int i = base + wid;
@@ -353,7 +536,7 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
 
 // ---------------------------------------------------------------------------
 
-void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st) {
+void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st, int want_inv) {
     static int occ[2] = {0, 0}, sms = 0;
     const int nt = (max_n + kNb - 1) / kNb;
     if (!sms) {
@@ -367,14 +550,25 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
     long long cap = (long long)occ[fp64 ? 1 : 0] * sms;
     int grid = (int)(work < cap ? work : cap);
     if (grid < 1) grid = 1;
-    void* args[] = {(void*)&d_insts, (void*)&count, (void*)&nt, (void*)&flags};
+    void* args[] = {(void*)&d_insts, (void*)&count, (void*)&nt, (void*)&flags, (void*)&want_inv};
+    cudaEvent_t pe = prof_start(st);
     cudaError_t e;
     if (fp64)
         e = cudaLaunchCooperativeKernel((void*)k_potrf_coop<double>, dim3(grid), dim3(256), args, 0, st);
     else
         e = cudaLaunchCooperativeKernel((void*)k_potrf_coop<float>, dim3(grid), dim3(256), args, 0, st);
     note_launches(1);
+    prof_stop(st, pe, fp64 ? "k_potrf_coop<double>" : "k_potrf_coop<float>");
     check_launch(st, e == cudaSuccess ? "k_potrf_coop" : "k_potrf_coop (launch refused)", __FILE__, __LINE__);
+}
+
+void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
+                       cudaStream_t st) {
+    int nb = (max_n + 7) / 8;
+    nb = nb > 1024 ? 1024 : nb;
+    LQ_LAUNCH(k_prec_lower<<<dim3(nb, count), 256, 0, st>>>(d_insts, in_role, flags));
+    nb = nb > 1024 ? 1024 : nb;
+    LQ_LAUNCH(k_prec_upper<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags));
 }
 
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

@@ -11,6 +11,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace lqmpc {
 
 // G_0 = B into its column block (N-1)*nu.
@@ -46,7 +48,9 @@ __global__ void k_gstack_cast(const Inst* __restrict__ insts) {
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (size_t)gridDim.x * blockDim.x) {
         double g = I.G64[q];
-        if (I.G32) I.G32[q] = (float)g;
+        float gh = (float)g;
+        if (I.G32) I.G32[q] = gh;
+        if (I.G32lo) I.G32lo[q] = (float)(g - (double)gh);
         if (I.G16) I.G16[q] = __double2bfloat16(g);
     }
 }
@@ -190,6 +194,233 @@ __global__ void k_gamma_tmv_sum(const Inst* __restrict__ insts, int o0_role, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Float-float products (mixed-precision solves).  The G-stack is held as two
+// FP32 planes (G32 + G32lo = G to ~48 bits) and each input as hi + lo; the
+// products run on the FP32 pipes with error-free transformations (product
+// error by FMA, sum error by TwoSum), about 2^-44 relative per term instead
+// of FP64's 2^-53, at several times FP64's throughput on this part.
+//
+// Both products are small GEMMs with a block-triangular zero pattern:
+//   Gamma v :   Y[i, r]   = sum_col G[i, col] V[col, r],   V[col, r] = v[col - off_r] (col >= off_r)
+//   Gamma' w:   P[col, r] = sum_i   G[i, col] w_r[i],      needed where col >= off_r,
+//               out[t nu + c] = sum_{d} P[(N-1-d) nu + c, t + d]
+// with off_r = (N-1-r) nu.  Tiles entirely in the zero pattern are skipped;
+// split-K partials are reduced in a fixed order.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = sh + p;
+    const float z = s - sh;
+    const float t = (sh - (s - z)) + (p - z);
+    sh = s;
+    sl += t + e;
+}
+
+__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+constexpr int kFfBM = 64, kFfBN = 16, kFfBK = 32, kFfThreads = 128, kFfMaxSplits = 8;
+
+// Gamma v: block (m-tile of states, r-tile, split of the column range).
+__global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
+                                                            int out_role, int flags, int splits) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
+    const int mt = (ns + kFfBM - 1) / kFfBM, nt = (N + kFfBN - 1) / kFfBN;
+    const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
+    if (tile >= mt * nt) return;
+    const int m0 = (tile % mt) * kFfBM, r0 = (tile / mt) * kFfBN;
+    const int r1 = min(r0 + kFfBN, N);
+    const double* v = role_ptr(I, in_role);
+    // columns needed by this r-tile: col >= off_{r1-1}
+    const int kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
+    const int nk = (n - kbeg + kFfBK - 1) / kFfBK;
+    const int k0t = nk * split / splits, k1t = nk * (split + 1) / splits;
+    __shared__ float Gh[kFfBK][kFfBM], Gl[kFfBK][kFfBM];
+    __shared__ float Vh[kFfBK][kFfBN + 1], Vl[kFfBK][kFfBN + 1];
+    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;   // 8 x 16 threads: 2 r x 4 states each
+    float sh[4][2], sl[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
+    for (int kt = k0t; kt < k1t; ++kt) {
+        const int c0 = kbeg + kt * kFfBK;
+        for (int e = threadIdx.x; e < kFfBK * kFfBM; e += kFfThreads) {
+            const int kk = e / kFfBM, mm = e % kFfBM;
+            const int col = c0 + kk, i = m0 + mm;
+            float h = 0.f, l = 0.f;
+            if (col < n && i < ns) {
+                h = I.G32[(size_t)ldg * col + i];
+                l = I.G32lo[(size_t)ldg * col + i];
+            }
+            Gh[kk][mm] = h;
+            Gl[kk][mm] = l;
+        }
+        for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
+            const int kk = e / kFfBN, rr = e % kFfBN;
+            const int col = c0 + kk, r = r0 + rr;
+            float h = 0.f, l = 0.f;
+            if (col < n && r < N) {
+                const int t = col - (N - 1 - r) * nu;
+                if (t >= 0) split_ff(v[t], h, l);
+            }
+            Vh[kk][rr] = h;
+            Vl[kk][rr] = l;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kFfBK; ++kk) {
+            float ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) { ah[a] = Gh[kk][ty + 16 * a]; al[a] = Gl[kk][ty + 16 * a]; }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) { bh[b] = Vh[kk][tx + 8 * b]; bl[b] = Vl[kk][tx + 8 * b]; }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) ff_mac(sh[a][b], sl[a][b], ah[a], al[a], bh[b], bl[b]);
+        }
+        __syncthreads();
+    }
+    // partial[split][r][i]
+    double* part = I.gpart + (size_t)split * I.SX;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
+            if (i < ns && r < r1) part[(size_t)r * ns + i] = (double)sh[a][b] + (double)sl[a][b];
+        }
+    (void)out_role;
+}
+
+__global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, int flags, int splits) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    double* out = role_ptr(I, out_role);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int q = 0; q < splits; ++q) s += I.gpart[(size_t)q * I.SX + k];
+        out[k] = s;
+    }
+}
+
+// Gamma' w for NV vectors: P[col, r'] over r' = vec * N + r, K = states.
+template <int NV>
+__global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restrict__ insts, int w0_role,
+                                                             int w1_role, int scale0, int flags, int splits) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
+    const int NR = NV * N;
+    const int mt = (n + kFfBM - 1) / kFfBM, nt = (NR + kFfBN - 1) / kFfBN;
+    const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
+    if (tile >= mt * nt) return;
+    const int c0 = (tile % mt) * kFfBM, rp0 = (tile / mt) * kFfBN;
+    // skip tiles wholly in the unused triangle: need some col >= off_r
+    {
+        bool any = false;
+        for (int rp = rp0; rp < min(rp0 + kFfBN, NR) && !any; ++rp) {
+            const int r = rp % N;
+            if (min(c0 + kFfBM, n) - 1 >= (N - 1 - r) * nu) any = true;
+        }
+        if (!any) return;
+    }
+    const double* w0 = role_ptr(I, w0_role);
+    const double* w1 = NV > 1 ? role_ptr(I, w1_role) : nullptr;
+    const int nk = (ns + kFfBK - 1) / kFfBK;
+    const int k0t = nk * split / splits, k1t = nk * (split + 1) / splits;
+    __shared__ float Gh[kFfBM][kFfBK + 1], Gl[kFfBM][kFfBK + 1];   // [col][state]: conflict-free stores
+    __shared__ float Wh[kFfBK][kFfBN + 1], Wl[kFfBK][kFfBN + 1];
+    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;
+    float sh[4][2], sl[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
+    for (int kt = k0t; kt < k1t; ++kt) {
+        const int i0 = kt * kFfBK;
+        for (int e = threadIdx.x; e < kFfBK * kFfBM; e += kFfThreads) {
+            const int mm = e / kFfBK, kk = e % kFfBK;    // consecutive threads: consecutive states
+            const int col = c0 + mm, i = i0 + kk;
+            float h = 0.f, l = 0.f;
+            if (col < n && i < ns) {
+                h = I.G32[(size_t)ldg * col + i];
+                l = I.G32lo[(size_t)ldg * col + i];
+            }
+            Gh[mm][kk] = h;
+            Gl[mm][kk] = l;
+        }
+        for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
+            const int rr = e / kFfBK, kk = e % kFfBK;
+            const int rp = rp0 + rr, i = i0 + kk;
+            float h = 0.f, l = 0.f;
+            if (rp < NR && i < ns) {
+                const int vec = rp / N, r = rp % N;
+                double wv = (vec == 0 ? w0 : w1)[(size_t)r * ns + i];
+                if (vec == 0 && scale0) wv *= I.sigx[(size_t)r * ns + i];
+                split_ff(wv, h, l);
+            }
+            Wh[kk][rr] = h;
+            Wl[kk][rr] = l;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kFfBK; ++kk) {
+            float ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) { ah[a] = Gh[ty + 16 * a][kk]; al[a] = Gl[ty + 16 * a][kk]; }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) { bh[b] = Wh[kk][tx + 8 * b]; bl[b] = Wl[kk][tx + 8 * b]; }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) ff_mac(sh[a][b], sl[a][b], ah[a], al[a], bh[b], bl[b]);
+        }
+        __syncthreads();
+    }
+    // partial[split][r'][col]
+    double* part = I.gpart + (size_t)split * NR * n;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int col = c0 + ty + 16 * a, rp = rp0 + tx + 8 * b;
+            if (col < n && rp < NR) part[(size_t)rp * n + col] = (double)sh[a][b] + (double)sl[a][b];
+        }
+}
+
+// out[t nu + c] = sum_split sum_{d=0}^{N-1-t} P[(N-1-d) nu + c, t + d]; one
+// warp per output, lanes over (split, d), then a fixed-order warp reduction.
+template <int NV>
+__global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags,
+                                   int splits) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int nu = I.nu, N = I.N, n = I.n, NR = NV * N;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < NV * n; q += gridDim.x * wpb) {
+        const int vec = q / n, j = q % n, t = j / nu, c = j % nu;
+        const int nd = N - t;
+        double s = 0.0;
+        for (int e = lane; e < splits * nd; e += 32) {
+            const int sp = e / nd, d = e % nd;
+            s += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
+        }
+        s = warp_sum(s);
+        if (lane == 0) (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
+    }
+}
+
 // y_t = A^t xbar for t = 1..N (one block per instance, sequential in t).
 __global__ void k_ychain(const Inst* __restrict__ insts) {
     const Inst& I = insts[blockIdx.y];
@@ -264,7 +495,10 @@ void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int 
 }
 
 size_t gamma_tmv_part_doubles(int ns, int n, int N) {
-    return (size_t)2 * tmv_groups(N) * ((ns + kTmvChunk - 1) / kTmvChunk) * n;
+    size_t fp64 = (size_t)2 * tmv_groups(N) * ((ns + kTmvChunk - 1) / kTmvChunk) * n;
+    size_t ff_mv = (size_t)kFfMaxSplits * ns * N;
+    size_t ff_tmv = (size_t)kFfMaxSplits * 2 * N * n;
+    return std::max(fp64, std::max(ff_mv, ff_tmv));
 }
 
 void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
@@ -279,6 +513,39 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
     } else {
         LQ_LAUNCH(k_gamma_tmv_part<1><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags));
         LQ_LAUNCH(k_gamma_tmv_sum<1><<<dim3(nbs, count), 256, 0, st>>>(d_insts, o0_role, R_NONE, flags));
+    }
+}
+
+static int ff_splits(int tiles, int nk) {
+    int s = (2 * 148 + tiles - 1) / (tiles > 0 ? tiles : 1);
+    if (s > nk) s = nk;
+    if (s > kFfMaxSplits) s = kFfMaxSplits;
+    return s < 1 ? 1 : s;
+}
+
+void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
+                        int out_role, int flags, cudaStream_t st) {
+    const int tiles = ((max_ns + kFfBM - 1) / kFfBM) * ((max_N + kFfBN - 1) / kFfBN);
+    const int splits = ff_splits(tiles * count, (max_n + kFfBK - 1) / kFfBK);
+    LQ_LAUNCH(k_gamma_mv_ff<<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
+    int nb = (max_ns * max_N + 255) / 256;
+    nb = nb > 4096 ? 4096 : nb;
+    LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits));
+}
+
+void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
+                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st) {
+    const int NV = w1_role != R_NONE ? 2 : 1;
+    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
+    const int splits = ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
+    int nb = (NV * max_n + 7) / 8;
+    nb = nb > 4096 ? 4096 : nb;
+    if (NV == 2) {
+        LQ_LAUNCH(k_gamma_tmv_ff<2><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags, splits));
+        LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 256, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));
+    } else {
+        LQ_LAUNCH(k_gamma_tmv_ff<1><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags, splits));
+        LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 256, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
     }
 }
 

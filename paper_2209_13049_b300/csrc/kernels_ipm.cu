@@ -154,7 +154,7 @@ __global__ void k_resid(const Inst* __restrict__ insts) {
         double wz = zu - zl;
         double wx = (zu - sgu * rpu) - (zl - sgl * rpl);
         if (k < I.SX) {
-            I.sigx[k] = sgu + sgl; I.sigx32[k] = (float)(sgu + sgl);
+            I.sigx[k] = sgu + sgl; I.sigx32[(size_t)(k / I.ns) * I.ldg + k % I.ns] = (float)(sgu + sgl);
             I.wz[k] = wz; I.wx[k] = wx;
         } else {
             int j = k - I.SX;

@@ -1,17 +1,29 @@
-// Iterative refinement of the mixed-precision KKT solve.
+// Accuracy recovery for the mixed-precision KKT solve: preconditioned
+// conjugate gradients on M du = b (M symmetric positive definite, Eq. 7) with
+// the low-precision Cholesky factor as preconditioner and every product with
+// M evaluated matrix-free in FP64:
+//     M p = H p + Gamma'(Sigma_x (Gamma p)) + Sigma_u p
+// (M itself is never formed in FP64).  Started from x0 = Mlow^{-1} b, the
+// first residual is that of plain iterative refinement; conjugate directions
+// keep converging when the low-precision factor is too inaccurate for the
+// stationary iteration to contract.  Gamma du is accumulated alongside
+// (dxs += alpha Gamma p) so the step recovery needs no extra product.
 //
-// M du = b is solved with the low-precision Cholesky factor; the residual
-//     rho = b - (H du + Gamma'(Sigma_x (Gamma du)) + Sigma_u du)
-// is evaluated matrix-free in FP64 (M itself is never formed in FP64), the
-// correction solve uses the same factor, and the loop stops when
-// ||rho||_inf <= refine_tol * ||b||_inf.  Every kernel is predicated on the
-// instance flags, so a fixed launch sequence serves any number of steps.
+// Stop: ||r||_inf <= refine_tol ||b||_inf, or <= 0.01 tol (1 + ||h||_inf) (the
+// stationarity residual left behind is then far below the stop test).
+// Failure: a non-positive curvature p'Mp or a non-finite value.  Every kernel
+// is predicated on the instance flags, so one launch sequence serves any
+// number of steps and any batch.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lqmpc {
 
-__global__ void k_refine_begin(const Inst* __restrict__ insts) {
+__device__ __forceinline__ bool pcg_skip(const Scal* S) {
+    return S->done || S->refine_ok || S->refine_fail;
+}
+
+__global__ void k_pcg_begin(const Inst* __restrict__ insts) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -25,64 +37,127 @@ __global__ void k_refine_begin(const Inst* __restrict__ insts) {
     }
 }
 
-// rho_j = b_j - (H du)_j - mv_j - sigu_j du_j, mv = Gamma'(Sigma_x Gamma du).
-// One warp per row; slot 6 partial = max |rho|.
-__global__ void k_refine_resid(const Inst* __restrict__ insts, int du_role) {
+// out_j = (H v)_j + mv_j + sigu_j v_j with mv = Gamma'(Sigma_x Gamma v); one
+// warp per row.  mode 0 (initial residual): r = b - M du, partial max|r| in
+// slot 6.  mode 1 (CG step): q = M p, partial p'q in slot 6.
+__global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    const Scal* S = I.sc;
-    if (S->done || S->refine_ok || S->refine_fail) return;
-    const double* du = role_ptr(I, du_role);
+    if (pcg_skip(I.sc)) return;
+    const double* v = mode == 0 ? I.du : I.pp;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    double rmax = 0.0;
+    double acc_red = 0.0;
     for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < I.n; j += gridDim.x * wpb) {
         const double* hc = I.H64 + (size_t)j * I.n;
         double acc = 0.0;
-        for (int k = lane; k < I.n; k += 32) acc += hc[k] * du[k];
+        for (int k = lane; k < I.n; k += 32) acc += hc[k] * v[k];
         acc = warp_sum(acc);
         if (lane == 0) {
-            double r = I.b[j] - acc - I.mv[j] - I.sigu[j] * du[j];
-            I.rho[j] = r;
-            rmax = fmax(rmax, fabs(r));
+            double mvj = acc + I.mv[j] + I.sigu[j] * v[j];
+            if (mode == 0) {
+                double r = I.b[j] - mvj;
+                I.rho[j] = r;
+                acc_red = fmax(acc_red, fabs(r));
+            } else {
+                I.qq[j] = mvj;
+                acc_red += v[j] * mvj;
+            }
         }
     }
-    double v = block_reduce<1>(rmax, red);
-    if (threadIdx.x == 0) I.part[6 * kMaxParts + blockIdx.x] = v;
+    double t = mode == 0 ? block_reduce<1>(acc_red, red) : block_reduce<0>(acc_red, red);
+    if (threadIdx.x == 0) I.part[6 * kMaxParts + blockIdx.x] = t;
 }
 
-__global__ void k_refine_check(const Inst* __restrict__ insts, int nb) {
+// Convergence test on the residual norm.
+__device__ void pcg_test(const Inst& I, double rn) {
+    Scal* S = I.sc;
+    S->rnorm = rn;
+    if (!(rn == rn)) { S->refine_fail = 1; return; }
+    const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
+    if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || S->rnorm0 == 0.0) S->refine_ok = 1;
+}
+
+__global__ void k_pcg_check(const Inst* __restrict__ insts, int nb, int slot) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (pcg_skip(I.sc)) return;
+    double m = 0.0;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) m = fmax(m, I.part[slot * kMaxParts + p]);
+    m = block_reduce<1>(m, red);
+    if (threadIdx.x == 0) pcg_test(I, m);
+}
+
+// p = z, rz = r'z (one block per instance).
+__global__ void k_pcg_pinit(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (pcg_skip(I.sc)) return;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
+        I.pp[j] = I.dcorr[j];
+        s += I.rho[j] * I.dcorr[j];
+    }
+    s = block_reduce<0>(s, red);
+    if (threadIdx.x == 0) I.sc->pcg_rz = s;
+}
+
+// alpha = r'z / p'Mp; a non-positive curvature marks failure.
+__global__ void k_pcg_alpha(const Inst* __restrict__ insts, int nb) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done || S->refine_ok || S->refine_fail) return;
-    double m = 0.0;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) m = fmax(m, I.part[6 * kMaxParts + p]);
-    m = block_reduce<1>(m, red);
+    if (pcg_skip(S)) return;
+    double s = 0.0;
+    for (int p = threadIdx.x; p < nb; p += blockDim.x) s += I.part[6 * kMaxParts + p];
+    s = block_reduce<0>(s, red);
     if (threadIdx.x == 0) {
-        S->rnorm = m;
-        if (!(m == m)) { S->refine_fail = 1; return; }
-        // converged: relative to ||b||, or small enough that the stationarity
-        // residual it leaves behind is far below the stop tolerance
-        const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
-        if (m <= S->refine_tol * S->rnorm0 || m <= floor_abs || S->rnorm0 == 0.0) { S->refine_ok = 1; return; }
-        if (m > 0.5 * S->rnorm_prev) S->stalled += 1;
-        else S->stalled = 0;
-        if (S->stalled >= 2) S->refine_fail = 1;
-        S->rnorm_prev = m;
+        if (!(s > 0.0) || !(S->pcg_rz == S->pcg_rz)) { S->refine_fail = 1; return; }
+        S->pcg_alpha = S->pcg_rz / s;
+        S->refine_cur += 1; S->refine_steps += 1; S->refine_iter += 1;
     }
 }
 
-__global__ void k_refine_update(const Inst* __restrict__ insts, int du_role, int last) {
+// du += alpha p, r -= alpha q (input rows), dxs += alpha (Gamma p) (state
+// rows).  Partial max|r| in slot 7.
+__global__ void k_pcg_axpy(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (pcg_skip(I.sc)) return;
+    const double al = I.sc->pcg_alpha;
+    const int total = I.SX + I.n;
+    double rmax = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
+        if (k < I.n) {
+            I.du[k] += al * I.pp[k];
+            double r = I.rho[k] - al * I.qq[k];
+            I.rho[k] = r;
+            rmax = fmax(rmax, fabs(r));
+        } else {
+            const int q = k - I.n;
+            I.dxs[q] += al * I.tmpx[q];
+        }
+    }
+    double v = block_reduce<1>(rmax, red);
+    if (threadIdx.x == 0) I.part[7 * kMaxParts + blockIdx.x] = v;
+}
+
+// beta = r'z_new / r'z_old; p = z + beta p (one block per instance).
+__global__ void k_pcg_beta(const Inst* __restrict__ insts) {
+    __shared__ double red[32];
+    __shared__ double beta_sh;
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done || S->refine_ok || S->refine_fail) return;
-    double* du = role_ptr(I, du_role);
-    if (!last)
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x)
-            du[j] += I.dcorr[j];
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !last) {
-        S->refine_cur += 1; S->refine_steps += 1; S->refine_iter += 1;
+    if (pcg_skip(S)) return;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) s += I.rho[j] * I.dcorr[j];
+    s = block_reduce<0>(s, red);
+    if (threadIdx.x == 0) {
+        beta_sh = S->pcg_rz != 0.0 ? s / S->pcg_rz : 0.0;
+        S->pcg_rz = s;
     }
+    __syncthreads();
+    const double be = beta_sh;
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) I.pp[j] = I.dcorr[j] + be * I.pp[j];
 }
 
 // dst = src over the instance's SX (len_kind 0) or n (len_kind 1) entries.
@@ -101,20 +176,31 @@ static int nblk(int len, int th, int cap) {
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-void launch_refine_begin(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
-    LQ_LAUNCH(k_refine_begin<<<dim3(1, count), 256, 0, st>>>(d_insts));
+void launch_pcg_begin(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts));
 }
 
-// one residual evaluation: rho = b - M du (needs tmpx = Gamma du and mv = Gamma'(Sigma tmpx))
-void launch_refine_residual(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
+// mode 0: r = b - M du and its convergence test; mode 1: q = M p and alpha.
+void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, cudaStream_t st) {
     int wpb = 8;
     int nb = nblk(max_n, wpb, kMaxParts);
-    LQ_LAUNCH(k_refine_resid<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, R_DU));
-    LQ_LAUNCH(k_refine_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb));
+    LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode));
+    if (mode == 0) LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 6));
+    else LQ_LAUNCH(k_pcg_alpha<<<dim3(1, count), 256, 0, st>>>(d_insts, nb));
 }
 
-void launch_refine_update(const Inst* d_insts, int count, int max_n, int last, cudaStream_t st) {
-    LQ_LAUNCH(k_refine_update<<<dim3(nblk(max_n, 256, 1024), count), 256, 0, st>>>(d_insts, R_DU, last));
+void launch_pcg_pinit(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_pinit<<<dim3(1, count), 256, 0, st>>>(d_insts));
+}
+
+void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
+    int nb = nblk(max_total, 256, kMaxParts);
+    LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 7));
+}
+
+void launch_pcg_beta(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_beta<<<dim3(1, count), 256, 0, st>>>(d_insts));
 }
 
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts,
         const int i = i0 + lk;
         T d = 0;
         if (i < ns) {
-            if (mode == 0) d = sizeof(T) == 8 ? (T)I.sigx[(size_t)r * ns + i] : (T)I.sigx32[(size_t)r * ns + i];
+            if (mode == 0) d = sizeof(T) == 8 ? (T)I.sigx[(size_t)r * ns + i] : (T)I.sigx32[(size_t)r * I.ldg + i];
             else if (mode == 1) d = (T)(r == N - 1 ? I.qfd[i] : I.qd[i]);
             else d = 1;
         }
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts,
 // TILE the tile edge of the partial layout.
 template <typename TP, typename Tout, int TILE, bool COLMAJOR = false>
 __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int base_mode,
-                              int add_sigu, int force, Tout* out_override) {
+                              int add_sigu, int force, Tout* out_override, double shift) {
     const Inst& I = insts[blockIdx.y];
     if (!force && I.sc->done) return;
     if (!force && I.sc->info) return;
@@ -125,10 +125,12 @@ __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int ba
         int p = j > k ? j : k, m = j > k ? k : j;
         int a = p / TILE, b = m / TILE;
         int t = a * (a + 1) / 2 + b;
-        const TP* src = ws + (size_t)t * splits * TILE * TILE +
+        int first = t * splits, cnt = splits;
+        if (COLMAJOR) { cnt = I.tc_plan[2 * t]; first = I.tc_plan[2 * t + 1]; }   // tensor-core plan
+        const TP* src = ws + (size_t)first * TILE * TILE +
                         (COLMAJOR ? (m % TILE) * TILE + (p % TILE) : (p % TILE) * TILE + (m % TILE));
         double acc = 0.0;
-        for (int s = 0; s < splits; ++s) acc += (double)src[(size_t)s * TILE * TILE];
+        for (int s = 0; s < cnt; ++s) acc += (double)src[(size_t)s * TILE * TILE];
         double base = 0.0;
         if (base_mode == 0) base = sizeof(Tout) == 8 ? I.H64[q] : (double)I.H32[q];
         else if (base_mode == 1) {
@@ -136,6 +138,7 @@ __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int ba
         }
         double v = base + acc;
         if (add_sigu && j == k) v += I.sigu[j];
+        if (j == k) v *= 1.0 + shift;   // relative diagonal shift of a retried low-precision factor
         M[q] = (Tout)v;
     }
 }
@@ -176,20 +179,20 @@ void launch_syrk_cc(const Inst* d_insts, int count, int max_n, int splits, int f
 
 void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, int part_kind,
                         int out_fp64, int base_mode, int add_sigu, int force, void* out_override,
-                        cudaStream_t st) {
+                        cudaStream_t st, double shift) {
     size_t total = (size_t)max_n * max_n;
     int nb = (int)((total + 255) / 256);
     nb = nb > 4096 ? 4096 : nb;
     dim3 grid(nb, count);
     if (part_kind == 0) {        // FP64 partials, 64-tiles
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<double, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override));
-        else LQ_LAUNCH(k_syrk_reduce<double, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override));
+        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<double, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(k_syrk_reduce<double, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     } else if (part_kind == 1) { // FP32 partials, 64-tiles
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override));
-        else LQ_LAUNCH(k_syrk_reduce<float, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override));
+        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(k_syrk_reduce<float, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     } else {                     // FP32 partials, 128-tiles, column-major (tensor-core SYRK)
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override));
-        else LQ_LAUNCH(k_syrk_reduce<float, float, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override));
+        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(k_syrk_reduce<float, float, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     }
 }
 

@@ -76,6 +76,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* map, int x
         : "memory");
 }
 
+// 1-D bulk copy global -> shared (both 16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // K-major operand tile, 128-byte swizzle: rows of 128 bytes, 8-row groups of
 // 1024 bytes (stride byte offset), descriptor version 1 (sm_100 family).
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
@@ -141,14 +148,19 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     __shared__ int issued_sh;
+    __shared__ __align__(16) float Ds[kStages][64];   // Sigma_x segment of each stage
 
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     const int n = I.n, ns = I.ns, nu = I.nu, N = I.N;
     const int nt = (n + kTcTile - 1) / kTcTile;
     const int ntiles = nt * (nt + 1) / 2;
-    const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
+    // balanced split-K plan: tile t owns partials [plan[2t+1], plan[2t+1] + plan[2t])
+    int tile = 0;
+    while (tile < ntiles && blockIdx.x >= I.tc_plan[2 * tile + 1] + I.tc_plan[2 * tile]) ++tile;
     if (tile >= ntiles) return;
+    const int nsplit = I.tc_plan[2 * tile], split = blockIdx.x - I.tc_plan[2 * tile + 1];
+    (void)splits;
     int a = 0;
     while ((a + 1) * (a + 2) / 2 <= tile) ++a;
     const int b = tile - a * (a + 1) / 2;
@@ -156,7 +168,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
     const int rmin = (a * kTcTile) / nu;
     const int nkc = (ns + KC - 1) / KC;
     const long long nchunks = (long long)(N - rmin) * nkc;
-    const int c0 = (int)(nchunks * split / splits), c1 = (int)(nchunks * (split + 1) / splits);
+    const int c0 = (int)(nchunks * split / nsplit), c1 = (int)(nchunks * (split + 1) / nsplit);
     const int nq = c1 - c0;
 
     // 1024-byte aligned stage buffers
@@ -199,9 +211,11 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 const int off = (N - 1 - r) * nu;
                 unsigned char* st = sbase + (size_t)s * kStageBytes;
                 const uint32_t fb = smem_u32(&bar_full[s]);
-                mbar_expect_tx(fb, kStageBytes);
+                mbar_expect_tx(fb, kStageBytes + KC * 4);
                 tma_load_2d(smem_u32(st), map, i0, off + a * kTcTile, fb);
                 tma_load_2d(smem_u32(st + kStageBytes / 2), map, i0, off + b * kTcTile, fb);
+                // Sigma_x[r, i0 : i0 + KC] (zero-padded rows of ldg floats, 16-byte aligned)
+                bulk_load(smem_u32(&Ds[s][0]), I.sigx32 + (size_t)r * I.ldg + i0, KC * 4, fb);
                 ++issued;
             }
             issued_sh = issued;
@@ -232,10 +246,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
         for (int q = 0; q < nq; ++q) {
             const int s = q % kStages, round = q / kStages;
             if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, abort_flag)) break;
-            const int ch = c0 + q;
-            const int r = rmin + ch / nkc;
-            const int i0 = (ch % nkc) * KC;
-            const float* D = I.sigx32 + (size_t)r * ns;
+            const float* D = &Ds[s][0];
             unsigned char* rowp = sbase + (size_t)s * kStageBytes + kStageBytes / 2 + (size_t)t * 128;
 #pragma unroll
             for (int lc = 0; lc < 8; ++lc) {
@@ -243,23 +254,18 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 uint4* cp = reinterpret_cast<uint4*>(rowp + p * 16);
                 uint4 v = *cp;
                 if (TF32) {
-                    const int kb = i0 + lc * 4;
+                    const float4 d = *reinterpret_cast<const float4*>(D + lc * 4);
                     float* f = reinterpret_cast<float*>(&v);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        float d = (kb + e < ns) ? __ldg(D + kb + e) : 0.0f;
-                        f[e] *= d;
-                    }
+                    f[0] *= d.x; f[1] *= d.y; f[2] *= d.z; f[3] *= d.w;
                 } else {
-                    const int kb = i0 + lc * 8;
+                    const float4 d0 = *reinterpret_cast<const float4*>(D + lc * 8);
+                    const float4 d1 = *reinterpret_cast<const float4*>(D + lc * 8 + 4);
                     __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&v);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        float d0 = (kb + 2 * e < ns) ? __ldg(D + kb + 2 * e) : 0.0f;
-                        float d1 = (kb + 2 * e + 1 < ns) ? __ldg(D + kb + 2 * e + 1) : 0.0f;
-                        float2 f = __bfloat1622float2(h2[e]);
-                        h2[e] = __floats2bfloat162_rn(f.x * d0, f.y * d1);
-                    }
+                    float2 f;
+                    f = __bfloat1622float2(h2[0]); h2[0] = __floats2bfloat162_rn(f.x * d0.x, f.y * d0.y);
+                    f = __bfloat1622float2(h2[1]); h2[1] = __floats2bfloat162_rn(f.x * d0.z, f.y * d0.w);
+                    f = __bfloat1622float2(h2[2]); h2[2] = __floats2bfloat162_rn(f.x * d1.x, f.y * d1.y);
+                    f = __bfloat1622float2(h2[3]); h2[3] = __floats2bfloat162_rn(f.x * d1.z, f.y * d1.w);
                 }
                 *cp = v;
             }
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
             mbar_arrive(smem_u32(&bar_scaled[s]));
         }
         // ---------------- epilogue: TMEM -> partial tile (column-major)
-        float* ws = (float*)I.syrk_ws + ((size_t)tile * splits + split) * kTcTile * kTcTile;
+        float* ws = (float*)I.syrk_ws + (size_t)blockIdx.x * kTcTile * kTcTile;
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         bool have = nq > 0 && mbar_wait(smem_u32(&bar_acc), 0, abort_flag);
@@ -323,6 +329,53 @@ int syrk_tc_splits(int ns, int nu, int N) {
     return s < 1 ? 1 : s;
 }
 
+static int g_sms = 0;
+static int sm_count() {
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_sms < 1)
+            g_sms = 148;
+    }
+    return g_sms;
+}
+
+// Split-K plan of the tensor-core SYRK: lower tile t of the 128-tiling gets
+// max(1, G chunks_t / C) CTAs (C = all chunks, G = number of SMs), so the
+// grid is about one wave and every CTA gets about the same number of K chunks.
+// Layout: plan[2t] = splits, plan[2t+1] = first partial; plan[2 ntiles] = total.
+std::vector<int> syrk_tc_make_plan(int ns, int nu, int N) {
+    const int n = nu * N, nt = (n + kTcTile - 1) / kTcTile, ntiles = nt * (nt + 1) / 2;
+    const long long nkc = (ns + 63) / 64;
+    std::vector<long long> ch(ntiles);
+    long long C = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= t) ++a;
+        const int rmin = (a * kTcTile) / nu;
+        ch[t] = (long long)(N - rmin) * nkc;
+        C += ch[t];
+    }
+    const int G = sm_count();
+    std::vector<int> plan(2 * (size_t)ntiles + 2, 0);
+    int off = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        long long sp = C > 0 ? (long long)G * ch[t] / C : 1;
+        if (sp < 1) sp = 1;
+        if (sp > ch[t] && ch[t] > 0) sp = ch[t];
+        plan[2 * t] = (int)sp;
+        plan[2 * t + 1] = off;
+        off += (int)sp;
+    }
+    plan[2 * (size_t)ntiles] = off;
+    return plan;
+}
+
+int syrk_tc_plan_partials(int ns, int nu, int N) {
+    std::vector<int> p = syrk_tc_make_plan(ns, nu, N);
+    return p[p.size() - 2];
+}
+
 bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -350,7 +403,7 @@ bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out) {
 void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int tf32, const void* d_maps,
                     int flags, cudaStream_t st) {
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    dim3 grid(syrk_tc_tiles(max_n) * splits, count);
+    dim3 grid(splits, count);   // splits = total partials of the plan
     if (tf32) {
         cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         LQ_LAUNCH(k_syrk_tc<true><<<grid, 192, smem, st>>>(d_insts, (const CUtensorMap*)d_maps, splits, flags));

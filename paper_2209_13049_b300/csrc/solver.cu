@@ -19,6 +19,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "../../include/lqmpc.h"
@@ -32,6 +33,62 @@ using namespace lqmpc;
 namespace lqmpc {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launches(int k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+static int g_prof = -1;
+static std::vector<cudaEvent_t> g_prof_pool;
+static size_t g_prof_next = 0;
+struct ProfRec { const char* what; cudaEvent_t a, b; };
+static std::vector<ProfRec> g_prof_recs;
+static cudaEvent_t prof_event() {
+    if (g_prof_next == g_prof_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        g_prof_pool.push_back(e);
+    }
+    return g_prof_pool[g_prof_next++];
+}
+cudaEvent_t prof_start(cudaStream_t st) {
+    if (g_prof < 0) {
+        const char* e = getenv("LQMPC_PROFILE");
+        g_prof = (e && e[0] == '1') ? 1 : 0;
+    }
+    if (!g_prof) return nullptr;
+    cudaEvent_t e = prof_event();
+    cudaEventRecord(e, st);
+    return e;
+}
+void prof_stop(cudaStream_t st, cudaEvent_t e0, const char* what) {
+    if (!e0) return;
+    cudaEvent_t e1 = prof_event();
+    cudaEventRecord(e1, st);
+    g_prof_recs.push_back({what, e0, e1});
+}
+// Print and clear the per-kernel table (kernel name = text before "<<<").
+static void prof_report(const char* title) {
+    if (g_prof != 1 || g_prof_recs.empty()) return;
+    cudaDeviceSynchronize();
+    struct Agg { std::string name; double ms; int n; };
+    std::vector<Agg> aggs;
+    double total = 0;
+    for (auto& r : g_prof_recs) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        std::string nm(r.what);
+        size_t k = nm.find("<<<");
+        if (k != std::string::npos) nm = nm.substr(0, k);
+        bool found = false;
+        for (auto& a : aggs)
+            if (a.name == nm) { a.ms += ms; a.n++; found = true; break; }
+        if (!found) aggs.push_back({nm, ms, 1});
+        total += ms;
+    }
+    std::sort(aggs.begin(), aggs.end(), [](const Agg& x, const Agg& y) { return x.ms > y.ms; });
+    fprintf(stderr, "lqmpc profile (%s): %.3f ms in %zu launches\n", title, total, g_prof_recs.size());
+    for (auto& a : aggs)
+        fprintf(stderr, "  %10.3f ms %5.1f%% %6d x %8.2f us  %s\n", a.ms, 100.0 * a.ms / total, a.n,
+                1e3 * a.ms / a.n, a.name.c_str());
+    g_prof_recs.clear();
+    g_prof_next = 0;
+}
 static int g_check = -1;
 void check_launch(cudaStream_t st, const char* what, const char* file, int line) {
     if (g_check < 0) {
@@ -140,7 +197,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto xl = c.take<double>(ns); auto xu = c.take<double>(ns);
     auto ul = c.take<double>(nu); auto uu = c.take<double>(nu);
     auto qd = c.take<double>(ns); auto qfd = c.take<double>(ns);
-    auto G64 = c.take<double>(G); auto G32 = c.take<float>(G); auto G16 = c.take<__nv_bfloat16>(G);
+    auto G64 = c.take<double>(G); auto G32 = c.take<float>(G); auto G32lo = c.take<float>(G);
+    auto G16 = c.take<__nv_bfloat16>(G);
     auto H64 = c.take<double>((size_t)n * n); auto H32 = c.take<float>((size_t)n * n);
     auto xbar = c.take<double>(ns); auto y = c.take<double>(SX); auto h = c.take<double>(n);
     auto u = c.take<double>(n); auto x = c.take<double>(SX);
@@ -148,7 +206,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto s2 = c.take<double>(SX); auto z2 = c.take<double>(SX);
     auto s3 = c.take<double>(n); auto z3 = c.take<double>(n);
     auto s4 = c.take<double>(n); auto z4 = c.take<double>(n);
-    auto sigx = c.take<double>(SX); auto sigu = c.take<double>(n); auto sigx32 = c.take<float>(SX);
+    auto sigx = c.take<double>(SX); auto sigu = c.take<double>(n);
+    auto sigx32 = c.take<float>((size_t)I.N * I.ldg);
     auto wz = c.take<double>(SX); auto wx = c.take<double>(SX);
     auto wzu = c.take<double>(n); auto wxu = c.take<double>(n);
     auto gz = c.take<double>(n); auto gw = c.take<double>(n);
@@ -159,12 +218,16 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto ds3 = c.take<double>(n); auto dz3 = c.take<double>(n);
     auto ds4 = c.take<double>(n); auto dz4 = c.take<double>(n);
     auto M64 = c.take<double>((size_t)n * n); auto M32 = c.take<float>((size_t)n * n);
+    auto Xinv32 = c.take<float>((size_t)n * n); auto Tinv32 = c.take<float>((size_t)n * n);
+    auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
+    auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);
     auto tmpx = c.take<double>(SX);
     auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n, I.N));
     auto r32 = c.take<float>(n);
     size_t ws_cc = (size_t)syrk_cc_tiles(n) * cc_splits * 64 * 64 * sizeof(double);
-    size_t ws_tc = (size_t)syrk_tc_tiles(n) * tc_splits * 128 * 128 * sizeof(float);
+    size_t ws_tc = (size_t)syrk_tc_plan_partials(I.ns, I.nu, I.N) * 128 * 128 * sizeof(float);
+    auto tc_plan = c.take<int>(2 * (size_t)syrk_tc_tiles(n) + 2);
     size_t ws = std::max(ws_cc, ws_tc);
     auto syrk_ws = c.take<unsigned char>(ws);
     auto part = c.take<double>((size_t)kParts * kMaxParts);
@@ -176,7 +239,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.q_ptr = q_ptr; I.q_idx = q_idx; I.q_val = q_val;
         I.qf_ptr = qf_ptr; I.qf_idx = qf_idx; I.qf_val = qf_val;
         I.B = B; I.R = R; I.xl = xl; I.xu = xu; I.ul = ul; I.uu = uu; I.qd = qd; I.qfd = qfd;
-        I.G64 = G64; I.G32 = G32; I.G16 = G16; I.H64 = H64; I.H32 = H32;
+        I.G64 = G64; I.G32 = G32; I.G32lo = G32lo; I.G16 = G16; I.H64 = H64; I.H32 = H32;
         I.xbar = xbar; I.y = y; I.h = h; I.u = u; I.x = x;
         I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
         I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32;
@@ -184,9 +247,10 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.rd = rd; I.b = b; I.du = du; I.dx = dx; I.du_aff = du_aff; I.dx_aff = dx_aff;
         I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
-        I.M64 = M64; I.M32 = M32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
+        I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
+        I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
-        I.part = part; I.bar = bar; I.sc = sc; I.trace = trace;
+        I.part = part; I.bar = bar; I.sc = sc; I.trace = trace; I.tc_plan = tc_plan;
     }
     return c.off;
 }
@@ -200,7 +264,20 @@ struct Batch {
     int cc_splits = 1, tc_splits = 1;
     cudaStream_t st = nullptr;
     const void* d_maps = nullptr;   // tensor maps (batch of one only)
+    bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
 };
+
+// Products with Gamma in the arithmetic of the solve: FP64 for the plain
+// FP64 path, float-float on the FP32 pipes for the mixed-precision paths.
+void gmv(const Batch& b, int in, int out, int flags) {
+    if (b.ff) launch_gamma_mv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, in, out, flags, b.st);
+    else launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, in, out, flags, b.st);
+}
+
+void gtmv(const Batch& b, int w0, int w1, int o0, int o1, int scale0, int flags) {
+    if (b.ff) launch_gamma_tmv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st);
+    else launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st);
+}
 
 void batch_dims(Batch& b) {
     b.count = (int)b.ctxs.size();
@@ -226,7 +303,7 @@ struct SyrkTimer {
     bool tc = false, cc = false;
 };
 
-void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr) {
+void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 0.0) {
     lqmpc_ctx* c0 = b.ctxs[0];
     if (prec == LQMPC_FP64) {
         if (tm) cudaEventRecord(c0->evk[2], b.st);
@@ -239,21 +316,21 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr) {
             if (tm) cudaEventRecord(c0->evk[2], b.st);
             launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
             if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; }
-            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st);
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st, shift);
         } else {
             if (tm) cudaEventRecord(c0->evk[0], b.st);
             launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
                            F_NONE, b.st);
             if (tm) { cudaEventRecord(c0->evk[1], b.st); tm->tc = true; }
-            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st);
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st, shift);
         }
-        launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st);
+        launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st, 1);
     }
 }
 
 void kkt_solve_fp64(const Batch& b) {
     launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
-    launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_DU, R_TMPX, F_NONE, b.st);
+    gmv(b, R_DU, R_DXS, F_NONE);
 }
 
 lqmpc_status read_scals(Batch& b) {
@@ -262,21 +339,29 @@ lqmpc_status read_scals(Batch& b) {
     return LQMPC_OK;
 }
 
-// Mixed-precision solve of M du = b (R_B -> R_DU, R_TMPX = Gamma du) with the
-// low-precision factor and FP64 iterative refinement.  The host looks at the
-// instance flags every second step and stops launching once every unfinished
-// instance has converged or failed; afterwards each h_scal holds the outcome.
+// Mixed-precision solve of M du = b (R_B -> R_DU, R_DXS = Gamma du):
+// preconditioned conjugate gradients with the low-precision Cholesky factor
+// as preconditioner and FP64 products with M.  The host looks at the instance
+// flags every second step and stops launching once every unfinished instance
+// has converged or failed; afterwards each h_scal holds the outcome.
 lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
-    launch_refine_begin(b.d_insts, b.count, b.max_n, b.st);
-    launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_B, R_DU, F_NONE, b.st);
-    for (int s = 0; s <= refine_max; ++s) {
-        launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_DU, R_TMPX, F_SKIP_REFINED, b.st);
-        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_TMPX, R_NONE, R_MV, R_NONE,
-                         1, F_SKIP_REFINED, b.st);
-        launch_refine_residual(b.d_insts, b.count, b.max_n, b.st);
-        if (s == refine_max) break;
-        launch_chol_solve(b.d_insts, b.count, b.max_n, 0, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
-        launch_refine_update(b.d_insts, b.count, b.max_n, 0, b.st);
+    launch_pcg_begin(b.d_insts, b.count, b.st);
+    launch_prec_apply(b.d_insts, b.count, b.max_n, R_B, R_DU, F_NONE, b.st);
+    // initial residual r = b - M du and Gamma du
+    gmv(b, R_DU, R_TMPX, F_SKIP_REFINED);
+    gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
+    launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, F_NONE, b.st);
+    launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, b.st);
+    launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+    launch_pcg_pinit(b.d_insts, b.count, b.st);
+    for (int s = 0; s < refine_max; ++s) {
+        gmv(b, R_P, R_TMPX, F_SKIP_REFINED);
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
+        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, b.st);
+        launch_pcg_step_update(b.d_insts, b.count, b.max_total, b.st);
+        if (s + 1 == refine_max) break;
+        launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+        launch_pcg_beta(b.d_insts, b.count, b.st);
         if (s % 2 == 0) {
             lqmpc_status st = read_scals(b);
             if (st != LQMPC_OK) return st;
@@ -295,13 +380,14 @@ void prepare(const Batch& b, const lqmpc_options& o) {
     for (auto* c : b.ctxs) cudaMemsetAsync(c->h.sc, 0, sizeof(Scal), b.st);
     launch_ychain(b.d_insts, b.count, b.st);
     launch_qbar_y(b.d_insts, b.count, b.max_sx, b.st);
-    launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_TMPX, R_NONE, R_H, R_NONE, 0,
-                     F_FORCE, b.st);
+    gtmv(b, R_TMPX, R_NONE, R_H, R_NONE, 0, F_FORCE);
     launch_set_u0(b.d_insts, b.count, b.max_n, b.st);
-    launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, R_U, R_TMPX, F_FORCE, b.st);
+    gmv(b, R_U, R_TMPX, F_FORCE);
     launch_init_point(b.d_insts, b.count, b.max_total, b.max_n, o.tol, o.tau, o.max_iter, o.refine_tol,
                       b.st);
 }
+
+constexpr int kLowPrecSteps = 12;   // conjugate-gradient steps allowed with a BF16/TF32 factor
 
 int next_precision(int p) {
     return (p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32) ? LQMPC_FP32 : LQMPC_FP64;
@@ -339,14 +425,52 @@ void mark_failures(Batch& b, bool fallback) {
 // Solve M du = b in the current precision `cur`, escalating BF16/TF32 ->
 // FP32 -> FP64 while refinement fails (if fallback is on).  `formed` says
 // whether M is already formed and factored in `cur`.
+bool any_pivot_failure(const Batch& b) {
+    for (auto* c : b.ctxs)
+        if (!c->h_scal->done && c->h_scal->info) return true;
+    return false;
+}
+
+void clear_pivot_failures(Batch& b) {
+    for (auto* c : b.ctxs) {
+        if (c->h_scal->done || !c->h_scal->info) continue;
+        c->h_scal->info = 0;
+        cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
+    }
+}
+
+// Solve M du = b in the current precision `cur`.  A low-precision factor
+// whose Cholesky meets a non-positive pivot (M rounded to BF16/TF32/FP32 can
+// lose definiteness when Sigma spreads) is retried with a small relative
+// diagonal shift -- the conjugate gradients with FP64 products still converge
+// to the exact solution, only with a weaker preconditioner.  If that fails or
+// the conjugate gradients do not converge, the batch escalates
+// BF16/TF32 -> FP32 -> FP64 (sticky for the rest of the solve) when fallback
+// is on.  `formed` says whether M is already formed and factored in `cur`.
 lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, SyrkTimer* tm) {
     for (;;) {
-        if (!formed) kkt_form(b, cur, tm);
+        if (!formed) {
+            // FP32 factors (the last step before FP64) are retried with a
+            // relative diagonal shift; BF16/TF32 factors escalate directly.
+            const double shifts_sp[3] = {0.0, 1e-6, 1e-4};
+            const int attempts = cur == LQMPC_FP32 ? 3 : 1;
+            for (int attempt = 0; attempt < attempts; ++attempt) {
+                kkt_form(b, cur, tm, cur == LQMPC_FP32 ? shifts_sp[attempt] : 0.0);
+                if (cur == LQMPC_FP64) break;
+                lqmpc_status s = read_scals(b);
+                if (s != LQMPC_OK) return s;
+                if (!any_pivot_failure(b) || attempt + 1 == attempts) break;
+                clear_pivot_failures(b);
+            }
+        }
         if (cur == LQMPC_FP64) {
             kkt_solve_fp64(b);
             return LQMPC_OK;
         }
-        lqmpc_status s = kkt_solve_mixed(b, o.refine_max);
+        // conjugate-gradient budget: a BF16/TF32 factor that needs many steps
+        // is cheaper to replace by an FP32 one than to iterate with
+        const int steps = cur == LQMPC_FP32 ? o.refine_max : std::min(o.refine_max, kLowPrecSteps);
+        lqmpc_status s = kkt_solve_mixed(b, steps);
         if (s != LQMPC_OK) return s;
         if (!refine_failed(b)) return LQMPC_OK;
         mark_failures(b, o.fallback != 0);
@@ -358,6 +482,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, S
 
 lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* t_kkt) {
     const int prec = o.precision;
+    b.ff = prec != LQMPC_FP64;
     if ((prec == LQMPC_MIXED_BF16 || prec == LQMPC_MIXED_TF32) && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
     lqmpc_ctx* c0 = b.ctxs[0];
     c0->t_tc = c0->t_cc = 0.0;
@@ -370,25 +495,23 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         SyrkTimer tm;
         // residuals, Sigma, stop test
         launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
-        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_WZ, R_WX, R_GZ, R_GW, 0,
-                         F_NONE, b.st);
+        gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
         launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
         cudaEventRecord(c0->ev[2], b.st);
         // predictor: form and factor M, solve M du_aff = b
         lqmpc_status s = kkt_step(b, o, cur, false, &tm);
         if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX_AFF, 0, F_NONE, b.st);
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
         // affine step, sigma, corrector right-hand side
         launch_aff(b.d_insts, b.count, b.max_total, b.st);
         launch_corr(b.d_insts, b.count, b.max_total, b.st);
-        launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, R_WX, R_NONE, R_GW, R_NONE, 0,
-                         F_NONE, b.st);
+        gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
         launch_rhs(b.d_insts, b.count, b.max_n, b.st);
         // corrector: same factor
         s = kkt_step(b, o, cur, true, &tm);
         if (s != LQMPC_OK) return s;
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DX, 0, F_NONE, b.st);
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
         launch_step_update(b.d_insts, b.count, b.max_total, 1, cur, b.st);
         s = read_scals(b);
@@ -407,6 +530,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     cudaEventRecord(c0->ev[1], b.st);
     lqmpc_status s = read_scals(b);
     if (s != LQMPC_OK) return s;
+    prof_report(prec == LQMPC_FP64 ? "fp64 solve" : "mixed solve");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c0->ev[0], c0->ev[1]);
     *t_total = ms;
@@ -478,7 +602,7 @@ lqmpc_options lqmpc_default_options(void) {
     o.tol = 1e-8;
     o.max_iter = 100;
     o.precision = LQMPC_FP64;
-    o.refine_max = 10;
+    o.refine_max = 30;
     o.refine_tol = 1e-10;
     o.fallback = 1;
     o.tau = 0.995;
@@ -547,7 +671,7 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     I.q_diag = qdiag ? 1 : 0;
     const int nnzA = a_ptr[ns], nnzQ = q_ptr[ns], nnzQf = qf_ptr[ns];
     ctx->cc_splits = syrk_cc_splits(ns, nu, N);
-    ctx->tc_splits = syrk_tc_splits(ns, nu, N);
+    ctx->tc_splits = syrk_tc_plan_partials(ns, nu, N);
     size_t bytes = layout<false>(I, nullptr, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits);
     auto fail = [&](lqmpc_status s) {
         lqmpc_free(ctx);
@@ -576,6 +700,10 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
               up(I.xu, xu, sizeof(double) * ns) && up(I.ul, ul, sizeof(double) * nu) &&
               up(I.uu, uu, sizeof(double) * nu);
     if (qdiag) ok = ok && up(I.qd, qd.data(), sizeof(double) * ns) && up(I.qfd, qfd.data(), sizeof(double) * ns);
+    {
+        std::vector<int> plan = syrk_tc_make_plan(ns, nu, N);
+        ok = ok && up(I.tc_plan, plan.data(), sizeof(int) * plan.size());
+    }
     if (!ok) return fail(LQMPC_ERR_CUDA);
     if (cudaMalloc(&ctx->d_inst, sizeof(Inst)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     if (!up(ctx->d_inst, &I, sizeof(Inst))) return fail(LQMPC_ERR_CUDA);
@@ -752,7 +880,10 @@ lqmpc_status lqmpc_gamma_mv(lqmpc_ctx* ctx, const double* v, double* out) {
     lqmpc_status s = reset_scal(ctx);
     if (s) return s;
     CK(cudaMemcpyAsync(I.du, v, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
-    launch_gamma_mv(ctx->d_inst, 1, I.ns, I.N, R_DU, R_TMPX, F_FORCE, ctx->stream);
+    if (ctx->opts.precision != LQMPC_FP64)
+        launch_gamma_mv_ff(ctx->d_inst, 1, I.ns, I.N, I.n, R_DU, R_TMPX, F_FORCE, ctx->stream);
+    else
+        launch_gamma_mv(ctx->d_inst, 1, I.ns, I.N, R_DU, R_TMPX, F_FORCE, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, I.tmpx, sizeof(double) * I.SX, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -766,7 +897,10 @@ lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out) {
     lqmpc_status s = reset_scal(ctx);
     if (s) return s;
     CK(cudaMemcpyAsync(I.tmpx, w, sizeof(double) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
-    launch_gamma_tmv(ctx->d_inst, 1, I.ns, I.N, I.n, R_TMPX, R_NONE, R_MV, R_NONE, 0, F_FORCE, ctx->stream);
+    if (ctx->opts.precision != LQMPC_FP64)
+        launch_gamma_tmv_ff(ctx->d_inst, 1, I.ns, I.N, I.n, R_TMPX, R_NONE, R_MV, R_NONE, 0, F_FORCE, ctx->stream);
+    else
+        launch_gamma_tmv(ctx->d_inst, 1, I.ns, I.N, I.n, R_TMPX, R_NONE, R_MV, R_NONE, 0, F_FORCE, ctx->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(out, I.mv, sizeof(double) * I.n, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -780,9 +914,11 @@ static lqmpc_status upload_sigma(lqmpc_ctx* ctx, const double* sigx, const doubl
         if (sigx[k] < 0) return LQMPC_ERR_ARG;
     for (int k = 0; k < I.n; ++k)
         if (sigu[k] < 0) return LQMPC_ERR_ARG;
-    std::vector<float> s32(sigx, sigx + I.SX);
+    std::vector<float> s32((size_t)I.N * I.ldg, 0.0f);
+    for (int r = 0; r < I.N; ++r)
+        for (int i = 0; i < I.ns; ++i) s32[(size_t)r * I.ldg + i] = (float)sigx[(size_t)r * I.ns + i];
     CK(cudaMemcpyAsync(I.sigx, sigx, sizeof(double) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaMemcpyAsync(I.sigx32, s32.data(), sizeof(float) * I.SX, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(I.sigx32, s32.data(), sizeof(float) * s32.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(I.sigu, sigu, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LQMPC_OK;
@@ -853,6 +989,7 @@ lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* s
     batch_dims(b);
     b.d_maps = ctx->d_maps;
     CK(cudaMemcpyAsync(I.b, rhs, sizeof(double) * I.n, cudaMemcpyHostToDevice, b.st));
+    b.ff = precision != LQMPC_FP64;
     kkt_form(b, precision);
     if (precision == LQMPC_FP64) kkt_solve_fp64(b);
     else {
