@@ -187,3 +187,22 @@ def test_solve_device_equals_host():
     ud = torch.zeros(p.n, dtype=torch.float64, device="cuda")
     s.solve_device(xd, ud)
     np.testing.assert_array_equal(ud.cpu().numpy(), u_host)
+
+
+def test_large_batch_cluster_factor_matches_single():
+    """A batch large enough to give every instance its own 8-CTA cluster for
+    the Cholesky factorisation (the single-instance solves use the
+    grid-cooperative kernel): same iterates up to rounding, so the same u*."""
+    sizes = [(20 + 3 * k, 2 + k % 4, 4 + k % 7) for k in range(20)]
+    solvers, x0s = [], []
+    for k, (ns, nu, N) in enumerate(sizes):
+        solvers.append(binding.Solver(inputs.heat1d(ns, nu, N), tol=1e-11))
+        x0s.append(inputs.x0_uniform(ns, 100 + k))
+    us, stats, code = binding.solve_batch(solvers, x0s)
+    assert code == 0
+    for k in range(len(sizes)):
+        assert stats[k]["status"] == 0
+        u1, _ = solvers[k].solve(x0s[k])
+        assert rel(us[k], u1) <= 1e-9, k
+    ref = oracle.ipm_solve(inputs.heat1d(*sizes[7]), x0s[7], tol=1e-11)
+    assert rel(us[7], ref["u"]) <= 1e-9
