@@ -235,15 +235,19 @@ def run_ours(args):
     value = world * K / (total_ms / 1e3)
     e2e_value = world * K / (e2e_ms / 1e3)
 
-    # parity of the timed solves' first instance against the stored oracle result
+    # parity against the stored oracle results for x0 seed 0: at the same stop
+    # tolerance (1e-8, "u8") and against the tight optimum (1e-12, "u12")
     errs = {}
     if os.path.exists(GOLD):
         g = np.load(GOLD)
-        ref = g["heat2d_32_s0_u12"]
-        u_m, _ = mixed.solve(g["heat2d_32_s0_x0"], check=False)
-        u_f, _ = fp64.solve(g["heat2d_32_s0_x0"], check=False)
-        scale = max(1.0, float(np.max(np.abs(ref))))
-        errs = {"mixed": float(np.max(np.abs(u_m - ref)) / scale), "fp64": float(np.max(np.abs(u_f - ref)) / scale)}
+        x0g = g["heat2d_32_s0_x0"]
+        u_m, _ = mixed.solve(x0g, check=False)
+        u_f, _ = fp64.solve(x0g, check=False)
+        for key in ("u8", "u12"):
+            ref = g[f"heat2d_32_s0_{key}"]
+            scale = max(1.0, float(np.max(np.abs(ref))))
+            errs[f"mixed_vs_oracle_{key}"] = float(np.max(np.abs(u_m - ref)) / scale)
+            errs[f"fp64_vs_oracle_{key}"] = float(np.max(np.abs(u_f - ref)) / scale)
 
     def summary(times, stats):
         iters = [s["iters"] for s in stats]
@@ -254,18 +258,37 @@ def run_ours(args):
                 "fallbacks_total": int(sum(s["fallbacks"] for s in stats)),
                 "status": sorted({int(s["status"]) for s in stats})}
 
-    # roofline of the tensor-core SYRK (a4), from events around its launches in the timed region
-    n_tc = sum(s["syrk_tc_launches"] for s in st_mixed)
-    t_tc = sum(s["t_syrk_tc_ms"] for s in st_mixed)
+    # Rooflines from the library's CUDA events around the SYRK launches inside
+    # the timed solves.  The dominant kernel of a mixed solve is the FP64
+    # CUDA-core SYRK of the FP64 fallback iterations (bound by the FP64 pipe:
+    # 148 SMs x 2 DFMA/clk x 2 flop x SM clock); the tensor-core SYRK of the
+    # BF16/TF32 iterations is reported beside it.
     peaks, which = measured_peaks()
     flops = syrk_alg_flops(NS, NU, N)
+    n64 = sum(s["syrk_fp64_launches"] for s in st_mixed)
+    t64 = sum(s["t_syrk_fp64_ms"] for s in st_mixed)
+    if not n64:      # no fallback in these solves: take the FP64 solves' launches
+        n64 = sum(s["syrk_fp64_launches"] for s in st_fp64)
+        t64 = sum(s["t_syrk_fp64_ms"] for s in st_fp64)
+    sm_mhz = clocks.get("sm_mhz") or 2032.0
+    fp64_peak = 148 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    ach64 = flops / (t64 / max(1, n64) / 1e3) / 1e12 if n64 else None
+    roofline = {"kernel": "k_syrk_cc<double> (FP64 KKT-matrix formation, Eq. 7)", "bound": "alu",
+                "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (ach64 / fp64_peak) if ach64 else None, "traffic": None,
+                "peak_source": f"derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
+                               f"sampled during the timed region)",
+                "flops_per_launch": flops, "launches": n64,
+                "avg_launch_us": (t64 / max(1, n64) * 1e3) if n64 else None}
+    n_tc = sum(s["syrk_tc_launches"] for s in st_mixed)
+    t_tc = sum(s["t_syrk_tc_ms"] for s in st_mixed)
     achieved = flops / (t_tc / max(1, n_tc) / 1e3) / 1e12 if n_tc else None
     peak = peaks.get("bf16_tflops_sustained", 1400.0)
-    roofline = {"kernel": "k_syrk_tc<bf16> (tcgen05 KKT-matrix formation)", "bound": "tensor",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
-                "peak_source": f"{which} bf16_tflops_sustained", "flops_per_launch": flops,
-                "launches": n_tc, "avg_launch_us": (t_tc / max(1, n_tc) * 1e3) if n_tc else None}
+    roofline_tc = {"kernel": "k_syrk_tc (tcgen05 KKT-matrix formation)", "bound": "tensor",
+                   "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                   "frac": (achieved / peak) if achieved else None,
+                   "peak_source": f"{which} bf16_tflops_sustained", "flops_per_launch": flops,
+                   "launches": n_tc, "avg_launch_us": (t_tc / max(1, n_tc) * 1e3) if n_tc else None}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -277,7 +300,8 @@ def run_ours(args):
                            "parallelism": f"replicas x{world}", "precision": args.precision},
                 "mixed": summary(t_mixed, st_mixed), "fp64": summary(t_fp64, st_fp64),
                 "speedup_mixed_vs_fp64": (value / world) / (kf / (sum(t_fp64) / 1e3)),
-                "u_rel_err_vs_oracle": errs, "roofline": roofline, "clocks": clocks,
+                "u_rel_err_vs_oracle": errs, "roofline": roofline, "roofline_tensor_syrk": roofline_tc,
+                "clocks": clocks,
                 "gpu_launches": int(launches),
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": NS * 8,
                         "d2h_bytes_per_step": plant.n * 8}}

@@ -80,7 +80,7 @@ typedef struct {
 typedef struct {
     int iters;           /* interior-point iterations taken */
     int refine_steps;    /* total refinement steps (mixed modes) */
-    int fallbacks;       /* iterations that fell back to FP64 */
+    int fallbacks;       /* precision escalations (BF16/TF32 -> FP32 -> FP64) */
     int status;          /* lqmpc_status of the solve */
     double mu;           /* final complementarity s'z/m */
     double res_primal;   /* final ||r_p||_inf/(1+||d||_inf) */
@@ -91,6 +91,8 @@ typedef struct {
     double t_syrk_cc_ms; /* device time of the CUDA-core (FP64/FP32) SYRK launches */
     int syrk_tc_launches;
     int syrk_cc_launches;
+    double t_syrk_fp64_ms; /* the FP64 share of t_syrk_cc_ms (FP64 solves and fallbacks) */
+    int syrk_fp64_launches;
 } lqmpc_stats;
 
 /* Default options (values in the comments above). */

@@ -47,7 +47,8 @@ class Stats(ctypes.Structure):
                 ("status", ctypes.c_int), ("mu", ctypes.c_double), ("res_primal", ctypes.c_double),
                 ("res_dual", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("t_kkt_ms", ctypes.c_double),
                 ("t_syrk_tc_ms", ctypes.c_double), ("t_syrk_cc_ms", ctypes.c_double),
-                ("syrk_tc_launches", ctypes.c_int), ("syrk_cc_launches", ctypes.c_int)]
+                ("syrk_tc_launches", ctypes.c_int), ("syrk_cc_launches", ctypes.c_int),
+                ("t_syrk_fp64_ms", ctypes.c_double), ("syrk_fp64_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -125,8 +125,8 @@ struct lqmpc_ctx {
     cudaEvent_t evk[4];         // around the SYRK launch: tensor-core pair, CUDA-core pair
     bool events = false;
     // per-solve SYRK timing
-    double t_tc = 0, t_cc = 0;
-    int n_tc = 0, n_cc = 0;
+    double t_tc = 0, t_cc = 0, t_cc64 = 0;
+    int n_tc = 0, n_cc = 0, n_cc64 = 0;
 };
 
 namespace {
@@ -300,7 +300,7 @@ void batch_dims(Batch& b) {
 // instance (the caller then falls back to FP64).
 // SYRK timing: the events of ctxs[0] bracket the SYRK launch itself.
 struct SyrkTimer {
-    bool tc = false, cc = false;
+    bool tc = false, cc = false, cc64 = false;   // cc64: the timed CUDA-core launch was FP64
 };
 
 void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 0.0) {
@@ -308,14 +308,14 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
     if (prec == LQMPC_FP64) {
         if (tm) cudaEventRecord(c0->evk[2], b.st);
         launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
-        if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; }
+        if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; tm->cc64 = true; }
         launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
         launch_potrf(b.d_insts, b.count, b.max_n, 1, F_NONE, b.st);
     } else {
         if (prec == LQMPC_FP32) {
             if (tm) cudaEventRecord(c0->evk[2], b.st);
             launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
-            if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; }
+            if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; tm->cc64 = false; }
             launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st, shift);
         } else {
             if (tm) cudaEventRecord(c0->evk[0], b.st);
@@ -485,8 +485,8 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     b.ff = prec != LQMPC_FP64;
     if ((prec == LQMPC_MIXED_BF16 || prec == LQMPC_MIXED_TF32) && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
     lqmpc_ctx* c0 = b.ctxs[0];
-    c0->t_tc = c0->t_cc = 0.0;
-    c0->n_tc = c0->n_cc = 0;
+    c0->t_tc = c0->t_cc = c0->t_cc64 = 0.0;
+    c0->n_tc = c0->n_cc = c0->n_cc64 = 0;
     cudaEventRecord(c0->ev[0], b.st);
     prepare(b, o);
     int cur = prec;          // sticky: once escalated, the rest of the solve stays there
@@ -519,7 +519,10 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]) == cudaSuccess) kkt_ms += ms;
         if (tm.tc && cudaEventElapsedTime(&ms, c0->evk[0], c0->evk[1]) == cudaSuccess) { c0->t_tc += ms; c0->n_tc++; }
-        if (tm.cc && cudaEventElapsedTime(&ms, c0->evk[2], c0->evk[3]) == cudaSuccess) { c0->t_cc += ms; c0->n_cc++; }
+        if (tm.cc && cudaEventElapsedTime(&ms, c0->evk[2], c0->evk[3]) == cudaSuccess) {
+            c0->t_cc += ms; c0->n_cc++;
+            if (tm.cc64) { c0->t_cc64 += ms; c0->n_cc64++; }
+        }
         bool all_done = true;
         for (auto* c : b.ctxs) {
             if (c->h_scal->err) return LQMPC_ERR_TIMEOUT;
@@ -555,6 +558,8 @@ void fill_stats(lqmpc_ctx* c, lqmpc_stats* st, double t_total, double t_kkt) {
     st->t_syrk_cc_ms = c->t_cc;
     st->syrk_tc_launches = c->n_tc;
     st->syrk_cc_launches = c->n_cc;
+    st->t_syrk_fp64_ms = c->t_cc64;
+    st->syrk_fp64_launches = c->n_cc64;
 }
 
 lqmpc_status final_status(lqmpc_ctx* c) {
