@@ -189,6 +189,40 @@ lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out);
 lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* sigu,
                             int precision, double* M);
 
+/* Allocation-free FP64 formation of the same M (the paper has no counterpart:
+ * this is a library facility, not a step of the method).
+ *
+ * For callers that must not allocate device memory while they run: a
+ * real-time control loop that cannot take the allocator's latency or the
+ * device-wide synchronisation cudaMalloc/cudaFree may imply, or a process
+ * whose device memory is entirely held by another allocator.  The call
+ * allocates nothing, host or device: the split-K partial tiles live in one
+ * fixed 16 MiB device array inside this library (one per device), and
+ * everything else is the context's (G-stack and H from setup) or the
+ * caller's.
+ *
+ * sigx: device pointer, ns*N doubles (stage r, state i at r*ns + i); sigu:
+ * device pointer, n doubles; M: device pointer, n*n doubles, receives the
+ * full symmetric M column-major.  All three 8-byte aligned and owned by the
+ * caller.  Sigma must be finite and >= 0; device data are not inspected.
+ * The work is enqueued on the context's stream and the call returns without
+ * waiting: synchronise that stream before reading M.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * outside any stream capture.  All calls on a device share the array, so
+ * calls whose work overlaps in time (different streams, or different host
+ * threads) race and corrupt each other's results: order them.  No part of
+ * the array needs to start at zero (every partial is written before it is
+ * read), so nothing is cleared between calls.
+ *
+ * Size limit: n = nu*N <= 1984 (one split of every 64 x 64 lower tile of M
+ * must fit in the array); larger contexts get LQMPC_ERR_UNSUPPORTED, with a
+ * message on stderr when opts.verbose is set, and nothing is launched.
+ * NULL or misaligned pointers give LQMPC_ERR_ARG; a failed launch or
+ * address lookup LQMPC_ERR_CUDA. */
+lqmpc_status lqmpc_form_kkt_noalloc(lqmpc_ctx* ctx, const double* sigx, const double* sigu, double* M);
+
 /* Form M as above, Cholesky-factor it and solve M x = b (mixed precisions
  * with FP64 iterative refinement).  L (nullable) receives the lower factor
  * as n x n doubles (upper triangle zero).  refine_steps (nullable) receives

@@ -27,7 +27,7 @@ EXPORTS = ["lqmpc_default_options", "lqmpc_status_str", "lqmpc_setup", "lqmpc_se
            "lqmpc_solve", "lqmpc_solve_device", "lqmpc_solve_batch", "lqmpc_free",
            "lqmpc_get_gstack", "lqmpc_get_hessian", "lqmpc_gamma_mv", "lqmpc_gamma_tmv",
            "lqmpc_form_kkt", "lqmpc_kkt_solve", "lqmpc_get_trace", "lqmpc_get_duals",
-           "lqmpc_kernel_launches"]
+           "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc"]
 
 
 class LqmpcError(RuntimeError):
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
         f.argtypes = [P, P, P]
     lib.lqmpc_form_kkt.restype = I
     lib.lqmpc_form_kkt.argtypes = [P, P, P, I, P]
+    lib.lqmpc_form_kkt_noalloc.restype = I
+    lib.lqmpc_form_kkt_noalloc.argtypes = [P, P, P, P]
     lib.lqmpc_kkt_solve.restype = I
     lib.lqmpc_kkt_solve.argtypes = [P, P, P, I, P, P, P, ctypes.POINTER(I)]
     lib.lqmpc_kernel_launches.restype = ctypes.c_ulonglong
@@ -218,6 +220,16 @@ class Solver:
         M = np.zeros((self.n, self.n), order="F")
         _check(load().lqmpc_form_kkt(self.h, _p(_f64(sigx)), _p(_f64(sigu)), p, _p(M)), "lqmpc_form_kkt")
         return np.asarray(M)
+
+    def form_kkt_noalloc(self, sigx, sigu, M):
+        """FP64 M into the CUDA tensor M (n x n, read column-major) from CUDA
+        tensors sigx (ns*N) and sigu (n); allocates nothing and does not wait
+        for the context's stream."""
+        for name, t, size in (("sigx", sigx, self.ns * self.N), ("sigu", sigu, self.n), ("M", M, self.n * self.n)):
+            if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous() and t.numel() == size):
+                raise ValueError(f"{name}: contiguous float64 CUDA tensor of {size} elements expected")
+        _check(load().lqmpc_form_kkt_noalloc(self.h, sigx.data_ptr(), sigu.data_ptr(), M.data_ptr()),
+               "lqmpc_form_kkt_noalloc")
 
     def kkt_solve(self, sigx, sigu, rhs, precision="fp64", want_L=False, check=True):
         p = PRECISIONS[precision] if isinstance(precision, str) else precision

@@ -76,4 +76,10 @@ bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out /* 128-byte CUtens
 void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int tf32,
                     const void* d_maps, int force, cudaStream_t st);
 
+// kernels_noalloc.cu (FP64 KKT formation with split-K partials in a fixed
+// device array; returns 0, 1 if n exceeds noalloc_max_n(), 2 on a CUDA error)
+int noalloc_max_n();
+int launch_form_kkt_noalloc(const double* G, int ldg, const double* H, const double* sigx, const double* sigu,
+                            double* M, int ns, int nu, int N, cudaStream_t st);
+
 }  // namespace lqmpc

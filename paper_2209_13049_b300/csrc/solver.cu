@@ -976,6 +976,22 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
     return download_matrix(ctx, precision == LQMPC_FP64, M, false);
 }
 
+lqmpc_status lqmpc_form_kkt_noalloc(lqmpc_ctx* ctx, const double* sigx, const double* sigu, double* M) {
+    if (!ctx || !sigx || !sigu || !M) return LQMPC_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(sigx) | reinterpret_cast<uintptr_t>(sigu) | reinterpret_cast<uintptr_t>(M)) & 7)
+        return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctx->device));
+    const Inst& I = ctx->h;
+    const int r = launch_form_kkt_noalloc(I.G64, I.ldg, I.H64, sigx, sigu, M, I.ns, I.nu, I.N, ctx->stream);
+    if (r == 1) {
+        if (ctx->opts.verbose)
+            fprintf(stderr, "lqmpc_form_kkt_noalloc: n = %d exceeds the fixed scratch (n <= %d)\n", I.n,
+                    noalloc_max_n());
+        return LQMPC_ERR_UNSUPPORTED;
+    }
+    return r == 0 ? LQMPC_OK : LQMPC_ERR_CUDA;
+}
+
 lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* sigu, int precision,
                              const double* rhs, double* x, double* L, int* refine_steps) {
     if (!ctx || !sigx || !sigu || !rhs || !x || precision < 0 || precision > 3) return LQMPC_ERR_ARG;
