@@ -37,6 +37,9 @@ METRIC = "LQ-MPC IPM solves/s & per-iter KKT ms at 1e-8 residual, mixed vs FP64"
 WORKLOAD = "heat2d 32x32 (ns=1024, nu=10, N=50), x0 = seeded 8-Gaussian fields, tol 1e-8"
 GOLD = os.path.join(ROOT, "tests", "golden", "heat2d_g32_nu10_N50.npz")
 NS, NU, N = 1024, 10, 50
+# DRAM bytes (read + write) of one k_syrk_cc<double> launch on this workload, from
+# the ncu capture summarised in profiles/kernels_heat2d_32x32_ncu_full.md
+SYRK_FP64_TRAFFIC = 4532480
 
 
 def syrk_alg_flops(ns, nu, N):
@@ -213,7 +216,9 @@ def run_ours(args):
     sampler.start()
     launches0 = binding.kernel_launches()
     barrier()
+    torch.cuda.nvtx.range_push("timed")
     t_mixed, st_mixed = timed_solves(mixed, range(W, W + K))
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = binding.kernel_launches() - launches0
     clocks = sampler.stop()
@@ -275,7 +280,7 @@ def run_ours(args):
     ach64 = flops / (t64 / max(1, n64) / 1e3) / 1e12 if n64 else None
     roofline = {"kernel": "k_syrk_cc<double> (FP64 KKT-matrix formation, Eq. 7)", "bound": "alu",
                 "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (ach64 / fp64_peak) if ach64 else None, "traffic": None,
+                "frac": (ach64 / fp64_peak) if ach64 else None, "traffic": SYRK_FP64_TRAFFIC,
                 "peak_source": f"derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
                                f"sampled during the timed region)",
                 "flops_per_launch": flops, "launches": n64,
@@ -315,6 +320,53 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """Uneven batch of 256 instances (1-D or 2-D heat plants, ns 200-2000,
+    nu 2-16, N 10-50) solved in lockstep through lqmpc_solve_batch: host x0 in,
+    host u out, copies inside the timed call."""
+    import torch
+    from paper_2209_13049_b300 import binding, build
+    torch.cuda.set_device(0)
+    build.build()
+    binding.load()
+    inst = inputs.batch_instances(args.batch, 0)
+    t0 = time.perf_counter()
+    solvers = [binding.Solver(p, precision=args.precision) for p, _ in inst]
+    t_setup = time.perf_counter() - t0
+    x0s = [x for _, x in inst]
+    for _ in range(args.warmup):
+        binding.solve_batch(solvers, x0s, check=False)
+    times, launches = [], []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for _ in range(args.steps):
+        k0 = binding.kernel_launches()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        us, stats, code = binding.solve_batch(solvers, x0s, check=False)
+        times.append(time.perf_counter() - t)
+        launches.append(binding.kernel_launches() - k0)
+    clocks = sampler.stop()
+    # parity: batched lockstep result against each sampled instance solved alone in FP64
+    errs = []
+    for k in range(0, len(inst), max(1, len(inst) // 8)):
+        ref, _ = binding.Solver(inst[k][0], precision="fp64").solve(x0s[k], check=False)
+        errs.append(float(np.max(np.abs(us[k] - ref)) / max(1.0, float(np.max(np.abs(ref))))))
+    ms = 1e3 * float(np.mean(times))
+    n = [p.n for p, _ in inst]
+    line = {"metric": "uneven-batch LQ-MPC IPM solves/s at 1e-8 residual", "value": len(inst) / (ms / 1e3),
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": f"{len(inst)} instances, coin-flip heat1d (ns 200-2000) / heat2d (g 15-44), "
+                                   f"nu 2-16, N 10-50 (n {min(n)}-{max(n)}), master seed 0",
+                       "api": "lqmpc_solve_batch (host buffers, copies inside the call)"},
+            "iters_max": int(max(s["iters"] for s in stats)), "status": sorted({int(s["status"]) for s in stats}),
+            "fallbacks_total": int(sum(s["fallbacks"] for s in stats)), "gpu_launches": int(np.mean(launches)),
+            "setup_s": t_setup, "u_rel_err_vs_single_fp64_max": max(errs), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,8 +376,13 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="heat2d32", choices=["heat2d32", "batch"],
+                    help="heat2d32: the metric's workload; batch: the uneven lockstep batch")
+    ap.add_argument("--batch", type=int, default=256)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "batch":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -26,8 +26,12 @@
  *    available values (the last iterate for a solve) or are left untouched
  *    for argument errors.
  *  - Bounds may be -INFINITY / +INFINITY; an infinite bound is absent.
- *  - All device work runs on the stream given at setup (NULL = legacy default
- *    stream).  Calls on one context are not thread-safe.
+ *  - All device work runs on the stream given at setup.  For NULL the context
+ *    creates its own blocking stream, which is ordered with the legacy
+ *    default stream both ways (so work the caller puts on the legacy stream
+ *    is ordered with the solves) and, unlike the legacy stream, can hold the
+ *    captured CUDA graphs the solves replay.  Calls on one context are not
+ *    thread-safe.
  *  - There is no CPU fallback: if the CUDA device or kernels are unavailable
  *    the calls return LQMPC_ERR_CUDA.
  */
@@ -113,7 +117,7 @@ const char* lqmpc_status_str(int status);
  *  R           : nu x nu dense column-major, symmetric positive definite.
  *  xl, xu      : ns state bounds; ul, uu: nu input bounds (+-INFINITY allowed).
  *  opts        : NULL for defaults; copied.
- *  stream      : a cudaStream_t (NULL for the default stream).
+ *  stream      : a cudaStream_t, or NULL (see the stream convention above).
  * Returns LQMPC_ERR_ARG for bad sizes/pointers/NaNs or crossed bounds,
  * LQMPC_ERR_CUDA if the device is unusable.  *out is NULL on failure.
  */
@@ -148,7 +152,8 @@ lqmpc_status lqmpc_solve_device(lqmpc_ctx* ctx, const double* x0_device, double*
  * options other than precision, which is taken from ctxs[0]) in lockstep:
  * every kernel launch of an iteration covers all unfinished instances.
  * x0s[i] / u_outs[i] are host pointers for instance i; stats may be NULL or
- * an array of `count`.  All contexts must share the stream of ctxs[0].
+ * an array of `count`.  All contexts must have been set up with the same
+ * stream argument; the batch runs on ctxs[0]'s stream.
  * Returns LQMPC_OK if every instance converged, otherwise the first failing
  * instance's status.
  */

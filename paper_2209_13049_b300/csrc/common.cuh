@@ -99,6 +99,7 @@ struct Inst {
     double *ds3, *dz3, *ds4, *dz4;    // n
     double* M64; float* M32;          // n x n
     float* Xinv32;                    // n x n: inverse of the FP32 Cholesky factor (preconditioner)
+    double* ldiag;                    // 2 x 32 x 32: factored diagonal blocks in flight (cooperative potrf)
     float* XinvT32;                   // its transpose (coalesced rows)
     float* Tinv32;                    // n x n scratch of the inversion
     double *rho, *dcorr;              // refinement: residual, correction (n)

@@ -134,10 +134,25 @@ __device__ void panel_tile(const Inst& I, int k, int p, T (*Ld)[kNb + 1], T (*Li
     if (!factor_diag<T>(I, M, k, p == k, Ld, fail_sh)) return;
     invert_diag<T>(Ld, Li);
     if (p == k) {
+        // Other CTAs of this panel phase may still be reading A_kk from M to
+        // factor it themselves, so L_kk is parked in ldiag[k % 2] and moved
+        // into M by the diagonal CTA of the next panel phase (after the grid
+        // barrier); the last panel has no other reader and writes M directly.
+        const int nt = (n + kNb - 1) / kNb;
+        T* park = reinterpret_cast<T*>(I.ldiag) + (size_t)(k % 2) * kNb * kNb;
+        if (k > 0) {
+            const T* prev = reinterpret_cast<const T*>(I.ldiag) + (size_t)((k - 1) % 2) * kNb * kNb;
+            const int p0 = k0 - kNb;
+            for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
+                const int r = e % kNb, c = e / kNb;
+                if (c <= r) M[(size_t)(p0 + r) + (size_t)n * (p0 + c)] = prev[e];
+            }
+        }
         for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
             const int r = e % kNb, c = e / kNb;
             if (r < kn && c < kn && c <= r) {
-                M[(size_t)(k0 + r) + (size_t)n * (k0 + c)] = Ld[r][c];
+                if (k + 1 < nt) park[e] = Ld[r][c];
+                else M[(size_t)(k0 + r) + (size_t)n * (k0 + c)] = Ld[r][c];
                 if (X) {
                     X[(size_t)(k0 + r) + (size_t)n * (k0 + c)] = Li[r][c];
                     I.XinvT32[(size_t)(k0 + c) + (size_t)n * (k0 + r)] = (float)Li[r][c];

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
     // 1024-byte aligned stage buffers
     unsigned char* sbase = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const CUtensorMap* map = maps + (TF32 ? 1 : 0);
+    const CUtensorMap* map = maps + 2 * blockIdx.y + (TF32 ? 1 : 0);   // per instance: BF16, TF32
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {

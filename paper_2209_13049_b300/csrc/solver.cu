@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -106,9 +107,30 @@ void check_launch(cudaStream_t st, const char* what, const char* file, int line)
 }
 }  // namespace lqmpc
 
+namespace lqmpc {
+// Captured CUDA graphs of the fixed launch sequences of an iteration (keyed
+// by segment and precision).  Every kernel reads its data through the
+// instance descriptors in device memory, so a graph stays valid for as long
+// as the descriptor array it was captured with.
+struct GraphSeg {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;   // kernel launches one replay performs
+    bool bad = false;                 // capture or instantiation failed: launch directly
+};
+struct GraphCache {
+    std::map<int, GraphSeg> segs;
+    ~GraphCache() {
+        for (auto& kv : segs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    }
+};
+}  // namespace lqmpc
+
 struct lqmpc_ctx {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // where the context's work runs
+    cudaStream_t user_stream = nullptr;  // the stream given at setup (NULL: legacy default)
+    bool own_stream = false;             // stream created here for a NULL user stream
     lqmpc_options opts;
     Inst h;                     // host copy of the descriptor
     Inst* d_inst = nullptr;     // device copy
@@ -127,6 +149,7 @@ struct lqmpc_ctx {
     // per-solve SYRK timing
     double t_tc = 0, t_cc = 0, t_cc64 = 0;
     int n_tc = 0, n_cc = 0, n_cc64 = 0;
+    lqmpc::GraphCache* graphs = nullptr;   // single-instance solves (d_inst is fixed)
 };
 
 namespace {
@@ -221,6 +244,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto Xinv32 = c.take<float>((size_t)n * n); auto Tinv32 = c.take<float>((size_t)n * n);
     auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
+    auto ldiag = c.take<double>(2 * 32 * 32);
     auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);
     auto tmpx = c.take<double>(SX);
     auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n, I.N));
@@ -248,6 +272,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
+        I.ldiag = ldiag;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
         I.part = part; I.bar = bar; I.sc = sc; I.trace = trace; I.tc_plan = tc_plan;
@@ -263,8 +288,63 @@ struct Batch {
     int count = 0, max_ns = 0, max_N = 0, max_n = 0, max_sx = 0, max_total = 0;
     int cc_splits = 1, tc_splits = 1;
     cudaStream_t st = nullptr;
-    const void* d_maps = nullptr;   // tensor maps (batch of one only)
+    const void* d_maps = nullptr;   // tensor maps: 2 per instance (BF16, TF32), instance order
     bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
+    GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
+};
+
+// Off under the per-launch debug modes (they synchronise or record events per
+// launch) or with LQMPC_GRAPH=0.
+bool graphs_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        auto env_is = [](const char* k, char c) { const char* e = getenv(k); return e && e[0] == c; };
+        on = !(env_is("LQMPC_GRAPH", '0') || env_is("LQMPC_PROFILE", '1') || env_is("LQMPC_CHECK", '1'));
+    }
+    return on == 1;
+}
+
+// Run a fixed launch sequence: the first time under stream capture into a
+// graph (then replayed), or directly when graphs are off or capture failed.
+template <class F>
+void seg_run(const Batch& b, int key, F&& body) {
+    if (!b.gc || !graphs_enabled()) { body(); return; }
+    GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];   // the Gamma products differ with the arithmetic
+    if (g.bad) { body(); return; }
+    if (!g.exec) {
+        const unsigned long long k0 = lqmpc_kernel_launches();
+        if (cudaStreamBeginCapture(b.st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            if (getenv("LQMPC_DEBUG")) fprintf(stderr, "lqmpc: stream capture unavailable on this stream\n");
+            cudaGetLastError();
+            g.bad = true;
+            body();
+            return;
+        }
+        body();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b.st, &graph);
+        const unsigned long long nk = lqmpc_kernel_launches() - k0;
+        note_launches(-(int)nk);          // captured, not run
+        if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || !g.exec) {
+            if (getenv("LQMPC_DEBUG"))
+                fprintf(stderr, "lqmpc: graph capture of segment %d failed (%s); launching directly\n", key,
+                        cudaGetErrorString(e));
+            cudaGetLastError();
+            g.exec = nullptr;
+            g.bad = true;
+            body();
+            return;
+        }
+        g.kernels = nk;
+    }
+    if (cudaGraphLaunch(g.exec, b.st) == cudaSuccess) note_launches((int)g.kernels);
+}
+
+enum SegKey {
+    SEG_HEAD = 1, SEG_FORM = 10 /* + precision */, SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31,
+    SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50 /* + precision */
 };
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
@@ -290,7 +370,7 @@ void batch_dims(Batch& b) {
         b.max_sx = std::max(b.max_sx, c->h.SX);
         b.max_total = std::max(b.max_total, c->h.SX + c->h.n);
         b.cc_splits = std::min(b.cc_splits, c->cc_splits);
-        b.tc_splits = std::min(b.tc_splits, c->tc_splits);
+        b.tc_splits = b.tc_splits == (1 << 30) ? c->tc_splits : std::max(b.tc_splits, c->tc_splits);
     }
     b.st = b.ctxs[0]->stream;
 }
@@ -305,32 +385,54 @@ struct SyrkTimer {
 
 void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 0.0) {
     lqmpc_ctx* c0 = b.ctxs[0];
-    if (prec == LQMPC_FP64) {
-        if (tm) cudaEventRecord(c0->evk[2], b.st);
-        launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
-        if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; tm->cc64 = true; }
-        launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
-        launch_potrf(b.d_insts, b.count, b.max_n, 1, F_NONE, b.st);
-    } else {
-        if (prec == LQMPC_FP32) {
-            if (tm) cudaEventRecord(c0->evk[2], b.st);
-            launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
-            if (tm) { cudaEventRecord(c0->evk[3], b.st); tm->cc = true; tm->cc64 = false; }
-            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st, shift);
+    // Under capture the records must be external event nodes (not graph-internal
+    // dependencies); the external flag is only valid while capturing.
+    auto rec = [&](cudaEvent_t e) {
+        if (!tm) return;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(b.st, &cs);
+        if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, b.st, cudaEventRecordExternal);
+        else cudaEventRecord(e, b.st);
+    };
+    auto body = [&]() {
+        if (prec == LQMPC_FP64) {
+            rec(c0->evk[2]);
+            launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
+            rec(c0->evk[3]);
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, F_NONE, b.st);
         } else {
-            if (tm) cudaEventRecord(c0->evk[0], b.st);
-            launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
-                           F_NONE, b.st);
-            if (tm) { cudaEventRecord(c0->evk[1], b.st); tm->tc = true; }
-            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st, shift);
+            if (prec == LQMPC_FP32) {
+                rec(c0->evk[2]);
+                launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
+                rec(c0->evk[3]);
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st,
+                                   shift);
+            } else {
+                rec(c0->evk[0]);
+                launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
+                               F_NONE, b.st);
+                rec(c0->evk[1]);
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st,
+                                   shift);
+            }
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st, 1);
         }
-        launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st, 1);
+    };
+    // the timed and untimed sequences differ (event nodes): separate graphs
+    if (shift == 0.0) seg_run(b, SEG_FORM + prec + (tm ? 4 : 0), body);
+    else body();
+    if (tm) {
+        if (prec == LQMPC_FP64 || prec == LQMPC_FP32) { tm->cc = true; tm->cc64 = prec == LQMPC_FP64; }
+        else tm->tc = true;
     }
 }
 
 void kkt_solve_fp64(const Batch& b) {
-    launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
-    gmv(b, R_DU, R_DXS, F_NONE);
+    seg_run(b, SEG_SOLVE64, [&]() {
+        launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
+        gmv(b, R_DU, R_DXS, F_NONE);
+    });
 }
 
 lqmpc_status read_scals(Batch& b) {
@@ -345,32 +447,47 @@ lqmpc_status read_scals(Batch& b) {
 // flags every second step and stops launching once every unfinished instance
 // has converged or failed; afterwards each h_scal holds the outcome.
 lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
-    launch_pcg_begin(b.d_insts, b.count, b.st);
-    launch_prec_apply(b.d_insts, b.count, b.max_n, R_B, R_DU, F_NONE, b.st);
-    // initial residual r = b - M du and Gamma du
-    gmv(b, R_DU, R_TMPX, F_SKIP_REFINED);
-    gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
-    launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, F_NONE, b.st);
-    launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, b.st);
-    launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
-    launch_pcg_pinit(b.d_insts, b.count, b.st);
-    for (int s = 0; s < refine_max; ++s) {
+    seg_run(b, SEG_PCG0, [&]() {
+        launch_pcg_begin(b.d_insts, b.count, b.st);
+        launch_prec_apply(b.d_insts, b.count, b.max_n, R_B, R_DU, F_NONE, b.st);
+        // initial residual r = b - M du and Gamma du
+        gmv(b, R_DU, R_TMPX, F_SKIP_REFINED);
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, F_NONE, b.st);
+        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, b.st);
+        launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+        launch_pcg_pinit(b.d_insts, b.count, b.st);
+    });
+    // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
+    // the new direction (harmless after the last step: every kernel is
+    // predicated on the instance's refinement flags)
+    auto step = [&](bool with_next) {
         gmv(b, R_P, R_TMPX, F_SKIP_REFINED);
         gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
         launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, b.st);
         launch_pcg_step_update(b.d_insts, b.count, b.max_total, b.st);
-        if (s + 1 == refine_max) break;
+        if (!with_next) return;
         launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
         launch_pcg_beta(b.d_insts, b.count, b.st);
-        if (s % 2 == 0) {
-            lqmpc_status st = read_scals(b);
-            if (st != LQMPC_OK) return st;
-            bool pending = false;
-            for (auto* c : b.ctxs)
-                if (!c->h_scal->done && !c->h_scal->refine_ok && !c->h_scal->refine_fail && !c->h_scal->info)
-                    pending = true;
-            if (!pending) break;
+    };
+    // The host looks at the flags after every second step and stops launching
+    // once every unfinished instance has converged or failed.
+    for (int s = 0; s < refine_max;) {
+        if (s + 2 <= refine_max) {
+            seg_run(b, SEG_PCG2, [&]() { step(true); step(true); });
+            s += 2;
+        } else {
+            step(false);
+            s += 1;
         }
+        if (s >= refine_max) break;
+        lqmpc_status st = read_scals(b);
+        if (st != LQMPC_OK) return st;
+        bool pending = false;
+        for (auto* c : b.ctxs)
+            if (!c->h_scal->done && !c->h_scal->refine_ok && !c->h_scal->refine_fail && !c->h_scal->info)
+                pending = true;
+        if (!pending) break;
     }
     return read_scals(b);
 }
@@ -494,26 +611,30 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     for (int it = 0; it <= o.max_iter; ++it) {
         SyrkTimer tm;
         // residuals, Sigma, stop test
-        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
-        gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
-        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
+        seg_run(b, SEG_HEAD, [&]() {
+            launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
+            gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
+            launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
+        });
         cudaEventRecord(c0->ev[2], b.st);
         // predictor: form and factor M, solve M du_aff = b
         lqmpc_status s = kkt_step(b, o, cur, false, &tm);
         if (s != LQMPC_OK) return s;
-        launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
-        // affine step, sigma, corrector right-hand side
-        launch_aff(b.d_insts, b.count, b.max_total, b.st);
-        launch_corr(b.d_insts, b.count, b.max_total, b.st);
-        gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
-        launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+        seg_run(b, SEG_PRED_TAIL, [&]() {
+            launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
+            launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
+            // affine step, sigma, corrector right-hand side
+            launch_aff(b.d_insts, b.count, b.max_total, b.st);
+            launch_corr(b.d_insts, b.count, b.max_total, b.st);
+            gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
+            launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+        });
         // corrector: same factor
         s = kkt_step(b, o, cur, true, &tm);
         if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
-        launch_step_update(b.d_insts, b.count, b.max_total, 1, cur, b.st);
+        seg_run(b, SEG_CORR_TAIL + cur, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, cur, b.st); });
         s = read_scals(b);
         if (s != LQMPC_OK) return s;
         float ms = 0.f;
@@ -584,6 +705,8 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
     b.d_insts = ctx->d_inst;
     batch_dims(b);
     b.d_maps = ctx->tc_ok ? ctx->d_maps : nullptr;
+    if (!ctx->graphs) ctx->graphs = new (std::nothrow) GraphCache();
+    b.gc = ctx->graphs;
     double tt = 0, tk = 0;
     lqmpc_status s = run_ipm(b, ctx->opts, &tt, &tk);
     if (s != LQMPC_OK) return s;
@@ -665,7 +788,18 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     lqmpc_ctx* ctx = new (std::nothrow) lqmpc_ctx();
     if (!ctx) return LQMPC_ERR_CUDA;
     cudaGetDevice(&ctx->device);
+    ctx->user_stream = (cudaStream_t)stream;
     ctx->stream = (cudaStream_t)stream;
+    if (!stream) {
+        // Own blocking stream: it stays ordered with the legacy default stream
+        // (where the caller's work goes) and, unlike it, can be captured into
+        // CUDA graphs.
+        if (cudaStreamCreate(&ctx->stream) != cudaSuccess) {
+            delete ctx;
+            return LQMPC_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
     ctx->opts = o;
     Inst& I = ctx->h;
     memset(&I, 0, sizeof(I));
@@ -775,10 +909,12 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
                                double* const* u_outs, lqmpc_stats* stats) {
     if (!ctxs || count < 1 || !x0s || !u_outs) return LQMPC_ERR_ARG;
     for (int i = 0; i < count; ++i)
-        if (!ctxs[i] || !x0s[i] || !u_outs[i] || ctxs[i]->stream != ctxs[0]->stream ||
+        if (!ctxs[i] || !x0s[i] || !u_outs[i] || ctxs[i]->user_stream != ctxs[0]->user_stream ||
             ctxs[i]->device != ctxs[0]->device)
             return LQMPC_ERR_ARG;
     CK(cudaSetDevice(ctxs[0]->device));
+    for (int i = 1; i < count; ++i)      // contexts with streams of their own: nothing may be in flight
+        if (ctxs[i]->stream != ctxs[0]->stream) CK(cudaStreamSynchronize(ctxs[i]->stream));
     Batch b;
     b.ctxs.assign(ctxs, ctxs + count);
     batch_dims(b);
@@ -787,16 +923,32 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (!all_finite(x0s[i], ctxs[i]->h.ns)) return LQMPC_ERR_ARG;
         if (ctxs[i]->opts.max_iter < o.max_iter) o.max_iter = ctxs[i]->opts.max_iter;
     }
-    if (o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32) {
-        if (count > 1) o.precision = LQMPC_FP32;  // per-instance tensor maps: single instance only
-        else b.d_maps = ctxs[0]->tc_ok ? ctxs[0]->d_maps : nullptr;
-    }
+    bool tc = o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32;
+    for (int i = 0; i < count && tc; ++i)
+        if (!ctxs[i]->tc_ok) tc = false;
+    if ((o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32) && !tc) o.precision = LQMPC_FP32;
     std::vector<Inst> hosts(count);
     for (int i = 0; i < count; ++i) hosts[i] = ctxs[i]->h;
     Inst* d = nullptr;
+    void* maps = nullptr;
     CK(cudaMalloc(&d, sizeof(Inst) * count));
+    if (tc && count > 1 && cudaMalloc(&maps, 256 * (size_t)count) != cudaSuccess) {
+        cudaFree(d);
+        return LQMPC_ERR_CUDA;
+    }
     b.d_insts = d;
     lqmpc_status s = LQMPC_OK;
+    if (tc) {
+        // every instance's two tensor maps, in instance order (the kernel indexes them by blockIdx.y)
+        if (count == 1) b.d_maps = ctxs[0]->d_maps;
+        else {
+            for (int i = 0; i < count && s == LQMPC_OK; ++i)
+                if (cudaMemcpyAsync((char*)maps + 256 * (size_t)i, ctxs[i]->d_maps, 256, cudaMemcpyDeviceToDevice,
+                                    b.st) != cudaSuccess)
+                    s = LQMPC_ERR_CUDA;
+            b.d_maps = maps;
+        }
+    }
     if (cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess)
         s = LQMPC_ERR_CUDA;
     for (int i = 0; i < count && s == LQMPC_OK; ++i)
@@ -804,7 +956,12 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
                             b.st) != cudaSuccess)
             s = LQMPC_ERR_CUDA;
     double tt = 0, tk = 0;
-    if (s == LQMPC_OK) s = run_ipm(b, o, &tt, &tk);
+    {
+        GraphCache gc;      // graphs of this call's descriptor array
+        b.gc = &gc;
+        if (s == LQMPC_OK) s = run_ipm(b, o, &tt, &tk);
+        b.gc = nullptr;
+    }
     if (s == LQMPC_OK) {
         for (int i = 0; i < count; ++i)
             if (cudaMemcpyAsync(u_outs[i], ctxs[i]->h.u, sizeof(double) * ctxs[i]->h.n, cudaMemcpyDeviceToHost,
@@ -813,6 +970,7 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (cudaStreamSynchronize(b.st) != cudaSuccess) s = LQMPC_ERR_CUDA;
     }
     cudaFree(d);
+    cudaFree(maps);
     if (s != LQMPC_OK) return s;
     lqmpc_status first = LQMPC_OK;
     for (int i = 0; i < count; ++i) {
@@ -830,6 +988,8 @@ void lqmpc_free(lqmpc_ctx* ctx) {
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
+    delete ctx->graphs;
+    ctx->graphs = nullptr;
     if (ctx->events)
         for (int e = 0; e < 4; ++e) {
             cudaEventDestroy(ctx->ev[e]);
@@ -839,6 +999,7 @@ void lqmpc_free(lqmpc_ctx* ctx) {
     cudaFree(ctx->d_inst);
     cudaFree(ctx->d_maps);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 

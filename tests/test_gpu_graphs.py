@@ -1,0 +1,63 @@
+"""Captured CUDA graphs of the fixed launch sequences of an iteration replay
+exactly the kernels a direct launch sequence runs: same results bit for bit
+and the same kernel count (child processes, graphs on and off)."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2209_13049_b300 import binding, build
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np
+from paper_2209_13049_b300 import binding, inputs
+out = {}
+for prec in ("fp64", "bf16", "fp32"):
+    p = inputs.heat2d(16, 6, 20)
+    s = binding.Solver(p, precision=prec)
+    k0 = binding.kernel_launches()
+    us = []
+    for seed in (0, 1):
+        u, st = s.solve(inputs.x0_gaussians(16, seed))
+        assert st["status"] == 0
+        us.append(u.tobytes().hex())
+    out[prec] = {"u": us, "launches": binding.kernel_launches() - k0}
+g = [inputs.heat1d(40 + 5 * k, 2 + k % 3, 6 + k) for k in range(4)]
+solvers = [binding.Solver(p, precision="bf16") for p in g]
+us, stats, code = binding.solve_batch(solvers, [inputs.x0_uniform(p.ns, k) for k, p in enumerate(g)])
+assert code == 0
+out["batch"] = {"u": [u.tobytes().hex() for u in us]}
+print(json.dumps(out))
+"""
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.load()
+
+
+def _run(graph):
+    env = dict(os.environ, LQMPC_GRAPH="1" if graph else "0", LQMPC_DEBUG="1")
+    env.pop("LQMPC_PROFILE", None)
+    env.pop("LQMPC_CHECK", None)
+    r = subprocess.run([sys.executable, "-c", CHILD], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1]), r.stderr
+
+
+def test_graph_replay_equals_direct_launches():
+    on, err_on = _run(True)
+    off, _ = _run(False)
+    assert "graph capture" not in err_on and "capture unavailable" not in err_on, err_on[-2000:]
+    for key in ("fp64", "bf16", "fp32"):
+        assert on[key]["u"] == off[key]["u"], key
+        assert on[key]["launches"] == off[key]["launches"], key
+    assert on["batch"]["u"] == off["batch"]["u"]

@@ -206,3 +206,39 @@ def test_large_batch_cluster_factor_matches_single():
         assert rel(us[k], u1) <= 1e-9, k
     ref = oracle.ipm_solve(inputs.heat1d(*sizes[7]), x0s[7], tol=1e-11)
     assert rel(us[7], ref["u"]) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_batch_uneven_tensor_core_matches_oracle(precision):
+    """Batches run the tensor-core SYRK with every instance's own tensor maps
+    and split plan (grid.y = instance)."""
+    g = np.load(os.path.join(GOLD, "batch_small.npz"))
+    solvers, x0s, refs = [], [], []
+    for k in range(6):
+        ns, nu, N, gside = (int(v) for v in g[f"b{k}_dims"])
+        p = inputs.heat1d(ns, nu, N) if gside == 0 else inputs.heat2d(gside, nu, N)
+        solvers.append(binding.Solver(p, tol=1e-11, precision=precision))
+        x0s.append(g[f"b{k}_x0"])
+        refs.append(g[f"b{k}_u12"])
+    us, stats, code = binding.solve_batch(solvers, x0s)
+    assert code == 0
+    for k in range(6):
+        assert stats[k]["status"] == 0
+        assert rel(us[k], refs[k]) <= 1e-6, k
+    assert stats[0]["syrk_tc_launches"] > 0
+
+
+def test_uneven_batch_cooperative_factor_matches_single():
+    """First 24 instances of the uneven 256-instance batch (n up to 800, too
+    large for the cluster factorisation): the grid-cooperative Cholesky then
+    interleaves the panels of many instances, and each instance must still
+    take the iterates it takes alone."""
+    inst = inputs.batch_instances(256, 0)[:24]
+    solvers = [binding.Solver(p) for p, _ in inst]
+    x0s = [x for _, x in inst]
+    singles = [s.solve(x)[0] for s, x in zip(solvers, x0s)]
+    us, stats, code = binding.solve_batch(solvers, x0s)
+    assert code == 0
+    for k in range(len(inst)):
+        assert stats[k]["status"] == 0
+        assert rel(us[k], singles[k]) <= 1e-8, k
