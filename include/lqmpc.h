@@ -148,6 +148,19 @@ lqmpc_status lqmpc_solve_device(lqmpc_ctx* ctx, const double* x0_device, double*
                                 lqmpc_stats* stats);
 
 /*
+ * Warm-started solve (the learned warm start; the paper starts cold): as
+ * lqmpc_solve, but the iterations start from the guess u_init (nu*N, host)
+ * instead of the box midpoint.  u0 = u_init clipped into the input box with a
+ * margin of 1% of each two-sided range (1e-2 from a one-sided bound); x0 =
+ * the rollout of u0; every slack s0 = max(slack, 1e-2) and every dual
+ * z0 = mu0 / s0, a start centred at complementarity mu0 (mu0 <= 0 selects
+ * 1e-2).  Any u_init gives the same optimum (the QP is strictly convex); a
+ * good one saves iterations.  LQMPC_ERR_ARG for a non-finite u_init.
+ */
+lqmpc_status lqmpc_solve_warm(lqmpc_ctx* ctx, const double* x0, const double* u_init, double mu0,
+                              double* u_out, lqmpc_stats* stats);
+
+/*
  * Solve `count` independent problems (contexts may differ in ns, nu, N and
  * options other than precision, which is taken from ctxs[0]) in lockstep:
  * every kernel launch of an iteration covers all unfinished instances.
@@ -245,6 +258,54 @@ lqmpc_status lqmpc_get_trace(lqmpc_ctx* ctx, double* trace, int max_rows, int* r
 
 /* Final duals of the last solve: [z_xu (ns*N), z_xl (ns*N), z_uu (n), z_ul (n)]. */
 lqmpc_status lqmpc_get_duals(lqmpc_ctx* ctx, double* z);
+
+/* ---------------------------------------------------------------------------
+ * Warm-start network (not in the paper): an MLP
+ *     x0 -> GELU(W1 x0 + b1) -> GELU(W2 . + b2) -> W3 . + b3 -> clamp to [lo, hi]
+ * mapping an initial state to an input sequence, trained on (x0, u*) pairs
+ * with Adam on the mean squared error, its products on the tcgen05 tensor
+ * cores in BF16 with FP32 accumulation (FP32 master weights).  GELU is the
+ * erf form.  Parameters are exchanged as one FP32 array in the order
+ * W1 (n_hidden x n_in, row-major), b1, W2 (n_hidden x n_hidden), b2,
+ * W3 (n_out x n_hidden), b3.  All calls run on the network's stream (NULL:
+ * an own blocking stream, as for contexts) and return when done.
+ * ------------------------------------------------------------------------ */
+typedef struct lqmpc_mlp lqmpc_mlp;
+
+/* Create a network; weights and biases ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in))
+ * from `seed`.  n_hidden must be a multiple of 128; batches of up to
+ * max_batch rows.  Output bounds start at (-inf, inf). */
+lqmpc_status lqmpc_mlp_create(lqmpc_mlp** out, int n_in, int n_hidden, int n_out, int max_batch,
+                              unsigned long long seed, void* stream);
+
+/* Projection box of the outputs (n_out each, lo <= hi). */
+lqmpc_status lqmpc_mlp_set_bounds(lqmpc_mlp* mlp, const double* lo, const double* hi);
+
+/* Copy the FP32 master parameters out / in (set also resets Adam's state). */
+lqmpc_status lqmpc_mlp_get_params(lqmpc_mlp* mlp, float* params);
+lqmpc_status lqmpc_mlp_set_params(lqmpc_mlp* mlp, const float* params);
+
+/* One forward and backward pass without an update: grads (same layout as
+ * the parameters) of L = mean over the B x n_out entries of (y - U)^2 at the
+ * unprojected output y; *loss = L.  X: B x n_in, U: B x n_out, FP32 host. */
+lqmpc_status lqmpc_mlp_grad(lqmpc_mlp* mlp, const float* X, const float* U, int B, float* grads,
+                            double* loss);
+
+/* Train for `epochs` passes over S samples (X: S x n_in, U: S x n_out, FP32
+ * host) in shuffled minibatches of `batch` (the last partial batch of an
+ * epoch is dropped), Adam (beta1 0.9, beta2 0.999, eps 1e-8) with step size
+ * lr.  epoch_loss (nullable, `epochs` entries) receives each epoch's mean
+ * training loss.  One training step is captured as a CUDA graph and
+ * replayed (LQMPC_GRAPH=0 launches directly). */
+lqmpc_status lqmpc_mlp_train(lqmpc_mlp* mlp, const float* X, const float* U, int S, int epochs, int batch,
+                             float lr, unsigned long long seed, double* epoch_loss);
+
+/* Projected outputs for `count` inputs (x: count x n_in, u_out: count x
+ * n_out, FP64 host); the inputs are rounded to BF16 like the training data. */
+lqmpc_status lqmpc_mlp_infer(lqmpc_mlp* mlp, const double* x, int count, double* u_out);
+
+/* Release a network (NULL is a no-op). */
+void lqmpc_mlp_free(lqmpc_mlp* mlp);
 
 #ifdef __cplusplus
 }

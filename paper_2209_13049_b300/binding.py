@@ -27,7 +27,9 @@ EXPORTS = ["lqmpc_default_options", "lqmpc_status_str", "lqmpc_setup", "lqmpc_se
            "lqmpc_solve", "lqmpc_solve_device", "lqmpc_solve_batch", "lqmpc_free",
            "lqmpc_get_gstack", "lqmpc_get_hessian", "lqmpc_gamma_mv", "lqmpc_gamma_tmv",
            "lqmpc_form_kkt", "lqmpc_kkt_solve", "lqmpc_get_trace", "lqmpc_get_duals",
-           "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc"]
+           "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc", "lqmpc_solve_warm", "lqmpc_mlp_create",
+           "lqmpc_mlp_set_bounds", "lqmpc_mlp_get_params", "lqmpc_mlp_set_params", "lqmpc_mlp_grad",
+           "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free"]
 
 
 class LqmpcError(RuntimeError):
@@ -100,6 +102,24 @@ def load(path: str = LIB_PATH):
     lib.lqmpc_kernel_launches.argtypes = []
     lib.lqmpc_get_trace.restype = I
     lib.lqmpc_get_trace.argtypes = [P, P, I, ctypes.POINTER(I)]
+    lib.lqmpc_solve_warm.restype = I
+    lib.lqmpc_solve_warm.argtypes = [P, P, P, D, P, ctypes.POINTER(Stats)]
+    lib.lqmpc_mlp_create.restype = I
+    lib.lqmpc_mlp_create.argtypes = [ctypes.POINTER(P), I, I, I, I, ctypes.c_ulonglong, VP]
+    lib.lqmpc_mlp_set_bounds.restype = I
+    lib.lqmpc_mlp_set_bounds.argtypes = [P, P, P]
+    for name in ("lqmpc_mlp_get_params", "lqmpc_mlp_set_params"):
+        f = getattr(lib, name)
+        f.restype = I
+        f.argtypes = [P, P]
+    lib.lqmpc_mlp_grad.restype = I
+    lib.lqmpc_mlp_grad.argtypes = [P, P, P, I, P, ctypes.POINTER(D)]
+    lib.lqmpc_mlp_train.restype = I
+    lib.lqmpc_mlp_train.argtypes = [P, P, P, I, I, I, ctypes.c_float, ctypes.c_ulonglong, P]
+    lib.lqmpc_mlp_infer.restype = I
+    lib.lqmpc_mlp_infer.argtypes = [P, P, I, P]
+    lib.lqmpc_mlp_free.restype = None
+    lib.lqmpc_mlp_free.argtypes = [P]
     _lib = lib
     return lib
 
@@ -221,6 +241,15 @@ class Solver:
         _check(load().lqmpc_form_kkt(self.h, _p(_f64(sigx)), _p(_f64(sigu)), p, _p(M)), "lqmpc_form_kkt")
         return np.asarray(M)
 
+    def solve_warm(self, x0, u_init, mu0: float = 0.0, check: bool = True):
+        """Warm-started solve from the guess u_init (nu*N); returns (u, stats)."""
+        u = np.zeros(self.n)
+        st = Stats()
+        code = load().lqmpc_solve_warm(self.h, _p(_f64(x0)), _p(_f64(u_init)), float(mu0), _p(u), ctypes.byref(st))
+        if check and code != 0:
+            raise LqmpcError(code, "lqmpc_solve_warm")
+        return u, st.as_dict()
+
     def form_kkt_noalloc(self, sigx, sigu, M):
         """FP64 M into the CUDA tensor M (n x n, read column-major) from CUDA
         tensors sigx (ns*N) and sigu (n); allocates nothing and does not wait
@@ -275,3 +304,65 @@ def solve_batch(solvers, x0s, check: bool = True):
     if check and code != 0:
         raise LqmpcError(code, "lqmpc_solve_batch")
     return us, [s.as_dict() for s in stats], code
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+
+
+class MLP:
+    """The warm-start network (lqmpc_mlp_*): n_in -> n_hidden -> n_hidden -> n_out."""
+
+    def __init__(self, n_in: int, n_hidden: int, n_out: int, max_batch: int, seed: int = 0, stream=None):
+        self.n_in, self.n_hidden, self.n_out = n_in, n_hidden, n_out
+        self.h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
+        _check(load().lqmpc_mlp_create(ctypes.byref(self.h), n_in, n_hidden, n_out, max_batch, seed, st),
+               "lqmpc_mlp_create")
+
+    @property
+    def n_params(self) -> int:
+        i, h, o = self.n_in, self.n_hidden, self.n_out
+        return h * i + h + h * h + h + o * h + o
+
+    def set_bounds(self, lo, hi):
+        _check(load().lqmpc_mlp_set_bounds(self.h, _p(_f64(lo)), _p(_f64(hi))), "lqmpc_mlp_set_bounds")
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().lqmpc_mlp_get_params(self.h, _p(out)), "lqmpc_mlp_get_params")
+        return out
+
+    def set_params(self, flat):
+        _check(load().lqmpc_mlp_set_params(self.h, _p(_f32(flat))), "lqmpc_mlp_set_params")
+
+    def grad(self, X, U):
+        X, U = _f32(X), _f32(U)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        _check(load().lqmpc_mlp_grad(self.h, _p(X), _p(U), X.shape[0], _p(g), ctypes.byref(loss)), "lqmpc_mlp_grad")
+        return g, loss.value
+
+    def train(self, X, U, epochs: int, batch: int, lr: float, seed: int = 0):
+        X, U = _f32(X), _f32(U)
+        losses = np.zeros(max(epochs, 1))
+        _check(load().lqmpc_mlp_train(self.h, _p(X), _p(U), X.shape[0], epochs, batch, float(lr), seed, _p(losses)),
+               "lqmpc_mlp_train")
+        return losses[:epochs]
+
+    def infer(self, X):
+        X = _f64(X)
+        out = np.zeros((X.shape[0], self.n_out))
+        _check(load().lqmpc_mlp_infer(self.h, _p(X), X.shape[0], _p(out)), "lqmpc_mlp_infer")
+        return out
+
+    def close(self):
+        if self.h:
+            load().lqmpc_mlp_free(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -2,6 +2,7 @@
 // instance descriptors; grid.y = instance).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -12,9 +13,10 @@ namespace lqmpc {
 struct Inst;
 
 // kernels_ipm.cu
-void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st);
+void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm = 0);
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
-                       double tau, int max_iter, double refine_tol, cudaStream_t st);
+                       double tau, int max_iter, double refine_tol, cudaStream_t st, double mu0 = 0.0,
+                       double smin = 1.0);
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
                         cudaStream_t st, bool do_resid, bool do_rd);
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st);
@@ -66,6 +68,7 @@ void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, cudaS
 void launch_pcg_beta(const Inst* d_insts, int count, cudaStream_t st);
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
                      int len_kind, int force, cudaStream_t st);
+void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st);
 
 // kernels_tc.cu (tcgen05 tensor-core SYRK)
 int syrk_tc_tiles(int n);
@@ -81,5 +84,37 @@ void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int t
 int noalloc_max_n();
 int launch_form_kkt_noalloc(const double* G, int ldg, const double* H, const double* sigx, const double* sigu,
                             double* M, int ns, int nu, int N, cudaStream_t st);
+
+// kernels_mlp.cu (warm-start network: tcgen05 GEMMs with fused epilogues)
+// Epilogue operands of one GEMM C[M x N] = A[M x K] B[N x K]^T: row-major
+// outputs of M x N (ld N); transposed BF16 copies N x (ld ldt).
+struct GemmEpi {
+    int M, N, ldt;
+    const float* bias;       // N
+    float* zf;               // M x N FP32 (z, y or the weight gradient)
+    const float* zin;        // M x N FP32 pre-activations (GELU backward)
+    __nv_bfloat16* yb;       // M x N BF16
+    __nv_bfloat16* ybt;      // N x ldt BF16
+    const float* target;     // M x N FP32 (loss)
+    int m_real, n_real;      // rows / columns that carry data
+    float gscale;            // loss gradient scale 2 / (B n_out)
+    double* loss_part;       // per-CTA partial sums of squares
+    const double* lo;        // N projection bounds (inference)
+    const double* hi;
+    double* out64;           // m_real x n_real FP64 (inference)
+    int* err;                // bit 0: a bounded wait gave up
+};
+enum { EPI_WGRAD = 0, EPI_BIAS_GELU = 1, EPI_BIAS_LOSS = 2, EPI_GELU_BWD = 3, EPI_BIAS_PROJ = 4 };
+bool mlp_make_map(void* map_out, const void* base, int rows, int cols);
+void mlp_gemm(int epi, const void* mapA, const void* mapB, int M, int N, int K, const GemmEpi& ep, cudaStream_t st);
+void mlp_gather(const float* Xs, const float* Us, const int* idx, int B, int Bp, int ldt, int nin, int inp, int nout,
+                int outp, __nv_bfloat16* X, __nv_bfloat16* XT, float* T, cudaStream_t st);
+void mlp_colsum(const __nv_bfloat16* GT, int F, int Bp, int ldt, float* db, cudaStream_t st);
+void mlp_adam(float* w, const float* g, float* m, float* v, size_t count, float lr, float b1, float b2, float eps,
+              const int* tstep, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wbt, cudaStream_t st);
+void mlp_tick(int* tstep, cudaStream_t st);
+void mlp_cast(const float* w, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wbt, cudaStream_t st);
+void mlp_load_x(const double* x, int count, int nin, int inp, int Bp, __nv_bfloat16* X, cudaStream_t st);
+void mlp_sum(const double* part, int n, double* out, cudaStream_t st);
 
 }  // namespace lqmpc

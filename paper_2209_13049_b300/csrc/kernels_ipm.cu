@@ -55,23 +55,41 @@ __device__ __forceinline__ void put_part(const Inst& I, int slot, double v) {
 // ---------------------------------------------------------------------------
 // Initial point.  u0 = box midpoint (lo+1 / hi-1 for one-sided boxes, 0 for
 // none); x0 = y + Gamma u0 (Gamma u0 precomputed into tmpx); s0 = max(slack, 1)
-// and z0 = 1 for present rows.  Also the norms ||d|| and ||h|| of the stop
+// and z0 = 1 for present rows.  The warm start replaces u0 by a clipped guess
+// and z0 by mu0 / s0.  Also the norms ||d|| and ||h|| of the stop
 // test and the row count m.
 // ---------------------------------------------------------------------------
 
-__global__ void k_set_u0(const Inst* __restrict__ insts) {
+__global__ void k_set_u0(const Inst* __restrict__ insts, int warm) {
     const Inst& I = insts[blockIdx.y];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x) {
         int c = j % I.nu;
         double lo = I.ul[c], hi = I.uu[c];
         bool fl = isfinite(lo), fh = isfinite(hi);
-        I.u[j] = (fl && fh) ? 0.5 * (lo + hi) : fl ? lo + 1.0 : fh ? hi - 1.0 : 0.0;
+        if (!warm) {
+            I.u[j] = (fl && fh) ? 0.5 * (lo + hi) : fl ? lo + 1.0 : fh ? hi - 1.0 : 0.0;
+        } else {
+            // warm start: the guess (staged in du_aff) clipped into the box with
+            // a margin of 1% of a two-sided range, 1e-2 for a one-sided bound
+            const double g = I.du_aff[j];
+            const double mg = (fl && fh) ? 0.01 * (hi - lo) : 0.01;
+            double v = g;
+            if (fl) v = fmax(v, lo + mg);
+            if (fh) v = fmin(v, hi - mg);
+            if (fl && fh && hi - lo <= 2.0 * mg) v = 0.5 * (lo + hi);
+            I.u[j] = v;
+        }
     }
 }
 
-__global__ void k_init_slacks(const Inst* __restrict__ insts) {
+// Cold start: s = max(slack, 1), z = 1.  Warm start (mu0 > 0): s =
+// max(slack, smin), z = mu0 / s, a start centred at complementarity mu0.
+__global__ void k_init_slacks(const Inst* __restrict__ insts, double mu0, double smin) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
+    const bool warm = mu0 > 0.0;
+    const double sfloor = warm ? smin : 1.0;
+    auto zof = [&](double sv) { return warm ? mu0 / sv : 1.0; };
     const int total = I.SX + I.n;
     double cnt = 0.0, dmax = 0.0, hmax = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -81,8 +99,8 @@ __global__ void k_init_slacks(const Inst* __restrict__ insts) {
             I.x[k] = xk;
             double hi = I.xu[i], lo = I.xl[i];
             bool fu = isfinite(hi), fl = isfinite(lo);
-            I.s1[k] = fu ? fmax(hi - xk, 1.0) : 1.0; I.z1[k] = fu ? 1.0 : 0.0;
-            I.s2[k] = fl ? fmax(xk - lo, 1.0) : 1.0; I.z2[k] = fl ? 1.0 : 0.0;
+            I.s1[k] = fu ? fmax(hi - xk, sfloor) : 1.0; I.z1[k] = fu ? zof(I.s1[k]) : 0.0;
+            I.s2[k] = fl ? fmax(xk - lo, sfloor) : 1.0; I.z2[k] = fl ? zof(I.s2[k]) : 0.0;
             cnt += (double)fu + (double)fl;
             double yk = I.y[k];
             if (fu) dmax = fmax(dmax, fabs(hi - yk));
@@ -91,8 +109,8 @@ __global__ void k_init_slacks(const Inst* __restrict__ insts) {
             int j = k - I.SX, c = j % I.nu;
             double uj = I.u[j], hi = I.uu[c], lo = I.ul[c];
             bool fu = isfinite(hi), fl = isfinite(lo);
-            I.s3[j] = fu ? fmax(hi - uj, 1.0) : 1.0; I.z3[j] = fu ? 1.0 : 0.0;
-            I.s4[j] = fl ? fmax(uj - lo, 1.0) : 1.0; I.z4[j] = fl ? 1.0 : 0.0;
+            I.s3[j] = fu ? fmax(hi - uj, sfloor) : 1.0; I.z3[j] = fu ? zof(I.s3[j]) : 0.0;
+            I.s4[j] = fl ? fmax(uj - lo, sfloor) : 1.0; I.z4[j] = fl ? zof(I.s4[j]) : 0.0;
             cnt += (double)fu + (double)fl;
             if (fu) dmax = fmax(dmax, fabs(hi));
             if (fl) dmax = fmax(dmax, fabs(lo));
@@ -406,14 +424,14 @@ static int ew_blocks(int total_max, int threads) {
 }
 
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
-                       double tau, int max_iter, double refine_tol, cudaStream_t st) {
+                       double tau, int max_iter, double refine_tol, cudaStream_t st, double mu0, double smin) {
     int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(k_init_slacks<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(k_init_slacks<<<dim3(nb, count), 256, 0, st>>>(d_insts, mu0, smin));
     LQ_LAUNCH(k_init_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, tol, tau, max_iter, refine_tol));
 }
 
-void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
-    LQ_LAUNCH(k_set_u0<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
+void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm) {
+    LQ_LAUNCH(k_set_u0<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts, warm));
 }
 
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,

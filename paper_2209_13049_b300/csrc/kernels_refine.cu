@@ -171,6 +171,15 @@ __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < len; k += gridDim.x * blockDim.x) d[k] = s[k];
 }
 
+// dst += src over the instance's n entries (instances not done).
+__global__ void k_vec_add(const Inst* __restrict__ insts, int src_role, int dst_role) {
+    const Inst& I = insts[blockIdx.y];
+    if (I.sc->done) return;
+    const double* s = role_ptr(I, src_role);
+    double* d = role_ptr(I, dst_role);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.n; k += gridDim.x * blockDim.x) d[k] += s[k];
+}
+
 static int nblk(int len, int th, int cap) {
     int b = (len + th - 1) / th;
     return b < 1 ? 1 : (b > cap ? cap : b);
@@ -207,6 +216,10 @@ void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, 
                      int len_kind, int force, cudaStream_t st) {
     LQ_LAUNCH(k_vec_copy<<<dim3(nblk(max_len, 256, 4096), count), 256, 0, st>>>(d_insts, src_role, dst_role,
                                                                                  len_kind, force));
+}
+
+void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st) {
+    LQ_LAUNCH(k_vec_add<<<dim3(nblk(max_n, 256, 1024), count), 256, 0, st>>>(d_insts, src_role, dst_role));
 }
 
 }  // namespace lqmpc

@@ -291,6 +291,7 @@ struct Batch {
     const void* d_maps = nullptr;   // tensor maps: 2 per instance (BF16, TF32), instance order
     bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
+    double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
 };
 
 // Off under the per-launch debug modes (they synchronise or record events per
@@ -428,6 +429,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
     }
 }
 
+// FP64 factor: the direct solve.
 void kkt_solve_fp64(const Batch& b) {
     seg_run(b, SEG_SOLVE64, [&]() {
         launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
@@ -446,16 +448,23 @@ lqmpc_status read_scals(Batch& b) {
 // as preconditioner and FP64 products with M.  The host looks at the instance
 // flags every second step and stops launching once every unfinished instance
 // has converged or failed; afterwards each h_scal holds the outcome.
-lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
-    seg_run(b, SEG_PCG0, [&]() {
+lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false) {
+    // preconditioner P^{-1}: the FP32 explicit inverse of the low-precision
+    // factor, or (prec64) the FP64 triangular solves
+    auto prec = [&](int in, int out, int flags) {
+        if (prec64) launch_chol_solve(b.d_insts, b.count, b.max_n, 1, in, out, flags, b.st);
+        else launch_prec_apply(b.d_insts, b.count, b.max_n, in, out, flags, b.st);
+    };
+    const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
+    seg_run(b, SEG_PCG0 + kp, [&]() {
         launch_pcg_begin(b.d_insts, b.count, b.st);
-        launch_prec_apply(b.d_insts, b.count, b.max_n, R_B, R_DU, F_NONE, b.st);
+        prec(R_B, R_DU, F_NONE);
         // initial residual r = b - M du and Gamma du
         gmv(b, R_DU, R_TMPX, F_SKIP_REFINED);
         gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, F_NONE, b.st);
         launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, b.st);
-        launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+        prec(R_RHO, R_DCORR, F_SKIP_REFINED);
         launch_pcg_pinit(b.d_insts, b.count, b.st);
     });
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
@@ -467,14 +476,14 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
         launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, b.st);
         launch_pcg_step_update(b.d_insts, b.count, b.max_total, b.st);
         if (!with_next) return;
-        launch_prec_apply(b.d_insts, b.count, b.max_n, R_RHO, R_DCORR, F_SKIP_REFINED, b.st);
+        prec(R_RHO, R_DCORR, F_SKIP_REFINED);
         launch_pcg_beta(b.d_insts, b.count, b.st);
     };
     // The host looks at the flags after every second step and stops launching
     // once every unfinished instance has converged or failed.
     for (int s = 0; s < refine_max;) {
         if (s + 2 <= refine_max) {
-            seg_run(b, SEG_PCG2, [&]() { step(true); step(true); });
+            seg_run(b, SEG_PCG2 + kp, [&]() { step(true); step(true); });
             s += 2;
         } else {
             step(false);
@@ -492,16 +501,20 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max) {
     return read_scals(b);
 }
 
+constexpr double kWarmSlackFloor = 1e-2;   // warm start: s0 = max(slack, 1e-2)
+constexpr double kWarmMu0 = 1e-2;          // default complementarity of a warm start
+
 // Per-solve preparation: y = Phi xbar, h = Gamma' Qbar y, initial point.
 void prepare(const Batch& b, const lqmpc_options& o) {
     for (auto* c : b.ctxs) cudaMemsetAsync(c->h.sc, 0, sizeof(Scal), b.st);
     launch_ychain(b.d_insts, b.count, b.st);
     launch_qbar_y(b.d_insts, b.count, b.max_sx, b.st);
     gtmv(b, R_TMPX, R_NONE, R_H, R_NONE, 0, F_FORCE);
-    launch_set_u0(b.d_insts, b.count, b.max_n, b.st);
+    const bool warm = b.warm_mu0 > 0.0;
+    launch_set_u0(b.d_insts, b.count, b.max_n, b.st, warm ? 1 : 0);
     gmv(b, R_U, R_TMPX, F_FORCE);
     launch_init_point(b.d_insts, b.count, b.max_total, b.max_n, o.tol, o.tau, o.max_iter, o.refine_tol,
-                      b.st);
+                      b.st, warm ? b.warm_mu0 : 0.0, kWarmSlackFloor);
 }
 
 constexpr int kLowPrecSteps = 12;   // conjugate-gradient steps allowed with a BF16/TF32 factor
@@ -564,7 +577,7 @@ void clear_pivot_failures(Batch& b) {
 // the conjugate gradients do not converge, the batch escalates
 // BF16/TF32 -> FP32 -> FP64 (sticky for the rest of the solve) when fallback
 // is on.  `formed` says whether M is already formed and factored in `cur`.
-lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, SyrkTimer* tm) {
+lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, SyrkTimer* tm, bool polish) {
     for (;;) {
         if (!formed) {
             // FP32 factors (the last step before FP64) are retried with a
@@ -581,8 +594,16 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, S
             }
         }
         if (cur == LQMPC_FP64) {
-            kkt_solve_fp64(b);
-            return LQMPC_OK;
+            if (!polish) {
+                kkt_solve_fp64(b);
+                return LQMPC_OK;
+            }
+            // Near a tight stop tolerance Sigma spreads over many decades and
+            // the factorisation of the condensed matrix alone no longer
+            // resolves the step: refine it by conjugate gradients with
+            // matrix-free products, the FP64 factor as preconditioner.  A
+            // refinement that does not converge keeps its best iterate.
+            return kkt_solve_mixed(b, o.refine_max, true);
         }
         // conjugate-gradient budget: a BF16/TF32 factor that needs many steps
         // is cheaper to replace by an FP32 one than to iterate with
@@ -617,8 +638,13 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
         });
         cudaEventRecord(c0->ev[2], b.st);
+        // FP64 solves get a refinement step once mu is within 1e3 of the stop
+        // tolerance (the mu of the latest host read)
+        bool polish = false;
+        for (auto* c : b.ctxs)
+            if (!c->h_scal->done && it > 0 && c->h_scal->mu < 1e3 * o.tol) polish = true;
         // predictor: form and factor M, solve M du_aff = b
-        lqmpc_status s = kkt_step(b, o, cur, false, &tm);
+        lqmpc_status s = kkt_step(b, o, cur, false, &tm, polish);
         if (s != LQMPC_OK) return s;
         seg_run(b, SEG_PRED_TAIL, [&]() {
             launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
@@ -630,7 +656,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             launch_rhs(b.d_insts, b.count, b.max_n, b.st);
         });
         // corrector: same factor
-        s = kkt_step(b, o, cur, true, &tm);
+        s = kkt_step(b, o, cur, true, &tm, polish);
         if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
@@ -690,7 +716,7 @@ lqmpc_status final_status(lqmpc_ctx* c) {
 }
 
 lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double* u, bool u_dev,
-                          lqmpc_stats* st) {
+                          lqmpc_stats* st, const double* u_init = nullptr, double mu0 = 0.0) {
     if (!ctx || !x0 || !u) return LQMPC_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     const Inst& I = ctx->h;
@@ -700,6 +726,10 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
     } else {
         CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    if (u_init) {
+        if (!all_finite(u_init, I.n)) return LQMPC_ERR_ARG;
+        CK(cudaMemcpyAsync(I.du_aff, u_init, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
+    }
     Batch b;
     b.ctxs = {ctx};
     b.d_insts = ctx->d_inst;
@@ -707,6 +737,7 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
     b.d_maps = ctx->tc_ok ? ctx->d_maps : nullptr;
     if (!ctx->graphs) ctx->graphs = new (std::nothrow) GraphCache();
     b.gc = ctx->graphs;
+    if (u_init) b.warm_mu0 = mu0 > 0.0 ? mu0 : kWarmMu0;
     double tt = 0, tk = 0;
     lqmpc_status s = run_ipm(b, ctx->opts, &tt, &tk);
     if (s != LQMPC_OK) return s;
@@ -903,6 +934,12 @@ lqmpc_status lqmpc_solve(lqmpc_ctx* ctx, const double* x0, double* u_out, lqmpc_
 lqmpc_status lqmpc_solve_device(lqmpc_ctx* ctx, const double* x0_device, double* u_device,
                                 lqmpc_stats* stats) {
     return solve_common(ctx, x0_device, true, u_device, true, stats);
+}
+
+lqmpc_status lqmpc_solve_warm(lqmpc_ctx* ctx, const double* x0, const double* u_init, double mu0, double* u_out,
+                              lqmpc_stats* stats) {
+    if (!u_init || std::isnan(mu0)) return LQMPC_ERR_ARG;
+    return solve_common(ctx, x0, false, u_out, false, stats, u_init, mu0);
 }
 
 lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
