@@ -367,6 +367,65 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args):
+    """Learned warm start on the heat2d 32x32 plant: (x0, u*) pairs from
+    lockstep batches of the GPU solver, the 1024 -> 512 -> 512 -> 500 network
+    trained by the library's own kernels, then warm- versus cold-started
+    solves on held-out x0 (seeds 10^6 + k)."""
+    import torch
+    from paper_2209_13049_b300 import binding, build
+    torch.cuda.set_device(0)
+    build.build()
+    binding.load()
+    plant = inputs.heat2d(32, 10, 50)
+    S, H, E = args.train_pairs, args.heldout, args.epochs
+    solvers = [binding.Solver(plant, precision=args.precision) for _ in range(256)]
+    t0 = time.perf_counter()
+    xs, us = [], []
+    for k0 in range(0, S, 256):
+        x0s = [inputs.x0_gaussians(32, s) for s in range(k0, min(S, k0 + 256))]
+        u, st, code = binding.solve_batch(solvers[:len(x0s)], x0s, check=False)
+        xs += x0s
+        us += u
+    t_data = time.perf_counter() - t0
+    X, U = np.array(xs), np.array(us)
+    net = binding.MLP(plant.ns, 512, plant.n, max_batch=256, seed=1)
+    net.set_bounds(np.tile(plant.ul, plant.N), np.tile(plant.uu, plant.N))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(X, U, epochs=E, batch=256, lr=args.lr, seed=2)
+    t_train = time.perf_counter() - t0
+    xt = np.array([inputs.x0_gaussians(32, 10**6 + k) for k in range(H)])
+    t0 = time.perf_counter()
+    guess = net.infer(xt)
+    t_infer = time.perf_counter() - t0
+    s = solvers[0]
+    cold_t, warm_t, cold_it, warm_it, errs = [], [], [], [], []
+    for k in range(H):
+        t = time.perf_counter()
+        uc, stc = s.solve(xt[k], check=False)
+        cold_t.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        uw, stw = s.solve_warm(xt[k], guess[k], check=False)
+        warm_t.append(time.perf_counter() - t)
+        cold_it.append(stc["iters"])
+        warm_it.append(stw["iters"])
+        errs.append(float(np.max(np.abs(uw - uc)) / max(1.0, float(np.max(np.abs(uc))))))
+    steps = E * (S // 256)
+    line = {"metric": "warm- vs cold-started LQ-MPC IPM solves/s at 1e-8 residual", "unit": "solves/s",
+            "value": H / sum(warm_t), "cold_value": H / sum(cold_t), "n_gpus": 1, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"heat2d 32x32 (ns=1024, nu=10, N=50); MLP 1024-512-512-500 BF16; "
+                                   f"{S} training pairs (x0 seeds 0..{S - 1}), {H} held-out (seeds 1e6..)",
+                       "train": {"epochs": E, "batch": 256, "lr": args.lr}},
+            "iters_cold_mean": float(np.mean(cold_it)), "iters_warm_mean": float(np.mean(warm_it)),
+            "ms_cold_mean": 1e3 * float(np.mean(cold_t)), "ms_warm_mean": 1e3 * float(np.mean(warm_t)),
+            "u_rel_err_warm_vs_cold_max": max(errs), "data_gen_s": t_data,
+            "train_s": t_train, "train_samples_per_s": steps * 256 / t_train,
+            "loss_first_last": [float(losses[0]), float(losses[-1])], "infer_ms": 1e3 * t_infer}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,12 +435,19 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="heat2d32", choices=["heat2d32", "batch"],
-                    help="heat2d32: the metric's workload; batch: the uneven lockstep batch")
+    ap.add_argument("--workload", default="heat2d32", choices=["heat2d32", "batch", "warmstart"],
+                    help="heat2d32: the metric's workload; batch: the uneven lockstep batch; "
+                         "warmstart: the learned warm start")
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--train-pairs", type=int, default=4096)
+    ap.add_argument("--heldout", type=int, default=64)
+    ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--lr", type=float, default=1e-3)
     args = ap.parse_args()
     if args.workload == "batch":
         run_batch(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

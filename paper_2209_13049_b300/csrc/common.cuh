@@ -59,6 +59,9 @@ struct Scal {
     int refine_fail;    // refinement stalled or produced a non-finite residual
     int refine_iter;    // refinement steps in the current interior-point iteration
     int prec_used;      // KKT precision of the current iteration (trace)
+    int prec_cur;       // KKT precision of this instance (escalates BF16/TF32 -> FP32 -> FP64, sticky)
+    int kkt_pending;    // the current KKT solve of this instance is not settled yet
+    int refine_budget;  // conjugate-gradient steps allowed for the current right-hand side
     int pad;
 };
 
@@ -139,12 +142,19 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
 }
 
 // Launch predicates: F_FORCE runs even after the instance finished (setup and
-// stage-level calls); F_SKIP_REFINED skips instances whose refinement converged.
-enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2 };
+// stage-level calls); F_SKIP_REFINED skips instances whose refinement converged
+// (or failed); F_PENDING skips instances whose KKT solve is settled; a
+// precision mask (bits 8-11, bit p for precision code p) keeps only the
+// instances currently at one of those precisions.
+enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2, F_PENDING = 4 };
+__host__ __device__ constexpr int prec_sel(int mask) { return mask << 8; }
 
 __device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
     if (!(flags & F_FORCE) && I.sc->done) return true;
     if ((flags & F_SKIP_REFINED) && (I.sc->refine_ok || I.sc->refine_fail)) return true;
+    if ((flags & F_PENDING) && !I.sc->kkt_pending) return true;
+    const int mask = (flags >> 8) & 15;
+    if (mask && !((mask >> I.sc->prec_cur) & 1)) return true;
     return false;
 }
 

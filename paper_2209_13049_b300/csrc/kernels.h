@@ -15,15 +15,14 @@ struct Inst;
 // kernels_ipm.cu
 void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm = 0);
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
-                       double tau, int max_iter, double refine_tol, cudaStream_t st, double mu0 = 0.0,
+                       double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0 = 0.0,
                        double smin = 1.0);
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
                         cudaStream_t st, bool do_resid, bool do_rd);
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st);
 void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st);
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st);
-void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, int prec,
-                        cudaStream_t st);
+void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, cudaStream_t st);
 
 // kernels_gamma.cu
 void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st);
@@ -60,12 +59,15 @@ void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, i
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,
                        int out_role, int force, cudaStream_t st);
 
-// kernels_refine.cu (preconditioned conjugate gradients on M du = b)
-void launch_pcg_begin(const Inst* d_insts, int count, cudaStream_t st);
-void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, cudaStream_t st);
-void launch_pcg_pinit(const Inst* d_insts, int count, cudaStream_t st);
-void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, cudaStream_t st);
-void launch_pcg_beta(const Inst* d_insts, int count, cudaStream_t st);
+// kernels_refine.cu (preconditioned conjugate gradients on M du = b; `sel`
+// is the launch predicate that picks the instances of the solve)
+void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, cudaStream_t st);
+void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st);
+void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st);
+void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st);
+void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st);
+void launch_kkt_begin(const Inst* d_insts, int count, cudaStream_t st);
+void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st);
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
                      int len_kind, int force, cudaStream_t st);
 void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st);

@@ -123,7 +123,7 @@ __global__ void k_init_slacks(const Inst* __restrict__ insts, double mu0, double
 }
 
 __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double tol, double tau,
-                           int max_iter, double refine_tol) {
+                           int max_iter, double refine_tol, int prec) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     double c = 0, d = 0, h = 0;
@@ -143,6 +143,7 @@ __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double to
         S->done = 0; S->status = 0; S->iter = 0; S->info = 0;
         S->refine_steps = 0; S->fallbacks = 0; S->use_fp64 = 0; S->err = 0;
         S->mu = S->sigma = S->alpha = S->alpha_aff = 0.0;
+        S->prec_cur = prec; S->kkt_pending = 0; S->refine_budget = 0;
     }
 }
 
@@ -374,7 +375,7 @@ __global__ void k_step(const Inst* __restrict__ insts) {
 }
 
 // alpha = min(1, tau * max step); trace; iteration count.
-__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on, int prec) {
+__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -388,7 +389,7 @@ __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on,
         if (trace_on && S->iter <= S->max_iter) {
             double* t = I.trace + (size_t)S->iter * kTraceW;
             t[3] = S->alpha_aff; t[4] = S->sigma; t[5] = al;
-            t[6] = S->refine_iter; t[7] = prec;
+            t[6] = S->refine_iter; t[7] = S->prec_cur;
         }
     }
 }
@@ -424,10 +425,11 @@ static int ew_blocks(int total_max, int threads) {
 }
 
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
-                       double tau, int max_iter, double refine_tol, cudaStream_t st, double mu0, double smin) {
+                       double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0,
+                       double smin) {
     int nb = ew_blocks(max_total, 256);
     LQ_LAUNCH(k_init_slacks<<<dim3(nb, count), 256, 0, st>>>(d_insts, mu0, smin));
-    LQ_LAUNCH(k_init_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, tol, tau, max_iter, refine_tol));
+    LQ_LAUNCH(k_init_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, tol, tau, max_iter, refine_tol, prec));
 }
 
 void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm) {
@@ -461,11 +463,11 @@ void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
     LQ_LAUNCH(k_rhs<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
 }
 
-void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, int prec,
+void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
                         cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
     LQ_LAUNCH(k_step<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on, prec));
+    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on));
     LQ_LAUNCH(k_update<<<dim3(nb, count), 256, 0, st>>>(d_insts));
     LQ_LAUNCH(k_iter_inc<<<dim3(1, count), 32, 0, st>>>(d_insts));
 }

@@ -19,31 +19,37 @@
 
 namespace lqmpc {
 
-__device__ __forceinline__ bool pcg_skip(const Scal* S) {
-    return S->done || S->refine_ok || S->refine_fail;
+// `sel` is the launch predicate that picks the instances of this solve
+// (pending, precision mask); refined or failed instances stop as well.
+__device__ __forceinline__ bool pcg_skip(const Inst& I, int sel) {
+    const Scal* S = I.sc;
+    return skip_instance(I, sel) || S->refine_ok || S->refine_fail;
 }
 
-__global__ void k_pcg_begin(const Inst* __restrict__ insts) {
+// Start: ||b||, flags cleared, step budget (BF16/TF32 factors get the low
+// budget: replacing such a factor is cheaper than iterating with it).
+__global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_hi, int budget_lo) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done) return;
+    if (skip_instance(I, sel)) return;
     double m = 0.0;
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) m = fmax(m, fabs(I.b[j]));
     m = block_reduce<1>(m, red);
     if (threadIdx.x == 0) {
         S->rnorm0 = m; S->rnorm = INFINITY; S->rnorm_prev = INFINITY;
         S->refine_ok = 0; S->refine_fail = 0; S->refine_cur = 0; S->stalled = 0;
+        S->refine_budget = (S->prec_cur == 1 || S->prec_cur == 2) ? budget_lo : budget_hi;
     }
 }
 
 // out_j = (H v)_j + mv_j + sigu_j v_j with mv = Gamma'(Sigma_x Gamma v); one
 // warp per row.  mode 0 (initial residual): r = b - M du, partial max|r| in
 // slot 6.  mode 1 (CG step): q = M p, partial p'q in slot 6.
-__global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode) {
+__global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    if (pcg_skip(I.sc)) return;
+    if (pcg_skip(I, sel)) return;
     const double* v = mode == 0 ? I.du : I.pp;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     double acc_red = 0.0;
@@ -75,12 +81,13 @@ __device__ void pcg_test(const Inst& I, double rn) {
     if (!(rn == rn)) { S->refine_fail = 1; return; }
     const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
     if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || S->rnorm0 == 0.0) S->refine_ok = 1;
+    else if (S->refine_cur >= S->refine_budget) S->refine_fail = 1;
 }
 
-__global__ void k_pcg_check(const Inst* __restrict__ insts, int nb, int slot) {
+__global__ void k_pcg_check(const Inst* __restrict__ insts, int nb, int slot, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    if (pcg_skip(I.sc)) return;
+    if (pcg_skip(I, sel)) return;
     double m = 0.0;
     for (int p = threadIdx.x; p < nb; p += blockDim.x) m = fmax(m, I.part[slot * kMaxParts + p]);
     m = block_reduce<1>(m, red);
@@ -88,10 +95,10 @@ __global__ void k_pcg_check(const Inst* __restrict__ insts, int nb, int slot) {
 }
 
 // p = z, rz = r'z (one block per instance).
-__global__ void k_pcg_pinit(const Inst* __restrict__ insts) {
+__global__ void k_pcg_pinit(const Inst* __restrict__ insts, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    if (pcg_skip(I.sc)) return;
+    if (pcg_skip(I, sel)) return;
     double s = 0.0;
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) {
         I.pp[j] = I.dcorr[j];
@@ -102,11 +109,11 @@ __global__ void k_pcg_pinit(const Inst* __restrict__ insts) {
 }
 
 // alpha = r'z / p'Mp; a non-positive curvature marks failure.
-__global__ void k_pcg_alpha(const Inst* __restrict__ insts, int nb) {
+__global__ void k_pcg_alpha(const Inst* __restrict__ insts, int nb, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (pcg_skip(S)) return;
+    if (pcg_skip(I, sel)) return;
     double s = 0.0;
     for (int p = threadIdx.x; p < nb; p += blockDim.x) s += I.part[6 * kMaxParts + p];
     s = block_reduce<0>(s, red);
@@ -119,10 +126,10 @@ __global__ void k_pcg_alpha(const Inst* __restrict__ insts, int nb) {
 
 // du += alpha p, r -= alpha q (input rows), dxs += alpha (Gamma p) (state
 // rows).  Partial max|r| in slot 7.
-__global__ void k_pcg_axpy(const Inst* __restrict__ insts) {
+__global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    if (pcg_skip(I.sc)) return;
+    if (pcg_skip(I, sel)) return;
     const double al = I.sc->pcg_alpha;
     const int total = I.SX + I.n;
     double rmax = 0.0;
@@ -142,12 +149,12 @@ __global__ void k_pcg_axpy(const Inst* __restrict__ insts) {
 }
 
 // beta = r'z_new / r'z_old; p = z + beta p (one block per instance).
-__global__ void k_pcg_beta(const Inst* __restrict__ insts) {
+__global__ void k_pcg_beta(const Inst* __restrict__ insts, int sel) {
     __shared__ double red[32];
     __shared__ double beta_sh;
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (pcg_skip(S)) return;
+    if (pcg_skip(I, sel)) return;
     double s = 0.0;
     for (int j = threadIdx.x; j < I.n; j += blockDim.x) s += I.rho[j] * I.dcorr[j];
     s = block_reduce<0>(s, red);
@@ -162,9 +169,9 @@ __global__ void k_pcg_beta(const Inst* __restrict__ insts) {
 
 // dst = src over the instance's SX (len_kind 0) or n (len_kind 1) entries.
 __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst_role, int len_kind,
-                           int force) {
+                           int flags) {
     const Inst& I = insts[blockIdx.y];
-    if (!force && I.sc->done) return;
+    if (skip_instance(I, flags)) return;
     const double* s = role_ptr(I, src_role);
     double* d = role_ptr(I, dst_role);
     const int len = len_kind == 0 ? I.SX : I.n;
@@ -172,6 +179,23 @@ __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst
 }
 
 // dst += src over the instance's n entries (instances not done).
+// Every unfinished instance needs a KKT solve.
+__global__ void k_kkt_begin(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.x];
+    if (threadIdx.x == 0) I.sc->kkt_pending = I.sc->done ? 0 : 1;
+}
+
+// Settle the pending KKT solves: an FP64 solve that met no failing pivot (a
+// refinement of it that did not converge keeps its best iterate), or a
+// low-precision one whose refinement converged.  The rest stay pending for
+// the host: escalation to a more accurate factor, or a final status.
+__global__ void k_kkt_settle(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.x];
+    Scal* S = I.sc;
+    if (threadIdx.x != 0 || S->done || !S->kkt_pending || S->info) return;
+    if (S->prec_cur == 0 || S->refine_ok) S->kkt_pending = 0;
+}
+
 __global__ void k_vec_add(const Inst* __restrict__ insts, int src_role, int dst_role) {
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -185,31 +209,31 @@ static int nblk(int len, int th, int cap) {
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-void launch_pcg_begin(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts));
+void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts, sel, budget_hi, budget_lo));
 }
 
 // mode 0: r = b - M du and its convergence test; mode 1: q = M p and alpha.
-void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, cudaStream_t st) {
+void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st) {
     int wpb = 8;
     int nb = nblk(max_n, wpb, kMaxParts);
-    LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode));
-    if (mode == 0) LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 6));
-    else LQ_LAUNCH(k_pcg_alpha<<<dim3(1, count), 256, 0, st>>>(d_insts, nb));
+    LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel));
+    if (mode == 0) LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 6, sel));
+    else LQ_LAUNCH(k_pcg_alpha<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, sel));
 }
 
-void launch_pcg_pinit(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_pinit<<<dim3(1, count), 256, 0, st>>>(d_insts));
+void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_pinit<<<dim3(1, count), 256, 0, st>>>(d_insts, sel));
 }
 
-void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
+void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st) {
     int nb = nblk(max_total, 256, kMaxParts);
-    LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 7));
+    LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts, sel));
+    LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 7, sel));
 }
 
-void launch_pcg_beta(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_beta<<<dim3(1, count), 256, 0, st>>>(d_insts));
+void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_beta<<<dim3(1, count), 256, 0, st>>>(d_insts, sel));
 }
 
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
@@ -220,6 +244,14 @@ void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, 
 
 void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st) {
     LQ_LAUNCH(k_vec_add<<<dim3(nblk(max_n, 256, 1024), count), 256, 0, st>>>(d_insts, src_role, dst_role));
+}
+
+void launch_kkt_begin(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_kkt_begin<<<count, 32, 0, st>>>(d_insts));
+}
+
+void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st) {
+    LQ_LAUNCH(k_kkt_settle<<<count, 32, 0, st>>>(d_insts));
 }
 
 }  // namespace lqmpc

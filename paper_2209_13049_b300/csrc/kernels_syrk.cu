@@ -28,13 +28,14 @@ __host__ __device__ inline void tile_of(int t, int& a, int& b) {
 
 // mode 0: right operand = D (sigx or its FP32 copy) * G; mode 1: D = qd / qfd
 // (setup, H); mode 2: right operand = Q G (r < N-1) or Qf G (r = N-1).
+// `force` holds the launch predicate flags (F_FORCE for setup).
 template <typename T>
 __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts, int mode,
                                                  const double* gq, const double* gqf, int splits,
                                                  int force) {
     const Inst& I = insts[blockIdx.y];
-    if (!force && I.sc->done) return;
-    if (!force && mode == 0 && I.sc->info) return;
+    if (skip_instance(I, force)) return;
+    if (!(force & F_FORCE) && mode == 0 && I.sc->info) return;
     const int n = I.n, ns = I.ns, nu = I.nu, N = I.N, ldg = I.ldg;
     const int nt = (n + kTile - 1) / kTile;
     const int ntiles = nt * (nt + 1) / 2;
@@ -113,8 +114,8 @@ template <typename TP, typename Tout, int TILE, bool COLMAJOR = false>
 __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int base_mode,
                               int add_sigu, int force, Tout* out_override, double shift) {
     const Inst& I = insts[blockIdx.y];
-    if (!force && I.sc->done) return;
-    if (!force && I.sc->info) return;
+    if (skip_instance(I, force)) return;
+    if (!(force & F_FORCE) && I.sc->info) return;
     const int n = I.n;
     const size_t total = (size_t)n * n;
     Tout* M = out_override ? out_override : (sizeof(Tout) == 8 ? (Tout*)I.M64 : (Tout*)I.M32);

@@ -345,7 +345,7 @@ void seg_run(const Batch& b, int key, F&& body) {
 
 enum SegKey {
     SEG_HEAD = 1, SEG_FORM = 10 /* + precision */, SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31,
-    SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50 /* + precision */
+    SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50
 };
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
@@ -384,7 +384,8 @@ struct SyrkTimer {
     bool tc = false, cc = false, cc64 = false;   // cc64: the timed CUDA-core launch was FP64
 };
 
-void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 0.0) {
+// Form and factor M in precision `prec` for the instances `sel` picks.
+void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 0.0, int sel = F_NONE) {
     lqmpc_ctx* c0 = b.ctxs[0];
     // Under capture the records must be external event nodes (not graph-internal
     // dependencies); the external flag is only valid while capturing.
@@ -398,26 +399,26 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
     auto body = [&]() {
         if (prec == LQMPC_FP64) {
             rec(c0->evk[2]);
-            launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
+            launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
             rec(c0->evk[3]);
-            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
-            launch_potrf(b.d_insts, b.count, b.max_n, 1, F_NONE, b.st);
+            launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, shift);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st);
         } else {
             if (prec == LQMPC_FP32) {
                 rec(c0->evk[2]);
-                launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
+                launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, sel, b.st);
                 rec(c0->evk[3]);
-                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st,
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
             } else {
                 rec(c0->evk[0]);
                 launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
-                               F_NONE, b.st);
+                               sel, b.st);
                 rec(c0->evk[1]);
-                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st,
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
             }
-            launch_potrf(b.d_insts, b.count, b.max_n, 0, F_NONE, b.st, 1);
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1);
         }
     };
     // the timed and untimed sequences differ (event nodes): separate graphs
@@ -430,11 +431,21 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
 }
 
 // FP64 factor: the direct solve.
-void kkt_solve_fp64(const Batch& b) {
+void kkt_solve_fp64(const Batch& b, int sel = F_NONE) {
     seg_run(b, SEG_SOLVE64, [&]() {
-        launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, F_NONE, b.st);
-        gmv(b, R_DU, R_DXS, F_NONE);
+        launch_chol_solve(b.d_insts, b.count, b.max_n, 1, R_B, R_DU, sel, b.st);
+        gmv(b, R_DU, R_DXS, sel);
     });
+}
+
+// Host view of the launch predicate (skip_instance) on a Scal copy.
+bool host_selected(const Scal& S, int sel) {
+    if (!(sel & F_FORCE) && S.done) return false;
+    if ((sel & F_SKIP_REFINED) && (S.refine_ok || S.refine_fail)) return false;
+    if ((sel & F_PENDING) && !S.kkt_pending) return false;
+    const int mask = (sel >> 8) & 15;
+    if (mask && !((mask >> S.prec_cur) & 1)) return false;
+    return true;
 }
 
 lqmpc_status read_scals(Batch& b) {
@@ -448,7 +459,10 @@ lqmpc_status read_scals(Batch& b) {
 // as preconditioner and FP64 products with M.  The host looks at the instance
 // flags every second step and stops launching once every unfinished instance
 // has converged or failed; afterwards each h_scal holds the outcome.
-lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false) {
+lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int sel = F_NONE,
+                             int budget_lo = -1) {
+    if (budget_lo < 0) budget_lo = refine_max;
+    const int selr = sel | F_SKIP_REFINED;
     // preconditioner P^{-1}: the FP32 explicit inverse of the low-precision
     // factor, or (prec64) the FP64 triangular solves
     auto prec = [&](int in, int out, int flags) {
@@ -457,27 +471,27 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false) {
     };
     const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
     seg_run(b, SEG_PCG0 + kp, [&]() {
-        launch_pcg_begin(b.d_insts, b.count, b.st);
-        prec(R_B, R_DU, F_NONE);
+        launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, b.st);
+        prec(R_B, R_DU, sel);
         // initial residual r = b - M du and Gamma du
-        gmv(b, R_DU, R_TMPX, F_SKIP_REFINED);
-        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, F_NONE, b.st);
-        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, b.st);
-        prec(R_RHO, R_DCORR, F_SKIP_REFINED);
-        launch_pcg_pinit(b.d_insts, b.count, b.st);
+        gmv(b, R_DU, R_TMPX, selr);
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
+        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, sel, b.st);
+        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, sel, b.st);
+        prec(R_RHO, R_DCORR, selr);
+        launch_pcg_pinit(b.d_insts, b.count, sel, b.st);
     });
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
     // the new direction (harmless after the last step: every kernel is
     // predicated on the instance's refinement flags)
     auto step = [&](bool with_next) {
-        gmv(b, R_P, R_TMPX, F_SKIP_REFINED);
-        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, F_SKIP_REFINED);
-        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, b.st);
-        launch_pcg_step_update(b.d_insts, b.count, b.max_total, b.st);
+        gmv(b, R_P, R_TMPX, selr);
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
+        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, sel, b.st);
+        launch_pcg_step_update(b.d_insts, b.count, b.max_total, sel, b.st);
         if (!with_next) return;
-        prec(R_RHO, R_DCORR, F_SKIP_REFINED);
-        launch_pcg_beta(b.d_insts, b.count, b.st);
+        prec(R_RHO, R_DCORR, selr);
+        launch_pcg_beta(b.d_insts, b.count, sel, b.st);
     };
     // The host looks at the flags after every second step and stops launching
     // once every unfinished instance has converged or failed.
@@ -494,8 +508,7 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false) {
         if (st != LQMPC_OK) return st;
         bool pending = false;
         for (auto* c : b.ctxs)
-            if (!c->h_scal->done && !c->h_scal->refine_ok && !c->h_scal->refine_fail && !c->h_scal->info)
-                pending = true;
+            if (host_selected(*c->h_scal, selr) && !c->h_scal->info) pending = true;
         if (!pending) break;
     }
     return read_scals(b);
@@ -514,7 +527,7 @@ void prepare(const Batch& b, const lqmpc_options& o) {
     launch_set_u0(b.d_insts, b.count, b.max_n, b.st, warm ? 1 : 0);
     gmv(b, R_U, R_TMPX, F_FORCE);
     launch_init_point(b.d_insts, b.count, b.max_total, b.max_n, o.tol, o.tau, o.max_iter, o.refine_tol,
-                      b.st, warm ? b.warm_mu0 : 0.0, kWarmSlackFloor);
+                      o.precision, b.st, warm ? b.warm_mu0 : 0.0, kWarmSlackFloor);
 }
 
 constexpr int kLowPrecSteps = 12;   // conjugate-gradient steps allowed with a BF16/TF32 factor
@@ -523,99 +536,100 @@ int next_precision(int p) {
     return (p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32) ? LQMPC_FP32 : LQMPC_FP64;
 }
 
-// After a refined solve: does some unfinished instance need a more accurate
-// factor (pivot failure or refinement that stalled / ran out of steps)?
-bool refine_failed(const Batch& b) {
-    for (auto* c : b.ctxs)
-        if (!c->h_scal->done && (c->h_scal->info || !c->h_scal->refine_ok)) return true;
-    return false;
+void write_scal(Batch& b, lqmpc_ctx* c) {
+    cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
 }
 
-// Without fallback: finish the failed instances with a status.  With
-// fallback: clear their pivot flag and count the switch (the caller moves the
-// whole batch to the next precision).
-void mark_failures(Batch& b, bool fallback) {
-    for (auto* c : b.ctxs) {
-        Scal fix = *c->h_scal;
-        if (fix.done) continue;
-        if (!fallback) {
-            if (fix.info || !fix.refine_ok) {
-                fix.done = 1;
-                fix.status = fix.info ? LQMPC_ERR_NOT_PD : LQMPC_ERR_STALL;
-            }
-        } else {
-            fix.info = 0;
-            fix.fallbacks += 1;
+// Solve M du = b for every unfinished instance, each with its own factor
+// precision (Scal::prec_cur).  Rounds: form and factor M for the instances
+// that need it (all of them unless `formed`; later only the escalated ones),
+// solve -- FP64 factors directly (or, with `polish`, refined by conjugate
+// gradients preconditioned by the FP64 factor), lower precisions by
+// conjugate gradients preconditioned by the explicit inverse of the factor --
+// then settle.  An instance whose refinement does not converge (or whose
+// low-precision Cholesky meets a non-positive pivot even after the FP32
+// shift retries) moves to the next precision, BF16/TF32 -> FP32 -> FP64, for
+// the rest of the solve (fallback on), or finishes with LQMPC_ERR_STALL /
+// LQMPC_ERR_NOT_PD.  Relative diagonal shifts of a retried FP32 factor
+// change only the preconditioner: the conjugate gradients with FP64 products
+// still converge to the exact solution.  The other instances keep their
+// precision: one instance's trouble does not move a whole batch to FP64.
+lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* tm, bool& polish) {
+    launch_kkt_begin(b.d_insts, b.count, b.st);
+    const int budget_lo = std::min(o.refine_max, kLowPrecSteps);
+    for (int round = 0; round < 4; ++round) {
+        int present = 0;   // precisions among the pending instances
+        for (auto* c : b.ctxs) {
+            const Scal& S = *c->h_scal;
+            if (!S.done && (round == 0 || S.kkt_pending)) present |= 1 << S.prec_cur;
         }
-        *c->h_scal = fix;
-        cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
-    }
-}
-
-// Solve M du = b in the current precision `cur`, escalating BF16/TF32 ->
-// FP32 -> FP64 while refinement fails (if fallback is on).  `formed` says
-// whether M is already formed and factored in `cur`.
-bool any_pivot_failure(const Batch& b) {
-    for (auto* c : b.ctxs)
-        if (!c->h_scal->done && c->h_scal->info) return true;
-    return false;
-}
-
-void clear_pivot_failures(Batch& b) {
-    for (auto* c : b.ctxs) {
-        if (c->h_scal->done || !c->h_scal->info) continue;
-        c->h_scal->info = 0;
-        cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
-    }
-}
-
-// Solve M du = b in the current precision `cur`.  A low-precision factor
-// whose Cholesky meets a non-positive pivot (M rounded to BF16/TF32/FP32 can
-// lose definiteness when Sigma spreads) is retried with a small relative
-// diagonal shift -- the conjugate gradients with FP64 products still converge
-// to the exact solution, only with a weaker preconditioner.  If that fails or
-// the conjugate gradients do not converge, the batch escalates
-// BF16/TF32 -> FP32 -> FP64 (sticky for the rest of the solve) when fallback
-// is on.  `formed` says whether M is already formed and factored in `cur`.
-lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, int& cur, bool formed, SyrkTimer* tm, bool polish) {
-    for (;;) {
-        if (!formed) {
-            // FP32 factors (the last step before FP64) are retried with a
-            // relative diagonal shift; BF16/TF32 factors escalate directly.
-            const double shifts_sp[3] = {0.0, 1e-6, 1e-4};
-            const int attempts = cur == LQMPC_FP32 ? 3 : 1;
-            for (int attempt = 0; attempt < attempts; ++attempt) {
-                kkt_form(b, cur, tm, cur == LQMPC_FP32 ? shifts_sp[attempt] : 0.0);
-                if (cur == LQMPC_FP64) break;
-                lqmpc_status s = read_scals(b);
-                if (s != LQMPC_OK) return s;
-                if (!any_pivot_failure(b) || attempt + 1 == attempts) break;
-                clear_pivot_failures(b);
+        if (!present) return LQMPC_OK;
+        if (!formed || round > 0) {
+            for (int p = 0; p < 4; ++p) {
+                if (!((present >> p) & 1)) continue;
+                const int sel = F_PENDING | prec_sel(1 << p);
+                if (p != LQMPC_FP32 && p != LQMPC_FP64) {
+                    kkt_form(b, p, tm, 0.0, sel);
+                    continue;
+                }
+                // FP32 and FP64 factors are retried with a relative diagonal
+                // shift (an FP64 pivot can fail on rounding when Sigma spans
+                // more decades than FP64 resolves); a shifted FP64 factor is
+                // only a preconditioner, so its solves are refined.
+                const double shifts32[3] = {0.0, 1e-6, 1e-4}, shifts64[3] = {0.0, 1e-12, 1e-9};
+                const double* shifts = p == LQMPC_FP32 ? shifts32 : shifts64;
+                for (int a = 0; a < 3; ++a) {
+                    if (a > 0 && p == LQMPC_FP64) polish = true;
+                    kkt_form(b, p, tm, shifts[a], sel);
+                    lqmpc_status st = read_scals(b);
+                    if (st != LQMPC_OK) return st;
+                    bool fail = false;
+                    for (auto* c : b.ctxs)
+                        if (host_selected(*c->h_scal, sel) && c->h_scal->info) fail = true;
+                    if (!fail || a == 2) break;
+                    for (auto* c : b.ctxs)
+                        if (host_selected(*c->h_scal, sel) && c->h_scal->info) {
+                            c->h_scal->info = 0;
+                            write_scal(b, c);
+                        }
+                }
             }
         }
-        if (cur == LQMPC_FP64) {
+        if (present & 1) {
+            const int sel = F_PENDING | prec_sel(1);
             if (!polish) {
-                kkt_solve_fp64(b);
-                return LQMPC_OK;
+                kkt_solve_fp64(b, sel);
+            } else {
+                // Near a tight stop tolerance Sigma spreads over many decades
+                // and the factorisation of the condensed matrix alone no
+                // longer resolves the step.
+                lqmpc_status st = kkt_solve_mixed(b, o.refine_max, true, sel);
+                if (st != LQMPC_OK) return st;
             }
-            // Near a tight stop tolerance Sigma spreads over many decades and
-            // the factorisation of the condensed matrix alone no longer
-            // resolves the step: refine it by conjugate gradients with
-            // matrix-free products, the FP64 factor as preconditioner.  A
-            // refinement that does not converge keeps its best iterate.
-            return kkt_solve_mixed(b, o.refine_max, true);
         }
-        // conjugate-gradient budget: a BF16/TF32 factor that needs many steps
-        // is cheaper to replace by an FP32 one than to iterate with
-        const int steps = cur == LQMPC_FP32 ? o.refine_max : std::min(o.refine_max, kLowPrecSteps);
-        lqmpc_status s = kkt_solve_mixed(b, steps);
-        if (s != LQMPC_OK) return s;
-        if (!refine_failed(b)) return LQMPC_OK;
-        mark_failures(b, o.fallback != 0);
-        if (!o.fallback) return LQMPC_OK;
-        cur = next_precision(cur);
-        formed = false;
+        if (present & 0xE) {
+            lqmpc_status st = kkt_solve_mixed(b, o.refine_max, false, F_PENDING | prec_sel(0xE), budget_lo);
+            if (st != LQMPC_OK) return st;
+        }
+        launch_kkt_settle(b.d_insts, b.count, b.st);
+        lqmpc_status st = read_scals(b);
+        if (st != LQMPC_OK) return st;
+        for (auto* c : b.ctxs) {
+            Scal& S = *c->h_scal;
+            if (S.done || !S.kkt_pending) continue;
+            if (S.prec_cur == LQMPC_FP64 || !o.fallback) {
+                S.done = 1;
+                S.status = S.info ? LQMPC_ERR_NOT_PD : LQMPC_ERR_STALL;
+                S.kkt_pending = 0;
+            } else {
+                S.prec_cur = next_precision(S.prec_cur);
+                S.info = 0;
+                S.fallbacks += 1;
+            }
+            write_scal(b, c);
+        }
     }
+    return LQMPC_OK;
 }
 
 lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* t_kkt) {
@@ -627,7 +641,10 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     c0->n_tc = c0->n_cc = c0->n_cc64 = 0;
     cudaEventRecord(c0->ev[0], b.st);
     prepare(b, o);
-    int cur = prec;          // sticky: once escalated, the rest of the solve stays there
+    {
+        lqmpc_status st = read_scals(b);   // host view of the initial per-instance state
+        if (st != LQMPC_OK) return st;
+    }
     double kkt_ms = 0.0;
     for (int it = 0; it <= o.max_iter; ++it) {
         SyrkTimer tm;
@@ -644,7 +661,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         for (auto* c : b.ctxs)
             if (!c->h_scal->done && it > 0 && c->h_scal->mu < 1e3 * o.tol) polish = true;
         // predictor: form and factor M, solve M du_aff = b
-        lqmpc_status s = kkt_step(b, o, cur, false, &tm, polish);
+        lqmpc_status s = kkt_step(b, o, false, &tm, polish);
         if (s != LQMPC_OK) return s;
         seg_run(b, SEG_PRED_TAIL, [&]() {
             launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
@@ -656,11 +673,11 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             launch_rhs(b.d_insts, b.count, b.max_n, b.st);
         });
         // corrector: same factor
-        s = kkt_step(b, o, cur, true, &tm, polish);
+        s = kkt_step(b, o, true, &tm, polish);
         if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
-        seg_run(b, SEG_CORR_TAIL + cur, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, cur, b.st); });
+        seg_run(b, SEG_CORR_TAIL, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st); });
         s = read_scals(b);
         if (s != LQMPC_OK) return s;
         float ms = 0.f;
