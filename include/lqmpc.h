@@ -173,6 +173,20 @@ lqmpc_status lqmpc_solve_warm(lqmpc_ctx* ctx, const double* x0, const double* u_
 lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
                                double* const* u_outs, lqmpc_stats* stats);
 
+/*
+ * Autotune the launch shapes of batches like this one (same count and
+ * largest ns, nu*N and N): the split-K factor of the CUDA-core SYRK and the
+ * Cholesky variant (grid-cooperative over all SMs, or one 8-CTA cluster per
+ * instance where the matrix fits distributed shared memory), each timed on
+ * the device with CUDA events on these contexts' data (a representative
+ * Sigma from the cold initial point), best of three.  The decision applies
+ * to later lqmpc_solve_batch (and, for count = 1, lqmpc_solve) calls with the
+ * same signature.  cache_path (nullable): a text file of earlier decisions,
+ * one line per signature; a signature found there is not re-measured, a new
+ * one is appended.  Contexts as for lqmpc_solve_batch.
+ */
+lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache_path);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all contexts); differences around a region count its launches. */
 unsigned long long lqmpc_kernel_launches(void);

@@ -29,7 +29,7 @@ EXPORTS = ["lqmpc_default_options", "lqmpc_status_str", "lqmpc_setup", "lqmpc_se
            "lqmpc_form_kkt", "lqmpc_kkt_solve", "lqmpc_get_trace", "lqmpc_get_duals",
            "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc", "lqmpc_solve_warm", "lqmpc_mlp_create",
            "lqmpc_mlp_set_bounds", "lqmpc_mlp_get_params", "lqmpc_mlp_set_params", "lqmpc_mlp_grad",
-           "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free"]
+           "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free", "lqmpc_autotune"]
 
 
 class LqmpcError(RuntimeError):
@@ -120,6 +120,8 @@ def load(path: str = LIB_PATH):
     lib.lqmpc_mlp_infer.argtypes = [P, P, I, P]
     lib.lqmpc_mlp_free.restype = None
     lib.lqmpc_mlp_free.argtypes = [P]
+    lib.lqmpc_autotune.restype = I
+    lib.lqmpc_autotune.argtypes = [P, I, ctypes.c_char_p]
     _lib = lib
     return lib
 
@@ -287,6 +289,14 @@ class Solver:
 def kernel_launches() -> int:
     """Cumulative count of CUDA kernels launched by the library in this process."""
     return int(load().lqmpc_kernel_launches())
+
+
+def autotune(solvers, cache_path=None):
+    """Autotune the launch shapes of batches like this one (lqmpc_autotune)."""
+    k = len(solvers)
+    hs = (ctypes.c_void_p * k)(*[s.h.value for s in solvers])
+    _check(load().lqmpc_autotune(ctypes.cast(hs, ctypes.c_void_p), k,
+                                 None if cache_path is None else str(cache_path).encode()), "lqmpc_autotune")
 
 
 def solve_batch(solvers, x0s, check: bool = True):

@@ -52,8 +52,9 @@ void launch_h_to_f32(const Inst* d_inst, int n, cudaStream_t st);
 
 // kernels_chol.cu
 void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st,
-                  int want_inv = 0);
+                  int want_inv = 0, int variant = -1);
 bool launch_potrf_cluster(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st);
+bool potrf_cluster_fits(int max_n);
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
                        cudaStream_t st);
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

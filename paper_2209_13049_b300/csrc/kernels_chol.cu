@@ -551,7 +551,8 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
 
 // ---------------------------------------------------------------------------
 
-void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st, int want_inv) {
+void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st, int want_inv,
+                  int variant) {
     static int occ[2] = {0, 0}, sms = 0;
     const int nt = (max_n + kNb - 1) / kNb;
     if (!sms) {
@@ -567,8 +568,10 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
     // every SM with the cooperative kernel (measured faster for one n = 500
     // matrix: 0.37-0.50 ms FP32 against 0.53 ms for the cluster kernel, and
     // 1.16 ms against 1.95 ms in FP64, whose pipe rate makes 8 SMs too few).
-    if ((fp64 || want_inv) && count * 8 >= sms && launch_potrf_cluster(d_insts, count, max_n, fp64, flags, st))
-        return;
+    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies (autotuned)
+    const bool cluster_ok = fp64 || want_inv;
+    const bool want_cluster = variant == 1 || (variant < 0 && count * 8 >= sms);
+    if (cluster_ok && want_cluster && launch_potrf_cluster(d_insts, count, max_n, fp64, flags, st)) return;
     long long work = (long long)count * (nt * (nt + 1) / 2 > nt ? nt * (nt + 1) / 2 : nt);
     long long cap = (long long)occ[fp64 ? 1 : 0] * sms;
     int grid = (int)(work < cap ? work : cap);

@@ -351,6 +351,8 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256, 1)
     cluster.sync();   // no CTA leaves while its shared memory may still be read
 }
 
+bool potrf_cluster_fits(int max_n) { return (max_n + kClNb - 1) / kClNb <= kClMaxTiles; }
+
 // Factor every instance with its own cluster when all fit (n <= 512).
 bool launch_potrf_cluster(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st) {
     if ((max_n + kClNb - 1) / kClNb > kClMaxTiles) return false;

@@ -18,7 +18,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -292,7 +294,23 @@ struct Batch {
     bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
     double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
+    int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster (autotuned)
 };
+
+// ---- autotuned launch shapes, keyed by batch signature (count and the
+// largest dimensions); filled by lqmpc_autotune, optionally from a cache file.
+struct Tuning {
+    int cc_splits = 0;          // CUDA-core SYRK split-K factor (0: setup heuristic)
+    int potrf[2] = {-1, -1};    // potrf variant for FP32 (with inverse) and FP64
+};
+std::mutex g_tune_mu;
+std::map<std::string, Tuning> g_tune;
+
+std::string batch_key(const Batch& b) {
+    char k[96];
+    snprintf(k, sizeof(k), "b%d-n%d-s%d-N%d", b.count, b.max_n, b.max_ns, b.max_N);
+    return k;
+}
 
 // Off under the per-launch debug modes (they synchronise or record events per
 // launch) or with LQMPC_GRAPH=0.
@@ -374,6 +392,13 @@ void batch_dims(Batch& b) {
         b.tc_splits = b.tc_splits == (1 << 30) ? c->tc_splits : std::max(b.tc_splits, c->tc_splits);
     }
     b.st = b.ctxs[0]->stream;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(batch_key(b));
+    if (it != g_tune.end()) {
+        if (it->second.cc_splits > 0 && it->second.cc_splits <= b.cc_splits) b.cc_splits = it->second.cc_splits;
+        b.potrf_variant[0] = it->second.potrf[0];
+        b.potrf_variant[1] = it->second.potrf[1];
+    }
 }
 
 // ---- one KKT solve M du = b (in role R_B) into R_DU, and R_TMPX = Gamma du.
@@ -402,7 +427,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
             launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
             rec(c0->evk[3]);
             launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, shift);
-            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1]);
         } else {
             if (prec == LQMPC_FP32) {
                 rec(c0->evk[2]);
@@ -418,7 +443,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
                 launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
             }
-            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1);
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0]);
         }
     };
     // the timed and untimed sequences differ (event nodes): separate graphs
@@ -1033,6 +1058,123 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (si != LQMPC_OK && first == LQMPC_OK) first = si;
     }
     return first;
+}
+
+lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache_path) {
+    if (!ctxs || count < 1) return LQMPC_ERR_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!ctxs[i] || ctxs[i]->user_stream != ctxs[0]->user_stream || ctxs[i]->device != ctxs[0]->device)
+            return LQMPC_ERR_ARG;
+    CK(cudaSetDevice(ctxs[0]->device));
+    for (int i = 1; i < count; ++i)
+        if (ctxs[i]->stream != ctxs[0]->stream) CK(cudaStreamSynchronize(ctxs[i]->stream));
+    Batch b;
+    b.ctxs.assign(ctxs, ctxs + count);
+    batch_dims(b);
+    const std::string key = batch_key(b);
+    // cached decisions
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char k[128];
+            int cc, p32, p64;
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            while (fscanf(f, "%127s %d %d %d", k, &cc, &p32, &p64) == 4) {
+                Tuning t;
+                t.cc_splits = cc; t.potrf[0] = p32; t.potrf[1] = p64;
+                g_tune[k] = t;
+            }
+            fclose(f);
+            if (g_tune.count(key)) return LQMPC_OK;
+        }
+    }
+    const int max_splits = b.cc_splits;   // the smallest workspace of the batch
+    b.potrf_variant[0] = b.potrf_variant[1] = -1;
+    std::vector<Inst> hosts(count);
+    for (int i = 0; i < count; ++i) hosts[i] = ctxs[i]->h;
+    Inst* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(Inst) * count));
+    b.d_insts = d;
+    lqmpc_status s = LQMPC_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        s = LQMPC_ERR_CUDA;
+    Tuning t;
+    if (s == LQMPC_OK) {
+        // a representative Sigma: the cold initial point (x0 = 0) and its residuals
+        for (auto* c : b.ctxs) cudaMemsetAsync(c->h.xbar, 0, sizeof(double) * c->h.ns, b.st);
+        lqmpc_options o = ctxs[0]->opts;
+        prepare(b, o);
+        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 0, b.st, true, false);
+        // best of three timed launches of fn; `pre` (untimed) restores the input
+        auto timed = [&](const std::function<void()>& pre, const std::function<void()>& fn) {
+            float best = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                if (pre) pre();
+                cudaEventRecord(e0, b.st);
+                fn();
+                cudaEventRecord(e1, b.st);
+                float ms = 0.f;
+                if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                    best = std::min(best, ms);
+            }
+            return best;
+        };
+        // 1. split-K factor of the CUDA-core SYRK (FP32 formation + reduce)
+        float best = 1e30f;
+        std::vector<int> cand;
+        for (int c = 1; c <= max_splits; c *= 2) cand.push_back(c);
+        if (cand.empty() || cand.back() != max_splits) cand.push_back(max_splits);
+        for (int c : cand) {
+            float ms = timed(nullptr, [&]() {
+                launch_syrk_cc(b.d_insts, b.count, b.max_n, c, 0, 0, nullptr, nullptr, F_NONE, b.st);
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, c, 1, 0, 0, 1, F_NONE, nullptr, b.st);
+            });
+            if (ms < best) { best = ms; t.cc_splits = c; }
+        }
+        b.cc_splits = t.cc_splits;
+        // 2. Cholesky variant (cooperative over all SMs, or one 8-CTA cluster per instance)
+        if (potrf_cluster_fits(b.max_n)) {
+            for (int fp64 = 0; fp64 < 2; ++fp64) {
+                float bv = 1e30f;
+                for (int v = 0; v < 2; ++v) {
+                    auto form = [&]() {
+                        const int prec = fp64 ? LQMPC_FP64 : LQMPC_FP32;
+                        launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, fp64, 0, nullptr, nullptr, F_NONE,
+                                       b.st);
+                        launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, fp64 ? 0 : 1, fp64, 0, 1,
+                                           F_NONE, nullptr, b.st);
+                        (void)prec;
+                    };
+                    float ms = timed(form, [&]() {
+                        launch_potrf(b.d_insts, b.count, b.max_n, fp64, F_NONE, b.st, fp64 ? 0 : 1, v);
+                    });
+                    if (ms < bv) { bv = ms; t.potrf[fp64] = v; }
+                }
+            }
+        } else {
+            t.potrf[0] = t.potrf[1] = 0;
+        }
+        if (cudaStreamSynchronize(b.st) != cudaSuccess || cudaGetLastError() != cudaSuccess) s = LQMPC_ERR_CUDA;
+        // the autotune launches left the instances mid-setup: mark them not started
+        for (auto* c : b.ctxs) cudaMemsetAsync(c->h.sc, 0, sizeof(Scal), b.st);
+        cudaStreamSynchronize(b.st);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(d);
+    if (s != LQMPC_OK) return s;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = t;
+    }
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d %d\n", key.c_str(), t.cc_splits, t.potrf[0], t.potrf[1]);
+            fclose(f);
+        }
+    }
+    return LQMPC_OK;
 }
 
 unsigned long long lqmpc_kernel_launches(void) { return g_launches.load(); }
