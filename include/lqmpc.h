@@ -175,9 +175,11 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
 
 /*
  * Autotune the launch shapes of batches like this one (same count and
- * largest ns, nu*N and N): the split-K factor of the CUDA-core SYRK and the
+ * largest ns, nu*N and N): the split-K factor of the CUDA-core SYRK, the
  * Cholesky variant (grid-cooperative over all SMs, or one 8-CTA cluster per
- * instance where the matrix fits distributed shared memory), each timed on
+ * instance where the matrix fits distributed shared memory) and the FP64
+ * formation of M (SYRK, or the backward recursion over the horizon where
+ * setup prepared it for a sparse A), each timed on
  * the device with CUDA events on these contexts' data (a representative
  * Sigma from the cold initial point), best of three.  The decision applies
  * to later lqmpc_solve_batch (and, for count = 1, lqmpc_solve) calls with the

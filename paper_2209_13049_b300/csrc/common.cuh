@@ -103,6 +103,11 @@ struct Inst {
     double* M64; float* M32;          // n x n
     float* Xinv32;                    // n x n: inverse of the FP32 Cholesky factor (preconditioner)
     double* ldiag;                    // 2 x 32 x 32: factored diagonal blocks in flight (cooperative potrf)
+    // FP64 KKT formation by the backward recursion (sparse A); lyP == nullptr: not used
+    double* lyP; double* lyT;         // ns x ns each
+    double* lyW;                      // N x ns x nu
+    const int* at_ptr; const int* at_idx; const double* at_val;   // A' in CSR (the columns of A)
+    const int* bc_ptr; const int* bc_idx; const double* bc_val;   // nonzeros of B per column
     float* XinvT32;                   // its transpose (coalesced rows)
     float* Tinv32;                    // n x n scratch of the inversion
     double *rho, *dcorr;              // refinement: residual, correction (n)

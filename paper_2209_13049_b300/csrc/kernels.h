@@ -50,6 +50,12 @@ void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, i
                         cudaStream_t st, double shift = 0.0);
 void launch_h_to_f32(const Inst* d_inst, int n, cudaStream_t st);
 
+// kernels_lyap.cu (FP64 KKT matrix by the backward recursion, sparse A)
+void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int flags, cudaStream_t st,
+                     double shift = 0.0);
+double kkt_cost_syrk(int ns, int nu, int N);
+double kkt_cost_lyap(int ns, int nu, int N, long long nnzA, long long nnzB);
+
 // kernels_chol.cu
 void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st,
                   int want_inv = 0, int variant = -1);

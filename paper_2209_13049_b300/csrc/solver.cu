@@ -152,6 +152,7 @@ struct lqmpc_ctx {
     double t_tc = 0, t_cc = 0, t_cc64 = 0;
     int n_tc = 0, n_cc = 0, n_cc64 = 0;
     lqmpc::GraphCache* graphs = nullptr;   // single-instance solves (d_inst is fixed)
+    bool lyap = false;                     // FP64 KKT matrix by the backward recursion
 };
 
 namespace {
@@ -211,10 +212,15 @@ bool csr_diag(int n, const int* ptr, const int* idx, const double* val, std::vec
 // Lay out every device array of an instance in one arena.
 template <bool kAssign>
 size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int max_iter,
-              int cc_splits, int tc_splits) {
+              int cc_splits, int tc_splits, int nnzB, bool lyap) {
     Carver c{base};
     const int ns = I.ns, nu = I.nu, n = I.n, SX = I.SX;
     const size_t G = (size_t)I.ldg * n;
+    auto at_ptr = c.take<int>(ns + 1); auto at_idx = c.take<int>(nnzA); auto at_val = c.take<double>(nnzA);
+    auto bc_ptr = c.take<int>(nu + 1); auto bc_idx = c.take<int>(nnzB); auto bc_val = c.take<double>(nnzB);
+    double* lyP = lyap ? c.take<double>((size_t)ns * ns) : nullptr;
+    double* lyT = lyap ? c.take<double>((size_t)ns * ns) : nullptr;
+    double* lyW = lyap ? c.take<double>((size_t)I.N * ns * nu) : nullptr;
     auto a_ptr = c.take<int>(ns + 1); auto a_idx = c.take<int>(nnzA); auto a_val = c.take<double>(nnzA);
     auto q_ptr = c.take<int>(ns + 1); auto q_idx = c.take<int>(nnzQ); auto q_val = c.take<double>(nnzQ);
     auto qf_ptr = c.take<int>(ns + 1); auto qf_idx = c.take<int>(nnzQf); auto qf_val = c.take<double>(nnzQf);
@@ -275,6 +281,9 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.ldiag = ldiag;
+        I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
+        I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
+        I.lyP = lyP; I.lyT = lyT; I.lyW = lyW;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
         I.part = part; I.bar = bar; I.sc = sc; I.trace = trace; I.tc_plan = tc_plan;
@@ -295,6 +304,8 @@ struct Batch {
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
     double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
     int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster (autotuned)
+    bool lyap = false;              // FP64 formation by the backward recursion (every instance has its buffers)
+    int max_nu = 0;
 };
 
 // ---- autotuned launch shapes, keyed by batch signature (count and the
@@ -302,6 +313,7 @@ struct Batch {
 struct Tuning {
     int cc_splits = 0;          // CUDA-core SYRK split-K factor (0: setup heuristic)
     int potrf[2] = {-1, -1};    // potrf variant for FP32 (with inverse) and FP64
+    int kkt64 = -1;             // FP64 formation: -1 setup choice, 0 SYRK, 1 backward recursion
 };
 std::mutex g_tune_mu;
 std::map<std::string, Tuning> g_tune;
@@ -382,7 +394,11 @@ void batch_dims(Batch& b) {
     b.count = (int)b.ctxs.size();
     b.max_ns = b.max_N = b.max_n = b.max_sx = b.max_total = 0;
     b.cc_splits = b.tc_splits = 1 << 30;
+    b.lyap = true;
+    b.max_nu = 0;
     for (auto* c : b.ctxs) {
+        b.lyap = b.lyap && c->lyap;
+        b.max_nu = std::max(b.max_nu, c->h.nu);
         b.max_ns = std::max(b.max_ns, c->h.ns);
         b.max_N = std::max(b.max_N, c->h.N);
         b.max_n = std::max(b.max_n, c->h.n);
@@ -398,6 +414,7 @@ void batch_dims(Batch& b) {
         if (it->second.cc_splits > 0 && it->second.cc_splits <= b.cc_splits) b.cc_splits = it->second.cc_splits;
         b.potrf_variant[0] = it->second.potrf[0];
         b.potrf_variant[1] = it->second.potrf[1];
+        if (it->second.kkt64 == 0) b.lyap = false;
     }
 }
 
@@ -422,7 +439,12 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
         else cudaEventRecord(e, b.st);
     };
     auto body = [&]() {
-        if (prec == LQMPC_FP64) {
+        if (prec == LQMPC_FP64 && b.lyap) {
+            rec(c0->evk[2]);
+            launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, sel, b.st, shift);
+            rec(c0->evk[3]);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1]);
+        } else if (prec == LQMPC_FP64) {
             rec(c0->evk[2]);
             launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
             rec(c0->evk[3]);
@@ -884,7 +906,43 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     const int nnzA = a_ptr[ns], nnzQ = q_ptr[ns], nnzQf = qf_ptr[ns];
     ctx->cc_splits = syrk_cc_splits(ns, nu, N);
     ctx->tc_splits = syrk_tc_plan_partials(ns, nu, N);
-    size_t bytes = layout<false>(I, nullptr, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits);
+    // A' in CSR (the columns of A) and the nonzeros of B per column, for the
+    // backward-recursion formation of the FP64 KKT matrix
+    std::vector<int> at_ptr(ns + 1, 0), at_idx(nnzA), bc_ptr(nu + 1, 0), bc_idx;
+    std::vector<double> at_val(nnzA), bc_val;
+    for (int k = 0; k < nnzA; ++k) at_ptr[a_idx[k] + 1]++;
+    for (int i = 0; i < ns; ++i) at_ptr[i + 1] += at_ptr[i];
+    {
+        std::vector<int> fill(at_ptr.begin(), at_ptr.end() - 1);
+        for (int r = 0; r < ns; ++r)
+            for (int k = a_ptr[r]; k < a_ptr[r + 1]; ++k) {
+                const int q = fill[a_idx[k]]++;
+                at_idx[q] = r;
+                at_val[q] = a_val[k];
+            }
+    }
+    for (int col = 0; col < nu; ++col) {
+        for (int i = 0; i < ns; ++i)
+            if (Bh[(size_t)col * ns + i] != 0.0) {
+                bc_idx.push_back(i);
+                bc_val.push_back(Bh[(size_t)col * ns + i]);
+            }
+        bc_ptr[col + 1] = (int)bc_idx.size();
+    }
+    const int nnzB = (int)bc_idx.size();
+    // the recursion when it needs clearly fewer FP64 operations than the SYRK
+    // and its two ns x ns buffers stay modest; LQMPC_KKT64=syrk|lyap overrides
+    {
+        const double cs = kkt_cost_syrk(ns, nu, N), cl = kkt_cost_lyap(ns, nu, N, nnzA, nnzB);
+        const double buf = 16.0 * ns * (double)ns;
+        ctx->lyap = cl < 0.6 * cs && buf <= 4e9;
+        if (const char* e = getenv("LQMPC_KKT64")) {
+            if (!strcmp(e, "syrk")) ctx->lyap = false;
+            if (!strcmp(e, "lyap") && buf <= 4e9) ctx->lyap = true;
+        }
+    }
+    size_t bytes = layout<false>(I, nullptr, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits, nnzB,
+                                 ctx->lyap);
     auto fail = [&](lqmpc_status s) {
         lqmpc_free(ctx);
         return s;
@@ -892,7 +950,7 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     ctx->arena_bytes = bytes;
     if (cudaMemsetAsync(ctx->arena, 0, bytes, ctx->stream) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
-    layout<true>(I, ctx->arena, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits);
+    layout<true>(I, ctx->arena, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits, nnzB, ctx->lyap);
     if (cudaMallocHost(&ctx->h_scal, sizeof(Scal)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     memset(ctx->h_scal, 0, sizeof(Scal));
     for (int e = 0; e < 4; ++e)
@@ -912,6 +970,9 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
               up(I.xu, xu, sizeof(double) * ns) && up(I.ul, ul, sizeof(double) * nu) &&
               up(I.uu, uu, sizeof(double) * nu);
     if (qdiag) ok = ok && up(I.qd, qd.data(), sizeof(double) * ns) && up(I.qfd, qfd.data(), sizeof(double) * ns);
+    ok = ok && up(I.at_ptr, at_ptr.data(), sizeof(int) * (ns + 1)) && up(I.at_idx, at_idx.data(), sizeof(int) * nnzA) &&
+         up(I.at_val, at_val.data(), sizeof(double) * nnzA) && up(I.bc_ptr, bc_ptr.data(), sizeof(int) * (nu + 1)) &&
+         up(I.bc_idx, bc_idx.data(), sizeof(int) * nnzB) && up(I.bc_val, bc_val.data(), sizeof(double) * nnzB);
     {
         std::vector<int> plan = syrk_tc_make_plan(ns, nu, N);
         ok = ok && up(I.tc_plan, plan.data(), sizeof(int) * plan.size());
@@ -1076,11 +1137,11 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "r")) {
             char k[128];
-            int cc, p32, p64;
+            int cc, p32, p64, k64;
             std::lock_guard<std::mutex> lock(g_tune_mu);
-            while (fscanf(f, "%127s %d %d %d", k, &cc, &p32, &p64) == 4) {
+            while (fscanf(f, "%127s %d %d %d %d", k, &cc, &p32, &p64, &k64) == 5) {
                 Tuning t;
-                t.cc_splits = cc; t.potrf[0] = p32; t.potrf[1] = p64;
+                t.cc_splits = cc; t.potrf[0] = p32; t.potrf[1] = p64; t.kkt64 = k64;
                 g_tune[k] = t;
             }
             fclose(f);
@@ -1155,6 +1216,17 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
         } else {
             t.potrf[0] = t.potrf[1] = 0;
         }
+        // 3. FP64 formation: SYRK or backward recursion (where every instance has its buffers)
+        if (b.lyap) {
+            const float ts = timed(nullptr, [&]() {
+                launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
+            });
+            const float tl = timed(nullptr, [&]() {
+                launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, F_NONE, b.st);
+            });
+            t.kkt64 = tl < ts ? 1 : 0;
+        }
         if (cudaStreamSynchronize(b.st) != cudaSuccess || cudaGetLastError() != cudaSuccess) s = LQMPC_ERR_CUDA;
         // the autotune launches left the instances mid-setup: mark them not started
         for (auto* c : b.ctxs) cudaMemsetAsync(c->h.sc, 0, sizeof(Scal), b.st);
@@ -1170,7 +1242,7 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
     }
     if (cache_path) {
         if (FILE* f = fopen(cache_path, "a")) {
-            fprintf(f, "%s %d %d %d\n", key.c_str(), t.cc_splits, t.potrf[0], t.potrf[1]);
+            fprintf(f, "%s %d %d %d %d\n", key.c_str(), t.cc_splits, t.potrf[0], t.potrf[1], t.kkt64);
             fclose(f);
         }
     }
