@@ -103,6 +103,8 @@ struct Inst {
     double* M64; float* M32;          // n x n
     float* Xinv32;                    // n x n: inverse of the FP32 Cholesky factor (preconditioner)
     double* ldiag;                    // 2 x 32 x 32: factored diagonal blocks in flight (cooperative potrf)
+    float* ffw;                       // 4 x SX: float-float split of the Gamma' operands (hi0, lo0, hi1, lo1)
+    float* ffv;                       // 2 x n: float-float split of the Gamma operand (hi, lo)
     // FP64 KKT formation by the backward recursion (sparse A); lyP == nullptr: not used
     double* lyP; double* lyT;         // ns x ns each
     double* lyW;                      // N x ns x nu

@@ -226,9 +226,22 @@ __device__ __forceinline__ void split_ff(double v, float& h, float& l) {
     l = (float)(v - (double)h);
 }
 
-constexpr int kFfBM = 64, kFfBN = 16, kFfBK = 32, kFfThreads = 128, kFfMaxSplits = 8;
+constexpr int kFfBM = 64, kFfBN = 16, kFfBK = 32, kFfThreads = 128, kFfMaxSplits = 16;
+constexpr int kFfLdT = kFfBK + 4;   // row stride of the transposed-product G tile (16-byte rows)
 
-// Gamma v: block (m-tile of states, r-tile, split of the column range).
+// 16-byte asynchronous global -> shared copy (zero-filled when !valid).
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Gamma v: block (m-tile of states, r-tile, split of the column range).  G
+// tiles stream through a double-buffered shared-memory ring (cp.async); the
+// input comes split into float-float by k_ff_prep_v.
 __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
                                                             int out_role, int flags, int splits) {
     const Inst& I = insts[blockIdx.y];
@@ -244,26 +257,19 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     const int kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
     const int nk = (n - kbeg + kFfBK - 1) / kFfBK;
     const int k0t = nk * split / splits, k1t = nk * (split + 1) / splits;
-    __shared__ float Gh[kFfBK][kFfBM], Gl[kFfBK][kFfBM];
-    __shared__ float Vh[kFfBK][kFfBN + 1], Vl[kFfBK][kFfBN + 1];
-    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;   // 8 x 16 threads: 2 r x 4 states each
-    float sh[4][2], sl[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
-    for (int kt = k0t; kt < k1t; ++kt) {
+    __shared__ __align__(16) float Gs[2][2][kFfBK][kFfBM];          // [buffer][hi, lo][col][state]
+    __shared__ float Vs[2][2][kFfBK][kFfBN + 1];                   // [buffer][hi, lo][col][r]
+    (void)v;
+    const float* vsp = I.ffv;                                       // the input, split by k_ff_prep_v
+    auto load = [&](int kt, int buf) {
         const int c0 = kbeg + kt * kFfBK;
-        for (int e = threadIdx.x; e < kFfBK * kFfBM; e += kFfThreads) {
-            const int kk = e / kFfBM, mm = e % kFfBM;
-            const int col = c0 + kk, i = m0 + mm;
-            float h = 0.f, l = 0.f;
-            if (col < n && i < ns) {
-                h = I.G32[(size_t)ldg * col + i];
-                l = I.G32lo[(size_t)ldg * col + i];
-            }
-            Gh[kk][mm] = h;
-            Gl[kk][mm] = l;
+        for (int e = threadIdx.x; e < kFfBK * (kFfBM / 4); e += kFfThreads) {
+            const int kk = e / (kFfBM / 4), q = e % (kFfBM / 4);
+            const int col = c0 + kk;
+            const bool ok = col < n;
+            const size_t off = (size_t)ldg * (ok ? col : 0) + m0 + 4 * q;   // rows past ns are zero padding
+            cp16(&Gs[buf][0][kk][4 * q], I.G32 + off, ok);
+            cp16(&Gs[buf][1][kk][4 * q], I.G32lo + off, ok);
         }
         for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
             const int kk = e / kFfBN, rr = e % kFfBN;
@@ -271,19 +277,36 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             float h = 0.f, l = 0.f;
             if (col < n && r < N) {
                 const int t = col - (N - 1 - r) * nu;
-                if (t >= 0) split_ff(v[t], h, l);
+                if (t >= 0) { h = vsp[t]; l = vsp[n + t]; }
             }
-            Vh[kk][rr] = h;
-            Vl[kk][rr] = l;
+            Vs[buf][0][kk][rr] = h;
+            Vs[buf][1][kk][rr] = l;
+        }
+        cp_commit();
+    };
+    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;   // 8 x 16 threads: 2 r x 4 states each
+    float sh[4][2], sl[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
+    if (k0t < k1t) load(k0t, 0);
+    for (int kt = k0t; kt < k1t; ++kt) {
+        const int buf = (kt - k0t) & 1;
+        if (kt + 1 < k1t) {
+            load(kt + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < kFfBK; ++kk) {
             float ah[4], al[4], bh[2], bl[2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) { ah[a] = Gh[kk][ty + 16 * a]; al[a] = Gl[kk][ty + 16 * a]; }
+            for (int a = 0; a < 4; ++a) { ah[a] = Gs[buf][0][kk][ty + 16 * a]; al[a] = Gs[buf][1][kk][ty + 16 * a]; }
 #pragma unroll
-            for (int b = 0; b < 2; ++b) { bh[b] = Vh[kk][tx + 8 * b]; bl[b] = Vl[kk][tx + 8 * b]; }
+            for (int b = 0; b < 2; ++b) { bh[b] = Vs[buf][0][kk][tx + 8 * b]; bl[b] = Vs[buf][1][kk][tx + 8 * b]; }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -314,7 +337,40 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
     }
 }
 
-// Gamma' w for NV vectors: P[col, r'] over r' = vec * N + r, K = states.
+// Float-float split of the Gamma operand, once per product.
+__global__ void k_ff_prep_v(const Inst* __restrict__ insts, int in_role, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const double* v = role_ptr(I, in_role);
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x)
+        split_ff(v[j], I.ffv[j], I.ffv[I.n + j]);
+}
+
+// Float-float split of the Gamma' operands (w0 scaled by Sigma_x when
+// scale0), once per product instead of once per tile that reads them.
+__global__ void k_ff_prep_w(const Inst* __restrict__ insts, int w0_role, int w1_role, int scale0, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const double* w0 = role_ptr(I, w0_role);
+    const double* w1 = w1_role != R_NONE ? role_ptr(I, w1_role) : nullptr;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
+        float h, l;
+        double wv = w0[k];
+        if (scale0) wv *= I.sigx[k];
+        split_ff(wv, h, l);
+        I.ffw[k] = h;
+        I.ffw[(size_t)I.SX + k] = l;
+        if (w1) {
+            split_ff(w1[k], h, l);
+            I.ffw[2 * (size_t)I.SX + k] = h;
+            I.ffw[3 * (size_t)I.SX + k] = l;
+        }
+    }
+}
+
+// Gamma' w for NV vectors: P[col, r'] over r' = vec * N + r, K = states.  G
+// tiles (transposed: [col][state]) and the pre-split operands stream through
+// a double-buffered ring.
 template <int NV>
 __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restrict__ insts, int w0_role,
                                                              int w1_role, int scale0, int flags, int splits) {
@@ -335,30 +391,20 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         }
         if (!any) return;
     }
-    const double* w0 = role_ptr(I, w0_role);
-    const double* w1 = NV > 1 ? role_ptr(I, w1_role) : nullptr;
+    (void)w0_role; (void)w1_role; (void)scale0;   // operands come split by k_ff_prep_w
     const int nk = (ns + kFfBK - 1) / kFfBK;
     const int k0t = nk * split / splits, k1t = nk * (split + 1) / splits;
-    __shared__ float Gh[kFfBM][kFfBK + 1], Gl[kFfBM][kFfBK + 1];   // [col][state]: conflict-free stores
-    __shared__ float Wh[kFfBK][kFfBN + 1], Wl[kFfBK][kFfBN + 1];
-    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;
-    float sh[4][2], sl[4][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
-    for (int kt = k0t; kt < k1t; ++kt) {
+    __shared__ __align__(16) float Gs[2][2][kFfBM][kFfLdT];   // [buffer][hi, lo][col][state]
+    __shared__ float Ws[2][2][kFfBK][kFfBN + 1];              // [buffer][hi, lo][state][r']
+    auto load = [&](int kt, int buf) {
         const int i0 = kt * kFfBK;
-        for (int e = threadIdx.x; e < kFfBK * kFfBM; e += kFfThreads) {
-            const int mm = e / kFfBK, kk = e % kFfBK;    // consecutive threads: consecutive states
-            const int col = c0 + mm, i = i0 + kk;
-            float h = 0.f, l = 0.f;
-            if (col < n && i < ns) {
-                h = I.G32[(size_t)ldg * col + i];
-                l = I.G32lo[(size_t)ldg * col + i];
-            }
-            Gh[mm][kk] = h;
-            Gl[mm][kk] = l;
+        for (int e = threadIdx.x; e < kFfBM * (kFfBK / 4); e += kFfThreads) {
+            const int mm = e / (kFfBK / 4), q = e % (kFfBK / 4);
+            const int col = c0 + mm;
+            const bool ok = col < n;                  // states past ns are zero padding
+            const size_t off = (size_t)ldg * (ok ? col : 0) + i0 + 4 * q;
+            cp16(&Gs[buf][0][mm][4 * q], I.G32 + off, ok);
+            cp16(&Gs[buf][1][mm][4 * q], I.G32lo + off, ok);
         }
         for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
             const int rr = e / kFfBK, kk = e % kFfBK;
@@ -366,21 +412,38 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
             float h = 0.f, l = 0.f;
             if (rp < NR && i < ns) {
                 const int vec = rp / N, r = rp % N;
-                double wv = (vec == 0 ? w0 : w1)[(size_t)r * ns + i];
-                if (vec == 0 && scale0) wv *= I.sigx[(size_t)r * ns + i];
-                split_ff(wv, h, l);
+                const size_t q = (size_t)r * ns + i;
+                h = I.ffw[(size_t)(2 * vec) * I.SX + q];
+                l = I.ffw[(size_t)(2 * vec + 1) * I.SX + q];
             }
-            Wh[kk][rr] = h;
-            Wl[kk][rr] = l;
+            Ws[buf][0][kk][rr] = h;
+            Ws[buf][1][kk][rr] = l;
+        }
+        cp_commit();
+    };
+    const int tx = threadIdx.x % 8, ty = threadIdx.x / 8;
+    float sh[4][2], sl[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) sh[a][b] = sl[a][b] = 0.f;
+    if (k0t < k1t) load(k0t, 0);
+    for (int kt = k0t; kt < k1t; ++kt) {
+        const int buf = (kt - k0t) & 1;
+        if (kt + 1 < k1t) {
+            load(kt + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < kFfBK; ++kk) {
             float ah[4], al[4], bh[2], bl[2];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) { ah[a] = Gh[ty + 16 * a][kk]; al[a] = Gl[ty + 16 * a][kk]; }
+            for (int a = 0; a < 4; ++a) { ah[a] = Gs[buf][0][ty + 16 * a][kk]; al[a] = Gs[buf][1][ty + 16 * a][kk]; }
 #pragma unroll
-            for (int b = 0; b < 2; ++b) { bh[b] = Wh[kk][tx + 8 * b]; bl[b] = Wl[kk][tx + 8 * b]; }
+            for (int b = 0; b < 2; ++b) { bh[b] = Ws[buf][0][kk][tx + 8 * b]; bl[b] = Ws[buf][1][kk][tx + 8 * b]; }
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -517,7 +580,7 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
 }
 
 static int ff_splits(int tiles, int nk) {
-    int s = (2 * 148 + tiles - 1) / (tiles > 0 ? tiles : 1);
+    int s = (4 * 148 + tiles - 1) / (tiles > 0 ? tiles : 1);   // about four CTAs per SM
     if (s > nk) s = nk;
     if (s > kFfMaxSplits) s = kFfMaxSplits;
     return s < 1 ? 1 : s;
@@ -527,6 +590,7 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
                         int out_role, int flags, cudaStream_t st) {
     const int tiles = ((max_ns + kFfBM - 1) / kFfBM) * ((max_N + kFfBN - 1) / kFfBN);
     const int splits = ff_splits(tiles * count, (max_n + kFfBK - 1) / kFfBK);
+    LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
     LQ_LAUNCH(k_gamma_mv_ff<<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
     int nb = (max_ns * max_N + 255) / 256;
     nb = nb > 4096 ? 4096 : nb;
@@ -540,6 +604,9 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
     const int splits = ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
     int nb = (NV * max_n + 7) / 8;
     nb = nb > 4096 ? 4096 : nb;
+    int npre = (max_ns * max_N + 255) / 256;
+    npre = npre > 4096 ? 4096 : npre;
+    LQ_LAUNCH(k_ff_prep_w<<<dim3(npre, count), 256, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
     if (NV == 2) {
         LQ_LAUNCH(k_gamma_tmv_ff<2><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags, splits));
         LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 256, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));

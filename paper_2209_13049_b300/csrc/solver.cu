@@ -253,6 +253,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto ldiag = c.take<double>(2 * 32 * 32);
+    auto ffw = c.take<float>(4 * (size_t)I.SX);
+    auto ffv = c.take<float>(2 * (size_t)n);
     auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);
     auto tmpx = c.take<double>(SX);
     auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n, I.N));
@@ -281,6 +283,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.ldiag = ldiag;
+        I.ffw = ffw;
+        I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
         I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
         I.lyP = lyP; I.lyT = lyT; I.lyW = lyW;
