@@ -124,6 +124,7 @@ struct Inst {
     const int* tc_plan;               // tensor-core SYRK: per lower tile (splits, first partial)
     double* part;                     // kParts x kMaxParts reduction partials
     unsigned* bar;                    // grid-barrier state of cooperative launches (2 words)
+    int* pflags;                      // 64 words: dataflow Cholesky epoch, finished CTAs, block-column flags
     Scal* sc;
     double* trace;                    // (max_iter+1) x kTraceW
 };

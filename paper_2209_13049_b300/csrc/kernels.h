@@ -61,6 +61,9 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
                   int want_inv = 0, int variant = -1);
 bool launch_potrf_cluster(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st);
 bool potrf_cluster_fits(int max_n);
+// kernels_flow.cu (dataflow Cholesky with inverse, one instance, FP32)
+bool potrf_flow_fits(int count, int max_n);
+bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t st);
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
                        cudaStream_t st);
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

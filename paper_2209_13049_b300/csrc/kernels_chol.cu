@@ -568,7 +568,11 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
     // every SM with the cooperative kernel (measured faster for one n = 500
     // matrix: 0.37-0.50 ms FP32 against 0.53 ms for the cluster kernel, and
     // 1.16 ms against 1.95 ms in FP64, whose pipe rate makes 8 SMs too few).
-    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies (autotuned)
+    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies, 2 dataflow
+    // (one instance, FP32 with the inverse) -- autotuned
+    if (!fp64 && want_inv && (variant == 2 || (variant < 0 && potrf_flow_fits(count, max_n))) &&
+        potrf_flow_fits(count, max_n) && launch_potrf_flow(d_insts, max_n, flags, st))
+        return;
     const bool cluster_ok = fp64 || want_inv;
     const bool want_cluster = variant == 1 || (variant < 0 && count * 8 >= sms);
     if (cluster_ok && want_cluster && launch_potrf_cluster(d_insts, count, max_n, fp64, flags, st)) return;

@@ -253,6 +253,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto ldiag = c.take<double>(2 * 32 * 32);
+    auto pflags = c.take<int>(64);
     auto ffw = c.take<float>(4 * (size_t)I.SX);
     auto ffv = c.take<float>(2 * (size_t)n);
     auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);
@@ -283,6 +284,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.ldiag = ldiag;
+        I.pflags = pflags;
         I.ffw = ffw;
         I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
@@ -1198,11 +1200,14 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
             if (ms < best) { best = ms; t.cc_splits = c; }
         }
         b.cc_splits = t.cc_splits;
-        // 2. Cholesky variant (cooperative over all SMs, or one 8-CTA cluster per instance)
-        if (potrf_cluster_fits(b.max_n)) {
+        // 2. Cholesky variant: cooperative over all SMs, one 8-CTA cluster per
+        //    instance, or (one instance, FP32 with the inverse) the dataflow kernel
+        if (potrf_cluster_fits(b.max_n) || potrf_flow_fits(b.count, b.max_n)) {
             for (int fp64 = 0; fp64 < 2; ++fp64) {
                 float bv = 1e30f;
-                for (int v = 0; v < 2; ++v) {
+                for (int v = 0; v < 3; ++v) {
+                    if (v == 1 && !potrf_cluster_fits(b.max_n)) continue;
+                    if (v == 2 && (fp64 || !potrf_flow_fits(b.count, b.max_n))) continue;
                     auto form = [&]() {
                         const int prec = fp64 ? LQMPC_FP64 : LQMPC_FP32;
                         launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, fp64, 0, nullptr, nullptr, F_NONE,
