@@ -85,6 +85,8 @@ struct Inst {
     float* G32;                       // FP32 rounding of G64 (also the TF32 operand)
     float* G32lo;                     // G64 - G32 in FP32 (float-float products)
     __nv_bfloat16* G16;
+    float* Gt;                        // G64 rounded to TF32 (FP32 storage, low 13 bits zero)
+    float* Gtlo;                      // G64 - Gt in FP32 (split-TF32 products)
     double* H64;                      // n x n
     float* H32;                       // n x n
     // per solve

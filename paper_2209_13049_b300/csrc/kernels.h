@@ -87,8 +87,10 @@ int syrk_tc_tiles(int n);
 int syrk_tc_splits(int ns, int nu, int N);
 int syrk_tc_plan_partials(int ns, int nu, int N);
 std::vector<int> syrk_tc_make_plan(int ns, int nu, int N);
-bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out /* 128-byte CUtensorMap */);
-void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int tf32,
+// map kinds: 0 BF16 G-stack, 1 TF32-rounded G-stack, 2 its FP32 low part; three maps per instance
+bool syrk_tc_make_maps(const Inst& h, int kind, void* map_out /* 128-byte CUtensorMap */);
+// mode: 0 BF16, 1 TF32, 2 split TF32 (FP32-accurate)
+void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int mode,
                     const void* d_maps, int force, cudaStream_t st);
 
 // kernels_noalloc.cu (FP64 KKT formation with split-K partials in a fixed

@@ -52,6 +52,13 @@ __global__ void k_gstack_cast(const Inst* __restrict__ insts) {
         if (I.G32) I.G32[q] = gh;
         if (I.G32lo) I.G32lo[q] = (float)(g - (double)gh);
         if (I.G16) I.G16[q] = __double2bfloat16(g);
+        if (I.Gt) {
+            unsigned t;   // round to the nearest TF32 (the tensor cores read 19 of the 32 bits)
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(gh));
+            const float th = __uint_as_float(t);
+            I.Gt[q] = th;
+            I.Gtlo[q] = (float)(g - (double)th);
+        }
     }
 }
 

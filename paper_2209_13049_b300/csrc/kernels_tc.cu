@@ -27,8 +27,16 @@
 namespace lqmpc {
 
 constexpr int kTcTile = 128;
-constexpr int kStages = 6;
-constexpr int kStageBytes = 2 * kTcTile * 128;   // A + B tiles, 128 bytes of K per row
+constexpr int kTileBytes = kTcTile * 128;          // one operand tile: 128 rows of 128 bytes of K
+// MODE 0 BF16, 1 TF32: A + B tiles per stage, 6 stages.  MODE 2 split TF32
+// (the FP32-accurate product from hi + lo operands, three TF32 products):
+// A_hi, A_lo, B_hi, B_lo per stage, 3 stages.  Both use 192 KB of shared memory.
+template <int MODE> struct TcCfg {
+    static constexpr int kTiles = MODE == 2 ? 4 : 2;
+    static constexpr int kStageBytes = kTiles * kTileBytes;
+    static constexpr int kStages = MODE == 2 ? 3 : 6;
+};
+constexpr int kStagesMax = 6;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -140,15 +148,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-template <bool TF32>
+template <int MODE>
 __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ insts, const CUtensorMap* maps,
                                                      int splits, int flags) {
+    constexpr bool TF32 = MODE != 0;
+    constexpr int kStages = TcCfg<MODE>::kStages;
+    constexpr int kStageBytes = TcCfg<MODE>::kStageBytes;
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
-    __shared__ __align__(8) uint64_t bar_full[kStages], bar_scaled[kStages], bar_empty[kStages], bar_acc;
+    __shared__ __align__(8) uint64_t bar_full[kStagesMax], bar_scaled[kStagesMax], bar_empty[kStagesMax], bar_acc;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     __shared__ int issued_sh;
-    __shared__ __align__(16) float Ds[kStages][64];   // Sigma_x segment of each stage
+    __shared__ __align__(16) float Ds[kStagesMax][64];   // Sigma_x segment of each stage
 
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
@@ -174,7 +185,9 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
     // 1024-byte aligned stage buffers
     unsigned char* sbase = (unsigned char*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const CUtensorMap* map = maps + 2 * blockIdx.y + (TF32 ? 1 : 0);   // per instance: BF16, TF32
+    // per instance: BF16 (hi), TF32, BF16 lo
+    const CUtensorMap* map = maps + 3 * blockIdx.y + (TF32 ? 1 : 0);
+    const CUtensorMap* map_lo = maps + 3 * blockIdx.y + 2;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -212,8 +225,15 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 unsigned char* st = sbase + (size_t)s * kStageBytes;
                 const uint32_t fb = smem_u32(&bar_full[s]);
                 mbar_expect_tx(fb, kStageBytes + KC * 4);
+                // stage layout: A (hi), [A lo], B (hi), [B lo]
                 tma_load_2d(smem_u32(st), map, i0, off + a * kTcTile, fb);
-                tma_load_2d(smem_u32(st + kStageBytes / 2), map, i0, off + b * kTcTile, fb);
+                if (MODE == 2) {
+                    tma_load_2d(smem_u32(st + kTileBytes), map_lo, i0, off + a * kTcTile, fb);
+                    tma_load_2d(smem_u32(st + 2 * kTileBytes), map, i0, off + b * kTcTile, fb);
+                    tma_load_2d(smem_u32(st + 3 * kTileBytes), map_lo, i0, off + b * kTcTile, fb);
+                } else {
+                    tma_load_2d(smem_u32(st + kTileBytes), map, i0, off + b * kTcTile, fb);
+                }
                 // Sigma_x[r, i0 : i0 + KC] (zero-padded rows of ldg floats, 16-byte aligned)
                 bulk_load(smem_u32(&Ds[s][0]), I.sigx32 + (size_t)r * I.ldg + i0, KC * 4, fb);
                 ++issued;
@@ -230,12 +250,27 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 if (!mbar_wait(smem_u32(&bar_scaled[s]), round & 1, abort_flag)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = smem_u32(sbase + (size_t)s * kStageBytes);
-                const uint32_t sb = sa + kStageBytes / 2;
-                const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+                if (MODE == 2) {
+                    // A_hi B_hi + A_hi B_lo + A_lo B_hi in TF32: each operand is hi + lo to about
+                    // 2^-22 and the dropped A_lo B_lo is about 2^-22 of the product
+                    const uint64_t dah = smem_desc_sw128(sa), dal = smem_desc_sw128(sa + kTileBytes);
+                    const uint64_t dbh = smem_desc_sw128(sa + 2 * kTileBytes);
+                    const uint64_t dbl = smem_desc_sw128(sa + 3 * kTileBytes);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)   // 4 MMAs of 32 bytes of K each
-                    mma_issue<TF32>(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
-                                    (q > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t o = (uint64_t)(2 * k);
+                        mma_issue<true>(tmem, dah + o, dbh + o, idesc, (q > 0 || k > 0) ? 1u : 0u);
+                        mma_issue<true>(tmem, dah + o, dbl + o, idesc, 1u);
+                        mma_issue<true>(tmem, dal + o, dbh + o, idesc, 1u);
+                    }
+                } else {
+                    const uint32_t sb = sa + kTileBytes;
+                    const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)   // 4 MMAs of 32 bytes of K each
+                        mma_issue<TF32>(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
+                                        (q > 0 || k > 0) ? 1u : 0u);
+                }
                 mma_commit(smem_u32(&bar_empty[s]));
             }
             if (ok && nq > 0) mma_commit(smem_u32(&bar_acc));
@@ -247,7 +282,31 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
             const int s = q % kStages, round = q / kStages;
             if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, abort_flag)) break;
             const float* D = &Ds[s][0];
-            unsigned char* rowp = sbase + (size_t)s * kStageBytes + kStageBytes / 2 + (size_t)t * 128;
+            unsigned char* rowp = sbase + (size_t)s * kStageBytes + (MODE == 2 ? 2 : 1) * kTileBytes + (size_t)t * 128;
+            if (MODE == 2) {
+                // B = D (B_hi + B_lo), re-split into TF32 hi + FP32 lo
+                unsigned char* rowl = rowp + kTileBytes;
+#pragma unroll
+                for (int lc = 0; lc < 8; ++lc) {
+                    const int p = lc ^ (t & 7);
+                    float4* ch = reinterpret_cast<float4*>(rowp + p * 16);
+                    float4* cl = reinterpret_cast<float4*>(rowl + p * 16);
+                    const float4 vh = *ch, vl = *cl;
+                    const float4 d = *reinterpret_cast<const float4*>(D + lc * 4);
+                    const float x[4] = {(vh.x + vl.x) * d.x, (vh.y + vl.y) * d.y, (vh.z + vl.z) * d.z,
+                                        (vh.w + vl.w) * d.w};
+                    float h[4], l[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        unsigned tb;
+                        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tb) : "f"(x[u]));
+                        h[u] = __uint_as_float(tb);
+                        l[u] = x[u] - h[u];
+                    }
+                    *ch = make_float4(h[0], h[1], h[2], h[3]);
+                    *cl = make_float4(l[0], l[1], l[2], l[3]);
+                }
+            } else {
 #pragma unroll
             for (int lc = 0; lc < 8; ++lc) {
                 const int p = lc ^ (t & 7);
@@ -268,6 +327,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                     f = __bfloat1622float2(h2[3]); h2[3] = __floats2bfloat162_rn(f.x * d1.z, f.y * d1.w);
                 }
                 *cp = v;
+            }
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_scaled[s]));
@@ -376,7 +436,9 @@ int syrk_tc_plan_partials(int ns, int nu, int N) {
     return p[p.size() - 2];
 }
 
-bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out) {
+// kind 0: BF16 G-stack, 1: TF32-rounded G-stack, 2: its FP32 low part.
+bool syrk_tc_make_maps(const Inst& h, int kind, void* map_out) {
+    const int tf32 = kind != 0;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -392,7 +454,7 @@ bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out) {
     cuuint64_t strides[1] = {(cuuint64_t)h.ldg * esz};
     cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)kTcTile};
     cuuint32_t estr[2] = {1, 1};
-    void* base = tf32 ? (void*)h.G32 : (void*)h.G16;
+    void* base = kind == 1 ? (void*)h.Gt : (kind == 2 ? (void*)h.Gtlo : (void*)h.G16);
     CUresult r = encode((CUtensorMap*)map_out, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                         2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -400,16 +462,22 @@ bool syrk_tc_make_maps(const Inst& h, int tf32, void* map_out) {
     return r == CUDA_SUCCESS;
 }
 
-void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int tf32, const void* d_maps,
+void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int mode, const void* d_maps,
                     int flags, cudaStream_t st) {
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
     dim3 grid(splits, count);   // splits = total partials of the plan
-    if (tf32) {
-        cudaFuncSetAttribute(k_syrk_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<true><<<grid, 192, smem, st>>>(d_insts, (const CUtensorMap*)d_maps, splits, flags));
+    const CUtensorMap* maps = (const CUtensorMap*)d_maps;
+    if (mode == 1) {
+        const size_t smem = (size_t)TcCfg<1>::kStages * TcCfg<1>::kStageBytes + 1024;
+        cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        LQ_LAUNCH(k_syrk_tc<1><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
+    } else if (mode == 2) {
+        const size_t smem = (size_t)TcCfg<2>::kStages * TcCfg<2>::kStageBytes + 1024;
+        cudaFuncSetAttribute(k_syrk_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        LQ_LAUNCH(k_syrk_tc<2><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
     } else {
-        cudaFuncSetAttribute(k_syrk_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<false><<<grid, 192, smem, st>>>(d_insts, (const CUtensorMap*)d_maps, splits, flags));
+        const size_t smem = (size_t)TcCfg<0>::kStages * TcCfg<0>::kStageBytes + 1024;
+        cudaFuncSetAttribute(k_syrk_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        LQ_LAUNCH(k_syrk_tc<0><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
     }
 }
 

@@ -144,7 +144,7 @@ struct lqmpc_ctx {
     int cc_splits = 1;          // CUDA-core SYRK split-K factor
     int tc_splits = 1;          // tensor-core SYRK split-K factor
     int tc_ok = 0;              // tensor maps built
-    void* d_maps = nullptr;     // 2 CUtensorMap (BF16, TF32), 64-byte aligned, device
+    void* d_maps = nullptr;     // 3 CUtensorMap (BF16, TF32, TF32 low part), 64-byte aligned, device
     cudaEvent_t ev[4];
     cudaEvent_t evk[4];         // around the SYRK launch: tensor-core pair, CUDA-core pair
     bool events = false;
@@ -230,6 +230,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto qd = c.take<double>(ns); auto qfd = c.take<double>(ns);
     auto G64 = c.take<double>(G); auto G32 = c.take<float>(G); auto G32lo = c.take<float>(G);
     auto G16 = c.take<__nv_bfloat16>(G);
+    auto Gt = c.take<float>(G); auto Gtlo = c.take<float>(G);
     auto H64 = c.take<double>((size_t)n * n); auto H32 = c.take<float>((size_t)n * n);
     auto xbar = c.take<double>(ns); auto y = c.take<double>(SX); auto h = c.take<double>(n);
     auto u = c.take<double>(n); auto x = c.take<double>(SX);
@@ -274,7 +275,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.q_ptr = q_ptr; I.q_idx = q_idx; I.q_val = q_val;
         I.qf_ptr = qf_ptr; I.qf_idx = qf_idx; I.qf_val = qf_val;
         I.B = B; I.R = R; I.xl = xl; I.xu = xu; I.ul = ul; I.uu = uu; I.qd = qd; I.qfd = qfd;
-        I.G64 = G64; I.G32 = G32; I.G32lo = G32lo; I.G16 = G16; I.H64 = H64; I.H32 = H32;
+        I.G64 = G64; I.G32 = G32; I.G32lo = G32lo; I.G16 = G16; I.Gt = Gt; I.Gtlo = Gtlo; I.H64 = H64; I.H32 = H32;
         I.xbar = xbar; I.y = y; I.h = h; I.u = u; I.x = x;
         I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
         I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32;
@@ -305,7 +306,7 @@ struct Batch {
     int count = 0, max_ns = 0, max_N = 0, max_n = 0, max_sx = 0, max_total = 0;
     int cc_splits = 1, tc_splits = 1;
     cudaStream_t st = nullptr;
-    const void* d_maps = nullptr;   // tensor maps: 2 per instance (BF16, TF32), instance order
+    const void* d_maps = nullptr;   // tensor maps: 3 per instance (BF16, TF32, TF32 low part), instance order
     bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
     double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
@@ -457,16 +458,17 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
             launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, shift);
             launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1]);
         } else {
-            if (prec == LQMPC_FP32) {
+            if (prec == LQMPC_FP32 && !b.d_maps) {
                 rec(c0->evk[2]);
                 launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 0, nullptr, nullptr, sel, b.st);
                 rec(c0->evk[3]);
                 launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
             } else {
+                // FP32: split-TF32 products on the tensor cores (FP32-accurate formation)
+                const int mode = prec == LQMPC_MIXED_TF32 ? 1 : (prec == LQMPC_FP32 ? 2 : 0);
                 rec(c0->evk[0]);
-                launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, prec == LQMPC_MIXED_TF32, b.d_maps,
-                               sel, b.st);
+                launch_syrk_tc(b.d_insts, b.count, b.max_n, b.tc_splits, mode, b.d_maps, sel, b.st);
                 rec(c0->evk[1]);
                 launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
@@ -478,7 +480,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
     if (shift == 0.0) seg_run(b, SEG_FORM + prec + (tm ? 4 : 0), body);
     else body();
     if (tm) {
-        if (prec == LQMPC_FP64 || prec == LQMPC_FP32) { tm->cc = true; tm->cc64 = prec == LQMPC_FP64; }
+        if (prec == LQMPC_FP64 || (prec == LQMPC_FP32 && !b.d_maps)) { tm->cc = true; tm->cc64 = prec == LQMPC_FP64; }
         else tm->tc = true;
     }
 }
@@ -1015,12 +1017,13 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         return fail(LQMPC_ERR_CUDA);
     // tensor maps for the tcgen05 SYRK (BF16 and TF32 views of the G-stack)
     {
-        alignas(64) unsigned char maps[256];
+        alignas(64) unsigned char maps[3 * 128];
         bool m0 = syrk_tc_make_maps(I, 0, maps);
         bool m1 = syrk_tc_make_maps(I, 1, maps + 128);
-        if (m0 && m1) {
-            if (cudaMalloc(&ctx->d_maps, 256) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
-            if (cudaMemcpy(ctx->d_maps, maps, 256, cudaMemcpyHostToDevice) != cudaSuccess)
+        bool m2 = syrk_tc_make_maps(I, 2, maps + 256);
+        if (m0 && m1 && m2) {
+            if (cudaMalloc(&ctx->d_maps, sizeof(maps)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+            if (cudaMemcpy(ctx->d_maps, maps, sizeof(maps), cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(LQMPC_ERR_CUDA);
             ctx->tc_ok = 1;
         }
@@ -1078,7 +1081,7 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
     Inst* d = nullptr;
     void* maps = nullptr;
     CK(cudaMalloc(&d, sizeof(Inst) * count));
-    if (tc && count > 1 && cudaMalloc(&maps, 256 * (size_t)count) != cudaSuccess) {
+    if (tc && count > 1 && cudaMalloc(&maps, 384 * (size_t)count) != cudaSuccess) {
         cudaFree(d);
         return LQMPC_ERR_CUDA;
     }
@@ -1089,7 +1092,7 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (count == 1) b.d_maps = ctxs[0]->d_maps;
         else {
             for (int i = 0; i < count && s == LQMPC_OK; ++i)
-                if (cudaMemcpyAsync((char*)maps + 256 * (size_t)i, ctxs[i]->d_maps, 256, cudaMemcpyDeviceToDevice,
+                if (cudaMemcpyAsync((char*)maps + 384 * (size_t)i, ctxs[i]->d_maps, 384, cudaMemcpyDeviceToDevice,
                                     b.st) != cudaSuccess)
                     s = LQMPC_ERR_CUDA;
             b.d_maps = maps;
