@@ -1,8 +1,9 @@
 #!/usr/bin/env python
 """Benchmark: LQ-MPC interior-point solves/s and per-iteration KKT time at a
-1e-8 scaled KKT residual, mixed precision (BF16 tensor-core SYRK + FP32
-Cholesky + FP64 refinement) versus FP64, on the 2-D heat plant of a 32 x 32
-grid (ns = 1024, nu = 10, N = 50; condensed M is 500 x 500).
+1e-8 scaled KKT residual, mixed precision (tensor-core formation of M, FP32
+Cholesky, FP64 refinement and fallback; --precision picks the formation:
+split TF32 = FP32-accurate (default), BF16 or TF32) versus FP64, on the 2-D
+heat plant of a 32 x 32 grid (ns = 1024, nu = 10, N = 50; M is 500 x 500).
 
 One step = one full IPM solve (all per-iteration steps of the hot path) for
 one seeded initial state x0.  Inputs sit in device memory before the timed
@@ -37,9 +38,16 @@ METRIC = "LQ-MPC IPM solves/s & per-iter KKT ms at 1e-8 residual, mixed vs FP64"
 WORKLOAD = "heat2d 32x32 (ns=1024, nu=10, N=50), x0 = seeded 8-Gaussian fields, tol 1e-8"
 GOLD = os.path.join(ROOT, "tests", "golden", "heat2d_g32_nu10_N50.npz")
 NS, NU, N = 1024, 10, 50
-# DRAM bytes (read + write) of one k_syrk_cc<double> launch on this workload, from
-# the ncu capture summarised in profiles/kernels_heat2d_32x32_ncu_full.md
-SYRK_FP64_TRAFFIC = 4532480
+# DRAM bytes (read + write) of one k_potrf_flow launch on this workload from the
+# ncu capture summarised in profiles/ (None until captured for this kernel version)
+POTRF_FLOW_TRAFFIC = 750848
+DTYPES = {
+    "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, FP64 "
+            "refinement and fallback",
+    "bf16": "mixed: BF16 tcgen05 formation (FP32 accumulate), FP32 Cholesky, FP64 refinement and fallback",
+    "tf32": "mixed: TF32 tcgen05 formation (FP32 accumulate), FP32 Cholesky, FP64 refinement and fallback",
+    "fp64": "f64",
+}
 
 
 def syrk_alg_flops(ns, nu, N):
@@ -47,6 +55,14 @@ def syrk_alg_flops(ns, nu, N):
     lower-triangular Toeplitz structure of Gamma: the lower-triangle blocks
     (j >= k) each need N - j products G_p' D G_q of 2 ns nu^2 flops."""
     return 2.0 * ns * nu * nu * N * (N + 1) * (N + 2) / 6.0
+
+
+def lyap_fma(p):
+    """Multiply-adds of the FP64 backward-recursion formation of M for plant p."""
+    import scipy.sparse as sp
+    nnz_a = sp.csr_matrix(p.A).nnz
+    nnz_b = int(np.count_nonzero(p.B))
+    return p.N * (2.0 * nnz_a * p.ns + nnz_b * p.ns) + 0.5 * p.N * (p.N + 1) * p.nu * p.nu * p.ns
 
 
 def measured_peaks():
@@ -263,42 +279,62 @@ def run_ours(args):
                 "fallbacks_total": int(sum(s["fallbacks"] for s in stats)),
                 "status": sorted({int(s["status"]) for s in stats})}
 
-    # Rooflines from the library's CUDA events around the SYRK launches inside
-    # the timed solves.  The dominant kernel of a mixed solve is the FP64
-    # CUDA-core SYRK of the FP64 fallback iterations (bound by the FP64 pipe:
-    # 148 SMs x 2 DFMA/clk x 2 flop x SM clock); the tensor-core SYRK of the
-    # BF16/TF32 iterations is reported beside it.
+    # Rooflines from the library's CUDA events around the launches inside the
+    # timed solves.  The dominant kernel of a mixed solve (ncu launch list in
+    # profiles/) is the FP32 Cholesky with the inverse (k_potrf_flow, one
+    # instance): latency-bound, so it is reported against the FP32 FMA pipe
+    # (148 SMs x 128 FMA/clk x 2 flop x SM clock); algorithmic work = n^3/3
+    # (factor) + n^3/3 (triangular inverse).  Beside it: the tensor-core
+    # formation of M and the FP64 formation.
     peaks, which = measured_peaks()
-    flops = syrk_alg_flops(NS, NU, N)
-    n64 = sum(s["syrk_fp64_launches"] for s in st_mixed)
-    t64 = sum(s["t_syrk_fp64_ms"] for s in st_mixed)
-    if not n64:      # no fallback in these solves: take the FP64 solves' launches
-        n64 = sum(s["syrk_fp64_launches"] for s in st_fp64)
-        t64 = sum(s["t_syrk_fp64_ms"] for s in st_fp64)
     sm_mhz = clocks.get("sm_mhz") or 2032.0
+    n = NU * N
+    npf = sum(s["potrf32_launches"] for s in st_mixed)
+    tpf = sum(s["t_potrf32_ms"] for s in st_mixed)
+    pf_flops = 2.0 * n ** 3 / 3.0
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    ach_pf = pf_flops / (tpf / max(1, npf) / 1e3) / 1e12 if npf else None
+    roofline = {"kernel": "k_potrf_flow (FP32 Cholesky + inverse of the factor, n = 500)", "bound": "alu",
+                "achieved": ach_pf, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (ach_pf / fp32_peak) if ach_pf else None, "traffic": POTRF_FLOW_TRAFFIC,
+                "peak_source": f"derived: 148 SMs x 128 FP32 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
+                               f"sampled during the timed region); latency-bound (one diagonal block after another)",
+                "flops_per_launch": pf_flops, "launches": npf,
+                "avg_launch_us": (tpf / max(1, npf) * 1e3) if npf else None}
+    flops = syrk_alg_flops(NS, NU, N)
+    n3 = sum(s["syrk_tc3_launches"] for s in st_mixed)
+    t3 = sum(s["t_syrk_tc3_ms"] for s in st_mixed)
+    n1 = sum(s["syrk_tc_launches"] for s in st_mixed) - n3
+    t1 = sum(s["t_syrk_tc_ms"] for s in st_mixed) - t3
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1400.0) * 0.5      # nominal TF32 : BF16 = 1 : 2
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1400.0)
+    roofline_tc = {
+        "kernel": "k_syrk_tc (tcgen05 formation of M, Eq. 7)", "bound": "tensor", "unit": "TFLOP/s",
+        "algorithmic_flops_per_launch": flops,
+        "split_tf32": {"launches": n3, "avg_launch_us": (t3 / n3 * 1e3) if n3 else None,
+                       "executed_flops_per_launch": 3 * flops,
+                       "achieved": (3 * flops / (t3 / n3 / 1e3) / 1e12) if n3 else None, "peak": tf32_peak,
+                       "frac": (3 * flops / (t3 / n3 / 1e3) / 1e12 / tf32_peak) if n3 else None,
+                       "peak_source": f"{which} bf16_tflops_sustained x 0.5 (nominal TF32 rate)"},
+        "bf16": {"launches": n1, "avg_launch_us": (t1 / n1 * 1e3) if n1 else None,
+                 "achieved": (flops / (t1 / n1 / 1e3) / 1e12) if n1 else None, "peak": bf16_peak,
+                 "frac": (flops / (t1 / n1 / 1e3) / 1e12 / bf16_peak) if n1 else None,
+                 "peak_source": f"{which} bf16_tflops_sustained"}}
+    n64 = sum(s["syrk_fp64_launches"] for s in st_fp64)
+    t64 = sum(s["t_syrk_fp64_ms"] for s in st_fp64)
     fp64_peak = 148 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    ach64 = flops / (t64 / max(1, n64) / 1e3) / 1e12 if n64 else None
-    roofline = {"kernel": "k_syrk_cc<double> (FP64 KKT-matrix formation, Eq. 7)", "bound": "alu",
-                "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": (ach64 / fp64_peak) if ach64 else None, "traffic": SYRK_FP64_TRAFFIC,
-                "peak_source": f"derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz (median SM clock "
-                               f"sampled during the timed region)",
-                "flops_per_launch": flops, "launches": n64,
-                "avg_launch_us": (t64 / max(1, n64) * 1e3) if n64 else None}
-    n_tc = sum(s["syrk_tc_launches"] for s in st_mixed)
-    t_tc = sum(s["t_syrk_tc_ms"] for s in st_mixed)
-    achieved = flops / (t_tc / max(1, n_tc) / 1e3) / 1e12 if n_tc else None
-    peak = peaks.get("bf16_tflops_sustained", 1400.0)
-    roofline_tc = {"kernel": "k_syrk_tc (tcgen05 KKT-matrix formation)", "bound": "tensor",
-                   "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                   "frac": (achieved / peak) if achieved else None,
-                   "peak_source": f"{which} bf16_tflops_sustained", "flops_per_launch": flops,
-                   "launches": n_tc, "avg_launch_us": (t_tc / max(1, n_tc) * 1e3) if n_tc else None}
+    ly_flops = 2.0 * lyap_fma(plant)
+    roofline_fp64 = {"kernel": "FP64 formation of M by the backward recursion (k_ly_*)", "bound": "alu",
+                     "unit": "TFLOP/s", "launches": n64, "avg_us": (t64 / n64 * 1e3) if n64 else None,
+                     "algorithmic_flops": ly_flops,
+                     "achieved": (ly_flops / (t64 / n64 / 1e3) / 1e12) if n64 else None, "peak": fp64_peak,
+                     "frac": (ly_flops / (t64 / n64 / 1e3) / 1e12 / fp64_peak) if n64 else None,
+                     "peak_source": "derived: 148 SMs x 2 FP64 FMA/clk x 2 flop x SM clock"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": K, "warmup": W,
                 "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "mixed-bf16 (bf16 SYRK, fp32 Cholesky, fp64 refinement)",
+                "vs_baseline": None, "dtype": DTYPES[args.precision],
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "ns": NS, "nu": NU, "N": N,
                            "l2": "flushed between steps (512 MB write, outside the timed events)",
@@ -306,6 +342,7 @@ def run_ours(args):
                 "mixed": summary(t_mixed, st_mixed), "fp64": summary(t_fp64, st_fp64),
                 "speedup_mixed_vs_fp64": (value / world) / (kf / (sum(t_fp64) / 1e3)),
                 "u_rel_err_vs_oracle": errs, "roofline": roofline, "roofline_tensor_syrk": roofline_tc,
+                "roofline_fp64_formation": roofline_fp64,
                 "clocks": clocks,
                 "gpu_launches": int(launches),
                 "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": NS * 8,
@@ -435,7 +472,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="heat2d32", choices=["heat2d32", "batch", "warmstart"],

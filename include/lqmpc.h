@@ -63,7 +63,9 @@ enum {
     LQMPC_MIXED_BF16 = 1,   /* BF16 tensor-core SYRK (FP32 accumulate), FP32 Cholesky,
                                FP64 iterative refinement, FP64 fallback */
     LQMPC_MIXED_TF32 = 2,   /* as above with TF32 tensor-core SYRK */
-    LQMPC_FP32 = 3          /* FP32 CUDA-core SYRK, FP32 Cholesky, FP64 refinement */
+    LQMPC_FP32 = 3          /* FP32-accurate SYRK (split-TF32 tensor-core products; CUDA cores
+                               where tensor maps are unavailable), FP32 Cholesky,
+                               FP64 refinement */
 };
 
 typedef struct {
@@ -95,8 +97,12 @@ typedef struct {
     double t_syrk_cc_ms; /* device time of the CUDA-core (FP64/FP32) SYRK launches */
     int syrk_tc_launches;
     int syrk_cc_launches;
-    double t_syrk_fp64_ms; /* the FP64 share of t_syrk_cc_ms (FP64 solves and fallbacks) */
+    double t_syrk_fp64_ms; /* device time of the FP64 formations of M (FP64 solves and fallbacks) */
     int syrk_fp64_launches;
+    double t_syrk_tc3_ms;  /* the split-TF32 (FP32-accurate) share of t_syrk_tc_ms */
+    int syrk_tc3_launches;
+    double t_potrf32_ms;   /* device time of the low-precision (FP32) Cholesky factorisations */
+    int potrf32_launches;
 } lqmpc_stats;
 
 /* Default options (values in the comments above). */

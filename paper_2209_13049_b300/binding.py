@@ -50,7 +50,9 @@ class Stats(ctypes.Structure):
                 ("res_dual", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("t_kkt_ms", ctypes.c_double),
                 ("t_syrk_tc_ms", ctypes.c_double), ("t_syrk_cc_ms", ctypes.c_double),
                 ("syrk_tc_launches", ctypes.c_int), ("syrk_cc_launches", ctypes.c_int),
-                ("t_syrk_fp64_ms", ctypes.c_double), ("syrk_fp64_launches", ctypes.c_int)]
+                ("t_syrk_fp64_ms", ctypes.c_double), ("syrk_fp64_launches", ctypes.c_int),
+                ("t_syrk_tc3_ms", ctypes.c_double), ("syrk_tc3_launches", ctypes.c_int),
+                ("t_potrf32_ms", ctypes.c_double), ("potrf32_launches", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

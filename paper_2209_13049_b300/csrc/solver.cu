@@ -146,11 +146,11 @@ struct lqmpc_ctx {
     int tc_ok = 0;              // tensor maps built
     void* d_maps = nullptr;     // 3 CUtensorMap (BF16, TF32, TF32 low part), 64-byte aligned, device
     cudaEvent_t ev[4];
-    cudaEvent_t evk[4];         // around the SYRK launch: tensor-core pair, CUDA-core pair
+    cudaEvent_t evk[6];         // around the SYRK launch (tensor-core pair, CUDA-core pair) and the FP32 factor
     bool events = false;
     // per-solve SYRK timing
-    double t_tc = 0, t_cc = 0, t_cc64 = 0;
-    int n_tc = 0, n_cc = 0, n_cc64 = 0;
+    double t_tc = 0, t_cc = 0, t_cc64 = 0, t_tc3 = 0, t_pf = 0;
+    int n_tc = 0, n_cc = 0, n_cc64 = 0, n_tc3 = 0, n_pf = 0;
     lqmpc::GraphCache* graphs = nullptr;   // single-instance solves (d_inst is fixed)
     bool lyap = false;                     // FP64 KKT matrix by the backward recursion
 };
@@ -431,6 +431,8 @@ void batch_dims(Batch& b) {
 // SYRK timing: the events of ctxs[0] bracket the SYRK launch itself.
 struct SyrkTimer {
     bool tc = false, cc = false, cc64 = false;   // cc64: the timed CUDA-core launch was FP64
+    bool tc3 = false;                            // the timed tensor-core launch was split TF32
+    bool pf = false;                             // an FP32 factorisation was timed
 };
 
 // Form and factor M in precision `prec` for the instances `sel` picks.
@@ -473,7 +475,9 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
                 launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.tc_splits, 2, 0, 0, 1, sel, nullptr, b.st,
                                    shift);
             }
+            rec(c0->evk[4]);
             launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0]);
+            rec(c0->evk[5]);
         }
     };
     // the timed and untimed sequences differ (event nodes): separate graphs
@@ -481,7 +485,8 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
     else body();
     if (tm) {
         if (prec == LQMPC_FP64 || (prec == LQMPC_FP32 && !b.d_maps)) { tm->cc = true; tm->cc64 = prec == LQMPC_FP64; }
-        else tm->tc = true;
+        else { tm->tc = true; tm->tc3 = prec == LQMPC_FP32; }
+        if (prec != LQMPC_FP64) tm->pf = true;
     }
 }
 
@@ -692,8 +697,8 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     b.ff = prec != LQMPC_FP64;
     if ((prec == LQMPC_MIXED_BF16 || prec == LQMPC_MIXED_TF32) && !b.d_maps) return LQMPC_ERR_UNSUPPORTED;
     lqmpc_ctx* c0 = b.ctxs[0];
-    c0->t_tc = c0->t_cc = c0->t_cc64 = 0.0;
-    c0->n_tc = c0->n_cc = c0->n_cc64 = 0;
+    c0->t_tc = c0->t_cc = c0->t_cc64 = c0->t_tc3 = c0->t_pf = 0.0;
+    c0->n_tc = c0->n_cc = c0->n_cc64 = c0->n_tc3 = c0->n_pf = 0;
     cudaEventRecord(c0->ev[0], b.st);
     prepare(b, o);
     {
@@ -737,7 +742,11 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         if (s != LQMPC_OK) return s;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]) == cudaSuccess) kkt_ms += ms;
-        if (tm.tc && cudaEventElapsedTime(&ms, c0->evk[0], c0->evk[1]) == cudaSuccess) { c0->t_tc += ms; c0->n_tc++; }
+        if (tm.tc && cudaEventElapsedTime(&ms, c0->evk[0], c0->evk[1]) == cudaSuccess) {
+            c0->t_tc += ms; c0->n_tc++;
+            if (tm.tc3) { c0->t_tc3 += ms; c0->n_tc3++; }
+        }
+        if (tm.pf && cudaEventElapsedTime(&ms, c0->evk[4], c0->evk[5]) == cudaSuccess) { c0->t_pf += ms; c0->n_pf++; }
         if (tm.cc && cudaEventElapsedTime(&ms, c0->evk[2], c0->evk[3]) == cudaSuccess) {
             c0->t_cc += ms; c0->n_cc++;
             if (tm.cc64) { c0->t_cc64 += ms; c0->n_cc64++; }
@@ -779,6 +788,10 @@ void fill_stats(lqmpc_ctx* c, lqmpc_stats* st, double t_total, double t_kkt) {
     st->syrk_cc_launches = c->n_cc;
     st->t_syrk_fp64_ms = c->t_cc64;
     st->syrk_fp64_launches = c->n_cc64;
+    st->t_syrk_tc3_ms = c->t_tc3;
+    st->syrk_tc3_launches = c->n_tc3;
+    st->t_potrf32_ms = c->t_pf;
+    st->potrf32_launches = c->n_pf;
 }
 
 lqmpc_status final_status(lqmpc_ctx* c) {
@@ -961,8 +974,8 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     layout<true>(I, ctx->arena, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits, nnzB, ctx->lyap);
     if (cudaMallocHost(&ctx->h_scal, sizeof(Scal)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     memset(ctx->h_scal, 0, sizeof(Scal));
-    for (int e = 0; e < 4; ++e)
-        if (cudaEventCreate(&ctx->ev[e]) != cudaSuccess || cudaEventCreate(&ctx->evk[e]) != cudaSuccess)
+    for (int e = 0; e < 6; ++e)
+        if ((e < 4 && cudaEventCreate(&ctx->ev[e]) != cudaSuccess) || cudaEventCreate(&ctx->evk[e]) != cudaSuccess)
             return fail(LQMPC_ERR_CUDA);
     ctx->events = true;
     cudaStream_t st = ctx->stream;
@@ -1271,8 +1284,8 @@ void lqmpc_free(lqmpc_ctx* ctx) {
     delete ctx->graphs;
     ctx->graphs = nullptr;
     if (ctx->events)
-        for (int e = 0; e < 4; ++e) {
-            cudaEventDestroy(ctx->ev[e]);
+        for (int e = 0; e < 6; ++e) {
+            if (e < 4) cudaEventDestroy(ctx->ev[e]);
             cudaEventDestroy(ctx->evk[e]);
         }
     cudaFree(ctx->arena);
