@@ -62,7 +62,7 @@ struct Scal {
     int prec_cur;       // KKT precision of this instance (escalates BF16/TF32 -> FP32 -> FP64, sticky)
     int kkt_pending;    // the current KKT solve of this instance is not settled yet
     int refine_budget;  // conjugate-gradient steps allowed for the current right-hand side
-    int pad;
+    int arrive;         // CTAs of the current launch that finished (last_arrival), 0 between launches
 };
 
 // Device descriptor of one instance (all pointers are device memory).
@@ -202,6 +202,23 @@ __device__ __forceinline__ double block_reduce(double v, double* smem32) {
         v = t;
     }
     return v;
+}
+
+// True in the one CTA of an instance that finishes last in this launch; it
+// then sees every other CTA's partial (written before its arrival) and
+// resets the counter for the next launch.  Every CTA of the instance must
+// call it (the launch predicates are uniform per instance).
+__device__ __forceinline__ bool last_arrival(Scal* S) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        last = atomicAdd(&S->arrive, 1) == (int)gridDim.x - 1;
+        if (last) atomicExch(&S->arrive, 0);
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }

@@ -64,8 +64,10 @@ bool potrf_cluster_fits(int max_n);
 // kernels_flow.cu (dataflow Cholesky with inverse, one instance, FP32)
 bool potrf_flow_fits(int count, int max_n);
 bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t st);
+// tail: 0 none; 1 / 2 also the conjugate-gradient direction from z = out
+// (p = z / p = z + beta p with r'z) in the same launch
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
-                       cudaStream_t st);
+                       cudaStream_t st, int tail = 0);
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,
                        int out_role, int force, cudaStream_t st);
 

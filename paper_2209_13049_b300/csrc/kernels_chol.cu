@@ -388,15 +388,25 @@ __global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int fl
     const float* XT = I.XinvT32;   // X' column-major: row i of X is contiguous
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
         const float* row = XT + (size_t)n * i;
-        float acc = 0.f;
-        for (int j = lane; j <= i; j += 32) acc = fmaf(row[j], (float)r[j], acc);
+        float a4[4] = {0.f, 0.f, 0.f, 0.f};   // independent chains: four loads in flight
+        int j = lane;
+        for (; j + 96 <= i; j += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a4[u] = fmaf(row[j + 32 * u], (float)r[j + 32 * u], a4[u]);
+        }
+        for (; j <= i; j += 32) a4[0] = fmaf(row[j], (float)r[j], a4[0]);
+        float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) I.r32[i] = acc;
     }
 }
 
-__global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags) {
+// tail (conjugate-gradient direction from z, run by the instance's last CTA):
+// 1 p = z and r'z; 2 beta = r'z_new / r'z_old, p = z + beta p.
+__global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags, int tail) {
+    __shared__ double red[32];
+    __shared__ double beta_sh;
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     double* z = role_ptr(I, out_role);
@@ -404,12 +414,30 @@ __global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int f
     const float* X = I.Xinv32;
     for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
         const float* col = X + (size_t)n * j;
-        float acc = 0.f;
-        for (int i = j + lane; i < n; i += 32) acc = fmaf(col[i], I.r32[i], acc);
+        float a4[4] = {0.f, 0.f, 0.f, 0.f};
+        int i = j + lane;
+        for (; i + 96 < n; i += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a4[u] = fmaf(col[i + 32 * u], I.r32[i + 32 * u], a4[u]);
+        }
+        for (; i < n; i += 32) a4[0] = fmaf(col[i], I.r32[i], a4[0]);
+        float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) z[j] = (double)acc;
     }
+    if (!tail || !last_arrival(I.sc)) return;
+    Scal* S = I.sc;
+    double rz = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) rz += I.rho[k] * __ldcg(z + k);
+    rz = block_reduce<0>(rz, red);
+    if (threadIdx.x == 0) {
+        beta_sh = (tail == 2 && S->pcg_rz != 0.0) ? rz / S->pcg_rz : 0.0;
+        S->pcg_rz = rz;
+    }
+    __syncthreads();
+    const double be = beta_sh;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) I.pp[k] = __ldcg(z + k) + (be != 0.0 ? be * I.pp[k] : 0.0);
 }
 
 // Solve L L' x = b for one right-hand side per instance (one CTA each).  The
@@ -593,12 +621,12 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
 }
 
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
-                       cudaStream_t st) {
-    int nb = (max_n + 7) / 8;
-    nb = nb > 1024 ? 1024 : nb;
-    LQ_LAUNCH(k_prec_lower<<<dim3(nb, count), 256, 0, st>>>(d_insts, in_role, flags));
-    nb = nb > 1024 ? 1024 : nb;
-    LQ_LAUNCH(k_prec_upper<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags));
+                       cudaStream_t st, int tail) {
+    // one warp per row (column), two warps per CTA: every SM takes part
+    int nb = (max_n + 1) / 2;
+    nb = nb > 8192 ? 8192 : nb;
+    LQ_LAUNCH(k_prec_lower<<<dim3(nb, count), 64, 0, st>>>(d_insts, in_role, flags));
+    LQ_LAUNCH(k_prec_upper<<<dim3(nb, count), 64, 0, st>>>(d_insts, out_role, flags, tail));
 }
 
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

@@ -481,12 +481,21 @@ __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, 
     for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < NV * n; q += gridDim.x * wpb) {
         const int vec = q / n, j = q % n, t = j / nu, c = j % nu;
         const int nd = N - t;
-        double s = 0.0;
-        for (int e = lane; e < splits * nd; e += 32) {
-            const int sp = e / nd, d = e % nd;
-            s += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
+        // four independent partial sums keep several L2 loads in flight per lane
+        double s4[4] = {0.0, 0.0, 0.0, 0.0};
+        int e = lane;
+        for (; e + 96 < splits * nd; e += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int eu = e + 32 * u, sp = eu / nd, d = eu % nd;
+                s4[u] += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
+            }
         }
-        s = warp_sum(s);
+        for (; e < splits * nd; e += 32) {
+            const int sp = e / nd, d = e % nd;
+            s4[0] += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
+        }
+        double s = warp_sum((s4[0] + s4[1]) + (s4[2] + s4[3]));
         if (lane == 0) (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
     }
 }
@@ -609,17 +618,17 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
     const int NV = w1_role != R_NONE ? 2 : 1;
     const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
     const int splits = ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
-    int nb = (NV * max_n + 7) / 8;
-    nb = nb > 4096 ? 4096 : nb;
+    int nb = (NV * max_n + 1) / 2;   // two warps (two outputs) per CTA: every SM takes part
+    nb = nb > 8192 ? 8192 : nb;
     int npre = (max_ns * max_N + 255) / 256;
     npre = npre > 4096 ? 4096 : npre;
     LQ_LAUNCH(k_ff_prep_w<<<dim3(npre, count), 256, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
     if (NV == 2) {
         LQ_LAUNCH(k_gamma_tmv_ff<2><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags, splits));
-        LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 256, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));
+        LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));
     } else {
         LQ_LAUNCH(k_gamma_tmv_ff<1><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags, splits));
-        LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 256, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
+        LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
     }
 }
 

@@ -45,7 +45,11 @@ __global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_
 
 // out_j = (H v)_j + mv_j + sigu_j v_j with mv = Gamma'(Sigma_x Gamma v); one
 // warp per row.  mode 0 (initial residual): r = b - M du, partial max|r| in
-// slot 6.  mode 1 (CG step): q = M p, partial p'q in slot 6.
+// slot 6, and the last CTA runs the convergence test.  mode 1 (CG step):
+// q = M p, partial p'q in slot 6, and the last CTA forms alpha.
+__device__ void pcg_test(const Inst& I, double rn);
+__device__ void pcg_alpha(const Inst& I, double pq);
+
 __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
@@ -72,6 +76,17 @@ __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) 
     }
     double t = mode == 0 ? block_reduce<1>(acc_red, red) : block_reduce<0>(acc_red, red);
     if (threadIdx.x == 0) I.part[6 * kMaxParts + blockIdx.x] = t;
+    if (!last_arrival(I.sc)) return;
+    double m = 0.0;
+    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) {
+        const double v = __ldcg(I.part + 6 * kMaxParts + p);
+        m = mode == 0 ? fmax(m, v) : m + v;
+    }
+    m = mode == 0 ? block_reduce<1>(m, red) : block_reduce<0>(m, red);
+    if (threadIdx.x == 0) {
+        if (mode == 0) pcg_test(I, m);
+        else pcg_alpha(I, m);
+    }
 }
 
 // Convergence test on the residual norm.
@@ -82,16 +97,6 @@ __device__ void pcg_test(const Inst& I, double rn) {
     const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
     if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || S->rnorm0 == 0.0) S->refine_ok = 1;
     else if (S->refine_cur >= S->refine_budget) S->refine_fail = 1;
-}
-
-__global__ void k_pcg_check(const Inst* __restrict__ insts, int nb, int slot, int sel) {
-    __shared__ double red[32];
-    const Inst& I = insts[blockIdx.y];
-    if (pcg_skip(I, sel)) return;
-    double m = 0.0;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) m = fmax(m, I.part[slot * kMaxParts + p]);
-    m = block_reduce<1>(m, red);
-    if (threadIdx.x == 0) pcg_test(I, m);
 }
 
 // p = z, rz = r'z (one block per instance).
@@ -109,23 +114,15 @@ __global__ void k_pcg_pinit(const Inst* __restrict__ insts, int sel) {
 }
 
 // alpha = r'z / p'Mp; a non-positive curvature marks failure.
-__global__ void k_pcg_alpha(const Inst* __restrict__ insts, int nb, int sel) {
-    __shared__ double red[32];
-    const Inst& I = insts[blockIdx.y];
+__device__ void pcg_alpha(const Inst& I, double pq) {
     Scal* S = I.sc;
-    if (pcg_skip(I, sel)) return;
-    double s = 0.0;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) s += I.part[6 * kMaxParts + p];
-    s = block_reduce<0>(s, red);
-    if (threadIdx.x == 0) {
-        if (!(s > 0.0) || !(S->pcg_rz == S->pcg_rz)) { S->refine_fail = 1; return; }
-        S->pcg_alpha = S->pcg_rz / s;
-        S->refine_cur += 1; S->refine_steps += 1; S->refine_iter += 1;
-    }
+    if (!(pq > 0.0) || !(S->pcg_rz == S->pcg_rz)) { S->refine_fail = 1; return; }
+    S->pcg_alpha = S->pcg_rz / pq;
+    S->refine_cur += 1; S->refine_steps += 1; S->refine_iter += 1;
 }
 
 // du += alpha p, r -= alpha q (input rows), dxs += alpha (Gamma p) (state
-// rows).  Partial max|r| in slot 7.
+// rows).  Partial max|r| in slot 7; the last CTA runs the convergence test.
 __global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
@@ -146,6 +143,11 @@ __global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
     }
     double v = block_reduce<1>(rmax, red);
     if (threadIdx.x == 0) I.part[7 * kMaxParts + blockIdx.x] = v;
+    if (!last_arrival(I.sc)) return;
+    double m = 0.0;
+    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) m = fmax(m, __ldcg(I.part + 7 * kMaxParts + p));
+    m = block_reduce<1>(m, red);
+    if (threadIdx.x == 0) pcg_test(I, m);
 }
 
 // beta = r'z_new / r'z_old; p = z + beta p (one block per instance).
@@ -218,8 +220,6 @@ void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int 
     int wpb = 8;
     int nb = nblk(max_n, wpb, kMaxParts);
     LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel));
-    if (mode == 0) LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 6, sel));
-    else LQ_LAUNCH(k_pcg_alpha<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, sel));
 }
 
 void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) {
@@ -229,7 +229,6 @@ void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) 
 void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st) {
     int nb = nblk(max_total, 256, kMaxParts);
     LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts, sel));
-    LQ_LAUNCH(k_pcg_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, 7, sel));
 }
 
 void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st) {

@@ -525,9 +525,16 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     const int selr = sel | F_SKIP_REFINED;
     // preconditioner P^{-1}: the FP32 explicit inverse of the low-precision
     // factor, or (prec64) the FP64 triangular solves
-    auto prec = [&](int in, int out, int flags) {
-        if (prec64) launch_chol_solve(b.d_insts, b.count, b.max_n, 1, in, out, flags, b.st);
-        else launch_prec_apply(b.d_insts, b.count, b.max_n, in, out, flags, b.st);
+    // (tail 1 / 2: then the new direction p from z = P^{-1} r, fused into the
+    // FP32 preconditioner's last launch)
+    auto prec = [&](int in, int out, int flags, int tail = 0) {
+        if (prec64) {
+            launch_chol_solve(b.d_insts, b.count, b.max_n, 1, in, out, flags, b.st);
+            if (tail == 1) launch_pcg_pinit(b.d_insts, b.count, sel, b.st);
+            if (tail == 2) launch_pcg_beta(b.d_insts, b.count, sel, b.st);
+        } else {
+            launch_prec_apply(b.d_insts, b.count, b.max_n, in, out, flags, b.st, tail);
+        }
     };
     const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
     seg_run(b, SEG_PCG0 + kp, [&]() {
@@ -538,8 +545,7 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, sel, b.st);
         launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, sel, b.st);
-        prec(R_RHO, R_DCORR, selr);
-        launch_pcg_pinit(b.d_insts, b.count, sel, b.st);
+        prec(R_RHO, R_DCORR, selr, 1);
     });
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
     // the new direction (harmless after the last step: every kernel is
@@ -550,8 +556,7 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, sel, b.st);
         launch_pcg_step_update(b.d_insts, b.count, b.max_total, sel, b.st);
         if (!with_next) return;
-        prec(R_RHO, R_DCORR, selr);
-        launch_pcg_beta(b.d_insts, b.count, sel, b.st);
+        prec(R_RHO, R_DCORR, selr, 2);
     };
     // The host looks at the flags after every second step and stops launching
     // once every unfinished instance has converged or failed.
