@@ -7,7 +7,8 @@
 // X_q* = R_q* / l_qq, R_i* -= l_iq X_q* (i > q).  The FP32 version takes
 // 1/sqrt(d) from rsqrtf refined by one Newton step (about one ulp: the
 // factor is a preconditioner) and reuses those reciprocals in the
-// substitution, so the serial chain has no division.
+// substitution (row q scaled by its own lane before it is broadcast), so the
+// serial chain has no division.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,7 +26,7 @@ __device__ __forceinline__ float rsqrt_refined(float d) {
 __device__ __forceinline__ int diag_factor_inverse(float (&a)[32], float (&x)[32]) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    float rdiag[32];
+    float myr = 1.f;                     // 1 / l_{lane, lane}
     int fail = 0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) if (c > lane) a[c] = 0.f;
@@ -34,7 +35,7 @@ __device__ __forceinline__ int diag_factor_inverse(float (&a)[32], float (&x)[32
         const float dqq = __shfl_sync(full, a[q], q);
         if (!(dqq > 0.f) && !fail) fail = q + 1;
         const float r = rsqrt_refined(fail ? 1.f : dqq);
-        rdiag[q] = r;
+        if (lane == q) myr = r;
         const float liq = lane > q ? a[q] * r : (lane == q ? dqq * r : 0.f);
         a[q] = liq;
 #pragma unroll
@@ -48,11 +49,13 @@ __device__ __forceinline__ int diag_factor_inverse(float (&a)[32], float (&x)[32
 #pragma unroll
     for (int q = 0; q < 32; ++q) {
         const float liq = a[q];          // l_{lane, q}
+        // row q of X is final once scaled by 1 / l_qq; the rows below take it off
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            if (c > q) break;
-            const float xqc = __shfl_sync(full, x[c], q) * rdiag[q];
-            x[c] = lane == q ? xqc : (lane > q ? fmaf(-liq, xqc, x[c]) : x[c]);
+        for (int c = 0; c <= q; ++c) if (lane == q) x[c] *= myr;
+#pragma unroll
+        for (int c = 0; c <= q; ++c) {
+            const float xqc = __shfl_sync(full, x[c], q);
+            if (lane > q) x[c] = fmaf(-liq, xqc, x[c]);
         }
     }
     return fail;

@@ -2,22 +2,26 @@
 // preconditioner of the mixed-precision solves, Eq. 7's M = L L') for one
 // instance of n <= 544, one CTA per 32-wide block column.
 //
-// CTA j keeps its block column (rows 32j..n-1) in shared memory and is
-// left-looking: it subtracts L_{:,k} L_{j,k}' for every earlier block column
-// k as soon as CTA k has published it, factors its diagonal block in
-// registers, solves the rows below by the inverse of that block, and
-// publishes the column.  Then it forms block column j of X = L^{-1} by
-// forward substitution down the column, X_pj = -L_pp^{-1} sum_{k=j}^{p-1}
-// L_pk X_kj, consuming block columns p > j as they appear (L_pp^{-1} is
-// published in X's diagonal block).  No grid-wide barrier: the critical path
-// is one diagonal factorisation per block column plus its last update.
+// CTA j computes block column j of L one 32 x 32 row block p = j, j+1, ...
+// at a time: L_pj = (A_pj - sum_{k<j} L_pk L_jk') L_jj^{-T}, the diagonal
+// block factored and inverted in registers.  Every row block is published on
+// its own (flag (j, p)), so CTA j+1 can factor its diagonal block as soon as
+// L_{j+1,j} is out, while CTA j is still working down its column: the
+// critical path is one diagonal factorisation plus two row blocks per block
+// column.  Then CTA j forms block column j of X = L^{-1} by forward
+// substitution down the column, X_pj = -X_pp sum_{k=j}^{p-1} L_pk X_kj,
+// consuming row blocks as they appear (X_pp = L_pp^{-1} comes with flag (p, p)).
+// The products sum over 32 k-columns per warp step in FP32 (the
+// contraction is split over the eight warps and reduced in shared memory).
 //
-// Publication: a block column is written with L2-coherent stores, fenced,
-// then its flag is set to the launch's epoch; readers poll the flag (bounded:
-// a wait that gives up raises Scal::err bit 4 and the kernel still runs to
-// its end) and read with L1-bypassing loads.  The epoch advances when the
-// last CTA finishes, so flags never need clearing.  A non-positive pivot is
+// Publication: a row block is written with L2-coherent stores, fenced, then
+// its flag is set to the launch's epoch; readers poll the flags (bounded: a
+// wait that gives up raises Scal::err bit 4 and the kernel still runs to its
+// end) and read with L1-bypassing loads.  The epoch advances when the last
+// CTA finishes, so flags never need clearing.  A non-positive pivot is
 // recorded in Scal::info; every CTA still publishes, so nobody waits forever.
+#include <algorithm>
+
 #include "chol_diag.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -27,7 +31,7 @@ namespace lqmpc {
 namespace {
 
 constexpr int kFb = 32;
-constexpr int kFlowMaxN = 544;          // three [32 x rows] FP32 panels fit shared memory
+constexpr int kFlowMaxN = 544;          // 17 block columns: the panels fit shared memory, 2 + 17^2 flags
 constexpr uint32_t kFlowSpin = 1u << 22;
 
 __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile int*)p; }
@@ -42,41 +46,102 @@ __device__ __forceinline__ void cpa_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
-// Rows [row0, row0 + rows) of `cols` consecutive columns starting at column
-// col0 of the column-major n x n matrix M into dst[c * ld + r] (zeros for
-// r in [rows, ld)).  Vector copies when every column start is 16-byte
-// aligned (n and row0 multiples of 4), scalar L2 loads otherwise.
-__device__ void stage_cols(float* dst, int ld, const float* M, int n, int row0, int rows, int col0, int cols,
-                           bool vec) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+// Rows [32p, 32p + pr) of the global columns [mm0, mm1) of the column-major
+// n x n matrix M into P[(mm - mmb) * 32 + r] (zeros for r >= pr): 16-byte
+// copies when every column start is 16-byte aligned (n a multiple of 4),
+// scalar L2 loads otherwise.  The copies are waited for by cpa_wait_all.
+__device__ __forceinline__ void stage_rowblock(float* P, int mmb, const float* M, int n, int p, int pr, int mm0, int mm1,
+                               bool vec) {
     if (vec) {
-        const int q4 = ld / 4;
-        for (int e = threadIdx.x; e < cols * q4; e += blockDim.x) {
-            const int c = e / q4, r = 4 * (e % q4);
-            const int left = rows - r;
+        for (int e = threadIdx.x; e < (mm1 - mm0) * 8; e += blockDim.x) {
+            const int mm = mm0 + e / 8, r = 4 * (e % 8);
+            const int left = pr - r;
             const int bytes = left >= 4 ? 16 : (left > 0 ? 4 * left : 0);
-            const float* src = M + (size_t)n * (col0 + c) + row0 + (left > 0 ? r : 0);
-            cpa16(dst + (size_t)c * ld + r, src, bytes);
+            cpa16(P + (mm - mmb) * kFb + r, M + (size_t)n * mm + kFb * p + (left > 0 ? r : 0), bytes);
         }
-        cpa_wait_all();
     } else {
-        for (int c = warp; c < cols; c += nw)
-            for (int r = lane; r < ld; r += 32) dst[(size_t)c * ld + r] = r < rows ? __ldcg(M + (size_t)n * (col0 + c) + row0 + r) : 0.f;
+        for (int e = threadIdx.x; e < (mm1 - mm0) * kFb; e += blockDim.x) {
+            const int mm = mm0 + e / kFb, r = e % kFb;
+            P[(mm - mmb) * kFb + r] = r < pr ? __ldcg(M + (size_t)n * mm + kFb * p + r) : 0.f;
+        }
     }
 }
 
-// Thread 0 waits for flag == ep (bounded), then the block proceeds.
-__device__ void flow_wait(const int* flag, int ep, int* err) {
-    if (threadIdx.x == 0) {
+// Warp 0 waits until the flags (k, p) for k in [k0, k1), and flag index
+// `extra` when >= 0, all equal ep (one flag per lane, bounded), then the
+// block proceeds.
+__device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k1, int p, int extra, int ep, int* err) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, cnt = k1 - k0;
+        int idx = -1;
+        if (lane < cnt) idx = (k0 + lane) * nt + p;
+        else if (lane == cnt && extra >= 0) idx = extra;
+        bool ok = idx < 0 || ld_flag(flg + idx) == ep;
         uint32_t it = 0;
-        // after one wait has given up anywhere, later waits do not spin
-        while (ld_flag(flag) != ep && !(ld_flag(err) & 4)) {
-            if (++it > kFlowSpin) { atomicOr(err, 4); break; }
+        while (!__all_sync(0xffffffffu, ok)) {
+            // give up after the bound, or at once after a wait anywhere gave up
+            int stop = 0;
+            if (lane == 0) stop = (++it > kFlowSpin) || (ld_flag(err) & 4);
+            if (__shfl_sync(0xffffffffu, stop, 0)) {
+                if (lane == 0) atomicOr(err, 4);
+                break;
+            }
             __nanosleep(64);
+            if (!ok) ok = ld_flag(flg + idx) == ep;
         }
         __threadfence();
     }
     __syncthreads();
+}
+
+// acc[c] += sum_m P[m * 32 + lane] B[m * 32 + c] over m in [m0, m1), warp w
+// taking m = m0 + w, m0 + w + 8, ... (partial sums per warp).
+__device__ __forceinline__ void acc_panel(float (&acc)[kFb], const float* P, const float* B, int m0, int m1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = m0 + warp; m < m1; m += 8) {
+        const float a = P[m * kFb + lane];
+        const float4* b4 = reinterpret_cast<const float4*>(B + m * kFb);
+#pragma unroll
+        for (int q = 0; q < kFb / 4; ++q) {
+            const float4 b = b4[q];
+            acc[4 * q + 0] = fmaf(a, b.x, acc[4 * q + 0]);
+            acc[4 * q + 1] = fmaf(a, b.y, acc[4 * q + 1]);
+            acc[4 * q + 2] = fmaf(a, b.z, acc[4 * q + 2]);
+            acc[4 * q + 3] = fmaf(a, b.w, acc[4 * q + 3]);
+        }
+    }
+}
+
+// Red[w][r][c] = warp w's partial (lane r); read back by reduce_into.
+__device__ __forceinline__ void store_partial(const float (&acc)[kFb], float* Red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* R = Red + (warp * kFb + lane) * (kFb + 1);
+#pragma unroll
+    for (int c = 0; c < kFb; ++c) R[c] = acc[c];
+}
+
+__device__ __forceinline__ float sum_partials(const float* Red, int r, int c) {
+    float s = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += Red[(w * kFb + r) * (kFb + 1) + c];
+    return s;
+}
+
+// Warp 0: T (32 x 33, shared) -> L (D) and L^{-1} (Dv), lower, zeros above.
+// Not inlined, so the factorisation's registers are allocated apart from the
+// kernel's.
+__device__ __noinline__ int factor_diag_block(const float* T, float* D, float* Dv) {
+    const int lane = threadIdx.x & 31;
+    float a[kFb], x[kFb];
+#pragma unroll
+    for (int c = 0; c < kFb; ++c) a[c] = T[lane * (kFb + 1) + c];
+    const int fail = diag_factor_inverse(a, x);
+#pragma unroll
+    for (int c = 0; c < kFb; ++c) {
+        D[lane * (kFb + 1) + c] = c <= lane ? a[c] : 0.f;
+        Dv[lane * (kFb + 1) + c] = c <= lane ? x[c] : 0.f;
+    }
+    return fail;
 }
 
 }  // namespace
@@ -85,10 +150,10 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     const Inst& I = insts[0];
     if (skip_instance(I, flags)) return;           // the same decision in every CTA
     extern __shared__ __align__(16) float fsm[];
-    __shared__ float D[kFb][kFb + 1], Dv[kFb][kFb + 1], Tt[kFb][kFb + 1];
+    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1];
     __shared__ int ep_sh;
     const int n = I.n, nt = (n + kFb - 1) / kFb, j = blockIdx.x;
-    int* epoch = I.pflags;        // [0] epoch, [1] finished CTAs, [2 + k] flag of block column k
+    int* epoch = I.pflags;        // [0] epoch, [1] finished CTAs, [2 + k nt + p] flag of row block p of column k
     int* done = I.pflags + 1;
     int* flg = I.pflags + 2;
     int* err = &I.sc->err;
@@ -97,151 +162,148 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     __syncthreads();
     const int ep = ep_sh;
     if (j >= nt) return;
-    const int r0 = kFb * j, R = n - r0, Rp = (R + kFb - 1) / kFb * kFb;
-    const int kn = min(kFb, R);                    // columns of this block column
-    float* Ps = fsm;                               // [32 cols][Rp rows]
-    float* Ls = Ps + (size_t)kFb * Rp;             // staging
-    float* Xs = Ls + (size_t)kFb * Rp;             // block column j of X
+    const int r0 = kFb * j, kn = min(kFb, n - r0);   // columns of this block column
+    const int capP = max(j, nt - 1 - j);
+    float* Rj = fsm;                                 // row block j of columns 0..r0-1: Rj[m * 32 + r] = L[r0 + r, m]
+    float* Pn = Rj + kFb * kFb * j;                  // row block p of earlier columns, same layout
+    float* Xs = Pn + kFb * kFb * capP;               // X[r0 + q, r0 + c] at Xs[q * 32 + c]
+    float* As = Xs + kFb * kFb * (nt - j);           // A_pj, column-major
+    float* Red = As + kFb * kFb;                     // [8 warps][32][33] partial sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // own block column, padded with the identity beyond n
     const bool vec = (n % 4) == 0;
-    stage_cols(Ps, Rp, M, n, r0, R, r0, kn, vec);
-    for (int c = kn + warp; c < kFb; c += 8)          // identity columns of a ragged last block column
-        for (int r = lane; r < Rp; r += 32) Ps[c * Rp + r] = r == c ? 1.f : 0.f;
-    __syncthreads();
 
-    // left-looking updates: A_{:,j} -= L_{:,k} L_{j,k}'  (rows r0.. of block column k)
-    for (int k = 0; k < j; ++k) {
-        flow_wait(flg + k, ep, err);
-        stage_cols(Ls, Rp, M, n, r0, R, kFb * k, kFb, vec);
+    for (int p = j; p < nt; ++p) {
+        const int p0 = kFb * p, pr = min(kFb, n - p0);
+        float* P = p == j ? Rj : Pn;
+        // own block A_pj (written by nobody else)
+        if (vec) {
+            for (int e = threadIdx.x; e < kFb * 8; e += blockDim.x) {
+                const int c = e / 8, r = 4 * (e % 8), left = pr - r;
+                if (c < kn) cpa16(As + c * kFb + r, M + (size_t)n * (r0 + c) + p0 + (left > 0 ? r : 0),
+                                  left >= 4 ? 16 : (left > 0 ? 4 * left : 0));
+                else *reinterpret_cast<float4*>(As + c * kFb + r) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+                const int c = e / kFb, r = e % kFb;
+                As[c * kFb + r] = (c < kn && r < pr) ? M[(size_t)n * (r0 + c) + p0 + r] : 0.f;
+            }
+        }
+        // S = sum_{k<j} L_pk L_jk'; for the diagonal block the last column's
+        // contribution comes last (it is the latest to be published)
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 0) {
+            const int kA = p == j ? j - 1 : j;
+            if (kA > 0) {
+                wait_flags(flg, nt, 0, kA, p, -1, ep, err);
+                stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
+                cpa_wait_all();
+                __syncthreads();
+                acc_panel(acc, P, Rj, 0, kFb * kA);
+            }
+            if (kA < j) {
+                wait_flags(flg, nt, j - 1, j, p, -1, ep, err);
+                stage_rowblock(P, 0, M, n, p, pr, kFb * (j - 1), kFb * j, vec);
+                cpa_wait_all();
+                __syncthreads();
+                acc_panel(acc, P, Rj, kFb * (j - 1), kFb * j);
+            }
+        }
+        cpa_wait_all();
+        store_partial(acc, Red);
         __syncthreads();
-        // Ps[c][r] -= sum_m Ls[m][r] Ls[m][c]; lane -> row, warp -> 4 columns
-        for (int rb = 0; rb < Rp; rb += kFb) {
-            const int r = rb + lane;
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            float v = As[c * kFb + r] - sum_partials(Red, r, c);
+            if (p == j && r == c && r >= kn) v = 1.f;     // identity padding of a ragged last block
+            T[r][c] = v;
+        }
+        __syncthreads();
+        if (p == j) {
+            // diagonal block: factor and invert in registers (warp 0, row i in lane i)
+            if (warp == 0) {
+                const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
+                if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
+            }
+            __syncthreads();
+            // publish L_jj and X_jj = L_jj^{-1}; X_jj is block 0 of Xs
+            for (int c = warp; c < kn; c += 8) {
+                if (lane < kn && lane >= c) {
+                    __stcg(M + (size_t)n * (r0 + c) + r0 + lane, D[lane][c]);
+                    const float xv = Dv[lane][c];
+                    __stcg(I.Xinv32 + (size_t)(r0 + lane) + (size_t)n * (r0 + c), xv);
+                    __stcg(I.XinvT32 + (size_t)(r0 + c) + (size_t)n * (r0 + lane), xv);
+                }
+            }
+            for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) Xs[e] = Dv[e >> 5][e & 31];
+        } else {
+            // L_pj = T X_jj': lane -> row, warp -> 4 columns
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
             for (int m = 0; m < kFb; ++m) {
-                const float a = Ls[m * Rp + r];
+                const float t = T[lane][m];
 #pragma unroll
-                for (int t = 0; t < 4; ++t) acc[t] = fmaf(a, Ls[m * Rp + warp + 8 * t], acc[t]);
+                for (int q = 0; q < 4; ++q) o[q] = fmaf(t, Dv[warp + 8 * q][m], o[q]);
             }
+            if (lane < pr) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t) Ps[(warp + 8 * t) * Rp + r] -= acc[t];
+                for (int q = 0; q < 4; ++q) {
+                    const int c = warp + 8 * q;
+                    if (c < kn) __stcg(M + (size_t)n * (r0 + c) + p0 + lane, o[q]);
+                }
+            }
+        }
+        __threadfence();   // every writer's stores before the flag
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(flg + j * nt + p, ep);
+        }
+    }
+
+    // block column j of X: X_pj = -X_pp sum_{k=j}^{p-1} L_pk X_kj
+    for (int p = j + 1; p < nt; ++p) {
+        const int p0 = kFb * p, pr = min(kFb, n - p0);
+        wait_flags(flg, nt, j + 1, p, p, p * nt + p, ep, err);
+        stage_rowblock(Pn, r0, M, n, p, pr, r0, p0, vec);
+        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+            const int r = e / kFb, c = e % kFb;   // X_pp[r][c]
+            D[r][c] = (r < pr && c <= r) ? __ldcg(I.Xinv32 + (size_t)(p0 + r) + (size_t)n * (p0 + c)) : 0.f;
+        }
+        cpa_wait_all();
+        __syncthreads();
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        acc_panel(acc, Pn, Xs, 0, p0 - r0);
+        store_partial(acc, Red);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            T[r][c] = sum_partials(Red, r, c);
         }
         __syncthreads();
-    }
-
-    // diagonal block: factor and invert in registers (warp 0, row i in lane i)
-    if (warp == 0) {
-        float a[kFb], x[kFb];
-#pragma unroll
-        for (int c = 0; c < kFb; ++c) a[c] = Ps[c * Rp + lane];
-        const int fail = diag_factor_inverse(a, x);
-#pragma unroll
-        for (int c = 0; c < kFb; ++c) {
-            D[lane][c] = c <= lane ? a[c] : 0.f;
-            Dv[lane][c] = c <= lane ? x[c] : 0.f;
-        }
-        if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
-    }
-    __syncthreads();
-
-    // rows below the diagonal block: L_pj = A_pj D^{-T}, into Ls (free now);
-    // the diagonal block L_jj goes to Ls as well, so Ls holds the column
-    for (int rb = kFb; rb < Rp; rb += kFb) {
-        const int r = rb + lane;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        // X_pj = -X_pp T: lane -> column, warp -> 4 rows
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
         for (int m = 0; m < kFb; ++m) {
-            const float a = Ps[m * Rp + r];
+            const float t = T[m][lane];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[t] = fmaf(a, Dv[warp + 8 * t][m], acc[t]);
+            for (int q = 0; q < 4; ++q) o[q] = fmaf(D[warp + 8 * q][m], t, o[q]);
         }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) Ls[(warp + 8 * t) * Rp + r] = acc[t];
-    }
-    for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
-        const int c = e / kFb, r = e % kFb;
-        Ls[c * Rp + r] = D[r][c];
-        Xs[c * Rp + r] = Dv[r][c];
-    }
-    __syncthreads();
-
-    // publish block column j of L and L_jj^{-1} (X's diagonal block)
-    for (int c = warp; c < kn; c += 8) {
-        float* dst = M + (size_t)n * (r0 + c) + r0;
-#pragma unroll 4
-        for (int r = lane; r < R; r += 32)
-            if (r >= c) __stcg(dst + r, Ls[c * Rp + r]);
-        if (lane < kn && lane >= c) {
-            const float xv = Xs[c * Rp + lane];
-            __stcg(I.Xinv32 + (size_t)(r0 + lane) + (size_t)n * (r0 + c), xv);
-            __stcg(I.XinvT32 + (size_t)(r0 + c) + (size_t)n * (r0 + lane), xv);
-        }
-    }
-    __threadfence();   // every writer's stores before the flag
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicExch(flg + j, ep);
-    }
-
-    // block column j of X: X_pj = -L_pp^{-1} sum_{k=j}^{p-1} L_pk X_kj
-    for (int p = j + 1; p < nt; ++p) {
-        flow_wait(flg + p, ep, err);
-        const int p0 = kFb * p, pr = min(kFb, n - p0);
-        const int K = p0 - r0;                       // columns r0 .. p0-1 of row block p
-        // Ls[q * 32 + i] = L[p0 + i, r0 + q]
-        {
-            const bool v2 = vec && pr == kFb;
-            if (v2) {
-                for (int e = threadIdx.x; e < K * (kFb / 4); e += blockDim.x) {
-                    const int q = e / (kFb / 4), i = 4 * (e % (kFb / 4));
-                    cpa16(Ls + q * kFb + i, M + (size_t)(p0 + i) + (size_t)n * (r0 + q), 16);
-                }
-                cpa_wait_all();
-            } else {
-                for (int q = warp; q < K; q += 8)
-                    Ls[q * kFb + lane] = lane < pr ? __ldcg(M + (size_t)(p0 + lane) + (size_t)n * (r0 + q)) : 0.f;
+        for (int q = 0; q < 4; ++q) {
+            const int r = warp + 8 * q;
+            Xs[(p0 - r0 + r) * kFb + lane] = -o[q];
+            if (r < pr && lane < kn) {
+                I.Xinv32[(size_t)(p0 + r) + (size_t)n * (r0 + lane)] = -o[q];
+                I.XinvT32[(size_t)(r0 + lane) + (size_t)n * (p0 + r)] = -o[q];
             }
-        }
-        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
-            const int r = e / kFb, c = e % kFb;   // L_pp^{-1}[r][c]
-            D[r][c] = (r < pr && c < pr && c <= r) ? __ldcg(I.Xinv32 + (size_t)(p0 + r) + (size_t)n * (p0 + c)) : 0.f;
-        }
-        __syncthreads();
-        {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int q = 0; q < K; ++q) {
-                const float a = Ls[q * kFb + lane];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) acc[t] = fmaf(a, Xs[(warp + 8 * t) * Rp + q], acc[t]);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) Tt[lane][warp + 8 * t] = acc[t];
-        }
-        __syncthreads();
-        {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-            for (int m = 0; m < kFb; ++m) {
-                const float dv = D[lane][m];
-#pragma unroll
-                for (int t = 0; t < 4; ++t) acc[t] = fmaf(dv, Tt[m][warp + 8 * t], acc[t]);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) Xs[(warp + 8 * t) * Rp + (p0 - r0) + lane] = -acc[t];
         }
         __syncthreads();
     }
-    // X below the diagonal block of column j (the diagonal block is already out)
-    for (int c = warp; c < kn; c += 8)
-        for (int r = kFb + lane; r < R; r += 32) {
-            const float xv = Xs[c * Rp + r];
-            I.Xinv32[(size_t)(r0 + r) + (size_t)n * (r0 + c)] = xv;
-            I.XinvT32[(size_t)(r0 + c) + (size_t)n * (r0 + r)] = xv;
-        }
     // the last CTA to finish advances the epoch (every CTA has read it by then)
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -258,8 +320,10 @@ bool potrf_flow_fits(int count, int max_n) { return count == 1 && max_n >= 1 && 
 
 bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t st) {
     const int nt = (max_n + kFb - 1) / kFb;
-    const int Rp = nt * kFb;
-    const size_t smem = 3 * sizeof(float) * kFb * (size_t)Rp;
+    // per CTA j: j + max(j, nt-1-j) + (nt-j) + 1 blocks of 32 x 32, plus the partial sums
+    int blocks = 0;
+    for (int j = 0; j < nt; ++j) blocks = std::max(blocks, nt + std::max(j, nt - 1 - j) + 1);
+    const size_t smem = sizeof(float) * ((size_t)blocks * kFb * kFb + 8 * kFb * (kFb + 1));
     cudaFuncSetAttribute(k_potrf_flow, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     void* args[] = {(void*)&d_insts, (void*)&flags};
     cudaEvent_t pe = prof_start(st);

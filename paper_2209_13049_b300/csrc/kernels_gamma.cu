@@ -339,6 +339,7 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
     double* out = role_ptr(I, out_role);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
         double s = 0.0;
+#pragma unroll 4
         for (int q = 0; q < splits; ++q) s += I.gpart[(size_t)q * I.SX + k];
         out[k] = s;
     }
@@ -458,19 +459,25 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         }
         __syncthreads();
     }
-    // partial[split][r'][col]
+    // partial[split] skewed along the anti-diagonals Gamma' sums: P[col, r']
+    // with col = (N-1-d) nu + c and r' = vec N + r goes to [vec][t][c][d],
+    // t = r - d, so the terms of one output are contiguous; t < 0 is not used
     double* part = I.gpart + (size_t)split * NR * n;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int col = c0 + ty + 16 * a, rp = rp0 + tx + 8 * b;
-            if (col < n && rp < NR) part[(size_t)rp * n + col] = (double)sh[a][b] + (double)sl[a][b];
+            if (col < n && rp < NR) {
+                const int vec = rp / N, r = rp % N, d = N - 1 - col / nu, c = col % nu, t = r - d;
+                if (t >= 0) part[(((size_t)vec * N + t) * nu + c) * N + d] = (double)sh[a][b] + (double)sl[a][b];
+            }
         }
 }
 
 // out[t nu + c] = sum_split sum_{d=0}^{N-1-t} P[(N-1-d) nu + c, t + d]; one
-// warp per output, lanes over (split, d), then a fixed-order warp reduction.
+// warp per output, lanes over the contiguous d run of each split, then a
+// fixed-order warp reduction.
 template <int NV>
 __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags,
                                    int splits) {
@@ -481,21 +488,16 @@ __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, 
     for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < NV * n; q += gridDim.x * wpb) {
         const int vec = q / n, j = q % n, t = j / nu, c = j % nu;
         const int nd = N - t;
-        // four independent partial sums keep several L2 loads in flight per lane
-        double s4[4] = {0.0, 0.0, 0.0, 0.0};
-        int e = lane;
-        for (; e + 96 < splits * nd; e += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int eu = e + 32 * u, sp = eu / nd, d = eu % nd;
-                s4[u] += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
-            }
+        const double* base = I.gpart + (((size_t)vec * N + t) * nu + c) * N;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll 4
+        for (int sp = 0; sp < splits; ++sp) {
+            const double* src = base + (size_t)sp * NR * n;
+            if (lane < nd) s0 += src[lane];
+            if (lane + 32 < nd) s1 += src[lane + 32];
+            for (int d = lane + 64; d < nd; d += 32) s0 += src[d];
         }
-        for (; e < splits * nd; e += 32) {
-            const int sp = e / nd, d = e % nd;
-            s4[0] += I.gpart[(size_t)sp * NR * n + (size_t)(vec * N + t + d) * n + (N - 1 - d) * nu + c];
-        }
-        double s = warp_sum((s4[0] + s4[1]) + (s4[2] + s4[3]));
+        double s = warp_sum(s0 + s1);
         if (lane == 0) (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
     }
 }

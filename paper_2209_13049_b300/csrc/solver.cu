@@ -254,7 +254,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto ldiag = c.take<double>(2 * 32 * 32);
-    auto pflags = c.take<int>(64);
+    auto pflags = c.take<int>(2 + 17 * 17);   // dataflow Cholesky: epoch, count, flag per row block
     auto ffw = c.take<float>(4 * (size_t)I.SX);
     auto ffv = c.take<float>(2 * (size_t)n);
     auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);

@@ -1,0 +1,70 @@
+"""The FP32 Cholesky factor of the condensed KKT matrix (Eq. 7, M = L L') and
+its inverse (the preconditioner of the mixed-precision solves) against the
+FP64 oracle matrix, over sizes spanning one to seventeen 32-wide block
+columns with ragged ends (a single instance of n <= 544 takes the dataflow
+factorisation).
+
+Tolerances.  The factor is judged by its backward error, element-wise:
+|L L' - M| <= 8 (n + 2) 2^-24 (|L| |L'|) + the FP32-accurate formation error
+of M (4 2^-24 (sqrt(K) + 2) of the absolute sum, K = ns N terms).  The
+inverse is judged by the conjugate gradients it preconditions: started from
+L^-T L^-1 b, FP64 products with M must reach a 2e-10 relative residual in a
+few steps (an FP32-accurate inverse contracts the error by about
+cond(M) 2^-24 per step; a wrong block of it would not).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_13049_b300 import binding, build, inputs
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+SIZES = [
+    ("n20_one_ragged_block", lambda: inputs.heat1d(10, 2, 10)),
+    ("n161_ragged", lambda: inputs.heat2d(10, 7, 23)),
+    ("n500_16_blocks_ragged", lambda: inputs.heat1d(40, 10, 50)),
+    ("n517_17_blocks_ragged5", lambda: inputs.heat1d(30, 11, 47)),
+    ("n544_17_full_blocks", lambda: inputs.heat1d(30, 16, 34)),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    binding.load()
+
+
+@pytest.fixture(scope="module", params=SIZES, ids=[c[0] for c in SIZES])
+def case(request):
+    p = request.param[1]()
+    s = binding.Solver(p)
+    Gam, _, H, _ = oracle.condensed(p, np.zeros(p.ns))
+    rng = np.random.default_rng(11)
+    sigx = 10.0 ** rng.uniform(-1, 1, p.ns * p.N)
+    sigu = 10.0 ** rng.uniform(-1, 1, p.n)
+    M = oracle.kkt_matrix(p, sigx, sigu, Gam, H)
+    absm = np.abs(H) + np.abs(Gam).T @ (sigx[:, None] * np.abs(Gam)) + np.diag(sigu)
+    return p, s, sigx, sigu, M, absm
+
+
+def test_fp32_factor_backward_error(case):
+    p, s, sigx, sigu, M, absm = case
+    b = np.random.default_rng(12).standard_normal(p.n)
+    r = s.kkt_solve(sigx, sigu, b, "fp32", want_L=True)
+    L = np.tril(r["L"])
+    assert np.all(np.isfinite(L)) and np.all(np.diag(L) > 0)
+    err = np.abs(L @ L.T - M)
+    bound = 8 * (p.n + 2) * U32 * (np.abs(L) @ np.abs(L).T) + 4 * U32 * (np.sqrt(p.ns * p.N) + 2) * absm
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+def test_fp32_inverse_preconditions_in_few_steps(case):
+    p, s, sigx, sigu, M, _ = case
+    b = np.random.default_rng(13).standard_normal(p.n)
+    r = s.kkt_solve(sigx, sigu, b, "fp32")
+    res = np.max(np.abs(b - M @ r["x"])) / np.max(np.abs(b))
+    assert res <= 2e-10, res
+    assert r["refine_steps"] <= 8, r["refine_steps"]
