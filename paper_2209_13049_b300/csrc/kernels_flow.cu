@@ -47,32 +47,59 @@ __device__ __forceinline__ void cpa_wait_all() {
 }
 
 // Rows [32p, 32p + pr) of the global columns [mm0, mm1) of the column-major
-// n x n matrix M into P[(mm - mmb) * 32 + r] (zeros for r >= pr): 16-byte
-// copies when every column start is 16-byte aligned (n a multiple of 4),
-// scalar L2 loads otherwise.  The copies are waited for by cpa_wait_all.
-__device__ __forceinline__ void stage_rowblock(float* P, int mmb, const float* M, int n, int p, int pr, int mm0, int mm1,
-                               bool vec) {
+// n x n matrix M into P[(mm - mmb) * 32 + r] (zeros for r >= pr) by the
+// threads [t0, t0 + nthr): 16-byte copies when every column start is
+// 16-byte aligned (n a multiple of 4), scalar L2 loads otherwise.  The
+// copies are waited for by cpa_wait_all.
+__device__ __forceinline__ void stage_rowblock(float* P, int mmb, const float* M, int n, int p, int pr, int mm0,
+                                               int mm1, bool vec, int t0 = 0, int nthr = 256) {
+    const int t = threadIdx.x - t0;
     if (vec) {
-        for (int e = threadIdx.x; e < (mm1 - mm0) * 8; e += blockDim.x) {
+        for (int e = t; e < (mm1 - mm0) * 8; e += nthr) {
             const int mm = mm0 + e / 8, r = 4 * (e % 8);
             const int left = pr - r;
             const int bytes = left >= 4 ? 16 : (left > 0 ? 4 * left : 0);
             cpa16(P + (mm - mmb) * kFb + r, M + (size_t)n * mm + kFb * p + (left > 0 ? r : 0), bytes);
         }
     } else {
-        for (int e = threadIdx.x; e < (mm1 - mm0) * kFb; e += blockDim.x) {
+        for (int e = t; e < (mm1 - mm0) * kFb; e += nthr) {
             const int mm = mm0 + e / kFb, r = e % kFb;
             P[(mm - mmb) * kFb + r] = r < pr ? __ldcg(M + (size_t)n * mm + kFb * p + r) : 0.f;
         }
     }
 }
 
-// Warp 0 waits until the flags (k, p) for k in [k0, k1), and flag index
-// `extra` when >= 0, all equal ep (one flag per lane, bounded), then the
-// block proceeds.
-__device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k1, int p, int extra, int ep, int* err) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x, cnt = k1 - k0;
+// The CTA's own block A_pj (columns r0 .. r0 + kn - 1, rows p0 .. p0 + pr - 1
+// of M, written by nobody else) into As column-major, zero-padded.
+__device__ __forceinline__ void stage_own(float* As, const float* M, int n, int r0, int kn, int p0, int pr,
+                                          bool vec, int t0 = 0, int nthr = 256) {
+    const int t = threadIdx.x - t0;
+    if (vec) {
+        for (int e = t; e < kFb * 8; e += nthr) {
+            const int c = e / 8, r = 4 * (e % 8), left = pr - r;
+            if (c < kn) cpa16(As + c * kFb + r, M + (size_t)n * (r0 + c) + p0 + (left > 0 ? r : 0),
+                              left >= 4 ? 16 : (left > 0 ? 4 * left : 0));
+            else *reinterpret_cast<float4*>(As + c * kFb + r) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    } else {
+        for (int e = t; e < kFb * kFb; e += nthr) {
+            const int c = e / kFb, r = e % kFb;
+            As[c * kFb + r] = (c < kn && r < pr) ? M[(size_t)n * (r0 + c) + p0 + r] : 0.f;
+        }
+    }
+}
+
+// Barrier of warps 1..7 (while warp 0 factors a diagonal block).
+__device__ __forceinline__ void bar_w17() { asm volatile("bar.sync 1, 224;" ::: "memory"); }
+
+// Warp W waits until the flags (k, p) for k in [k0, k1), and flag index
+// `extra` when >= 0, all equal ep (one flag per lane, bounded); then the
+// whole block (W = 0) or warps 1..7 (W = 1) proceed.
+template <int W>
+__device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k1, int p, int extra, int ep,
+                                           int* err) {
+    if ((threadIdx.x >> 5) == W) {
+        const int lane = threadIdx.x & 31, cnt = k1 - k0;
         int idx = -1;
         if (lane < cnt) idx = (k0 + lane) * nt + p;
         else if (lane == cnt && extra >= 0) idx = extra;
@@ -91,14 +118,16 @@ __device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k
         }
         __threadfence();
     }
-    __syncthreads();
+    if (W == 0) __syncthreads();
+    else bar_w17();
 }
 
-// acc[c] += sum_m P[m * 32 + lane] B[m * 32 + c] over m in [m0, m1), warp w
-// taking m = m0 + w, m0 + w + 8, ... (partial sums per warp).
-__device__ __forceinline__ void acc_panel(float (&acc)[kFb], const float* P, const float* B, int m0, int m1) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int m = m0 + warp; m < m1; m += 8) {
+// acc[c] += sum_m P[m * 32 + lane] B[m * 32 + c] over m in [m0, m1), this
+// warp (wi of nw) taking m = m0 + wi, m0 + wi + nw, ... (partial sums per warp).
+__device__ __forceinline__ void acc_panel(float (&acc)[kFb], const float* P, const float* B, int m0, int m1,
+                                          int wi = threadIdx.x >> 5, int nw = 8) {
+    const int lane = threadIdx.x & 31;
+    for (int m = m0 + wi; m < m1; m += nw) {
         const float a = P[m * kFb + lane];
         const float4* b4 = reinterpret_cast<const float4*>(B + m * kFb);
 #pragma unroll
@@ -120,26 +149,38 @@ __device__ __forceinline__ void store_partial(const float (&acc)[kFb], float* Re
     for (int c = 0; c < kFb; ++c) R[c] = acc[c];
 }
 
-__device__ __forceinline__ float sum_partials(const float* Red, int r, int c) {
+__device__ __forceinline__ float sum_partials(const float* Red, int r, int c, int w0 = 0) {
     float s = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) s += Red[(w * kFb + r) * (kFb + 1) + c];
+    for (int w = 0; w < 8; ++w) s += w >= w0 ? Red[(w * kFb + r) * (kFb + 1) + c] : 0.f;
     return s;
 }
 
-// Warp 0: T (32 x 33, shared) -> L (D) and L^{-1} (Dv), lower, zeros above.
-// Not inlined, so the factorisation's registers are allocated apart from the
+// Warp 0: T (32 x 33, shared) -> L (D) and X = L^{-1} (Dv), lower, zeros
+// above.  The inverse by forward substitution L X = I with column `lane` of
+// X in lane `lane`: x_i = (delta_{i,lane} - sum_{k<i} l_ik x_k) / l_ii, rows
+// of L read from shared memory as broadcasts, 1 / l_ii from the factor.  Not
+// inlined, so the factorisation's registers are allocated apart from the
 // kernel's.
-__device__ __noinline__ int factor_diag_block(const float* T, float* D, float* Dv) {
+__device__ __noinline__ int factor_diag_block(const float* T, float* D, float* Dv, float* rsh) {
     const int lane = threadIdx.x & 31;
-    float a[kFb], x[kFb];
+    float a[kFb];
 #pragma unroll
     for (int c = 0; c < kFb; ++c) a[c] = T[lane * (kFb + 1) + c];
-    const int fail = diag_factor_inverse(a, x);
+    float rd;
+    const int fail = diag_factor(a, rd);
 #pragma unroll
-    for (int c = 0; c < kFb; ++c) {
-        D[lane * (kFb + 1) + c] = c <= lane ? a[c] : 0.f;
-        Dv[lane * (kFb + 1) + c] = c <= lane ? x[c] : 0.f;
+    for (int c = 0; c < kFb; ++c) D[lane * (kFb + 1) + c] = c <= lane ? a[c] : 0.f;
+    rsh[lane] = rd;
+    __syncwarp();
+    float x[kFb];
+#pragma unroll
+    for (int i = 0; i < kFb; ++i) {
+        float s = i == lane ? 1.f : 0.f;
+#pragma unroll
+        for (int k = 0; k < i; ++k) s = fmaf(-D[i * (kFb + 1) + k], x[k], s);
+        x[i] = s * rsh[i];
+        Dv[i * (kFb + 1) + lane] = x[i];     // zero above the diagonal (i < lane)
     }
     return fail;
 }
@@ -150,7 +191,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     const Inst& I = insts[0];
     if (skip_instance(I, flags)) return;           // the same decision in every CTA
     extern __shared__ __align__(16) float fsm[];
-    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1];
+    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1], rsh[kFb];
     __shared__ int ep_sh;
     const int n = I.n, nt = (n + kFb - 1) / kFb, j = blockIdx.x;
     int* epoch = I.pflags;        // [0] epoch, [1] finished CTAs, [2 + k nt + p] flag of row block p of column k
@@ -172,62 +213,75 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (n % 4) == 0;
 
+    // pre: the partial sums of row block p are already in Red (warps 1..7)
+    // and A_pj in As, gathered while warp 0 factored the diagonal block
+    bool pre = false;
     for (int p = j; p < nt; ++p) {
         const int p0 = kFb * p, pr = min(kFb, n - p0);
-        float* P = p == j ? Rj : Pn;
-        // own block A_pj (written by nobody else)
-        if (vec) {
-            for (int e = threadIdx.x; e < kFb * 8; e += blockDim.x) {
-                const int c = e / 8, r = 4 * (e % 8), left = pr - r;
-                if (c < kn) cpa16(As + c * kFb + r, M + (size_t)n * (r0 + c) + p0 + (left > 0 ? r : 0),
-                                  left >= 4 ? 16 : (left > 0 ? 4 * left : 0));
-                else *reinterpret_cast<float4*>(As + c * kFb + r) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        } else {
-            for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
-                const int c = e / kFb, r = e % kFb;
-                As[c * kFb + r] = (c < kn && r < pr) ? M[(size_t)n * (r0 + c) + p0 + r] : 0.f;
-            }
-        }
-        // S = sum_{k<j} L_pk L_jk'; for the diagonal block the last column's
-        // contribution comes last (it is the latest to be published)
-        float acc[kFb];
+        if (!pre) {
+            float* P = p == j ? Rj : Pn;
+            stage_own(As, M, n, r0, kn, p0, pr, vec);
+            // S = sum_{k<j} L_pk L_jk'; for the diagonal block the last
+            // column's contribution comes last (it is the latest published)
+            float acc[kFb];
 #pragma unroll
-        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
-        if (j > 0) {
-            const int kA = p == j ? j - 1 : j;
-            if (kA > 0) {
-                wait_flags(flg, nt, 0, kA, p, -1, ep, err);
-                stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
-                cpa_wait_all();
-                __syncthreads();
-                acc_panel(acc, P, Rj, 0, kFb * kA);
+            for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+            if (j > 0) {
+                const int kA = p == j ? j - 1 : j;
+                if (kA > 0) {
+                    wait_flags<0>(flg, nt, 0, kA, p, -1, ep, err);
+                    stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
+                    cpa_wait_all();
+                    __syncthreads();
+                    acc_panel(acc, P, Rj, 0, kFb * kA);
+                }
+                if (kA < j) {
+                    wait_flags<0>(flg, nt, j - 1, j, p, -1, ep, err);
+                    stage_rowblock(P, 0, M, n, p, pr, kFb * (j - 1), kFb * j, vec);
+                    cpa_wait_all();
+                    __syncthreads();
+                    acc_panel(acc, P, Rj, kFb * (j - 1), kFb * j);
+                }
             }
-            if (kA < j) {
-                wait_flags(flg, nt, j - 1, j, p, -1, ep, err);
-                stage_rowblock(P, 0, M, n, p, pr, kFb * (j - 1), kFb * j, vec);
-                cpa_wait_all();
-                __syncthreads();
-                acc_panel(acc, P, Rj, kFb * (j - 1), kFb * j);
-            }
+            cpa_wait_all();
+            store_partial(acc, Red);
+            __syncthreads();
         }
-        cpa_wait_all();
-        store_partial(acc, Red);
-        __syncthreads();
         for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
             const int r = e & 31, c = e >> 5;
-            float v = As[c * kFb + r] - sum_partials(Red, r, c);
+            float v = As[c * kFb + r] - sum_partials(Red, r, c, pre ? 1 : 0);
             if (p == j && r == c && r >= kn) v = 1.f;     // identity padding of a ragged last block
             T[r][c] = v;
         }
         __syncthreads();
+        pre = false;
         if (p == j) {
-            // diagonal block: factor and invert in registers (warp 0, row i in lane i)
+            // diagonal block: factor and invert (warp 0, row i in lane i);
+            // meanwhile warps 1..7 gather row block j+1 (its A block and the
+            // partial sums of its update), which no longer waits on anything
+            // but this factorisation
             if (warp == 0) {
-                const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
+                const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0], rsh);
                 if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
+            } else if (p + 1 < nt) {
+                const int q0 = p0 + kFb, qr = min(kFb, n - q0);
+                stage_own(As, M, n, r0, kn, q0, qr, vec, 32, 224);
+                float acc[kFb];
+#pragma unroll
+                for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+                if (j > 0) {
+                    wait_flags<1>(flg, nt, 0, j, p + 1, -1, ep, err);
+                    stage_rowblock(Pn, 0, M, n, p + 1, qr, 0, kFb * j, vec, 32, 224);
+                    cpa_wait_all();
+                    bar_w17();
+                    acc_panel(acc, Pn, Rj, 0, kFb * j, warp - 1, 7);
+                } else {
+                    cpa_wait_all();
+                }
+                store_partial(acc, Red);
             }
             __syncthreads();
+            pre = p + 1 < nt;
             // publish L_jj and X_jj = L_jj^{-1}; X_jj is block 0 of Xs
             for (int c = warp; c < kn; c += 8) {
                 if (lane < kn && lane >= c) {
@@ -266,7 +320,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     // block column j of X: X_pj = -X_pp sum_{k=j}^{p-1} L_pk X_kj
     for (int p = j + 1; p < nt; ++p) {
         const int p0 = kFb * p, pr = min(kFb, n - p0);
-        wait_flags(flg, nt, j + 1, p, p, p * nt + p, ep, err);
+        wait_flags<0>(flg, nt, j + 1, p, p, p * nt + p, ep, err);
         stage_rowblock(Pn, r0, M, n, p, pr, r0, p0, vec);
         for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
             const int r = e / kFb, c = e % kFb;   // X_pp[r][c]
