@@ -213,103 +213,121 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (n % 4) == 0;
 
-    // pre: the partial sums of row block p are already in Red (warps 1..7)
-    // and A_pj in As, gathered while warp 0 factored the diagonal block
-    bool pre = false;
-    for (int p = j; p < nt; ++p) {
+    // Row block p: A_pj into As and the partial sums of S = sum_{k<j} L_pk
+    // L_jk' into Red (all warps); for the diagonal block the last column's
+    // contribution comes last (it is the latest to be published).
+    auto gather = [&](int p) {
         const int p0 = kFb * p, pr = min(kFb, n - p0);
-        if (!pre) {
-            float* P = p == j ? Rj : Pn;
-            stage_own(As, M, n, r0, kn, p0, pr, vec);
-            // S = sum_{k<j} L_pk L_jk'; for the diagonal block the last
-            // column's contribution comes last (it is the latest published)
-            float acc[kFb];
+        float* P = p == j ? Rj : Pn;
+        stage_own(As, M, n, r0, kn, p0, pr, vec);
+        float acc[kFb];
 #pragma unroll
-            for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
-            if (j > 0) {
-                const int kA = p == j ? j - 1 : j;
-                if (kA > 0) {
-                    wait_flags<0>(flg, nt, 0, kA, p, -1, ep, err);
-                    stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
-                    cpa_wait_all();
-                    __syncthreads();
-                    acc_panel(acc, P, Rj, 0, kFb * kA);
-                }
-                if (kA < j) {
-                    wait_flags<0>(flg, nt, j - 1, j, p, -1, ep, err);
-                    stage_rowblock(P, 0, M, n, p, pr, kFb * (j - 1), kFb * j, vec);
-                    cpa_wait_all();
-                    __syncthreads();
-                    acc_panel(acc, P, Rj, kFb * (j - 1), kFb * j);
-                }
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 0) {
+            const int kA = p == j ? j - 1 : j;
+            if (kA > 0) {
+                wait_flags<0>(flg, nt, 0, kA, p, -1, ep, err);
+                stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
+                cpa_wait_all();
+                __syncthreads();
+                acc_panel(acc, P, Rj, 0, kFb * kA);
             }
-            cpa_wait_all();
-            store_partial(acc, Red);
-            __syncthreads();
+            if (kA < j) {
+                wait_flags<0>(flg, nt, j - 1, j, p, -1, ep, err);
+                stage_rowblock(P, 0, M, n, p, pr, kFb * (j - 1), kFb * j, vec);
+                cpa_wait_all();
+                __syncthreads();
+                acc_panel(acc, P, Rj, kFb * (j - 1), kFb * j);
+            }
         }
+        cpa_wait_all();
+        store_partial(acc, Red);
+        __syncthreads();
+    };
+    // T = A_pj - S from the partials of warps w0..7 (identity padding of a
+    // ragged diagonal block)
+    auto form_t = [&](bool diag, int w0) {
         for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
             const int r = e & 31, c = e >> 5;
-            float v = As[c * kFb + r] - sum_partials(Red, r, c, pre ? 1 : 0);
-            if (p == j && r == c && r >= kn) v = 1.f;     // identity padding of a ragged last block
+            float v = As[c * kFb + r] - sum_partials(Red, r, c, w0);
+            if (diag && r == c && r >= kn) v = 1.f;
             T[r][c] = v;
         }
         __syncthreads();
-        pre = false;
-        if (p == j) {
-            // diagonal block: factor and invert (warp 0, row i in lane i);
-            // meanwhile warps 1..7 gather row block j+1 (its A block and the
-            // partial sums of its update), which no longer waits on anything
-            // but this factorisation
-            if (warp == 0) {
-                const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0], rsh);
-                if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
-            } else if (p + 1 < nt) {
-                const int q0 = p0 + kFb, qr = min(kFb, n - q0);
-                stage_own(As, M, n, r0, kn, q0, qr, vec, 32, 224);
-                float acc[kFb];
-#pragma unroll
-                for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
-                if (j > 0) {
-                    wait_flags<1>(flg, nt, 0, j, p + 1, -1, ep, err);
-                    stage_rowblock(Pn, 0, M, n, p + 1, qr, 0, kFb * j, vec, 32, 224);
-                    cpa_wait_all();
-                    bar_w17();
-                    acc_panel(acc, Pn, Rj, 0, kFb * j, warp - 1, 7);
-                } else {
-                    cpa_wait_all();
-                }
-                store_partial(acc, Red);
-            }
-            __syncthreads();
-            pre = p + 1 < nt;
-            // publish L_jj and X_jj = L_jj^{-1}; X_jj is block 0 of Xs
-            for (int c = warp; c < kn; c += 8) {
-                if (lane < kn && lane >= c) {
-                    __stcg(M + (size_t)n * (r0 + c) + r0 + lane, D[lane][c]);
-                    const float xv = Dv[lane][c];
-                    __stcg(I.Xinv32 + (size_t)(r0 + lane) + (size_t)n * (r0 + c), xv);
-                    __stcg(I.XinvT32 + (size_t)(r0 + c) + (size_t)n * (r0 + lane), xv);
-                }
-            }
-            for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) Xs[e] = Dv[e >> 5][e & 31];
-        } else {
-            // L_pj = T X_jj': lane -> row, warp -> 4 columns
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
+    };
+    // L_pj = T X_jj' (lane -> row, warp -> 4 columns), stored to M
+    auto solve_store = [&](int p) {
+        const int p0 = kFb * p, pr = min(kFb, n - p0);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-            for (int m = 0; m < kFb; ++m) {
-                const float t = T[lane][m];
+        for (int m = 0; m < kFb; ++m) {
+            const float t = T[lane][m];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) o[q] = fmaf(t, Dv[warp + 8 * q][m], o[q]);
-            }
-            if (lane < pr) {
+            for (int q = 0; q < 4; ++q) o[q] = fmaf(t, Dv[warp + 8 * q][m], o[q]);
+        }
+        if (lane < pr) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int c = warp + 8 * q;
-                    if (c < kn) __stcg(M + (size_t)n * (r0 + c) + p0 + lane, o[q]);
-                }
+            for (int q = 0; q < 4; ++q) {
+                const int c = warp + 8 * q;
+                if (c < kn) __stcg(M + (size_t)n * (r0 + c) + p0 + lane, o[q]);
             }
         }
-        __threadfence();   // every writer's stores before the flag
+    };
+
+    // diagonal block: warp 0 factors and inverts it (row i in lane i) while
+    // warps 1..7 gather row block j+1, which then waits on nothing but this
+    // factorisation; L_{j+1,j} goes out first (the next block column's
+    // diagonal needs it), L_jj and X_jj with it
+    gather(j);
+    form_t(true, 0);
+    const bool next = j + 1 < nt;
+    if (warp == 0) {
+        const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0], rsh);
+        if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
+    } else if (next) {
+        const int q0 = r0 + kFb, qr = min(kFb, n - q0);
+        stage_own(As, M, n, r0, kn, q0, qr, vec, 32, 224);
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 0) {
+            wait_flags<1>(flg, nt, 0, j, j + 1, -1, ep, err);
+            stage_rowblock(Pn, 0, M, n, j + 1, qr, 0, kFb * j, vec, 32, 224);
+            cpa_wait_all();
+            bar_w17();
+            acc_panel(acc, Pn, Rj, 0, kFb * j, warp - 1, 7);
+        } else {
+            cpa_wait_all();
+        }
+        store_partial(acc, Red);
+    }
+    __syncthreads();
+    if (next) {
+        form_t(false, 1);
+        solve_store(j + 1);
+    }
+    for (int c = warp; c < kn; c += 8) {
+        if (lane < kn && lane >= c) {
+            __stcg(M + (size_t)n * (r0 + c) + r0 + lane, D[lane][c]);
+            const float xv = Dv[lane][c];
+            __stcg(I.Xinv32 + (size_t)(r0 + lane) + (size_t)n * (r0 + c), xv);
+            __stcg(I.XinvT32 + (size_t)(r0 + c) + (size_t)n * (r0 + lane), xv);
+        }
+    }
+    for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) Xs[e] = Dv[e >> 5][e & 31];
+    __threadfence();   // every writer's stores before the flags
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (next) atomicExch(flg + j * nt + j + 1, ep);
+        atomicExch(flg + j * nt + j, ep);
+    }
+    // the rest of the column
+    for (int p = j + 2; p < nt; ++p) {
+        gather(p);
+        form_t(false, 0);
+        solve_store(p);
+        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
