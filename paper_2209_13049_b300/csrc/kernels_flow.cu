@@ -157,32 +157,105 @@ __device__ __forceinline__ float sum_partials(const float* Red, int r, int c, in
 }
 
 // Warp 0: T (32 x 33, shared) -> L (D) and X = L^{-1} (Dv), lower, zeros
-// above.  The inverse by forward substitution L X = I with column `lane` of
-// X in lane `lane`: x_i = (delta_{i,lane} - sum_{k<i} l_ik x_k) / l_ii, rows
-// of L read from shared memory as broadcasts, 1 / l_ii from the factor.  Not
-// inlined, so the factorisation's registers are allocated apart from the
-// kernel's.
-__device__ __noinline__ int factor_diag_block(const float* T, float* D, float* Dv, float* rsh) {
+// above; returns 0, or q + 1 for the first non-positive pivot q.
+//
+// Left-looking by rounds of four columns, lane i holding row i of L in
+// registers and every row also in shared memory: round j0 forms
+// s_i,t = a_i,j0+t - sum_{k<j0} l_ik l_j0+t,k (rows j0..j0+3 read as
+// broadcasts), takes the 4 x 4 pivot block from lanes j0..j0+3 by shuffles,
+// factors it in every lane, and finishes the lane's four entries by
+// substitution with it: one shared-memory exchange per four columns.  1/sqrt
+// comes from rsqrtf refined by one Newton step, so the serial chain has no
+// division.  The inverse by forward substitution L X = I with column `lane`
+// of X in lane `lane`: x_i = (delta_{i,lane} - sum_{k<i} l_ik x_k) / l_ii.
+// Not inlined, so its registers are allocated apart from the kernel's.
+__device__ __noinline__ int factor_diag_block(const float* T, float* D, float* Dv) {
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    float a[kFb];
+    __shared__ __align__(16) float Ls[kFb][kFb + 4];
+    __shared__ float rs[kFb];
+    float tr[kFb], l[kFb];
 #pragma unroll
-    for (int c = 0; c < kFb; ++c) a[c] = T[lane * (kFb + 1) + c];
-    float rd;
-    const int fail = diag_factor(a, rd);
+    for (int c = 0; c < kFb; ++c) tr[c] = T[lane * (kFb + 1) + c];
+    int fail = 0;
+    float rown = 1.f;
 #pragma unroll
-    for (int c = 0; c < kFb; ++c) D[lane * (kFb + 1) + c] = c <= lane ? a[c] : 0.f;
-    rsh[lane] = rd;
+    for (int j0 = 0; j0 < kFb; j0 += 4) {
+        float s[4][4];   // four partial sums per column
+#pragma unroll
+        for (int t = 0; t < 4; ++t) { s[t][0] = tr[j0 + t]; s[t][1] = s[t][2] = s[t][3] = 0.f; }
+#pragma unroll
+        for (int k4 = 0; k4 < j0 / 4; ++k4) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const float4 lj = *reinterpret_cast<const float4*>(&Ls[j0 + t][4 * k4]);
+                s[t][0] = fmaf(-l[4 * k4 + 0], lj.x, s[t][0]);
+                s[t][1] = fmaf(-l[4 * k4 + 1], lj.y, s[t][1]);
+                s[t][2] = fmaf(-l[4 * k4 + 2], lj.z, s[t][2]);
+                s[t][3] = fmaf(-l[4 * k4 + 3], lj.w, s[t][3]);
+            }
+        }
+        float sv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) sv[t] = (s[t][0] + s[t][1]) + (s[t][2] + s[t][3]);
+        float P[4][4];   // pivot block, lower: P[t][u] = sv[u] of lane j0 + t
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int u = 0; u <= t; ++u) P[t][u] = __shfl_sync(full, sv[u], j0 + t);
+        float B[4][4], rb[4];   // its factor and the reciprocals of the diagonal
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float d = P[t][t];
+#pragma unroll
+            for (int u = 0; u < t; ++u) d = fmaf(-B[t][u], B[t][u], d);
+            const bool bad = !(d > 0.f);
+            if (bad && !fail && lane == j0 + t) fail = j0 + t + 1;
+            rb[t] = rsqrt_refined(bad ? 1.f : d);
+            B[t][t] = d * rb[t];
+#pragma unroll
+            for (int v = t + 1; v < 4; ++v) {
+                float e = P[v][t];
+#pragma unroll
+                for (int u = 0; u < t; ++u) e = fmaf(-B[v][u], B[t][u], e);
+                B[v][t] = e * rb[t];
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            float e = sv[t];
+#pragma unroll
+            for (int u = 0; u < t; ++u) e = fmaf(-l[j0 + u], B[t][u], e);
+            const int col = j0 + t;
+            l[col] = lane > col ? e * rb[t] : (lane == col ? B[t][t] : 0.f);
+            if (lane == col) rown = rb[t];
+        }
+        *reinterpret_cast<float4*>(&Ls[lane][j0]) = make_float4(l[j0], l[j0 + 1], l[j0 + 2], l[j0 + 3]);
+        __syncwarp();
+    }
+    rs[lane] = rown;
     __syncwarp();
     float x[kFb];
 #pragma unroll
     for (int i = 0; i < kFb; ++i) {
-        float s = i == lane ? 1.f : 0.f;
+        float v = i == lane ? 1.f : 0.f;
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = fmaf(-D[i * (kFb + 1) + k], x[k], s);
-        x[i] = s * rsh[i];
-        Dv[i * (kFb + 1) + lane] = x[i];     // zero above the diagonal (i < lane)
+        for (int k4 = 0; k4 < (i + 3) / 4; ++k4) {
+            const float4 li = *reinterpret_cast<const float4*>(&Ls[i][4 * k4]);
+            if (4 * k4 + 0 < i) v = fmaf(-li.x, x[4 * k4 + 0], v);
+            if (4 * k4 + 1 < i) v = fmaf(-li.y, x[4 * k4 + 1], v);
+            if (4 * k4 + 2 < i) v = fmaf(-li.z, x[4 * k4 + 2], v);
+            if (4 * k4 + 3 < i) v = fmaf(-li.w, x[4 * k4 + 3], v);
+        }
+        x[i] = v * rs[i];
     }
-    return fail;
+#pragma unroll
+    for (int c = 0; c < kFb; ++c) {
+        D[lane * (kFb + 1) + c] = l[c];
+        Dv[c * (kFb + 1) + lane] = x[c];
+    }
+    const int f = __reduce_min_sync(full, fail ? fail : 0x7fffffff);
+    return f == 0x7fffffff ? 0 : f;
 }
 
 }  // namespace
@@ -191,7 +264,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     const Inst& I = insts[0];
     if (skip_instance(I, flags)) return;           // the same decision in every CTA
     extern __shared__ __align__(16) float fsm[];
-    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1], rsh[kFb];
+    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1];
     __shared__ int ep_sh;
     const int n = I.n, nt = (n + kFb - 1) / kFb, j = blockIdx.x;
     int* epoch = I.pflags;        // [0] epoch, [1] finished CTAs, [2 + k nt + p] flag of row block p of column k
@@ -282,7 +355,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     form_t(true, 0);
     const bool next = j + 1 < nt;
     if (warp == 0) {
-        const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0], rsh);
+        const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
         if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
     } else if (next) {
         const int q0 = r0 + kFb, qr = min(kFb, n - q0);
