@@ -14,8 +14,9 @@
 // The products sum over 32 k-columns per warp step in FP32 (the
 // contraction is split over the eight warps and reduced in shared memory).
 //
-// Publication: a row block is written with L2-coherent stores, fenced, then
-// its flag is set to the launch's epoch; readers poll the flags (bounded: a
+// Publication: a row block is written with L2-coherent stores, the CTA
+// synchronises, and one thread sets its flag to the launch's epoch with a
+// release store; readers poll the flags (bounded: a
 // wait that gives up raises Scal::err bit 4 and the kernel still runs to its
 // end) and read with L1-bypassing loads.  The epoch advances when the last
 // CTA finishes, so flags never need clearing.  A non-positive pivot is
@@ -35,6 +36,14 @@ constexpr int kFlowMaxN = 544;          // 17 block columns: the panels fit shar
 constexpr uint32_t kFlowSpin = 1u << 22;
 
 __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile int*)p; }
+
+// Flag store with release semantics at GPU scope: the CTA's stores ordered
+// before it (by the CTA barrier in front of it) are visible to whoever
+// observes the flag and then acquires.
+__device__ __forceinline__ void st_flag_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // 16-byte global -> shared copy through L2 only (other CTAs' data is read
 // after their flag), zero-filled past `bytes` (0..16).
@@ -116,7 +125,7 @@ __device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k
             __nanosleep(64);
             if (!ok) ok = ld_flag(flg + idx) == ep;
         }
-        __threadfence();
+        fence_acquire();
     }
     if (W == 0) __syncthreads();
     else bar_w17();
@@ -285,10 +294,19 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     float* Red = As + kFb * kFb;                     // [8 warps][32][33] partial sums
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (n % 4) == 0;
+    if (j > 0 && warp == 0) {
+        // Run the diagonal factorisation once on an identity block while
+        // this CTA waits for its first columns anyway: its code (unrolled,
+        // tens of KB) is then in the SM's instruction cache when the real
+        // block arrives on the critical path.
+        for (int e = lane; e < kFb * kFb; e += 32) T[e >> 5][e & 31] = (e >> 5) == (e & 31) ? 1.f : 0.f;
+        __syncwarp();
+        factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
+    }
 
     // Row block p: A_pj into As and the partial sums of S = sum_{k<j} L_pk
-    // L_jk' into Red (all warps); for the diagonal block the last column's
-    // contribution comes last (it is the latest to be published).
+    // L_jk' into Red (all warps); the last column's contribution comes last
+    // (it is the latest to be published, on the critical path).
     auto gather = [&](int p) {
         const int p0 = kFb * p, pr = min(kFb, n - p0);
         float* P = p == j ? Rj : Pn;
@@ -297,7 +315,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
 #pragma unroll
         for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
         if (j > 0) {
-            const int kA = p == j ? j - 1 : j;
+            const int kA = j - 1;
             if (kA > 0) {
                 wait_flags<0>(flg, nt, 0, kA, p, -1, ep, err);
                 stage_rowblock(P, 0, M, n, p, pr, 0, kFb * kA, vec);
@@ -363,12 +381,19 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
         float acc[kFb];
 #pragma unroll
         for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
-        if (j > 0) {
-            wait_flags<1>(flg, nt, 0, j, j + 1, -1, ep, err);
-            stage_rowblock(Pn, 0, M, n, j + 1, qr, 0, kFb * j, vec, 32, 224);
+        if (j > 1) {   // the columns published long ago, then the last one
+            wait_flags<1>(flg, nt, 0, j - 1, j + 1, -1, ep, err);
+            stage_rowblock(Pn, 0, M, n, j + 1, qr, 0, kFb * (j - 1), vec, 32, 224);
             cpa_wait_all();
             bar_w17();
-            acc_panel(acc, Pn, Rj, 0, kFb * j, warp - 1, 7);
+            acc_panel(acc, Pn, Rj, 0, kFb * (j - 1), warp - 1, 7);
+        }
+        if (j > 0) {
+            wait_flags<1>(flg, nt, j - 1, j, j + 1, -1, ep, err);
+            stage_rowblock(Pn, 0, M, n, j + 1, qr, kFb * (j - 1), kFb * j, vec, 32, 224);
+            cpa_wait_all();
+            bar_w17();
+            acc_panel(acc, Pn, Rj, kFb * (j - 1), kFb * j, warp - 1, 7);
         } else {
             cpa_wait_all();
         }
@@ -388,24 +413,20 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
         }
     }
     for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) Xs[e] = Dv[e >> 5][e & 31];
-    __threadfence();   // every writer's stores before the flags
+    // the CTA barrier orders every thread's stores before thread 0's
+    // release of the flags
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (next) atomicExch(flg + j * nt + j + 1, ep);
-        atomicExch(flg + j * nt + j, ep);
+        if (next) st_flag_release(flg + j * nt + j + 1, ep);
+        st_flag_release(flg + j * nt + j, ep);
     }
     // the rest of the column
     for (int p = j + 2; p < nt; ++p) {
         gather(p);
         form_t(false, 0);
         solve_store(p);
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicExch(flg + j * nt + p, ep);
-        }
+        if (threadIdx.x == 0) st_flag_release(flg + j * nt + p, ep);
     }
 
     // block column j of X: X_pj = -X_pp sum_{k=j}^{p-1} L_pk X_kj
