@@ -32,10 +32,19 @@ size_t gamma_tmv_part_doubles(int ns, int n, int N);
 void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int max_n,
                       int w0_role, int w1_role, int o0_role, int o1_role, int scale0, int force,
                       cudaStream_t st);
+// Fusion options of the float-float Gamma products: the input is already
+// split (kFuseInSplit: no split kernel), the Gamma v sum also writes the split
+// of Sigma_x (Gamma v) for a following Gamma' product (kFuseOutW) and a copy
+// into dxs (kFuseOutDxs); the Gamma' product leaves its partials for a fused
+// consumer (kFuseNoSum).
+enum FuseFlags : int { kFuseInSplit = 1, kFuseOutW = 2, kFuseOutDxs = 4, kFuseNoSum = 8 };
 void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
-                        int out_role, int flags, cudaStream_t st);
+                        int out_role, int flags, cudaStream_t st, int fuse = 0);
+// split count of the float-float Gamma' product (its partials' layout)
+int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV);
 void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
-                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st);
+                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st,
+                         int fuse = 0);
 void launch_ychain(const Inst* d_insts, int count, cudaStream_t st);
 void launch_qbar_y(const Inst* d_insts, int count, int max_sx, cudaStream_t st);
 void launch_q_times_g(const Inst* d_inst, const Inst& h, int use_qf, double* out, cudaStream_t st);
@@ -75,6 +84,10 @@ void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int 
 // is the launch predicate that picks the instances of the solve)
 void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, cudaStream_t st);
 void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st);
+// The same with mv = Gamma'(Sigma_x Gamma v) summed from the float-float
+// partials of the preceding Gamma' product (launched with kFuseNoSum).
+void launch_pcg_matvec_ff(const Inst* d_insts, int count, int max_n, int splits, int mode, int sel,
+                          cudaStream_t st);
 void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st);
 void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st);
 void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st);

@@ -9,6 +9,7 @@
 // every later step of the iteration is skipped.
 #include "common.cuh"
 #include "kernels.h"
+#include "gamma_ff.cuh"
 
 namespace lqmpc {
 
@@ -437,7 +438,11 @@ __global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int f
     }
     __syncthreads();
     const double be = beta_sh;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) I.pp[k] = __ldcg(z + k) + (be != 0.0 ? be * I.pp[k] : 0.0);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const double pk = __ldcg(z + k) + (be != 0.0 ? be * I.pp[k] : 0.0);
+        I.pp[k] = pk;
+        split_ff(pk, I.ffv[k], I.ffv[n + k]);   // the next float-float Gamma p needs no split launch
+    }
 }
 
 // Solve L L' x = b for one right-hand side per instance (one CTA each).  The

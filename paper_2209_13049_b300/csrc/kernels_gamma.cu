@@ -10,6 +10,7 @@
 // through TMA coordinates.
 #include "common.cuh"
 #include "kernels.h"
+#include "gamma_ff.cuh"
 
 #include <algorithm>
 
@@ -228,12 +229,8 @@ __device__ __forceinline__ void ff_mac(float& sh, float& sl, float ah, float al,
     sl += t + e;
 }
 
-__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
-    h = (float)v;
-    l = (float)(v - (double)h);
-}
 
-constexpr int kFfBM = 64, kFfBN = 16, kFfBK = 32, kFfThreads = 128, kFfMaxSplits = 16;
+constexpr int kFfBM = 64, kFfBN = 16, kFfBK = 32, kFfThreads = 128;
 constexpr int kFfLdT = kFfBK + 4;   // row stride of the transposed-product G tile (16-byte rows)
 
 // 16-byte asynchronous global -> shared copy (zero-filled when !valid).
@@ -333,7 +330,10 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     (void)out_role;
 }
 
-__global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, int flags, int splits) {
+// out = sum of the split partials; with kFuseOutW also the float-float split
+// of Sigma_x out (the operand of a following Gamma' (Sigma_x .)), with
+// kFuseOutDxs also a copy into dxs.
+__global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, int flags, int splits, int fuse) {
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     double* out = role_ptr(I, out_role);
@@ -342,6 +342,13 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
 #pragma unroll 4
         for (int q = 0; q < splits; ++q) s += I.gpart[(size_t)q * I.SX + k];
         out[k] = s;
+        if (fuse & kFuseOutDxs) I.dxs[k] = s;
+        if (fuse & kFuseOutW) {
+            float h, l;
+            split_ff(s * I.sigx[k], h, l);
+            I.ffw[k] = h;
+            I.ffw[(size_t)I.SX + k] = l;
+        }
     }
 }
 
@@ -475,29 +482,16 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         }
 }
 
-// out[t nu + c] = sum_split sum_{d=0}^{N-1-t} P[(N-1-d) nu + c, t + d]; one
-// warp per output, lanes over the contiguous d run of each split, then a
-// fixed-order warp reduction.
+// Gamma' w from the split partials: one warp per output.
 template <int NV>
 __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags,
                                    int splits) {
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
-    const int nu = I.nu, N = I.N, n = I.n, NR = NV * N;
-    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < NV * n; q += gridDim.x * wpb) {
-        const int vec = q / n, j = q % n, t = j / nu, c = j % nu;
-        const int nd = N - t;
-        const double* base = I.gpart + (((size_t)vec * N + t) * nu + c) * N;
-        double s0 = 0.0, s1 = 0.0;
-#pragma unroll 4
-        for (int sp = 0; sp < splits; ++sp) {
-            const double* src = base + (size_t)sp * NR * n;
-            if (lane < nd) s0 += src[lane];
-            if (lane + 32 < nd) s1 += src[lane + 32];
-            for (int d = lane + 64; d < nd; d += 32) s0 += src[d];
-        }
-        double s = warp_sum(s0 + s1);
+        const int vec = q / n, j = q % n;
+        const double s = gamma_tmv_ff_gather(I, NV, vec, j, splits);
         if (lane == 0) (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
     }
 }
@@ -605,32 +599,40 @@ static int ff_splits(int tiles, int nk) {
 }
 
 void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
-                        int out_role, int flags, cudaStream_t st) {
+                        int out_role, int flags, cudaStream_t st, int fuse) {
     const int tiles = ((max_ns + kFfBM - 1) / kFfBM) * ((max_N + kFfBN - 1) / kFfBN);
     const int splits = ff_splits(tiles * count, (max_n + kFfBK - 1) / kFfBK);
-    LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
+    if (!(fuse & kFuseInSplit))
+        LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
     LQ_LAUNCH(k_gamma_mv_ff<<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
     int nb = (max_ns * max_N + 255) / 256;
     nb = nb > 4096 ? 4096 : nb;
-    LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits));
+    LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits, fuse));
+}
+
+int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV) {
+    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
+    return ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
 }
 
 void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
-                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st) {
+                         int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st, int fuse) {
     const int NV = w1_role != R_NONE ? 2 : 1;
     const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
-    const int splits = ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
+    const int splits = gamma_tmv_ff_splits(count, max_ns, max_N, max_n, NV);
     int nb = (NV * max_n + 1) / 2;   // two warps (two outputs) per CTA: every SM takes part
     nb = nb > 8192 ? 8192 : nb;
     int npre = (max_ns * max_N + 255) / 256;
     npre = npre > 4096 ? 4096 : npre;
-    LQ_LAUNCH(k_ff_prep_w<<<dim3(npre, count), 256, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
+    if (!(fuse & kFuseInSplit))
+        LQ_LAUNCH(k_ff_prep_w<<<dim3(npre, count), 256, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
     if (NV == 2) {
         LQ_LAUNCH(k_gamma_tmv_ff<2><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags, splits));
         LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));
     } else {
         LQ_LAUNCH(k_gamma_tmv_ff<1><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags, splits));
-        LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
+        if (!(fuse & kFuseNoSum))
+            LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
     }
 }
 

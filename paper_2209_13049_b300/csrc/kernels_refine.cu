@@ -16,6 +16,7 @@
 // number of steps and any batch.
 #include "common.cuh"
 #include "kernels.h"
+#include "gamma_ff.cuh"
 
 namespace lqmpc {
 
@@ -81,6 +82,56 @@ __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) 
     for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) {
         const double v = __ldcg(I.part + 6 * kMaxParts + p);
         m = mode == 0 ? fmax(m, v) : m + v;
+    }
+    m = mode == 0 ? block_reduce<1>(m, red) : block_reduce<0>(m, red);
+    if (threadIdx.x == 0) {
+        if (mode == 0) pcg_test(I, m);
+        else pcg_alpha(I, m);
+    }
+}
+
+// k_pcg_matvec with mv_j gathered from the float-float Gamma' partials (no
+// separate sum launch) and the row of H read with four loads in flight.
+// In the conjugate-gradient steps the last CTA's tail also leaves nothing
+// else to do: alpha is formed there as in k_pcg_matvec.
+__global__ void k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int sel, int splits) {
+    __shared__ double red[32];
+    const Inst& I = insts[blockIdx.y];
+    if (pcg_skip(I, sel)) return;
+    const double* v = mode == 0 ? I.du : I.pp;
+    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    double acc_red = 0.0;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
+        const double* hc = I.H64 + (size_t)j * n;
+        double a4[4] = {0.0, 0.0, 0.0, 0.0};
+        int k = lane;
+#pragma unroll 2
+        for (; k + 96 < n; k += 128) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a4[u] += hc[k + 32 * u] * v[k + 32 * u];
+        }
+        for (; k < n; k += 32) a4[0] += hc[k] * v[k];
+        const double hv = warp_sum((a4[0] + a4[1]) + (a4[2] + a4[3]));
+        const double mvj = gamma_tmv_ff_gather(I, 1, 0, j, splits);
+        if (lane == 0) {
+            const double mj = hv + mvj + I.sigu[j] * v[j];
+            if (mode == 0) {
+                const double r = I.b[j] - mj;
+                I.rho[j] = r;
+                acc_red = fmax(acc_red, fabs(r));
+            } else {
+                I.qq[j] = mj;
+                acc_red += v[j] * mj;
+            }
+        }
+    }
+    double t = mode == 0 ? block_reduce<1>(acc_red, red) : block_reduce<0>(acc_red, red);
+    if (threadIdx.x == 0) I.part[6 * kMaxParts + blockIdx.x] = t;
+    if (!last_arrival(I.sc)) return;
+    double m = 0.0;
+    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) {
+        const double w = __ldcg(I.part + 6 * kMaxParts + p);
+        m = mode == 0 ? fmax(m, w) : m + w;
     }
     m = mode == 0 ? block_reduce<1>(m, red) : block_reduce<0>(m, red);
     if (threadIdx.x == 0) {
@@ -220,6 +271,13 @@ void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int 
     int wpb = 8;
     int nb = nblk(max_n, wpb, kMaxParts);
     LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel));
+}
+
+void launch_pcg_matvec_ff(const Inst* d_insts, int count, int max_n, int splits, int mode, int sel,
+                          cudaStream_t st) {
+    const int wpb = 2;   // two rows per CTA: every SM takes part
+    const int nb = nblk(max_n, wpb, kMaxParts);
+    LQ_LAUNCH(k_pcg_matvec_ff<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel, splits));
 }
 
 void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) {

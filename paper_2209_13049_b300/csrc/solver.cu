@@ -387,14 +387,34 @@ enum SegKey {
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
 // FP64 path, float-float on the FP32 pipes for the mixed-precision paths.
-void gmv(const Batch& b, int in, int out, int flags) {
-    if (b.ff) launch_gamma_mv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, in, out, flags, b.st);
+// (fuse: kFuse* options, float-float path only)
+void gmv(const Batch& b, int in, int out, int flags, int fuse = 0) {
+    if (b.ff) launch_gamma_mv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, in, out, flags, b.st, fuse);
     else launch_gamma_mv(b.d_insts, b.count, b.max_ns, b.max_N, in, out, flags, b.st);
 }
 
-void gtmv(const Batch& b, int w0, int w1, int o0, int o1, int scale0, int flags) {
-    if (b.ff) launch_gamma_tmv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st);
+void gtmv(const Batch& b, int w0, int w1, int o0, int o1, int scale0, int flags, int fuse = 0) {
+    if (b.ff) launch_gamma_tmv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st, fuse);
     else launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st);
+}
+
+// M v for the conjugate gradients: Gamma v into tmpx (and dxs when
+// to_dxs), then mv = Gamma'(Sigma_x tmpx) and the H and Sigma_u terms (mode
+// 0: residual of du, 1: q = M p).  On the float-float path the Sigma_x
+// scaling and split ride on the Gamma v sum, the Gamma' sum on the matvec,
+// and a direction p split by the preconditioner needs no split launch.
+void pcg_apply_m(const Batch& b, int in, int mode, int sel, int selr, bool to_dxs, bool in_split) {
+    if (b.ff) {
+        const int splits = gamma_tmv_ff_splits(b.count, b.max_ns, b.max_N, b.max_n, 1);
+        gmv(b, in, R_TMPX, selr, kFuseOutW | (to_dxs ? kFuseOutDxs : 0) | (in_split ? kFuseInSplit : 0));
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr, kFuseInSplit | kFuseNoSum);
+        launch_pcg_matvec_ff(b.d_insts, b.count, b.max_n, splits, mode, sel, b.st);
+    } else {
+        gmv(b, in, R_TMPX, selr);
+        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
+        if (to_dxs) launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, sel, b.st);
+        launch_pcg_matvec(b.d_insts, b.count, b.max_n, mode, sel, b.st);
+    }
 }
 
 void batch_dims(Batch& b) {
@@ -541,19 +561,14 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, b.st);
         prec(R_B, R_DU, sel);
         // initial residual r = b - M du and Gamma du
-        gmv(b, R_DU, R_TMPX, selr);
-        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_TMPX, R_DXS, 0, sel, b.st);
-        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 0, sel, b.st);
+        pcg_apply_m(b, R_DU, 0, sel, selr, true, false);
         prec(R_RHO, R_DCORR, selr, 1);
     });
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
     // the new direction (harmless after the last step: every kernel is
     // predicated on the instance's refinement flags)
     auto step = [&](bool with_next) {
-        gmv(b, R_P, R_TMPX, selr);
-        gtmv(b, R_TMPX, R_NONE, R_MV, R_NONE, 1, selr);
-        launch_pcg_matvec(b.d_insts, b.count, b.max_n, 1, sel, b.st);
+        pcg_apply_m(b, R_P, 1, sel, selr, false, !prec64);   // p split by the FP32 preconditioner
         launch_pcg_step_update(b.d_insts, b.count, b.max_total, sel, b.st);
         if (!with_next) return;
         prec(R_RHO, R_DCORR, selr, 2);
