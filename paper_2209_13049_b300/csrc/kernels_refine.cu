@@ -9,7 +9,8 @@
 // stationary iteration to contract.  Gamma du is accumulated alongside
 // (dxs += alpha Gamma p) so the step recovery needs no extra product.
 //
-// Stop: ||r||_inf <= refine_tol ||b||_inf, or <= 0.01 tol (1 + ||h||_inf) (the
+// Stop: ||r||_inf <= refine_tol ||b||_inf, or <= 1e-4 res (1 + ||h||_inf) (the
+// inexact-Newton forcing term, see pcg_test), or <= 0.01 tol (1 + ||h||_inf) (the
 // stationarity residual left behind is then far below the stop test).
 // Failure: a non-positive curvature p'Mp or a non-finite value.  Every kernel
 // is predicated on the instance flags, so one launch sequence serves any
@@ -140,13 +141,22 @@ __global__ void k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int se
     }
 }
 
-// Convergence test on the residual norm.
+// Convergence test on the residual norm.  Besides the relative and absolute
+// tolerances, an inexact-Newton forcing term: the residual of the Newton
+// system need only be small next to the interior-point residual it is to
+// reduce, ||r|| <= 1e-4 res (1 + ||h||) with res = max(res_d, res_p, mu) of
+// the current iterate (zero outside an interior-point solve).  Early
+// iterations then stop at the preconditioner's own solution; as res falls
+// to the stop tolerance this meets the absolute floor.
+constexpr double kForcing = 1e-4;
 __device__ void pcg_test(const Inst& I, double rn) {
     Scal* S = I.sc;
     S->rnorm = rn;
     if (!(rn == rn)) { S->refine_fail = 1; return; }
-    const double floor_abs = 0.01 * S->tol * (1.0 + S->hnorm);
-    if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || S->rnorm0 == 0.0) S->refine_ok = 1;
+    const double scale = 1.0 + S->hnorm;
+    const double floor_abs = 0.01 * S->tol * scale;
+    const double forcing = kForcing * S->res * scale;
+    if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || rn <= forcing || S->rnorm0 == 0.0) S->refine_ok = 1;
     else if (S->refine_cur >= S->refine_budget) S->refine_fail = 1;
 }
 

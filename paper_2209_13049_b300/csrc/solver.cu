@@ -735,6 +735,21 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
         });
         cudaEventRecord(c0->ev[2], b.st);
+        // An FP64 formation is costly even for instances it then skips: when
+        // one is ahead, take the stop test's outcome to the host first.
+        {
+            bool fp64_ahead = false;
+            for (auto* c : b.ctxs)
+                if (!c->h_scal->done && c->h_scal->prec_cur == LQMPC_FP64) fp64_ahead = true;
+            if (fp64_ahead) {
+                lqmpc_status st = read_scals(b);
+                if (st != LQMPC_OK) return st;
+                bool all_done = true;
+                for (auto* c : b.ctxs)
+                    if (!c->h_scal->done) all_done = false;
+                if (all_done) break;
+            }
+        }
         // FP64 solves get a refinement step once mu is within 1e3 of the stop
         // tolerance (the mu of the latest host read)
         bool polish = false;
