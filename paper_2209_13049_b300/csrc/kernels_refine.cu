@@ -149,6 +149,7 @@ __global__ void k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int se
 // iterations then stop at the preconditioner's own solution; as res falls
 // to the stop tolerance this meets the absolute floor.
 constexpr double kForcing = 1e-4;
+constexpr int kProjectAfter = 8;   // steps before the contraction rate is trusted
 __device__ void pcg_test(const Inst& I, double rn) {
     Scal* S = I.sc;
     S->rnorm = rn;
@@ -156,8 +157,18 @@ __device__ void pcg_test(const Inst& I, double rn) {
     const double scale = 1.0 + S->hnorm;
     const double floor_abs = 0.01 * S->tol * scale;
     const double forcing = kForcing * S->res * scale;
-    if (rn <= S->refine_tol * S->rnorm0 || rn <= floor_abs || rn <= forcing || S->rnorm0 == 0.0) S->refine_ok = 1;
-    else if (S->refine_cur >= S->refine_budget) S->refine_fail = 1;
+    const double target = fmax(S->refine_tol * S->rnorm0, fmax(floor_abs, forcing));
+    if (rn <= target || S->rnorm0 == 0.0) {
+        S->refine_ok = 1;
+    } else if (S->refine_cur >= S->refine_budget) {
+        S->refine_fail = 1;
+    } else if (S->refine_cur >= kProjectAfter) {
+        // Hopeless runs stop early: at the mean contraction so far the
+        // target would take more than the step budget.
+        const double k = S->refine_cur, got = log(rn / S->rnorm0);
+        const double need = got < 0.0 ? k * log(target / rn) / got : INFINITY;
+        if (k + need > S->refine_budget) S->refine_fail = 1;
+    }
 }
 
 // p = z, rz = r'z (one block per instance).
