@@ -573,9 +573,18 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         if (!with_next) return;
         prec(R_RHO, R_DCORR, selr, 2);
     };
-    // The host looks at the flags after every second step and stops launching
-    // once every unfinished instance has converged or failed.
-    for (int s = 0; s < refine_max;) {
+    // The host looks at the flags after the initial residual and after every
+    // second step, and stops launching once every unfinished instance has
+    // converged or failed (one read per look; the last one leaves each h_scal
+    // holding the outcome).
+    auto pending = [&]() {
+        for (auto* c : b.ctxs)
+            if (host_selected(*c->h_scal, selr) && !c->h_scal->info) return true;
+        return false;
+    };
+    lqmpc_status st = read_scals(b);
+    if (st != LQMPC_OK) return st;
+    for (int s = 0; s < refine_max && pending();) {
         if (s + 2 <= refine_max) {
             seg_run(b, SEG_PCG2 + kp, [&]() { step(true); step(true); });
             s += 2;
@@ -583,15 +592,10 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
             step(false);
             s += 1;
         }
-        if (s >= refine_max) break;
-        lqmpc_status st = read_scals(b);
+        st = read_scals(b);
         if (st != LQMPC_OK) return st;
-        bool pending = false;
-        for (auto* c : b.ctxs)
-            if (host_selected(*c->h_scal, selr) && !c->h_scal->info) pending = true;
-        if (!pending) break;
     }
-    return read_scals(b);
+    return LQMPC_OK;
 }
 
 constexpr double kWarmSlackFloor = 1e-2;   // warm start: s0 = max(slack, 1e-2)
@@ -636,6 +640,7 @@ void write_scal(Batch& b, lqmpc_ctx* c) {
 // precision: one instance's trouble does not move a whole batch to FP64.
 lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* tm, bool& polish) {
     launch_kkt_begin(b.d_insts, b.count, b.st);
+    for (auto* c : b.ctxs) c->h_scal->kkt_pending = c->h_scal->done ? 0 : 1;   // the same on the host copy
     const int budget_lo = std::min(o.refine_max, kLowPrecSteps);
     for (int round = 0; round < 4; ++round) {
         int present = 0;   // precisions among the pending instances
@@ -691,9 +696,13 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
             lqmpc_status st = kkt_solve_mixed(b, o.refine_max, false, F_PENDING | prec_sel(0xE), budget_lo);
             if (st != LQMPC_OK) return st;
         }
+        // settle on the device and, from the host copies the solves just read
+        // (or that no solve since has changed), the same decision here
         launch_kkt_settle(b.d_insts, b.count, b.st);
-        lqmpc_status st = read_scals(b);
-        if (st != LQMPC_OK) return st;
+        for (auto* c : b.ctxs) {
+            Scal& S = *c->h_scal;
+            if (!S.done && S.kkt_pending && !S.info && (S.prec_cur == LQMPC_FP64 || S.refine_ok)) S.kkt_pending = 0;
+        }
         for (auto* c : b.ctxs) {
             Scal& S = *c->h_scal;
             if (S.done || !S.kkt_pending) continue;
