@@ -107,9 +107,6 @@ struct Inst {
     double* ldiag;                    // 2 x 32 x 32: factored diagonal blocks in flight (cooperative potrf)
     float* ffw;                       // 4 x SX: float-float split of the Gamma' operands (hi0, lo0, hi1, lo1)
     float* ffv;                       // 2 x n: float-float split of the Gamma operand (hi, lo)
-    // FP64 KKT formation by the backward recursion (sparse A); lyP == nullptr: not used
-    double* lyP; double* lyT;         // ns x ns each
-    double* lyW;                      // N x ns x nu
     const int* at_ptr; const int* at_idx; const double* at_val;   // A' in CSR (the columns of A)
     const int* bc_ptr; const int* bc_idx; const double* bc_val;   // nonzeros of B per column
     float* XinvT32;                   // its transpose (coalesced rows)

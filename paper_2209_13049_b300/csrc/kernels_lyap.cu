@@ -1,129 +1,90 @@
-// FP64 condensed KKT matrix (Eq. 7) by a backward recursion over the
-// horizon instead of the SYRK, for plants whose A is sparse.
+// FP64 condensed KKT matrix (Eq. 7) for plants whose A is sparse, without
+// the SYRK: Horner chains over the horizon, one per block column.
 //
-// With Gamma's blocks A^k B (Section II), block (c1, c) of Gamma' Sigma_x
-// Gamma for c1 <= c is
-//     sum_{r >= c} (A^{r-c1} B)' Sigma_r A^{r-c} B = (A^{c-c1} B)' P_c B,
-//     P_c = sum_{r >= c} (A^{r-c})' Sigma_r A^{r-c},
-// and P satisfies P_{N-1} = Sigma_{N-1}, P_c = Sigma_c + A' P_{c+1} A.  So the
-// matrix costs N products A' P A with a sparse A (2 nnz(A) ns multiply-adds
-// each) plus the blocks G_d' W_c with W_c = P_c B, instead of the SYRK's
-// ns nu^2 N^3 / 6: about 3x fewer FP64 operations for the 2-D heat plants
-// (FP64 runs at 1/64 of the FP32 rate on this part).  The same matrix up to
-// rounding order.
+// With Gamma's blocks G_d = A^d B (Section II), block (c1, c) of
+// Gamma' Sigma_x Gamma for c1 <= c is
+//     sum_{r >= c} (A^{r-c1} B)' Sigma_r A^{r-c} B = B' (A')^{c-c1} W_c,
+//     W_c = sum_{d >= 0} (A')^d Sigma_{c+d} G_d.
+// Column `col` of W_c comes from Horner's scheme backwards in d,
+//     z <- Sigma_{N-1} G_{N-1-c}[:, col];  z <- A' z + Sigma_{c+d} G_d[:, col]  (d = N-2-c .. 0),
+// and then z <- A' z walks c1 = c-1 .. 0, each z giving the entries
+// B' z of column `col` of block (c1, c).  One CTA per (c, col): N sparse
+// products A' z per CTA (2 nnz(A) flop each), no ns x ns intermediates and no
+// dense products with the G-stack: N^2 nu nnz(A) + N(N+1)/2 nu (ns + nnz(B))
+// multiply-adds, ~15x fewer FP64 operations than the SYRK and ~4x fewer than
+// the recursion P_c = Sigma_c + A' P_{c+1} A with its block products G_d' W_c,
+// for the 2-D heat plants (FP64 runs at 1/64 of the FP32 rate on this part).
+// The same matrix up to rounding order.
 //
-// Layout: P and T are ns x ns column-major FP64; W holds W_c for every stage
-// (N x ns x nu).  A' is available as CSR (the columns of A); B's nonzeros as
-// per-column lists.  For batches the stage loop runs over the largest horizon
-// and instance q uses its own stage c = N_q - 1 - g.
+// A' is available as CSR (the columns of A); B's nonzeros as per-column
+// lists.  For batches blockIdx.x runs over the largest (N, nu) and CTAs
+// outside an instance's own sizes return.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace lqmpc {
 
-// g = 0: P = diag(Sigma_{N-1}).
-__global__ void k_ly_init(const Inst* __restrict__ insts, int flags) {
+__global__ void k_ly_chain(const Inst* __restrict__ insts, int flags, int max_nu, double shift) {
     const Inst& I = insts[blockIdx.y];
-    if (skip_instance(I, flags) || !I.lyP) return;
-    const int ns = I.ns;
-    const double* sg = I.sigx + (size_t)(I.N - 1) * ns;
-    const size_t total = (size_t)ns * ns;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q % ns), j = (int)(q / ns);
-        I.lyP[q] = i == j ? sg[i] : 0.0;
-    }
-}
-
-// T = P A: T[:, j] = sum over the nonzeros A[k, j] of P[:, k] A[k, j].
-__global__ void k_ly_pa(const Inst* __restrict__ insts, int flags, int g) {
-    const Inst& I = insts[blockIdx.y];
-    if (skip_instance(I, flags) || !I.lyP || I.N - 1 - g < 0) return;
-    const int ns = I.ns;
-    const size_t total = (size_t)ns * ns;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q % ns), j = (int)(q / ns);
-        double acc = 0.0;
-        for (int p = I.at_ptr[j]; p < I.at_ptr[j + 1]; ++p) acc += I.lyP[i + (size_t)ns * I.at_idx[p]] * I.at_val[p];
-        I.lyT[q] = acc;
-    }
-}
-
-// P = A' T + diag(Sigma_c): P[i, j] = sum over the nonzeros A[k, i] of A[k, i] T[k, j].
-__global__ void k_ly_atp(const Inst* __restrict__ insts, int flags, int g) {
-    const Inst& I = insts[blockIdx.y];
-    const int c = I.N - 1 - g;
-    if (skip_instance(I, flags) || !I.lyP || c < 0) return;
-    const int ns = I.ns;
-    const double* sg = I.sigx + (size_t)c * ns;
-    const size_t total = (size_t)ns * ns;
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(q % ns), j = (int)(q / ns);
-        double acc = i == j ? sg[i] : 0.0;
-        for (int p = I.at_ptr[i]; p < I.at_ptr[i + 1]; ++p) acc += I.at_val[p] * I.lyT[I.at_idx[p] + (size_t)ns * j];
-        I.lyP[q] = acc;
-    }
-}
-
-// W_c = P_c B from B's per-column nonzero lists.
-__global__ void k_ly_w(const Inst* __restrict__ insts, int flags, int g) {
-    const Inst& I = insts[blockIdx.y];
-    const int c = I.N - 1 - g;
-    if (skip_instance(I, flags) || !I.lyP || c < 0) return;
-    const int ns = I.ns, nu = I.nu;
-    double* W = I.lyW + (size_t)c * ns * nu;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ns * nu; q += gridDim.x * blockDim.x) {
-        const int i = q % ns, b = q / ns;
-        double acc = 0.0;
-        for (int p = I.bc_ptr[b]; p < I.bc_ptr[b + 1]; ++p) acc += I.lyP[i + (size_t)ns * I.bc_idx[p]] * I.bc_val[p];
-        W[q] = acc;
-    }
-}
-
-// M = H + [G_{c-c1}' W_c] + diag(Sigma_u): one block (c1 <= c) per CTA,
-// nu x nu outputs over the threads, states strided; both triangles written.
-__global__ void k_ly_assemble(const Inst* __restrict__ insts, int flags, double shift) {
-    const Inst& I = insts[blockIdx.y];
-    if (skip_instance(I, flags) || !I.lyP) return;
-    const int ns = I.ns, nu = I.nu, N = I.N, n = I.n;
-    const int npairs = N * (N + 1) / 2;
-    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-        int c = 0;
-        while ((c + 1) * (c + 2) / 2 <= pr) ++c;
-        const int c1 = pr - c * (c + 1) / 2;    // c1 <= c
-        const int d = c - c1;
-        const double* W = I.lyW + (size_t)c * ns * nu;
-        for (int o = threadIdx.x; o < nu * nu; o += blockDim.x) {
-            const int a = o % nu, b = o / nu;
-            const double* Ga = I.G64 + (size_t)I.ldg * ((N - 1 - d) * nu + a);
-            const double* Wb = W + (size_t)b * ns;
-            double acc = 0.0;
-            for (int i = 0; i < ns; ++i) acc += Ga[i] * Wb[i];
-            const int row = c1 * nu + a, col = c * nu + b;
-            double v = acc + I.H64[(size_t)row + (size_t)n * col];
-            if (row == col) v = (v + I.sigu[row]) * (1.0 + shift);   // shift: a retried factor
-            I.M64[(size_t)row + (size_t)n * col] = v;
-            if (row != col) I.M64[(size_t)col + (size_t)n * row] = v;
+    if (skip_instance(I, flags)) return;
+    const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
+    const int c = blockIdx.x / max_nu, col = blockIdx.x % max_nu;
+    if (c >= N || col >= nu) return;
+    extern __shared__ double zs[];
+    double* z0 = zs;
+    double* z1 = zs + ns;
+    // z = A' z_old + Sigma_{c+d} G_d[:, col]  (scaled term only when d >= 0)
+    auto step = [&](const double* zin, double* zout, int d) {
+        const double* sg = d >= 0 ? I.sigx + (size_t)(c + d) * ns : nullptr;
+        const double* g = d >= 0 ? I.G64 + (size_t)ldg * ((N - 1 - d) * nu + col) : nullptr;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            double acc = sg ? sg[i] * g[i] : 0.0;
+            for (int p = I.at_ptr[i]; p < I.at_ptr[i + 1]; ++p) acc += I.at_val[p] * zin[I.at_idx[p]];
+            zout[i] = acc;
         }
+        __syncthreads();
+    };
+    // W_c[:, col]
+    {
+        const int d = N - 1 - c;
+        const double* sg = I.sigx + (size_t)(N - 1) * ns;
+        const double* g = I.G64 + (size_t)ldg * ((N - 1 - d) * nu + col);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) z0[i] = sg[i] * g[i];
+        __syncthreads();
     }
-}
-
-static int ly_blocks(size_t work) {
-    size_t b = (work + 255) / 256;
-    return (int)(b > 8192 ? 8192 : (b < 1 ? 1 : b));
+    for (int d = N - 2 - c; d >= 0; --d) {
+        step(z0, z1, d);
+        double* t = z0; z0 = z1; z1 = t;
+    }
+    // blocks (c1, c), c1 = c .. 0: entries B' z, one warp per row a of the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c1 = c; c1 >= 0; --c1) {
+        if (c1 < c) {
+            step(z0, z1, -1);
+            double* t = z0; z0 = z1; z1 = t;
+        }
+        for (int a = warp; a < nu; a += nw) {
+            double s = 0.0;
+            for (int p = I.bc_ptr[a] + lane; p < I.bc_ptr[a + 1]; p += 32) s += I.bc_val[p] * z0[I.bc_idx[p]];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const int row = c1 * nu + a, cc = c * nu + col;
+                double v = s + I.H64[(size_t)row + (size_t)n * cc];
+                if (row == cc) v = (v + I.sigu[row]) * (1.0 + shift);   // shift: a retried factor
+                I.M64[(size_t)row + (size_t)n * cc] = v;
+                if (c1 < c) I.M64[(size_t)cc + (size_t)n * row] = v;
+            }
+        }
+        // the next step overwrites the other buffer only; the dots above read
+        // z0, which the step after it overwrites behind a barrier
+    }
 }
 
 void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int flags,
                      cudaStream_t st, double shift) {
-    const size_t sq = (size_t)max_ns * max_ns;
-    LQ_LAUNCH(k_ly_init<<<dim3(ly_blocks(sq), count), 256, 0, st>>>(d_insts, flags));
-    LQ_LAUNCH(k_ly_w<<<dim3(ly_blocks((size_t)max_ns * max_nu), count), 256, 0, st>>>(d_insts, flags, 0));
-    for (int g = 1; g < max_N; ++g) {
-        LQ_LAUNCH(k_ly_pa<<<dim3(ly_blocks(sq), count), 256, 0, st>>>(d_insts, flags, g));
-        LQ_LAUNCH(k_ly_atp<<<dim3(ly_blocks(sq), count), 256, 0, st>>>(d_insts, flags, g));
-        LQ_LAUNCH(k_ly_w<<<dim3(ly_blocks((size_t)max_ns * max_nu), count), 256, 0, st>>>(d_insts, flags, g));
-    }
-    const int npairs = max_N * (max_N + 1) / 2;
-    LQ_LAUNCH(k_ly_assemble<<<dim3(npairs < 4096 ? npairs : 4096, count), 128, 0, st>>>(d_insts, flags, shift));
+    const size_t smem = 2 * sizeof(double) * (size_t)max_ns;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_ly_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LQ_LAUNCH(k_ly_chain<<<dim3(max_N * max_nu, count), 256, smem, st>>>(d_insts, flags, max_nu, shift));
 }
 
 // Multiply-add counts of the two ways to form Gamma' Sigma Gamma (the SYRK
@@ -133,7 +94,7 @@ double kkt_cost_syrk(int ns, int nu, int N) {
 }
 
 double kkt_cost_lyap(int ns, int nu, int N, long long nnzA, long long nnzB) {
-    return (double)N * (2.0 * (double)nnzA * ns + (double)nnzB * ns) + 0.5 * N * (N + 1.0) * nu * nu * ns;
+    return (double)N * N * nu * (double)nnzA + 0.5 * N * (N + 1.0) * nu * (double)(ns + nnzB);
 }
 
 }  // namespace lqmpc

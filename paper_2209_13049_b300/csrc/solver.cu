@@ -152,7 +152,7 @@ struct lqmpc_ctx {
     double t_tc = 0, t_cc = 0, t_cc64 = 0, t_tc3 = 0, t_pf = 0;
     int n_tc = 0, n_cc = 0, n_cc64 = 0, n_tc3 = 0, n_pf = 0;
     lqmpc::GraphCache* graphs = nullptr;   // single-instance solves (d_inst is fixed)
-    bool lyap = false;                     // FP64 KKT matrix by the backward recursion
+    bool lyap = false;                     // FP64 KKT matrix by the Horner chains (sparse A)
 };
 
 namespace {
@@ -212,15 +212,12 @@ bool csr_diag(int n, const int* ptr, const int* idx, const double* val, std::vec
 // Lay out every device array of an instance in one arena.
 template <bool kAssign>
 size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int max_iter,
-              int cc_splits, int tc_splits, int nnzB, bool lyap) {
+              int cc_splits, int tc_splits, int nnzB, bool /*lyap: no buffers of its own*/) {
     Carver c{base};
     const int ns = I.ns, nu = I.nu, n = I.n, SX = I.SX;
     const size_t G = (size_t)I.ldg * n;
     auto at_ptr = c.take<int>(ns + 1); auto at_idx = c.take<int>(nnzA); auto at_val = c.take<double>(nnzA);
     auto bc_ptr = c.take<int>(nu + 1); auto bc_idx = c.take<int>(nnzB); auto bc_val = c.take<double>(nnzB);
-    double* lyP = lyap ? c.take<double>((size_t)ns * ns) : nullptr;
-    double* lyT = lyap ? c.take<double>((size_t)ns * ns) : nullptr;
-    double* lyW = lyap ? c.take<double>((size_t)I.N * ns * nu) : nullptr;
     auto a_ptr = c.take<int>(ns + 1); auto a_idx = c.take<int>(nnzA); auto a_val = c.take<double>(nnzA);
     auto q_ptr = c.take<int>(ns + 1); auto q_idx = c.take<int>(nnzQ); auto q_val = c.take<double>(nnzQ);
     auto qf_ptr = c.take<int>(ns + 1); auto qf_idx = c.take<int>(nnzQf); auto qf_val = c.take<double>(nnzQf);
@@ -290,7 +287,6 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
         I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
-        I.lyP = lyP; I.lyT = lyT; I.lyW = lyW;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
         I.part = part; I.bar = bar; I.sc = sc; I.trace = trace; I.tc_plan = tc_plan;
@@ -311,7 +307,7 @@ struct Batch {
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
     double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
     int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster (autotuned)
-    bool lyap = false;              // FP64 formation by the backward recursion (every instance has its buffers)
+    bool lyap = false;              // FP64 formation by the Horner chains (every instance's A is sparse enough)
     int max_nu = 0;
 };
 
@@ -995,15 +991,14 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         bc_ptr[col + 1] = (int)bc_idx.size();
     }
     const int nnzB = (int)bc_idx.size();
-    // the recursion when it needs clearly fewer FP64 operations than the SYRK
-    // and its two ns x ns buffers stay modest; LQMPC_KKT64=syrk|lyap overrides
+    // the Horner chains when they need clearly fewer FP64 operations than the
+    // SYRK; LQMPC_KKT64=syrk|lyap overrides
     {
         const double cs = kkt_cost_syrk(ns, nu, N), cl = kkt_cost_lyap(ns, nu, N, nnzA, nnzB);
-        const double buf = 16.0 * ns * (double)ns;
-        ctx->lyap = cl < 0.6 * cs && buf <= 4e9;
+        ctx->lyap = cl < 0.6 * cs;
         if (const char* e = getenv("LQMPC_KKT64")) {
             if (!strcmp(e, "syrk")) ctx->lyap = false;
-            if (!strcmp(e, "lyap") && buf <= 4e9) ctx->lyap = true;
+            if (!strcmp(e, "lyap")) ctx->lyap = true;
         }
     }
     size_t bytes = layout<false>(I, nullptr, nnzA, nnzQ, nnzQf, o.max_iter, ctx->cc_splits, ctx->tc_splits, nnzB,

@@ -1,7 +1,7 @@
-"""The FP64 KKT matrix by the backward recursion over the horizon against
-the SYRK formation (child processes choose each with LQMPC_KKT64): the same
-matrix up to rounding order, so the same FP64 interior-point iterates and
-the oracle's optimum."""
+"""The FP64 KKT matrix by Horner chains over the horizon against the SYRK
+formation (child processes choose each with LQMPC_KKT64): the same matrix up
+to rounding order, so the same FP64 interior-point iterates and the oracle's
+optimum."""
 import json
 import os
 import subprocess
