@@ -393,17 +393,19 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
     const int NR = NV * N;
-    const int mt = (n + kFfBM - 1) / kFfBM, nt = (NR + kFfBN - 1) / kFfBN;
+    // r tiles per vector aligned to the horizon's end: the partial tile holds
+    // the first stages, whose useful columns are only the last few blocks
+    const int tpv = (N + kFfBN - 1) / kFfBN;
+    const int mt = (n + kFfBM - 1) / kFfBM, nt = NV * tpv;
     const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
     if (tile >= mt * nt) return;
-    const int c0 = (tile % mt) * kFfBM, rp0 = (tile / mt) * kFfBN;
+    const int rt = tile / mt, vec_t = rt / tpv;
+    const int c0 = (tile % mt) * kFfBM, r_lo = N - kFfBN * (rt % tpv + 1);   // rows r_lo .. r_lo + 15 (r >= 0)
     // skip tiles wholly in the unused triangle: need some col >= off_r
     {
         bool any = false;
-        for (int rp = rp0; rp < min(rp0 + kFfBN, NR) && !any; ++rp) {
-            const int r = rp % N;
+        for (int r = max(r_lo, 0); r < r_lo + kFfBN && !any; ++r)
             if (min(c0 + kFfBM, n) - 1 >= (N - 1 - r) * nu) any = true;
-        }
         if (!any) return;
     }
     (void)w0_role; (void)w1_role; (void)scale0;   // operands come split by k_ff_prep_w
@@ -423,13 +425,12 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         }
         for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
             const int rr = e / kFfBK, kk = e % kFfBK;
-            const int rp = rp0 + rr, i = i0 + kk;
+            const int r = r_lo + rr, i = i0 + kk;
             float h = 0.f, l = 0.f;
-            if (rp < NR && i < ns) {
-                const int vec = rp / N, r = rp % N;
+            if (r >= 0 && i < ns) {
                 const size_t q = (size_t)r * ns + i;
-                h = I.ffw[(size_t)(2 * vec) * I.SX + q];
-                l = I.ffw[(size_t)(2 * vec + 1) * I.SX + q];
+                h = I.ffw[(size_t)(2 * vec_t) * I.SX + q];
+                l = I.ffw[(size_t)(2 * vec_t + 1) * I.SX + q];
             }
             Ws[buf][0][kk][rr] = h;
             Ws[buf][1][kk][rr] = l;
@@ -474,10 +475,10 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            const int col = c0 + ty + 16 * a, rp = rp0 + tx + 8 * b;
-            if (col < n && rp < NR) {
-                const int vec = rp / N, r = rp % N, d = N - 1 - col / nu, c = col % nu, t = r - d;
-                if (t >= 0) part[(((size_t)vec * N + t) * nu + c) * N + d] = (double)sh[a][b] + (double)sl[a][b];
+            const int col = c0 + ty + 16 * a, r = r_lo + tx + 8 * b;
+            if (col < n && r >= 0) {
+                const int d = N - 1 - col / nu, c = col % nu, t = r - d;
+                if (t >= 0) part[(((size_t)vec_t * N + t) * nu + c) * N + d] = (double)sh[a][b] + (double)sl[a][b];
             }
         }
 }
@@ -611,14 +612,14 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
 }
 
 int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV) {
-    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
+    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * (NV * ((max_N + kFfBN - 1) / kFfBN));
     return ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
 }
 
 void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
                          int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st, int fuse) {
     const int NV = w1_role != R_NONE ? 2 : 1;
-    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * ((NV * max_N + kFfBN - 1) / kFfBN);
+    const int tiles = ((max_n + kFfBM - 1) / kFfBM) * (NV * ((max_N + kFfBN - 1) / kFfBN));
     const int splits = gamma_tmv_ff_splits(count, max_ns, max_N, max_n, NV);
     int nb = (NV * max_n + 1) / 2;   // two warps (two outputs) per CTA: every SM takes part
     nb = nb > 8192 ? 8192 : nb;
