@@ -254,8 +254,10 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     const int mt = (ns + kFfBM - 1) / kFfBM, nt = (N + kFfBN - 1) / kFfBN;
     const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
     if (tile >= mt * nt) return;
-    const int m0 = (tile % mt) * kFfBM, r0 = (tile / mt) * kFfBN;
-    const int r1 = min(r0 + kFfBN, N);
+    // r tiles aligned to the horizon's end (rows r0 .. r1-1, r0 may be
+    // negative): the partial tile holds the first stages, which need only the
+    // last columns
+    const int m0 = (tile % mt) * kFfBM, r1 = N - kFfBN * (tile / mt), r0 = r1 - kFfBN;
     const double* v = role_ptr(I, in_role);
     // columns needed by this r-tile: col >= off_{r1-1}
     const int kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
@@ -279,7 +281,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             const int kk = e / kFfBN, rr = e % kFfBN;
             const int col = c0 + kk, r = r0 + rr;
             float h = 0.f, l = 0.f;
-            if (col < n && r < N) {
+            if (col < n && r >= 0) {
                 const int t = col - (N - 1 - r) * nu;
                 if (t >= 0) { h = vsp[t]; l = vsp[n + t]; }
             }
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
-            if (i < ns && r < r1) part[(size_t)r * ns + i] = (double)sh[a][b] + (double)sl[a][b];
+            if (i < ns && r >= 0) part[(size_t)r * ns + i] = (double)sh[a][b] + (double)sl[a][b];
         }
     (void)out_role;
 }
