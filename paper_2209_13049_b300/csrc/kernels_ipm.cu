@@ -437,15 +437,15 @@ void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, i
 }
 
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
-                        cudaStream_t st, bool do_resid, bool do_rd) {
+                        cudaStream_t st, bool do_resid, bool do_rd, int rd_parts) {
     int nb1 = ew_blocks(max_total, 256);
     if (do_resid) LQ_LAUNCH(k_resid<<<dim3(nb1, count), 256, 0, st>>>(d_insts));
     int wpb = 8;
     int nb2 = (max_n + wpb - 1) / wpb;
     nb2 = nb2 > kMaxParts ? kMaxParts : nb2;
     if (do_rd) {
-        LQ_LAUNCH(k_rd<<<dim3(nb2, count), wpb * 32, 0, st>>>(d_insts));
-        LQ_LAUNCH(k_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb1, nb2, trace_on));
+        if (rd_parts & 1) LQ_LAUNCH(k_rd<<<dim3(nb2, count), wpb * 32, 0, st>>>(d_insts));
+        if (rd_parts & 2) LQ_LAUNCH(k_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb1, nb2, trace_on));
     }
 }
 

@@ -153,6 +153,10 @@ struct lqmpc_ctx {
     int n_tc = 0, n_cc = 0, n_cc64 = 0, n_tc3 = 0, n_pf = 0;
     lqmpc::GraphCache* graphs = nullptr;   // single-instance solves (d_inst is fixed)
     bool lyap = false;                     // FP64 KKT matrix by the Horner chains (sparse A)
+    // side stream: the residual head's Gamma' product and r_d run there while
+    // the context's stream forms and factors M (joined before the solves)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -309,6 +313,9 @@ struct Batch {
     int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster (autotuned)
     bool lyap = false;              // FP64 formation by the Horner chains (every instance's A is sparse enough)
     int max_nu = 0;
+    cudaStream_t side = nullptr;    // ctxs[0]'s side stream and events (nullptr: no overlap)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_pending = false;      // head work on the side stream not joined yet
 };
 
 // ---- autotuned launch shapes, keyed by batch signature (count and the
@@ -377,8 +384,8 @@ void seg_run(const Batch& b, int key, F&& body) {
 }
 
 enum SegKey {
-    SEG_HEAD = 1, SEG_FORM = 10 /* + precision */, SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31,
-    SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50
+    SEG_HEAD = 1, SEG_HEAD_R = 2, SEG_HEAD_SIDE = 3, SEG_HEAD_CHECK = 4, SEG_FORM = 10 /* + precision */,
+    SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31, SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50
 };
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
@@ -392,6 +399,34 @@ void gmv(const Batch& b, int in, int out, int flags, int fuse = 0) {
 void gtmv(const Batch& b, int w0, int w1, int o0, int o1, int scale0, int flags, int fuse = 0) {
     if (b.ff) launch_gamma_tmv_ff(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st, fuse);
     else launch_gamma_tmv(b.d_insts, b.count, b.max_ns, b.max_N, b.max_n, w0, w1, o0, o1, scale0, flags, b.st);
+}
+
+// The residual head split across streams: r_p and Sigma (k_resid) on the
+// solve's stream, then the Gamma' product and r_d / the right-hand side on
+// the side stream while the solve's stream forms and factors M; join_head
+// waits for the side stream and runs the stop test (which may finish an
+// instance: no kernel of the formation may see that change mid-launch).
+void head_fork(Batch& b) {
+    seg_run(b, SEG_HEAD_R, [&]() { launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false); });
+    cudaEventRecord(b.ev_fork, b.st);
+    cudaStreamWaitEvent(b.side, b.ev_fork, 0);
+    Batch bs = b;
+    bs.st = b.side;
+    seg_run(bs, SEG_HEAD_SIDE, [&]() {
+        gtmv(bs, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
+        launch_resid_check(bs.d_insts, bs.count, bs.max_total, bs.max_n, 1, bs.st, false, true, 1);
+    });
+    cudaEventRecord(b.ev_join, b.side);
+    b.side_pending = true;
+}
+
+void join_head(Batch& b) {
+    if (!b.side_pending) return;
+    cudaStreamWaitEvent(b.st, b.ev_join, 0);
+    seg_run(b, SEG_HEAD_CHECK, [&]() {
+        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true, 2);
+    });
+    b.side_pending = false;
 }
 
 // M v for the conjugate gradients: Gamma v into tmpx (and dxs when
@@ -431,6 +466,9 @@ void batch_dims(Batch& b) {
         b.tc_splits = b.tc_splits == (1 << 30) ? c->tc_splits : std::max(b.tc_splits, c->tc_splits);
     }
     b.st = b.ctxs[0]->stream;
+    b.side = b.ctxs[0]->side;
+    b.ev_fork = b.ctxs[0]->ev_fork;
+    b.ev_join = b.ctxs[0]->ev_join;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(batch_key(b));
     if (it != g_tune.end()) {
@@ -644,7 +682,10 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
             const Scal& S = *c->h_scal;
             if (!S.done && (round == 0 || S.kkt_pending)) present |= 1 << S.prec_cur;
         }
-        if (!present) return LQMPC_OK;
+        if (!present) {
+            join_head(b);
+            return LQMPC_OK;
+        }
         if (!formed || round > 0) {
             for (int p = 0; p < 4; ++p) {
                 if (!((present >> p) & 1)) continue;
@@ -662,6 +703,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
                 for (int a = 0; a < 3; ++a) {
                     if (a > 0 && p == LQMPC_FP64) polish = true;
                     kkt_form(b, p, tm, shifts[a], sel);
+                    join_head(b);
                     lqmpc_status st = read_scals(b);
                     if (st != LQMPC_OK) return st;
                     bool fail = false;
@@ -676,6 +718,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
                 }
             }
         }
+        join_head(b);
         if (present & 1) {
             const int sel = F_PENDING | prec_sel(1);
             if (!polish) {
@@ -725,6 +768,9 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     c0->t_tc = c0->t_cc = c0->t_cc64 = c0->t_tc3 = c0->t_pf = 0.0;
     c0->n_tc = c0->n_cc = c0->n_cc64 = c0->n_tc3 = c0->n_pf = 0;
     cudaEventRecord(c0->ev[0], b.st);
+    // whatever an earlier solve left on the side stream (an error return) is
+    // done before this one writes
+    if (b.side) cudaStreamWaitEvent(b.st, b.ev_join, 0);
     prepare(b, o);
     {
         lqmpc_status st = read_scals(b);   // host view of the initial per-instance state
@@ -734,18 +780,23 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     for (int it = 0; it <= o.max_iter; ++it) {
         SyrkTimer tm;
         // residuals, Sigma, stop test
-        seg_run(b, SEG_HEAD, [&]() {
-            launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
-            gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
-            launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
-        });
-        cudaEventRecord(c0->ev[2], b.st);
         // An FP64 formation is costly even for instances it then skips: when
-        // one is ahead, take the stop test's outcome to the host first.
+        // one is ahead, take the stop test's outcome to the host first
+        // (no overlap of the head with the formation then).
+        bool fp64_ahead = false;
+        for (auto* c : b.ctxs)
+            if (!c->h_scal->done && c->h_scal->prec_cur == LQMPC_FP64) fp64_ahead = true;
+        if (b.side && !fp64_ahead) {
+            head_fork(b);
+        } else {
+            seg_run(b, SEG_HEAD, [&]() {
+                launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
+                gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
+                launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
+            });
+        }
+        cudaEventRecord(c0->ev[2], b.st);
         {
-            bool fp64_ahead = false;
-            for (auto* c : b.ctxs)
-                if (!c->h_scal->done && c->h_scal->prec_cur == LQMPC_FP64) fp64_ahead = true;
             if (fp64_ahead) {
                 lqmpc_status st = read_scals(b);
                 if (st != LQMPC_OK) return st;
@@ -798,6 +849,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         }
         if (all_done) break;
     }
+    join_head(b);
     cudaEventRecord(c0->ev[1], b.st);
     lqmpc_status s = read_scals(b);
     if (s != LQMPC_OK) return s;
@@ -1017,6 +1069,10 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         if ((e < 4 && cudaEventCreate(&ctx->ev[e]) != cudaSuccess) || cudaEventCreate(&ctx->evk[e]) != cudaSuccess)
             return fail(LQMPC_ERR_CUDA);
     ctx->events = true;
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return fail(LQMPC_ERR_CUDA);
     cudaStream_t st = ctx->stream;
     auto up = [&](const void* dst, const void* src, size_t n) {
         return cudaMemcpyAsync((void*)dst, src, n, cudaMemcpyHostToDevice, st) == cudaSuccess;
@@ -1331,6 +1387,12 @@ void lqmpc_free(lqmpc_ctx* ctx) {
     cudaFree(ctx->d_inst);
     cudaFree(ctx->d_maps);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
