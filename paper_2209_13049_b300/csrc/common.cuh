@@ -153,7 +153,10 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
 // (or failed); F_PENDING skips instances whose KKT solve is settled; a
 // precision mask (bits 8-11, bit p for precision code p) keeps only the
 // instances currently at one of those precisions.
-enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2, F_PENDING = 4 };
+// F_N_LE_512 / F_N_GT_512 keep only the instances with n <= 512 / n > 512 (the
+// cluster Cholesky's limit: a batch then factors its small instances in
+// clusters and only its large ones with the grid-cooperative kernel).
+enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2, F_PENDING = 4, F_N_LE_512 = 16, F_N_GT_512 = 32 };
 __host__ __device__ constexpr int prec_sel(int mask) { return mask << 8; }
 
 __device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
@@ -162,6 +165,8 @@ __device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
     if ((flags & F_PENDING) && !I.sc->kkt_pending) return true;
     const int mask = (flags >> 8) & 15;
     if (mask && !((mask >> I.sc->prec_cur) & 1)) return true;
+    if ((flags & F_N_LE_512) && I.n > 512) return true;
+    if ((flags & F_N_GT_512) && I.n <= 512) return true;
     return false;
 }
 

@@ -601,14 +601,18 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
     // every SM with the cooperative kernel (measured faster for one n = 500
     // matrix: 0.37-0.50 ms FP32 against 0.53 ms for the cluster kernel, and
     // 1.16 ms against 1.95 ms in FP64, whose pipe rate makes 8 SMs too few).
-    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies, 2 dataflow
-    // (one instance, FP32 with the inverse) -- autotuned
+    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies (in a
+    // batch with instances over the cluster limit: clusters for the others,
+    // then the cooperative kernel for those), 2 dataflow (one instance, FP32
+    // with the inverse) -- autotuned
     if (!fp64 && want_inv && (variant == 2 || (variant < 0 && potrf_flow_fits(count, max_n))) &&
         potrf_flow_fits(count, max_n) && launch_potrf_flow(d_insts, max_n, flags, st))
         return;
     const bool cluster_ok = fp64 || want_inv;
     const bool want_cluster = variant == 1 || (variant < 0 && count * 8 >= sms);
     if (cluster_ok && want_cluster && launch_potrf_cluster(d_insts, count, max_n, fp64, flags, st)) return;
+    if (cluster_ok && want_cluster && count > 1 && launch_potrf_cluster(d_insts, count, 512, fp64, flags | F_N_LE_512, st))
+        flags |= F_N_GT_512;   // the small instances are factored; the cooperative kernel takes the rest
     long long work = (long long)count * (nt * (nt + 1) / 2 > nt ? nt * (nt + 1) / 2 : nt);
     long long cap = (long long)occ[fp64 ? 1 : 0] * sms;
     int grid = (int)(work < cap ? work : cap);

@@ -1043,11 +1043,13 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         bc_ptr[col + 1] = (int)bc_idx.size();
     }
     const int nnzB = (int)bc_idx.size();
-    // the Horner chains when they need clearly fewer FP64 operations than the
-    // SYRK; LQMPC_KKT64=syrk|lyap overrides
+    // the Horner chains when they need fewer FP64 operations than the SYRK, or
+    // when both are small (a batch forms all its FP64 instances one way, so one
+    // small instance should not move the others to the SYRK); LQMPC_KKT64=
+    // syrk|lyap overrides
     {
         const double cs = kkt_cost_syrk(ns, nu, N), cl = kkt_cost_lyap(ns, nu, N, nnzA, nnzB);
-        ctx->lyap = cl < 0.6 * cs;
+        ctx->lyap = cl < cs || cl < 4e6;
         if (const char* e = getenv("LQMPC_KKT64")) {
             if (!strcmp(e, "syrk")) ctx->lyap = false;
             if (!strcmp(e, "lyap")) ctx->lyap = true;
@@ -1180,7 +1182,9 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (!all_finite(x0s[i], ctxs[i]->h.ns)) return LQMPC_ERR_ARG;
         if (ctxs[i]->opts.max_iter < o.max_iter) o.max_iter = ctxs[i]->opts.max_iter;
     }
-    bool tc = o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32;
+    // tensor maps for the tensor-core formations (BF16, TF32 and the split-TF32
+    // FP32 tier, which falls back to the CUDA-core SYRK without them)
+    bool tc = o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32 || o.precision == LQMPC_FP32;
     for (int i = 0; i < count && tc; ++i)
         if (!ctxs[i]->tc_ok) tc = false;
     if ((o.precision == LQMPC_MIXED_BF16 || o.precision == LQMPC_MIXED_TF32) && !tc) o.precision = LQMPC_FP32;
@@ -1312,12 +1316,14 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
         }
         b.cc_splits = t.cc_splits;
         // 2. Cholesky variant: cooperative over all SMs, one 8-CTA cluster per
-        //    instance, or (one instance, FP32 with the inverse) the dataflow kernel
-        if (potrf_cluster_fits(b.max_n) || potrf_flow_fits(b.count, b.max_n)) {
+        //    instance (in a batch with larger instances: clusters for those
+        //    that fit, the cooperative kernel for the rest), or (one instance,
+        //    FP32 with the inverse) the dataflow kernel
+        if (potrf_cluster_fits(b.max_n) || potrf_flow_fits(b.count, b.max_n) || b.count > 1) {
             for (int fp64 = 0; fp64 < 2; ++fp64) {
                 float bv = 1e30f;
                 for (int v = 0; v < 3; ++v) {
-                    if (v == 1 && !potrf_cluster_fits(b.max_n)) continue;
+                    if (v == 1 && !potrf_cluster_fits(b.max_n) && b.count == 1) continue;
                     if (v == 2 && (fp64 || !potrf_flow_fits(b.count, b.max_n))) continue;
                     auto form = [&]() {
                         const int prec = fp64 ? LQMPC_FP64 : LQMPC_FP32;
