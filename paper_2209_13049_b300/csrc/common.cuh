@@ -122,8 +122,9 @@ struct Inst {
     size_t syrk_ws_bytes;
     const int* tc_plan;               // tensor-core SYRK: per lower tile (splits, first partial)
     double* part;                     // kParts x kMaxParts reduction partials
-    unsigned* bar;                    // grid-barrier state of cooperative launches (2 words)
-    int* pflags;                      // 64 words: dataflow Cholesky epoch, finished CTAs, block-column flags
+    unsigned* bar;                    // grid-barrier state (2 words), queued Cholesky tickets (2 words)
+    int* pflags;                      // dataflow Cholesky: epoch, finished tasks, flag per (block column, row block)
+    const int* ftasks;                // queued dataflow Cholesky: task list of this instance alone
     Scal* sc;
     double* trace;                    // (max_iter+1) x kTraceW
 };

@@ -68,12 +68,19 @@ double kkt_cost_lyap(int ns, int nu, int N, long long nnzA, long long nnzB);
 
 // kernels_chol.cu
 void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st,
-                  int want_inv = 0, int variant = -1);
+                  int want_inv = 0, int variant = -1, const int* d_tasks = nullptr, int ntasks = 0);
 bool launch_potrf_cluster(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st);
 bool potrf_cluster_fits(int max_n);
 // kernels_flow.cu (dataflow Cholesky with inverse, one instance, FP32)
 bool potrf_flow_fits(int count, int max_n);
 bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t st);
+// queued dataflow Cholesky (FP32 with the inverse, any count, n <= 1024):
+// the task list holds flowq_task_count(n) entries per instance, written by
+// flowq_tasks(instance index, n, out), largest instances first
+bool potrf_flowq_fits(int max_n);
+int flowq_task_count(int n);
+void flowq_tasks(int q, int n, int* out);
+bool launch_potrf_flowq(const Inst* d_insts, const int* d_tasks, int ntasks, int max_n, int flags, cudaStream_t st);
 // tail: 0 none; 1 / 2 also the conjugate-gradient direction from z = out
 // (p = z / p = z + beta p with r'z) in the same launch
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,

@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
 // ---------------------------------------------------------------------------
 
 void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st, int want_inv,
-                  int variant) {
+                  int variant, const int* d_tasks, int ntasks) {
     static int occ[2] = {0, 0}, sms = 0;
     const int nt = (max_n + kNb - 1) / kNb;
     if (!sms) {
@@ -595,24 +595,32 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_potrf_coop<float>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_potrf_coop<double>, 256, 0);
     }
-    // Batches that fill the GPU with one 8-CTA cluster per instance factor in
-    // distributed shared memory (no grid barrier; FP32 also forms the
-    // inverse); a single instance or a small batch spreads its tiles over
-    // every SM with the cooperative kernel (measured faster for one n = 500
-    // matrix: 0.37-0.50 ms FP32 against 0.53 ms for the cluster kernel, and
-    // 1.16 ms against 1.95 ms in FP64, whose pipe rate makes 8 SMs too few).
-    // variant: -1 this rule, 0 cooperative, 1 cluster where it applies (in a
-    // batch with instances over the cluster limit: clusters for the others,
-    // then the cooperative kernel for those), 2 dataflow (one instance, FP32
-    // with the inverse) -- autotuned
-    if (!fp64 && want_inv && (variant == 2 || (variant < 0 && potrf_flow_fits(count, max_n))) &&
-        potrf_flow_fits(count, max_n) && launch_potrf_flow(d_insts, max_n, flags, st))
+    // variant: -1 the rule below, 0 cooperative, 1 clusters where they apply
+    // (in a batch with instances over the cluster limit: clusters for the
+    // others, then the queued dataflow kernel -- or the cooperative one past
+    // its limit -- for those), 2 dataflow (one instance of n <= 544: one CTA
+    // per block column; otherwise the queued kernel), 3 the queued kernel --
+    // autotuned.  The rule: FP32 with the inverse takes the dataflow kernels
+    // (one instance: measured 0.20 ms for n = 500 against 0.37-0.50 ms
+    // cooperative and 0.53 ms in a cluster), except that a batch filling the
+    // GPU with one 8-CTA cluster per instance factors its small instances in
+    // clusters; FP64 takes clusters for such batches and the cooperative
+    // kernel otherwise (its pipe rate makes 8 SMs too few for one instance).
+    const bool dataflow = !fp64 && want_inv;
+    const bool flowq_ok = dataflow && d_tasks && potrf_flowq_fits(max_n);
+    const bool want_cluster = variant == 1 || (variant < 0 && count * 8 >= sms);
+    if (dataflow && (variant == 2 || (variant < 0 && !want_cluster)) && potrf_flow_fits(count, max_n) &&
+        launch_potrf_flow(d_insts, max_n, flags, st))
+        return;
+    if (flowq_ok && (variant == 2 || variant == 3 || (variant < 0 && !want_cluster)) &&
+        launch_potrf_flowq(d_insts, d_tasks, ntasks, max_n, flags, st))
         return;
     const bool cluster_ok = fp64 || want_inv;
-    const bool want_cluster = variant == 1 || (variant < 0 && count * 8 >= sms);
     if (cluster_ok && want_cluster && launch_potrf_cluster(d_insts, count, max_n, fp64, flags, st)) return;
-    if (cluster_ok && want_cluster && count > 1 && launch_potrf_cluster(d_insts, count, 512, fp64, flags | F_N_LE_512, st))
-        flags |= F_N_GT_512;   // the small instances are factored; the cooperative kernel takes the rest
+    if (cluster_ok && want_cluster && count > 1 && launch_potrf_cluster(d_insts, count, 512, fp64, flags | F_N_LE_512, st)) {
+        flags |= F_N_GT_512;   // the small instances are factored; the rest follow
+        if (flowq_ok && launch_potrf_flowq(d_insts, d_tasks, ntasks, max_n, flags, st)) return;
+    }
     long long work = (long long)count * (nt * (nt + 1) / 2 > nt ? nt * (nt + 1) / 2 : nt);
     long long cap = (long long)occ[fp64 ? 1 : 0] * sms;
     int grid = (int)(work < cap ? work : cap);

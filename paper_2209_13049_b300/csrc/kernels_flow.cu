@@ -482,6 +482,352 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Queued dataflow Cholesky: any number of instances of n <= 1024 in one
+// persistent cooperative launch (one CTA per SM).  The work is a list of
+// tasks, per instance (largest first) the factor tasks of its block columns
+// j = 0 .. nt-1 (L_pj for p >= j, as above, with X_jj) and then the inverse
+// tasks j = 0 .. nt-2 (X_pj for p > j).  CTAs take tasks from a global
+// ticket counter in list order.  A task waits only on the flags of tasks
+// earlier in the list (a factor task on earlier block columns, an inverse
+// task on factor tasks), and every earlier task has been taken by a
+// resident CTA that does not wait on later ones, so every wait ends.  The
+// earlier row blocks of L are staged through a chunk buffer of C blocks, so
+// the shared memory holds one block row or column (nt blocks) plus a chunk.
+
+namespace {
+
+constexpr int kFlowQMaxN = 1024;        // 32 block columns: 2 + 32^2 flags, nt blocks of 32 x 32 per CTA
+
+// acc += sum over block columns k in [k0, k1) of L(32p + lane, 32k + m)
+// B[(32k + m) * 32 + c], the row block staged C block columns at a time
+// through Pn after their flags (k, p); W = 0: all warps, W = 1: warps 1..7.
+template <int W>
+__device__ __forceinline__ void acc_rowblock(float (&acc)[kFb], float* Pn, int C, const float* B, const float* M,
+                                             int n, const int* flg, int nt, int p, int pr, int k0, int k1, int ep,
+                                             int* err, bool vec) {
+    const int t0 = W ? 32 : 0, nthr = W ? 224 : 256;
+    const int wi = (threadIdx.x >> 5) - (W ? 1 : 0), nw = W ? 7 : 8;
+    for (int kc = k0; kc < k1; kc += C) {
+        const int ke = min(k1, kc + C);
+        // ends with a barrier of the participating warps: the previous chunk is consumed
+        wait_flags<W>(flg, nt, kc, ke, p, -1, ep, err);
+        stage_rowblock(Pn, kFb * kc, M, n, p, pr, kFb * kc, kFb * ke, vec, t0, nthr);
+        cpa_wait_all();
+        if (W) bar_w17();
+        else __syncthreads();
+        acc_panel(acc, Pn, B + kFb * kFb * kc, 0, kFb * (ke - kc), wi, nw);
+    }
+}
+
+// T = A_pj - (sum of the partials of warps w0..7), identity padding of a
+// ragged diagonal block
+__device__ __forceinline__ void form_t_q(float (*T)[kFb + 1], const float* As, const float* Red, bool diag, int kn,
+                                         int w0) {
+    for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+        const int r = e & 31, c = e >> 5;
+        float v = As[c * kFb + r] - sum_partials(Red, r, c, w0);
+        if (diag && r == c && r >= kn) v = 1.f;
+        T[r][c] = v;
+    }
+    __syncthreads();
+}
+
+// L_pj = T X_jj' (lane -> row, warp -> 4 columns), stored to M
+__device__ __forceinline__ void solve_store_q(float (*T)[kFb + 1], float (*Dv)[kFb + 1], float* M, int n, int r0,
+                                              int kn, int p) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p0 = kFb * p, pr = min(kFb, n - p0);
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int m = 0; m < kFb; ++m) {
+        const float t = T[lane][m];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = fmaf(t, Dv[warp + 8 * q][m], o[q]);
+    }
+    if (lane < pr) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = warp + 8 * q;
+            if (c < kn) __stcg(M + (size_t)n * (r0 + c) + p0 + lane, o[q]);
+        }
+    }
+}
+
+struct FlowQSm {
+    float* Big;    // nt blocks: row block j of the earlier columns (factor task), block column j of X (inverse task)
+    float* Pn;     // C blocks: a chunk of an earlier row block of L
+    float* As;     // A_pj, column-major
+    float* Red;    // [8 warps][32][33] partial sums
+    int C;
+};
+
+// Factor task of block column j of instance I.
+__device__ __forceinline__ void flowq_factor(const Inst& I, int j, int ep, const FlowQSm& s, float (*T)[kFb + 1],
+                                             float (*D)[kFb + 1], float (*Dv)[kFb + 1], bool warm) {
+    const int n = I.n, nt = (n + kFb - 1) / kFb;
+    const int r0 = kFb * j, kn = min(kFb, n - r0);
+    int* flg = I.pflags + 2;
+    int* err = &I.sc->err;
+    float* M = I.M32;
+    float* Rj = s.Big;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (n % 4) == 0;
+    if (warm && j > 0 && warp == 0) {   // instruction-cache warm-up of the diagonal factorisation
+        for (int e = lane; e < kFb * kFb; e += 32) T[e >> 5][e & 31] = (e >> 5) == (e & 31) ? 1.f : 0.f;
+        __syncwarp();
+        factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
+    }
+    // diagonal row block: row block j of columns 0..r0-1 into Rj (kept for
+    // the whole task), the last column's part last
+    {
+        stage_own(s.As, M, n, r0, kn, r0, kn, vec);
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 1) {
+            wait_flags<0>(flg, nt, 0, j - 1, j, -1, ep, err);
+            stage_rowblock(Rj, 0, M, n, j, kn, 0, kFb * (j - 1), vec);
+            cpa_wait_all();
+            __syncthreads();
+            acc_panel(acc, Rj, Rj, 0, kFb * (j - 1));
+        }
+        if (j > 0) {
+            wait_flags<0>(flg, nt, j - 1, j, j, -1, ep, err);
+            stage_rowblock(Rj, 0, M, n, j, kn, kFb * (j - 1), kFb * j, vec);
+            cpa_wait_all();
+            __syncthreads();
+            acc_panel(acc, Rj, Rj, kFb * (j - 1), kFb * j);
+        }
+        cpa_wait_all();
+        store_partial(acc, s.Red);
+        __syncthreads();
+    }
+    form_t_q(T, s.As, s.Red, true, kn, 0);
+    // warp 0 factors and inverts the diagonal block while warps 1..7 gather
+    // row block j+1; L_{j+1,j} goes out first (the next column's diagonal
+    // waits for it), L_jj and X_jj with it
+    const bool next = j + 1 < nt;
+    if (warp == 0) {
+        const int fail = factor_diag_block(&T[0][0], &D[0][0], &Dv[0][0]);
+        if (lane == 0 && fail) atomicCAS(&I.sc->info, 0, r0 + fail);
+    } else if (next) {
+        const int q0 = r0 + kFb, qr = min(kFb, n - q0);
+        stage_own(s.As, M, n, r0, kn, q0, qr, vec, 32, 224);
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 1) acc_rowblock<1>(acc, s.Pn, s.C, Rj, M, n, flg, nt, j + 1, qr, 0, j - 1, ep, err, vec);
+        if (j > 0) acc_rowblock<1>(acc, s.Pn, s.C, Rj, M, n, flg, nt, j + 1, qr, j - 1, j, ep, err, vec);
+        cpa_wait_all();
+        store_partial(acc, s.Red);
+    }
+    __syncthreads();
+    if (next) {
+        form_t_q(T, s.As, s.Red, false, kn, 1);
+        solve_store_q(T, Dv, M, n, r0, kn, j + 1);
+    }
+    for (int c = warp; c < kn; c += 8) {
+        if (lane < kn && lane >= c) {
+            __stcg(M + (size_t)n * (r0 + c) + r0 + lane, D[lane][c]);
+            const float xv = Dv[lane][c];
+            __stcg(I.Xinv32 + (size_t)(r0 + lane) + (size_t)n * (r0 + c), xv);
+            __stcg(I.XinvT32 + (size_t)(r0 + c) + (size_t)n * (r0 + lane), xv);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (next) st_flag_release(flg + j * nt + j + 1, ep);
+        st_flag_release(flg + j * nt + j, ep);
+    }
+    // the rest of the column
+    for (int p = j + 2; p < nt; ++p) {
+        const int p0 = kFb * p, pr = min(kFb, n - p0);
+        stage_own(s.As, M, n, r0, kn, p0, pr, vec);
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        if (j > 1) acc_rowblock<0>(acc, s.Pn, s.C, Rj, M, n, flg, nt, p, pr, 0, j - 1, ep, err, vec);
+        if (j > 0) acc_rowblock<0>(acc, s.Pn, s.C, Rj, M, n, flg, nt, p, pr, j - 1, j, ep, err, vec);
+        cpa_wait_all();
+        store_partial(acc, s.Red);
+        __syncthreads();
+        form_t_q(T, s.As, s.Red, false, kn, 0);
+        solve_store_q(T, Dv, M, n, r0, kn, p);
+        __syncthreads();
+        if (threadIdx.x == 0) st_flag_release(flg + j * nt + p, ep);
+    }
+}
+
+// Inverse task of block column j < nt-1: X_pj = -X_pp sum_{k=j}^{p-1} L_pk X_kj
+// down the column, X_jj from the factor task's flag (j, j).
+__device__ __forceinline__ void flowq_inverse(const Inst& I, int j, int ep, const FlowQSm& s, float (*T)[kFb + 1],
+                                              float (*D)[kFb + 1]) {
+    const int n = I.n, nt = (n + kFb - 1) / kFb;
+    const int r0 = kFb * j;
+    const int* flg = I.pflags + 2;
+    int* err = &I.sc->err;
+    const float* M = I.M32;
+    float* Xs = s.Big;                  // X[r0 + q, r0 + c] at Xs[q * 32 + c]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (n % 4) == 0;
+    wait_flags<0>(flg, nt, j, j + 1, j, -1, ep, err);
+    for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {   // j < nt-1: a full block
+        const int q = e >> 5, c = e & 31;
+        Xs[e] = c <= q ? __ldcg(I.Xinv32 + (size_t)(r0 + q) + (size_t)n * (r0 + c)) : 0.f;
+    }
+    for (int p = j + 1; p < nt; ++p) {
+        const int p0 = kFb * p, pr = min(kFb, n - p0);
+        // L_pk for k in [j, p) and X_pp (flag (p, p)); ends with a barrier
+        wait_flags<0>(flg, nt, j, p, p, p * nt + p, ep, err);
+        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+            const int r = e / kFb, c = e % kFb;
+            D[r][c] = (r < pr && c <= r) ? __ldcg(I.Xinv32 + (size_t)(p0 + r) + (size_t)n * (p0 + c)) : 0.f;
+        }
+        float acc[kFb];
+#pragma unroll
+        for (int c = 0; c < kFb; ++c) acc[c] = 0.f;
+        for (int kc = j; kc < p; kc += s.C) {
+            const int ke = min(p, kc + s.C);
+            if (kc > j) __syncthreads();   // the previous chunk is consumed
+            stage_rowblock(s.Pn, kFb * kc, M, n, p, pr, kFb * kc, kFb * ke, vec);
+            cpa_wait_all();
+            __syncthreads();
+            acc_panel(acc, s.Pn, Xs + kFb * kFb * (kc - j), 0, kFb * (ke - kc));
+        }
+        store_partial(acc, s.Red);
+        __syncthreads();
+        for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) {
+            const int r = e & 31, c = e >> 5;
+            T[r][c] = sum_partials(s.Red, r, c);
+        }
+        __syncthreads();
+        // X_pj = -X_pp T: lane -> column, warp -> 4 rows
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int m = 0; m < kFb; ++m) {
+            const float t = T[m][lane];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) o[q] = fmaf(D[warp + 8 * q][m], t, o[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = warp + 8 * q;
+            Xs[(p0 - r0 + r) * kFb + lane] = -o[q];
+            if (r < pr) {
+                I.Xinv32[(size_t)(p0 + r) + (size_t)n * (r0 + lane)] = -o[q];
+                I.XinvT32[(size_t)(r0 + lane) + (size_t)n * (p0 + r)] = -o[q];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+// tasks[t] = instance << 8 | kind << 7 | j (kind 0 factor, 1 inverse), in
+// the order tickets are taken; ctl (2 words, zero between launches): ticket
+// counter, exited CTAs.  Dynamic shared memory: (max_nt + C + 1) blocks of
+// 32 x 32 and the partial sums.
+__global__ void __launch_bounds__(256, 1) k_potrf_flowq(const Inst* __restrict__ insts, const int* __restrict__ tasks,
+                                                        int ntasks, int max_nt, int C, int flags) {
+    extern __shared__ __align__(16) float fsm[];
+    __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1];
+    __shared__ int task_sh, ep_sh;
+    int* ctl = reinterpret_cast<int*>(insts[0].bar + 2);
+    FlowQSm s;
+    s.Big = fsm;
+    s.Pn = s.Big + kFb * kFb * max_nt;
+    s.As = s.Pn + kFb * kFb * C;
+    s.Red = s.As + kFb * kFb;
+    s.C = C;
+    bool warm = true;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int t = atomicAdd(ctl, 1);
+            int task = t < ntasks ? tasks[t] : -1;
+            if (task >= 0) {
+                const Inst& I = insts[task >> 8];
+                if (skip_instance(I, flags)) task = -2;
+                else ep_sh = ld_flag(I.pflags) + 1;
+            }
+            task_sh = task;
+        }
+        __syncthreads();
+        const int task = task_sh;
+        const int ep = ep_sh;
+        __syncthreads();
+        if (task == -1) break;
+        if (task == -2) continue;
+        const Inst& I = insts[task >> 8];
+        const int j = task & 127;
+        if (task & 128) flowq_inverse(I, j, ep, s, T, D);
+        else flowq_factor(I, j, ep, s, T, D, Dv, warm);
+        warm = false;
+        // the instance's last task to finish advances its epoch (every task
+        // of it has read the epoch by then)
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nt = (I.n + kFb - 1) / kFb;
+            __threadfence();
+            if (atomicAdd(I.pflags + 1, 1) == 2 * nt - 2) {
+                atomicExch(I.pflags + 1, 0);
+                __threadfence();
+                atomicAdd(I.pflags, 1);
+            }
+        }
+    }
+    // the last CTA out resets the ticket counter for the next launch
+    if (threadIdx.x == 0 && atomicAdd(ctl + 1, 1) == (int)gridDim.x - 1) {
+        atomicExch(ctl, 0);
+        atomicExch(ctl + 1, 0);
+    }
+}
+
+
+bool potrf_flowq_fits(int max_n) { return max_n >= 1 && max_n <= kFlowQMaxN; }
+
+int flowq_task_count(int n) { return 2 * ((n + kFb - 1) / kFb) - 1; }
+
+void flowq_tasks(int q, int n, int* out) {
+    const int nt = (n + kFb - 1) / kFb;
+    for (int j = 0; j < nt; ++j) *out++ = (q << 8) | j;
+    for (int j = 0; j + 1 < nt; ++j) *out++ = (q << 8) | 128 | j;
+}
+
+bool launch_potrf_flowq(const Inst* d_insts, const int* d_tasks, int ntasks, int max_n, int flags, cudaStream_t st) {
+    static int sms = 0, optin = 0, stat = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_potrf_flowq) == cudaSuccess) stat = (int)fa.sharedSizeBytes;
+    }
+    if (!potrf_flowq_fits(max_n) || !d_tasks || ntasks < 1) return false;
+    const int nt = (max_n + kFb - 1) / kFb;
+    const int blk = (int)sizeof(float) * kFb * kFb, red = (int)sizeof(float) * 8 * kFb * (kFb + 1);
+    // the chunk: what is left after the block row / column and A_pj (at most nt blocks)
+    const int C = std::min(nt, (optin - stat - red - (nt + 1) * blk) / blk);
+    if (C < 1) return false;
+    const size_t smem = (size_t)(nt + C + 1) * blk + red;
+    if (cudaFuncSetAttribute(k_potrf_flowq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_potrf_flowq, 256, smem);
+    const int grid = std::min(ntasks, std::max(1, occ) * sms);
+    int mnt = nt, c = C;
+    void* args[] = {(void*)&d_insts, (void*)&d_tasks, (void*)&ntasks, (void*)&mnt, (void*)&c, (void*)&flags};
+    cudaEvent_t pe = prof_start(st);
+    // cooperative: every CTA is resident, so a task's waits on earlier tasks can end
+    cudaError_t e = cudaLaunchCooperativeKernel((void*)k_potrf_flowq, dim3(grid), dim3(256), args, smem, st);
+    note_launches(1);
+    prof_stop(st, pe, "k_potrf_flowq");
+    check_launch(st, "k_potrf_flowq", __FILE__, __LINE__);
+    return e == cudaSuccess;
+}
+
 bool potrf_flow_fits(int count, int max_n) { return count == 1 && max_n >= 1 && max_n <= kFlowMaxN; }
 
 bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t st) {

@@ -255,7 +255,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto XinvT32 = c.take<float>((size_t)n * n);
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto ldiag = c.take<double>(2 * 32 * 32);
-    auto pflags = c.take<int>(2 + 17 * 17);   // dataflow Cholesky: epoch, count, flag per row block
+    auto pflags = c.take<int>(2 + 32 * 32);   // dataflow Cholesky: epoch, count, flag per row block
+    auto ftasks = c.take<int>(64);
     auto ffw = c.take<float>(4 * (size_t)I.SX);
     auto ffv = c.take<float>(2 * (size_t)n);
     auto pp = c.take<double>(n); auto qq = c.take<double>(n); auto dxs = c.take<double>(SX);
@@ -268,7 +269,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     size_t ws = std::max(ws_cc, ws_tc);
     auto syrk_ws = c.take<unsigned char>(ws);
     auto part = c.take<double>((size_t)kParts * kMaxParts);
-    auto bar = c.take<unsigned>(2);
+    auto bar = c.take<unsigned>(4);
     auto sc = c.take<Scal>(1);
     auto trace = c.take<double>((size_t)(max_iter + 1) * kTraceW);
     if (kAssign) {
@@ -287,6 +288,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.ldiag = ldiag;
         I.pflags = pflags;
+        I.ftasks = ftasks;
         I.ffw = ffw;
         I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
@@ -310,7 +312,9 @@ struct Batch {
     bool ff = false;                // products with Gamma in float-float (mixed solves) or FP64
     GraphCache* gc = nullptr;       // nullptr: launch every kernel directly
     double warm_mu0 = 0.0;          // > 0: warm start from the guess staged in du_aff
-    int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster (autotuned)
+    int potrf_variant[2] = {-1, -1};  // [fp64]: -1 rule, 0 cooperative, 1 cluster, 2 dataflow, 3 queued (autotuned)
+    const int* d_ftasks = nullptr;  // queued dataflow Cholesky: task list (nullptr: not available)
+    int nftasks = 0;
     bool lyap = false;              // FP64 formation by the Horner chains (every instance's A is sparse enough)
     int max_nu = 0;
     cudaStream_t side = nullptr;    // ctxs[0]'s side stream and events (nullptr: no overlap)
@@ -465,6 +469,10 @@ void batch_dims(Batch& b) {
         b.cc_splits = std::min(b.cc_splits, c->cc_splits);
         b.tc_splits = b.tc_splits == (1 << 30) ? c->tc_splits : std::max(b.tc_splits, c->tc_splits);
     }
+    if (b.count == 1 && potrf_flowq_fits(b.max_n)) {   // the instance's own task list
+        b.d_ftasks = b.ctxs[0]->h.ftasks;
+        b.nftasks = flowq_task_count(b.max_n);
+    }
     b.st = b.ctxs[0]->stream;
     b.side = b.ctxs[0]->side;
     b.ev_fork = b.ctxs[0]->ev_fork;
@@ -477,6 +485,28 @@ void batch_dims(Batch& b) {
         b.potrf_variant[1] = it->second.potrf[1];
         if (it->second.kkt64 == 0) b.lyap = false;
     }
+    // LQMPC_POTRF=coop|cluster|flow|queued fixes the FP32 Cholesky variant
+    if (const char* e = getenv("LQMPC_POTRF")) {
+        static const char* names[] = {"coop", "cluster", "flow", "queued"};
+        for (int v = 0; v < 4; ++v)
+            if (!strcmp(e, names[v])) b.potrf_variant[0] = v;
+    }
+}
+
+// Task list of the queued dataflow Cholesky for a batch: the instances by
+// decreasing n (the longest chains start first), none if one is too large.
+std::vector<int> batch_flow_tasks(const Batch& b) {
+    std::vector<int> order(b.count), t;
+    if (!potrf_flowq_fits(b.max_n)) return t;
+    for (int i = 0; i < b.count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return b.ctxs[x]->h.n > b.ctxs[y]->h.n; });
+    for (int q : order) {
+        const size_t o = t.size();
+        t.resize(o + flowq_task_count(b.ctxs[q]->h.n));
+        flowq_tasks(q, b.ctxs[q]->h.n, t.data() + o);
+    }
+    return t;
 }
 
 // ---- one KKT solve M du = b (in role R_B) into R_DU, and R_TMPX = Gamma du.
@@ -506,13 +536,13 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
             rec(c0->evk[2]);
             launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, sel, b.st, shift);
             rec(c0->evk[3]);
-            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1]);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1], b.d_ftasks, b.nftasks);
         } else if (prec == LQMPC_FP64) {
             rec(c0->evk[2]);
             launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
             rec(c0->evk[3]);
             launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, shift);
-            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1]);
+            launch_potrf(b.d_insts, b.count, b.max_n, 1, sel, b.st, 0, b.potrf_variant[1], b.d_ftasks, b.nftasks);
         } else {
             if (prec == LQMPC_FP32 && !b.d_maps) {
                 rec(c0->evk[2]);
@@ -530,7 +560,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
                                    shift);
             }
             rec(c0->evk[4]);
-            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0]);
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0], b.d_ftasks, b.nftasks);
             rec(c0->evk[5]);
         }
     };
@@ -1095,6 +1125,11 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         std::vector<int> plan = syrk_tc_make_plan(ns, nu, N);
         ok = ok && up(I.tc_plan, plan.data(), sizeof(int) * plan.size());
     }
+    if (potrf_flowq_fits(I.n)) {
+        std::vector<int> ft(flowq_task_count(I.n));
+        flowq_tasks(0, I.n, ft.data());
+        ok = ok && up(I.ftasks, ft.data(), sizeof(int) * ft.size());
+    }
     if (!ok) return fail(LQMPC_ERR_CUDA);
     if (cudaMalloc(&ctx->d_inst, sizeof(Inst)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     if (!up(ctx->d_inst, &I, sizeof(Inst))) return fail(LQMPC_ERR_CUDA);
@@ -1192,7 +1227,12 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
     for (int i = 0; i < count; ++i) hosts[i] = ctxs[i]->h;
     Inst* d = nullptr;
     void* maps = nullptr;
-    CK(cudaMalloc(&d, sizeof(Inst) * count));
+    const std::vector<int> ftasks = count > 1 ? batch_flow_tasks(b) : std::vector<int>();
+    CK(cudaMalloc(&d, sizeof(Inst) * count + sizeof(int) * ftasks.size()));
+    if (!ftasks.empty()) {
+        b.d_ftasks = reinterpret_cast<const int*>(d + count);
+        b.nftasks = (int)ftasks.size();
+    }
     if (tc && count > 1 && cudaMalloc(&maps, 384 * (size_t)count) != cudaSuccess) {
         cudaFree(d);
         return LQMPC_ERR_CUDA;
@@ -1211,6 +1251,9 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         }
     }
     if (cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess)
+        s = LQMPC_ERR_CUDA;
+    if (!ftasks.empty() && cudaMemcpyAsync(d + count, ftasks.data(), sizeof(int) * ftasks.size(),
+                                           cudaMemcpyHostToDevice, b.st) != cudaSuccess)
         s = LQMPC_ERR_CUDA;
     for (int i = 0; i < count && s == LQMPC_OK; ++i)
         if (cudaMemcpyAsync(ctxs[i]->h.xbar, x0s[i], sizeof(double) * ctxs[i]->h.ns, cudaMemcpyHostToDevice,
@@ -1274,11 +1317,18 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
     std::vector<Inst> hosts(count);
     for (int i = 0; i < count; ++i) hosts[i] = ctxs[i]->h;
     Inst* d = nullptr;
-    CK(cudaMalloc(&d, sizeof(Inst) * count));
+    const std::vector<int> ftasks = count > 1 ? batch_flow_tasks(b) : std::vector<int>();
+    CK(cudaMalloc(&d, sizeof(Inst) * count + sizeof(int) * ftasks.size()));
     b.d_insts = d;
+    if (!ftasks.empty()) {
+        b.d_ftasks = reinterpret_cast<const int*>(d + count);
+        b.nftasks = (int)ftasks.size();
+    }
     lqmpc_status s = LQMPC_OK;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess ||
+    if ((!ftasks.empty() && cudaMemcpyAsync(d + count, ftasks.data(), sizeof(int) * ftasks.size(),
+                                            cudaMemcpyHostToDevice, b.st) != cudaSuccess) ||
+        cudaMemcpyAsync(d, hosts.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, b.st) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         s = LQMPC_ERR_CUDA;
     Tuning t;
@@ -1317,14 +1367,17 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
         b.cc_splits = t.cc_splits;
         // 2. Cholesky variant: cooperative over all SMs, one 8-CTA cluster per
         //    instance (in a batch with larger instances: clusters for those
-        //    that fit, the cooperative kernel for the rest), or (one instance,
-        //    FP32 with the inverse) the dataflow kernel
-        if (potrf_cluster_fits(b.max_n) || potrf_flow_fits(b.count, b.max_n) || b.count > 1) {
+        //    that fit, the queued or cooperative kernel for the rest), or (FP32
+        //    with the inverse) the dataflow kernel of one instance and the
+        //    queued dataflow kernel
+        const bool flowq = b.d_ftasks && potrf_flowq_fits(b.max_n);
+        if (potrf_cluster_fits(b.max_n) || potrf_flow_fits(b.count, b.max_n) || flowq || b.count > 1) {
             for (int fp64 = 0; fp64 < 2; ++fp64) {
                 float bv = 1e30f;
-                for (int v = 0; v < 3; ++v) {
+                for (int v = 0; v < 4; ++v) {
                     if (v == 1 && !potrf_cluster_fits(b.max_n) && b.count == 1) continue;
                     if (v == 2 && (fp64 || !potrf_flow_fits(b.count, b.max_n))) continue;
+                    if (v == 3 && (fp64 || !flowq)) continue;
                     auto form = [&]() {
                         const int prec = fp64 ? LQMPC_FP64 : LQMPC_FP32;
                         launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, fp64, 0, nullptr, nullptr, F_NONE,
@@ -1334,7 +1387,8 @@ lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache
                         (void)prec;
                     };
                     float ms = timed(form, [&]() {
-                        launch_potrf(b.d_insts, b.count, b.max_n, fp64, F_NONE, b.st, fp64 ? 0 : 1, v);
+                        launch_potrf(b.d_insts, b.count, b.max_n, fp64, F_NONE, b.st, fp64 ? 0 : 1, v, b.d_ftasks,
+                                     b.nftasks);
                     });
                     if (ms < bv) { bv = ms; t.potrf[fp64] = v; }
                 }

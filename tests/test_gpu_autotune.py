@@ -37,7 +37,7 @@ def test_autotune_cache_and_parity(tmp_path):
     lines = [l for l in lines if l.strip()]
     assert len(lines) == 1
     key, cc, p32, p64, k64 = lines[0].split()
-    assert key.startswith("b6-") and int(cc) >= 1 and int(p32) in (0, 1, 2) and int(p64) in (0, 1)
+    assert key.startswith("b6-") and int(cc) >= 1 and int(p32) in (0, 1, 2, 3) and int(p64) in (0, 1)
     assert int(k64) in (-1, 0, 1)
     # a second call finds the signature in the cache and appends nothing
     binding.autotune(solvers, cache)

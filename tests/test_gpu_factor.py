@@ -11,7 +11,13 @@ inverse is judged by the conjugate gradients it preconditions: started from
 L^-T L^-1 b, FP64 products with M must reach a 2e-10 relative residual in a
 few steps (an FP32-accurate inverse contracts the error by about
 cond(M) 2^-24 per step; a wrong block of it would not).
+
+Single instances of 544 < n <= 1024 take the queued dataflow kernel (block
+columns as tasks from a ticket counter, factor tasks before inverse tasks);
+the `queued` cases force it on the small sizes as well (LQMPC_POTRF).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -28,6 +34,12 @@ SIZES = [
     ("n500_16_blocks_ragged", lambda: inputs.heat1d(40, 10, 50)),
     ("n517_17_blocks_ragged5", lambda: inputs.heat1d(30, 11, 47)),
     ("n544_17_full_blocks", lambda: inputs.heat1d(30, 16, 34)),
+    ("n800_25_full_blocks", lambda: inputs.heat1d(40, 16, 50)),
+    ("n1000_32_blocks_ragged8", lambda: inputs.heat1d(30, 20, 50)),
+    ("n1024_32_full_blocks", lambda: inputs.heat1d(30, 16, 64)),
+    ("n161_ragged_queued", lambda: inputs.heat2d(10, 7, 23), "queued"),
+    ("n500_16_blocks_ragged_queued", lambda: inputs.heat1d(40, 10, 50), "queued"),
+    ("n517_17_blocks_ragged5_queued", lambda: inputs.heat1d(30, 11, 47), "queued"),
 ]
 
 
@@ -40,6 +52,9 @@ def _lib():
 @pytest.fixture(scope="module", params=SIZES, ids=[c[0] for c in SIZES])
 def case(request):
     p = request.param[1]()
+    variant = request.param[2] if len(request.param) > 2 else None
+    if variant:
+        os.environ["LQMPC_POTRF"] = variant
     s = binding.Solver(p)
     Gam, _, H, _ = oracle.condensed(p, np.zeros(p.ns))
     rng = np.random.default_rng(11)
@@ -47,7 +62,8 @@ def case(request):
     sigu = 10.0 ** rng.uniform(-1, 1, p.n)
     M = oracle.kkt_matrix(p, sigx, sigu, Gam, H)
     absm = np.abs(H) + np.abs(Gam).T @ (sigx[:, None] * np.abs(Gam)) + np.diag(sigu)
-    return p, s, sigx, sigu, M, absm
+    yield p, s, sigx, sigu, M, absm
+    os.environ.pop("LQMPC_POTRF", None)
 
 
 def test_fp32_factor_backward_error(case):

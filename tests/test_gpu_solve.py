@@ -242,3 +242,26 @@ def test_uneven_batch_cooperative_factor_matches_single():
     for k in range(len(inst)):
         assert stats[k]["status"] == 0
         assert rel(us[k], singles[k]) <= 1e-8, k
+
+
+@pytest.mark.parametrize("variant", ["rule", "queued", "coop"])
+def test_uneven_batch_fp32_factor_variants_match_single(variant):
+    """The 24 first instances of the uneven batch in the FP32 tier (n up to
+    800): by the rule the queued dataflow Cholesky factors every instance
+    (too few instances for one cluster each), and the forced variants must
+    agree too; each instance within the FP32 tier's own solve-to-solve spread
+    of its single solve (both stop at the 1e-8 test)."""
+    inst = inputs.batch_instances(256, 0)[:24]
+    if variant != "rule":
+        os.environ["LQMPC_POTRF"] = variant
+    try:
+        solvers = [binding.Solver(p, precision="fp32") for p, _ in inst]
+        x0s = [x for _, x in inst]
+        us, stats, code = binding.solve_batch(solvers, x0s)
+    finally:
+        os.environ.pop("LQMPC_POTRF", None)
+    assert code == 0
+    for k in range(len(inst)):
+        assert stats[k]["status"] == 0
+        ref = binding.Solver(inst[k][0], precision="fp64").solve(x0s[k])[0]
+        assert rel(us[k], ref) <= 1e-6, k
