@@ -10,6 +10,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "gamma_ff.cuh"
+#include "chol_diag.cuh"
 
 namespace lqmpc {
 
@@ -19,10 +20,6 @@ template <typename T>
 __device__ __forceinline__ T* kkt_mat(const Inst& I) {
     return sizeof(T) == 8 ? (T*)I.M64 : (T*)I.M32;
 }
-
-template <typename T> __device__ __forceinline__ T sqrt_t(T v);
-template <> __device__ __forceinline__ double sqrt_t<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float sqrt_t<float>(float v) { return sqrtf(v); }
 
 // Grid-wide barrier for the cooperative factorisation kernel (all CTAs are
 // co-resident by the cooperative launch).  The spin is bounded: a barrier
@@ -80,8 +77,8 @@ __device__ bool factor_diag(const Inst& I, T* M, int k, bool owner, T (*Ld)[kNb 
                 if (!(djj > T(0))) {
                     fail = k0 + j + 1;
                 } else {
-                    T d = sqrt_t<T>(djj);
-                    T rd = T(1) / d;
+                    T d, rd;
+                    pivot_t<T>(djj, d, rd);
                     T lij = lane > j ? a[j] * rd : (lane == j ? d : T(0));
                     a[j] = lij;
 #pragma unroll
@@ -104,8 +101,11 @@ __device__ bool factor_diag(const Inst& I, T* M, int k, bool owner, T (*Ld)[kNb 
 }
 
 // Inverse of the factored 32 x 32 diagonal block (lower triangular), one
-// column per thread of warp 0: Li[c][c] = 1/L[c][c], then forward
-// substitution down the column.
+// column per thread of warp 0, by forward substitution L x = e_c taken
+// right-looking: once x_m is final it is subtracted from every later row at
+// once (independent multiply-adds), so the dependent chain is two operations
+// per row instead of a dot product per row (FP64 multiply-adds have a
+// 64-cycle latency on this part).
 template <typename T>
 __device__ void invert_diag(T (*Ld)[kNb + 1], T (*Li)[kNb + 1]) {
     __shared__ T rd[kNb];
@@ -113,13 +113,19 @@ __device__ void invert_diag(T (*Ld)[kNb + 1], T (*Li)[kNb + 1]) {
     __syncthreads();
     if (threadIdx.x < kNb) {
         const int c = threadIdx.x;
-        for (int i = 0; i < c; ++i) Li[i][c] = T(0);
-        Li[c][c] = rd[c];
-        for (int i = c + 1; i < kNb; ++i) {
-            T acc = 0;
-            for (int m = c; m < i; ++m) acc += Ld[i][m] * Li[m][c];
-            Li[i][c] = -acc * rd[i];
+        T x[kNb];
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) x[i] = i == c ? T(1) : T(0);
+#pragma unroll
+        for (int m = 0; m < kNb; ++m) {
+            if (m >= c) {
+                x[m] *= rd[m];
+#pragma unroll
+                for (int i = m + 1; i < kNb; ++i) x[i] = fma_t<T>(-Ld[i][m], x[m], x[i]);
+            }
         }
+#pragma unroll
+        for (int i = 0; i < kNb; ++i) Li[i][c] = x[i];
     }
     __syncthreads();
 }
@@ -169,12 +175,23 @@ __device__ void panel_tile(const Inst& I, int k, int p, T (*Ld)[kNb + 1], T (*Li
         A[r][c] = (p0 + r < n && c < kn) ? M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] : T(0);
     }
     __syncthreads();
-    // out[r][c] = sum_{m <= c} A[r][m] Li[c][m]
-    for (int e = threadIdx.x; e < kNb * kNb; e += blockDim.x) {
-        const int r = e % kNb, c = e / kNb;
-        T acc = 0;
-        for (int m = 0; m <= c; ++m) acc += A[r][m] * Li[c][m];
-        if (p0 + r < n && c < kn) M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] = acc;
+    // out[r][c] = sum_{m <= c} A[r][m] Li[c][m]: each thread's four entries
+    // (row r, columns cb + 8q) as four interleaved chains
+    {
+        const int r = threadIdx.x % kNb, cb = threadIdx.x / kNb;   // 256 threads
+        T acc[4] = {0, 0, 0, 0};
+#pragma unroll 8
+        for (int m = 0; m < kNb; ++m) {
+            const T a = A[r][m];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (m <= cb + 8 * q) acc[q] = fma_t<T>(a, Li[cb + 8 * q][m], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = cb + 8 * q;
+            if (p0 + r < n && c < kn) M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] = acc[q];
+        }
     }
     __syncthreads();
 }
@@ -462,6 +479,7 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* y = (T*)smem_raw;
     __shared__ double red[32];
+    // y: nt*32 entries, then the reciprocals of L's diagonal (nt*32)
     __shared__ double s_scale;
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
@@ -479,7 +497,14 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
     const int nt = (n + kNb - 1) / kNb;
     // y holds nt*32 entries: the block updates read all 32 entries of the
     // last (short) block, whose tail stays zero.
-    for (int j = threadIdx.x; j < nt * kNb; j += blockDim.x) y[j] = j < n ? (T)(bin[j] / sc) : T(0);
+    // reciprocals of the diagonal up front (in parallel): the substitution
+    // chains then multiply instead of divide (an FP64 division takes ~430
+    // cycles of latency on this part, a multiply 64)
+    T* rdiag = y + nt * kNb;
+    for (int j = threadIdx.x; j < nt * kNb; j += blockDim.x) {
+        y[j] = j < n ? (T)(bin[j] / sc) : T(0);
+        rdiag[j] = j < n ? T(1) / L[(size_t)j + (size_t)n * j] : T(1);
+    }
     __syncthreads();
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -497,11 +522,11 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
         const int k0 = kb * kNb, kn = min(kNb, n - k0);
         if (warp == 0) {
             T v = lane < kn ? y[k0 + lane] : T(0);
+            const T rl = rdiag[k0 + lane];
 #pragma unroll
             for (int j = 0; j < kNb; ++j) {
                 if (j < kn) {
-                    T diag = __shfl_sync(full, Ld[j], j);
-                    T yj = __shfl_sync(full, v, j) / diag;
+                    const T yj = __shfl_sync(full, v * rl, j);
                     if (lane == j) v = yj;
                     if (lane > j) v -= Ld[j] * yj;
                 }
@@ -524,10 +549,10 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
             }
             if (base == k0 + kn) __syncthreads();   // y of this block is ready
             if (warp > 0 && i < n) {
-                T acc = 0;
+                T acc[4] = {0, 0, 0, 0};   // four independent chains
 #pragma unroll
-                for (int j = 0; j < kNb; ++j) acc += Lr[j] * y[k0 + j];
-                y[i] -= acc;
+                for (int j = 0; j < kNb; ++j) acc[j & 3] += Lr[j] * y[k0 + j];
+                y[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
             }
         }
         if (k0 + kn >= n) __syncthreads();
@@ -544,11 +569,11 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
         const int k0 = kb * kNb, kn = min(kNb, n - k0);
         if (warp == 0) {
             T v = lane < kn ? y[k0 + lane] : T(0);
+            const T rl = rdiag[k0 + lane];
 #pragma unroll
             for (int j = kNb - 1; j >= 0; --j) {
                 if (j < kn) {
-                    T diag = __shfl_sync(full, Ld[j], j);
-                    T xj = __shfl_sync(full, v, j) / diag;
+                    const T xj = __shfl_sync(full, v * rl, j);
                     if (lane == j) v = xj;
                     if (lane < j) v -= Ld[j] * xj;
                 }
@@ -570,10 +595,10 @@ __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* _
             }
             if (base == 0) __syncthreads();
             if (warp > 0 && i < k0) {
-                T acc = 0;
+                T acc[4] = {0, 0, 0, 0};
 #pragma unroll
-                for (int j = 0; j < kNb; ++j) acc += Lr[j] * y[k0 + j];
-                y[i] -= acc;
+                for (int j = 0; j < kNb; ++j) acc[j & 3] += Lr[j] * y[k0 + j];
+                y[i] -= (acc[0] + acc[1]) + (acc[2] + acc[3]);
             }
         }
         if (k0 == 0) __syncthreads();
@@ -648,7 +673,7 @@ void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, i
 
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,
                        int out_role, int flags, cudaStream_t st) {
-    size_t smem = (size_t)((max_n + kNb - 1) / kNb) * kNb * (fp64 ? 8 : 4);
+    size_t smem = 2 * (size_t)((max_n + kNb - 1) / kNb) * kNb * (fp64 ? 8 : 4);
     if (fp64) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_chol_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -19,6 +19,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "chol_diag.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -177,6 +178,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256, 1)
 #pragma unroll
                 for (int c = 0; c < kClNb; ++c) a[c] = c <= lane ? D[lane * kClLd + c] : T(0);
                 int fail = 0;
+                T rdl = T(1);   // lane j: 1 / l_jj
 #pragma unroll
                 for (int j = 0; j < kClNb; ++j) {
                     if (!fail) {
@@ -184,8 +186,9 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256, 1)
                         if (!(djj > T(0))) {
                             fail = k * kClNb + j + 1;
                         } else {
-                            const T d = sizeof(T) == 8 ? (T)sqrt((double)djj) : (T)sqrtf((float)djj);
-                            const T rd = T(1) / d;
+                            T d, rd;
+                            pivot_t<T>(djj, d, rd);
+                            if (lane == j) rdl = rd;
                             const T lij = lane > j ? a[j] * rd : (lane == j ? d : T(0));
                             a[j] = lij;
 #pragma unroll
@@ -206,7 +209,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256, 1)
                     for (int c = 0; c < kClNb; ++c) x[c] = c == lane ? T(1) : T(0);
 #pragma unroll
                     for (int j = 0; j < kClNb; ++j) {
-                        const T rd = T(1) / D[j * kClLd + j];
+                        const T rd = __shfl_sync(full, rdl, j);
                         const T lij = D[lane * kClLd + j];
 #pragma unroll
                         for (int c = 0; c < kClNb; ++c) {
