@@ -63,15 +63,20 @@ enum {
     LQMPC_MIXED_BF16 = 1,   /* BF16 tensor-core SYRK (FP32 accumulate), FP32 Cholesky,
                                FP64 iterative refinement, FP64 fallback */
     LQMPC_MIXED_TF32 = 2,   /* as above with TF32 tensor-core SYRK */
-    LQMPC_FP32 = 3          /* FP32-accurate SYRK (split-TF32 tensor-core products; CUDA cores
+    LQMPC_FP32 = 3,         /* FP32-accurate SYRK (split-TF32 tensor-core products; CUDA cores
                                where tensor maps are unavailable), FP32 Cholesky,
                                FP64 refinement */
+    LQMPC_FP32X2 = 4        /* two-level FP32 preconditioner: FP64 formation, FP32 Cholesky
+                               L1 of M, then FP32 Cholesky L2 of L1^-1 M L1^-T (formed from
+                               E = M - L1 L1' in float-float), preconditioner (L1 L2)^-T (L1 L2)^-1,
+                               FP64 refinement; the tier between LQMPC_FP32 and LQMPC_FP64 */
 };
 
 typedef struct {
     double tol;          /* stop: max(||r_d||/(1+||h||), ||r_p||/(1+||d||), mu) <= tol; 1e-8 */
     int max_iter;        /* iteration limit; 100 */
-    int precision;       /* LQMPC_FP64 (default) / LQMPC_MIXED_BF16 / LQMPC_MIXED_TF32 / LQMPC_FP32 */
+    int precision;       /* LQMPC_FP64 (default) / LQMPC_MIXED_BF16 / LQMPC_MIXED_TF32 / LQMPC_FP32 /
+                            LQMPC_FP32X2 */
     int refine_max;      /* conjugate-gradient steps per KKT solve with an FP32 factor (30);
                             BF16/TF32 factors get min(refine_max, 12) before escalating */
     double refine_tol;   /* refinement stops at ||b - M du||_inf <= refine_tol ||b||_inf (1e-10)
@@ -86,7 +91,7 @@ typedef struct {
 typedef struct {
     int iters;           /* interior-point iterations taken */
     int refine_steps;    /* total refinement steps (mixed modes) */
-    int fallbacks;       /* precision escalations (BF16/TF32 -> FP32 -> FP64) */
+    int fallbacks;       /* precision escalations (BF16/TF32 -> FP32 -> FP32X2 -> FP64) */
     int status;          /* lqmpc_status of the solve */
     double mu;           /* final complementarity s'z/m */
     double res_primal;   /* final ||r_p||_inf/(1+||d||_inf) */

@@ -16,8 +16,8 @@ import scipy.sparse as sp
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblqmpc.so")
 
-FP64, MIXED_BF16, MIXED_TF32, FP32 = 0, 1, 2, 3
-PRECISIONS = {"fp64": FP64, "bf16": MIXED_BF16, "tf32": MIXED_TF32, "fp32": FP32}
+FP64, MIXED_BF16, MIXED_TF32, FP32, FP32X2 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": FP64, "bf16": MIXED_BF16, "tf32": MIXED_TF32, "fp32": FP32, "fp32x2": FP32X2}
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "KKT matrix not positive definite",
           4: "iteration limit reached", 5: "infeasible", 6: "non-finite iterate",

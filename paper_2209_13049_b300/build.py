@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "liblqmpc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 SOURCES = ["kernels_ipm.cu", "kernels_gamma.cu", "kernels_syrk.cu", "kernels_chol.cu",
            "kernels_cluster.cu", "kernels_refine.cu", "kernels_tc.cu", "kernels_noalloc.cu",
-           "kernels_mlp.cu", "mlp_api.cu", "kernels_lyap.cu", "kernels_flow.cu", "solver.cu"]
+           "kernels_mlp.cu", "mlp_api.cu", "kernels_lyap.cu", "kernels_flow.cu", "kernels_x2.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

@@ -59,7 +59,7 @@ struct Scal {
     int refine_fail;    // refinement stalled or produced a non-finite residual
     int refine_iter;    // refinement steps in the current interior-point iteration
     int prec_used;      // KKT precision of the current iteration (trace)
-    int prec_cur;       // KKT precision of this instance (escalates BF16/TF32 -> FP32 -> FP64, sticky)
+    int prec_cur;       // KKT precision of this instance (escalates BF16/TF32 -> FP32 -> FP32X2 -> FP64, sticky)
     int kkt_pending;    // the current KKT solve of this instance is not settled yet
     int refine_budget;  // conjugate-gradient steps allowed for the current right-hand side
     int arrive;         // CTAs of the current launch that finished (last_arrival), 0 between launches
@@ -118,6 +118,8 @@ struct Inst {
     double* tmpx;                     // SX scratch
     double* gpart;                    // Gamma' stage-1 partial sums
     float* r32;                       // n FP32 right-hand side
+    float *Xlo32, *XloT32;            // two-level tier: low parts of the combined inverse and its transpose (n x n)
+    float* r32lo;                     // two-level tier: low part of the preconditioner's intermediate vector (n)
     void* syrk_ws;                    // split-K partial tiles
     size_t syrk_ws_bytes;
     const int* tc_plan;               // tensor-core SYRK: per lower tile (splits, first partial)
@@ -157,6 +159,8 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
 // F_N_LE_512 / F_N_GT_512 keep only the instances with n <= 512 / n > 512 (the
 // cluster Cholesky's limit: a batch then factors its small instances in
 // clusters and only its large ones with the grid-cooperative kernel).
+constexpr int kPrecTwoLevel = 4;   // Scal::prec_cur of the two-level FP32 tier (LQMPC_FP32X2)
+
 enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2, F_PENDING = 4, F_N_LE_512 = 16, F_N_GT_512 = 32 };
 __host__ __device__ constexpr int prec_sel(int mask) { return mask << 8; }
 
@@ -164,7 +168,7 @@ __device__ __forceinline__ bool skip_instance(const Inst& I, int flags) {
     if (!(flags & F_FORCE) && I.sc->done) return true;
     if ((flags & F_SKIP_REFINED) && (I.sc->refine_ok || I.sc->refine_fail)) return true;
     if ((flags & F_PENDING) && !I.sc->kkt_pending) return true;
-    const int mask = (flags >> 8) & 15;
+    const int mask = (flags >> 8) & 31;
     if (mask && !((mask >> I.sc->prec_cur) & 1)) return true;
     if ((flags & F_N_LE_512) && I.n > 512) return true;
     if ((flags & F_N_GT_512) && I.n <= 512) return true;

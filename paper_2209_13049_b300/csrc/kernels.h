@@ -77,6 +77,12 @@ bool launch_potrf_flow(const Inst* d_insts, int max_n, int flags, cudaStream_t s
 // queued dataflow Cholesky (FP32 with the inverse, any count, n <= 1024):
 // the task list holds flowq_task_count(n) entries per instance, written by
 // flowq_tasks(instance index, n, out), largest instances first
+// two-level FP32 preconditioner (kernels_x2.cu): M32 = fl(M64) with a
+// relative diagonal shift; after the first FP32 factor: E, G = X1 E and
+// M32 = I + X1 E X1'; after the second: the combined inverse
+void launch_x2_round(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st, double shift);
+void launch_x2_refine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st);
+void launch_x2_combine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st);
 bool potrf_flowq_fits(int max_n);
 int flowq_task_count(int n);
 void flowq_tasks(int q, int n, int* out);
@@ -90,7 +96,8 @@ void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int 
 
 // kernels_refine.cu (preconditioned conjugate gradients on M du = b; `sel`
 // is the launch predicate that picks the instances of the solve)
-void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, cudaStream_t st);
+void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, int budget_mid,
+                      cudaStream_t st);
 void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st);
 // The same with mv = Gamma'(Sigma_x Gamma v) summed from the float-float
 // partials of the preceding Gamma' product (launched with kFuseNoSum).

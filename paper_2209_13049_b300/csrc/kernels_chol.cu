@@ -398,12 +398,58 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
 // with X = L^{-1} (FP32, lower).  Stage 1: t = X r, one thread per row
 // (coalesced along the column-major rows); stage 2: z = X' t, one warp per
 // column.
+//
+// The two-level tier's combined inverse Y is held as hi + lo planes
+// (Xinv32 + Xlo32, transposes likewise) and applied with float-float sums:
+// t = Y r (t as hi + lo), z = Y' t.
+__device__ __forceinline__ void ffp_mac(float& sh, float& sl, float xh, float xl, float vh, float vl) {
+    const float p = xh * vh;
+    float e = fmaf(xh, vh, -p);
+    e = fmaf(xh, vl, e);
+    e = fmaf(xl, vh, e);
+    const float s = sh + p;
+    const float z = s - sh;
+    sl += ((sh - (s - z)) + (p - z)) + e;
+    sh = s;
+}
+__device__ __forceinline__ void ffp_warp_sum(float& sh, float& sl) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        const float s = sh + oh;
+        const float z = s - sh;
+        sl += ((sh - (s - z)) + (oh - z)) + ol;
+        sh = s;
+    }
+}
+
 __global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int flags) {
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     const double* r = role_ptr(I, in_role);
     const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const float* XT = I.XinvT32;   // X' column-major: row i of X is contiguous
+    if (I.sc->prec_cur == kPrecTwoLevel) {
+        for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
+            const float* rh = XT + (size_t)n * i;
+            const float* rl = I.XloT32 + (size_t)n * i;
+            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+            int j = lane, u = 0;
+            for (; j <= i; j += 32, u ^= 1) {
+                const float vh = (float)r[j], vl = (float)(r[j] - (double)vh);
+                ffp_mac(sh[u], sl[u], rh[j], rl[j], vh, vl);
+            }
+            ffp_warp_sum(sh[0], sl[0]);
+            ffp_warp_sum(sh[1], sl[1]);
+            if (lane == 0) {
+                const float s = sh[0] + sh[1], z = s - sh[0];
+                const float lo = ((sh[0] - (s - z)) + (sh[1] - z)) + sl[0] + sl[1];
+                I.r32[i] = s + lo;
+                I.r32lo[i] = lo - ((s + lo) - s);
+            }
+        }
+        return;
+    }
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
         const float* row = XT + (size_t)n * i;
         float a4[4] = {0.f, 0.f, 0.f, 0.f};   // independent chains: four loads in flight
@@ -430,6 +476,18 @@ __global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int f
     double* z = role_ptr(I, out_role);
     const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const float* X = I.Xinv32;
+    if (I.sc->prec_cur == kPrecTwoLevel) {
+        for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
+            const float* ch = X + (size_t)n * j;
+            const float* cl = I.Xlo32 + (size_t)n * j;
+            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+            int i = j + lane, u = 0;
+            for (; i < n; i += 32, u ^= 1) ffp_mac(sh[u], sl[u], ch[i], cl[i], I.r32[i], I.r32lo[i]);
+            ffp_warp_sum(sh[0], sl[0]);
+            ffp_warp_sum(sh[1], sl[1]);
+            if (lane == 0) z[j] = ((double)sh[0] + (double)sh[1]) + ((double)sl[0] + (double)sl[1]);
+        }
+    } else
     for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
         const float* col = X + (size_t)n * j;
         float a4[4] = {0.f, 0.f, 0.f, 0.f};

@@ -29,8 +29,9 @@ __device__ __forceinline__ bool pcg_skip(const Inst& I, int sel) {
 }
 
 // Start: ||b||, flags cleared, step budget (BF16/TF32 factors get the low
-// budget: replacing such a factor is cheaper than iterating with it).
-__global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_hi, int budget_lo) {
+// budget and FP32 factors the middle one: replacing such a factor by the next
+// tier is cheaper than iterating with it).
+__global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_hi, int budget_lo, int budget_mid) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -41,7 +42,7 @@ __global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_
     if (threadIdx.x == 0) {
         S->rnorm0 = m; S->rnorm = INFINITY; S->rnorm_prev = INFINITY;
         S->refine_ok = 0; S->refine_fail = 0; S->refine_cur = 0; S->stalled = 0;
-        S->refine_budget = (S->prec_cur == 1 || S->prec_cur == 2) ? budget_lo : budget_hi;
+        S->refine_budget = (S->prec_cur == 1 || S->prec_cur == 2) ? budget_lo : (S->prec_cur == 3 ? budget_mid : budget_hi);
     }
 }
 
@@ -283,8 +284,9 @@ static int nblk(int len, int th, int cap) {
     return b < 1 ? 1 : (b > cap ? cap : b);
 }
 
-void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts, sel, budget_hi, budget_lo));
+void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, int budget_mid,
+                      cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts, sel, budget_hi, budget_lo, budget_mid));
 }
 
 // mode 0: r = b - M du and its convergence test; mode 1: q = M p and alpha.

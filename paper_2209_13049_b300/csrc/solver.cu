@@ -263,6 +263,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto tmpx = c.take<double>(SX);
     auto gpart = c.take<double>(gamma_tmv_part_doubles(ns, n, I.N));
     auto r32 = c.take<float>(n);
+    auto Xlo32 = c.take<float>((size_t)n * n); auto XloT32 = c.take<float>((size_t)n * n);
+    auto r32lo = c.take<float>(n);
     size_t ws_cc = (size_t)syrk_cc_tiles(n) * cc_splits * 64 * 64 * sizeof(double);
     size_t ws_tc = (size_t)syrk_tc_plan_partials(I.ns, I.nu, I.N) * 128 * 128 * sizeof(float);
     auto tc_plan = c.take<int>(2 * (size_t)syrk_tc_tiles(n) + 2);
@@ -295,6 +297,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
+        I.Xlo32 = Xlo32; I.XloT32 = XloT32; I.r32lo = r32lo;
         I.part = part; I.bar = bar; I.sc = sc; I.trace = trace; I.tc_plan = tc_plan;
     }
     return c.off;
@@ -532,7 +535,24 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
         else cudaEventRecord(e, b.st);
     };
     auto body = [&]() {
-        if (prec == LQMPC_FP64 && b.lyap) {
+        if (prec == LQMPC_FP32X2) {
+            // two-level FP32 preconditioner: M in FP64 (unshifted: E is taken
+            // against the exact M), its FP32 rounding (shifted on retries)
+            // factored, then the factor of I + X1 E X1' and the combined inverse
+            rec(c0->evk[2]);
+            if (b.lyap) {
+                launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, sel, b.st, 0.0);
+            } else {
+                launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
+                launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, 0.0);
+            }
+            rec(c0->evk[3]);
+            launch_x2_round(b.d_insts, b.count, b.max_n, sel, b.st, shift);
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0], b.d_ftasks, b.nftasks);
+            launch_x2_refine(b.d_insts, b.count, b.max_n, sel, b.st);
+            launch_potrf(b.d_insts, b.count, b.max_n, 0, sel, b.st, 1, b.potrf_variant[0], b.d_ftasks, b.nftasks);
+            launch_x2_combine(b.d_insts, b.count, b.max_n, sel, b.st);
+        } else if (prec == LQMPC_FP64 && b.lyap) {
             rec(c0->evk[2]);
             launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, sel, b.st, shift);
             rec(c0->evk[3]);
@@ -565,12 +585,17 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
         }
     };
     // the timed and untimed sequences differ (event nodes): separate graphs
-    if (shift == 0.0) seg_run(b, SEG_FORM + prec + (tm ? 4 : 0), body);
+    if (shift == 0.0) seg_run(b, SEG_FORM + prec + (tm ? 5 : 0), body);
     else body();
     if (tm) {
-        if (prec == LQMPC_FP64 || (prec == LQMPC_FP32 && !b.d_maps)) { tm->cc = true; tm->cc64 = prec == LQMPC_FP64; }
-        else { tm->tc = true; tm->tc3 = prec == LQMPC_FP32; }
-        if (prec != LQMPC_FP64) tm->pf = true;
+        if (prec == LQMPC_FP64 || prec == LQMPC_FP32X2 || (prec == LQMPC_FP32 && !b.d_maps)) {
+            tm->cc = true;
+            tm->cc64 = prec == LQMPC_FP64 || prec == LQMPC_FP32X2;
+        } else {
+            tm->tc = true;
+            tm->tc3 = prec == LQMPC_FP32;
+        }
+        if (prec != LQMPC_FP64 && prec != LQMPC_FP32X2) tm->pf = true;
     }
 }
 
@@ -587,7 +612,7 @@ bool host_selected(const Scal& S, int sel) {
     if (!(sel & F_FORCE) && S.done) return false;
     if ((sel & F_SKIP_REFINED) && (S.refine_ok || S.refine_fail)) return false;
     if ((sel & F_PENDING) && !S.kkt_pending) return false;
-    const int mask = (sel >> 8) & 15;
+    const int mask = (sel >> 8) & 31;
     if (mask && !((mask >> S.prec_cur) & 1)) return false;
     return true;
 }
@@ -604,8 +629,9 @@ lqmpc_status read_scals(Batch& b) {
 // flags every second step and stops launching once every unfinished instance
 // has converged or failed; afterwards each h_scal holds the outcome.
 lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int sel = F_NONE,
-                             int budget_lo = -1) {
+                             int budget_lo = -1, int budget_mid = -1) {
     if (budget_lo < 0) budget_lo = refine_max;
+    if (budget_mid < 0) budget_mid = refine_max;
     const int selr = sel | F_SKIP_REFINED;
     // preconditioner P^{-1}: the FP32 explicit inverse of the low-precision
     // factor, or (prec64) the FP64 triangular solves
@@ -622,7 +648,7 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     };
     const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
     seg_run(b, SEG_PCG0 + kp, [&]() {
-        launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, b.st);
+        launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, budget_mid, b.st);
         prec(R_B, R_DU, sel);
         // initial residual r = b - M du and Gamma du
         pcg_apply_m(b, R_DU, 0, sel, selr, true, false);
@@ -679,9 +705,17 @@ void prepare(const Batch& b, const lqmpc_options& o) {
 }
 
 constexpr int kLowPrecSteps = 12;   // conjugate-gradient steps allowed with a BF16/TF32 factor
+// With fallback on, an FP32 factor gets kFp32Steps steps per solve (the
+// two-level tier then costs less than iterating on), and an instance whose
+// FP32 solves took more than kFp32IterSteps steps in one interior-point
+// iteration (predictor and corrector) moves to the two-level tier for the
+// next: the step counts only grow as the iterations close in.
+constexpr int kFp32Steps = 8;
+constexpr int kFp32IterSteps = 8;
 
 int next_precision(int p) {
-    return (p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32) ? LQMPC_FP32 : LQMPC_FP64;
+    if (p == LQMPC_MIXED_BF16 || p == LQMPC_MIXED_TF32) return LQMPC_FP32;
+    return p == LQMPC_FP32 ? LQMPC_FP32X2 : LQMPC_FP64;
 }
 
 void write_scal(Batch& b, lqmpc_ctx* c) {
@@ -696,7 +730,8 @@ void write_scal(Batch& b, lqmpc_ctx* c) {
 // conjugate gradients preconditioned by the explicit inverse of the factor --
 // then settle.  An instance whose refinement does not converge (or whose
 // low-precision Cholesky meets a non-positive pivot even after the FP32
-// shift retries) moves to the next precision, BF16/TF32 -> FP32 -> FP64, for
+// shift retries) moves to the next precision, BF16/TF32 -> FP32 -> FP32X2
+// (the two-level FP32 preconditioner) -> FP64, for
 // the rest of the solve (fallback on), or finishes with LQMPC_ERR_STALL /
 // LQMPC_ERR_NOT_PD.  Relative diagonal shifts of a retried FP32 factor
 // change only the preconditioner: the conjugate gradients with FP64 products
@@ -706,6 +741,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
     launch_kkt_begin(b.d_insts, b.count, b.st);
     for (auto* c : b.ctxs) c->h_scal->kkt_pending = c->h_scal->done ? 0 : 1;   // the same on the host copy
     const int budget_lo = std::min(o.refine_max, kLowPrecSteps);
+    const int budget_mid = o.fallback ? std::min(o.refine_max, kFp32Steps) : o.refine_max;
     for (int round = 0; round < 4; ++round) {
         int present = 0;   // precisions among the pending instances
         for (auto* c : b.ctxs) {
@@ -717,10 +753,10 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
             return LQMPC_OK;
         }
         if (!formed || round > 0) {
-            for (int p = 0; p < 4; ++p) {
+            for (int p = 0; p < 5; ++p) {
                 if (!((present >> p) & 1)) continue;
                 const int sel = F_PENDING | prec_sel(1 << p);
-                if (p != LQMPC_FP32 && p != LQMPC_FP64) {
+                if (p != LQMPC_FP32 && p != LQMPC_FP32X2 && p != LQMPC_FP64) {
                     kkt_form(b, p, tm, 0.0, sel);
                     continue;
                 }
@@ -729,7 +765,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
                 // more decades than FP64 resolves); a shifted FP64 factor is
                 // only a preconditioner, so its solves are refined.
                 const double shifts32[3] = {0.0, 1e-6, 1e-4}, shifts64[3] = {0.0, 1e-12, 1e-9};
-                const double* shifts = p == LQMPC_FP32 ? shifts32 : shifts64;
+                const double* shifts = p == LQMPC_FP64 ? shifts64 : shifts32;
                 for (int a = 0; a < 3; ++a) {
                     if (a > 0 && p == LQMPC_FP64) polish = true;
                     kkt_form(b, p, tm, shifts[a], sel);
@@ -761,8 +797,9 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
                 if (st != LQMPC_OK) return st;
             }
         }
-        if (present & 0xE) {
-            lqmpc_status st = kkt_solve_mixed(b, o.refine_max, false, F_PENDING | prec_sel(0xE), budget_lo);
+        if (present & 0x1E) {
+            lqmpc_status st =
+                kkt_solve_mixed(b, o.refine_max, false, F_PENDING | prec_sel(0x1E), budget_lo, budget_mid);
             if (st != LQMPC_OK) return st;
         }
         // settle on the device and, from the host copies the solves just read
@@ -815,7 +852,8 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         // (no overlap of the head with the formation then).
         bool fp64_ahead = false;
         for (auto* c : b.ctxs)
-            if (!c->h_scal->done && c->h_scal->prec_cur == LQMPC_FP64) fp64_ahead = true;
+            if (!c->h_scal->done && (c->h_scal->prec_cur == LQMPC_FP64 || c->h_scal->prec_cur == LQMPC_FP32X2))
+                fp64_ahead = true;
         if (b.side && !fp64_ahead) {
             head_fork(b);
         } else {
@@ -878,6 +916,15 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             if (!c->h_scal->done) all_done = false;
         }
         if (all_done) break;
+        // an FP32 instance whose solves grew costly moves on to the two-level tier
+        for (auto* c : b.ctxs) {
+            Scal& S = *c->h_scal;
+            if (o.fallback && !S.done && S.prec_cur == LQMPC_FP32 && S.refine_iter > kFp32IterSteps) {
+                S.prec_cur = LQMPC_FP32X2;
+                S.fallbacks += 1;
+                write_scal(b, c);
+            }
+        }
     }
     join_head(b);
     cudaEventRecord(c0->ev[1], b.st);
@@ -993,7 +1040,7 @@ const char* lqmpc_status_str(int s) {
 }
 
 static bool opts_ok(const lqmpc_options& o) {
-    return o.tol > 0 && o.max_iter >= 1 && o.max_iter <= 100000 && o.precision >= 0 && o.precision <= 3 &&
+    return o.tol > 0 && o.max_iter >= 1 && o.max_iter <= 100000 && o.precision >= 0 && o.precision <= 4 &&
            o.refine_max >= 0 && o.refine_max <= 100 && o.refine_tol > 0 && o.tau > 0 && o.tau < 1;
 }
 
@@ -1609,7 +1656,7 @@ lqmpc_status lqmpc_form_kkt_noalloc(lqmpc_ctx* ctx, const double* sigx, const do
 
 lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* sigu, int precision,
                              const double* rhs, double* x, double* L, int* refine_steps) {
-    if (!ctx || !sigx || !sigu || !rhs || !x || precision < 0 || precision > 3) return LQMPC_ERR_ARG;
+    if (!ctx || !sigx || !sigu || !rhs || !x || precision < 0 || precision > 4) return LQMPC_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     if ((precision == LQMPC_MIXED_BF16 || precision == LQMPC_MIXED_TF32) && !ctx->tc_ok)
         return LQMPC_ERR_UNSUPPORTED;

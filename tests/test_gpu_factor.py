@@ -84,3 +84,28 @@ def test_fp32_inverse_preconditions_in_few_steps(case):
     res = np.max(np.abs(b - M @ r["x"])) / np.max(np.abs(b))
     assert res <= 2e-10, res
     assert r["refine_steps"] <= 8, r["refine_steps"]
+
+
+@pytest.mark.parametrize("spread", [1, 6])
+def test_two_level_preconditioner_converges_where_fp32_struggles(case, spread):
+    """LQMPC_FP32X2: the FP32 factor L1 of M, then the FP32 factor of
+    L1^-1 M L1^-T formed from E = M - L1 L1' (float-float), combined into
+    one explicit inverse.  With Sigma spread over 2 * spread decades either
+    side of one the solve must reach the same 2e-10 residual, in no more
+    conjugate-gradient steps than the FP32 factor alone needs (and in few
+    steps outright)."""
+    p, s, _, _, _, _ = case
+    rng = np.random.default_rng(21)
+    sigx = 10.0 ** rng.uniform(-spread, spread, p.ns * p.N)
+    sigu = 10.0 ** rng.uniform(-spread, spread, p.n) + 1e-3
+    Gam, _, H, _ = oracle.condensed(p, np.zeros(p.ns))
+    M = oracle.kkt_matrix(p, sigx, sigu, Gam, H)
+    b = rng.standard_normal(p.n)
+    r2 = s.kkt_solve(sigx, sigu, b, "fp32x2", check=False)
+    assert r2["status"] == 0, r2["status"]
+    res = np.max(np.abs(b - M @ r2["x"])) / np.max(np.abs(b))
+    assert res <= 2e-10, res
+    assert r2["refine_steps"] <= 6, r2["refine_steps"]
+    r1 = s.kkt_solve(sigx, sigu, b, "fp32", check=False)
+    if r1["status"] == 0:
+        assert r2["refine_steps"] <= r1["refine_steps"], (r2["refine_steps"], r1["refine_steps"])

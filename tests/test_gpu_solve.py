@@ -91,7 +91,7 @@ def test_mixed_heat2d_matches_oracle(precision, heat2d_gold):
     assert rel(u, heat2d_gold["heat2d_32_s0_u12"]) <= 1e-6
 
 
-@pytest.mark.parametrize("precision", ["fp64", "bf16"])
+@pytest.mark.parametrize("precision", ["fp64", "bf16", "fp32x2"])
 def test_mixed_heat1d_matches_oracle(precision, heat1d_gold):
     p, x0 = inputs.config_1d_small(1)
     s = binding.Solver(p, precision=precision, tol=1e-11)
@@ -260,6 +260,21 @@ def test_uneven_batch_fp32_factor_variants_match_single(variant):
         us, stats, code = binding.solve_batch(solvers, x0s)
     finally:
         os.environ.pop("LQMPC_POTRF", None)
+    assert code == 0
+    for k in range(len(inst)):
+        assert stats[k]["status"] == 0
+        ref = binding.Solver(inst[k][0], precision="fp64").solve(x0s[k])[0]
+        assert rel(us[k], ref) <= 1e-6, k
+
+
+def test_two_level_tier_batch_matches_fp64():
+    """A batch started in the two-level FP32 tier (FP64 formation, FP32
+    factor of M, FP32 factor of L1^-1 M L1^-T, combined inverse): every
+    instance within the mixed tiers' spread of its FP64 single solve."""
+    inst = inputs.batch_instances(256, 0)[:12]
+    solvers = [binding.Solver(p, precision="fp32x2") for p, _ in inst]
+    x0s = [x for _, x in inst]
+    us, stats, code = binding.solve_batch(solvers, x0s)
     assert code == 0
     for k in range(len(inst)):
         assert stats[k]["status"] == 0
