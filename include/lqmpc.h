@@ -229,8 +229,11 @@ lqmpc_status lqmpc_gamma_mv(lqmpc_ctx* ctx, const double* v, double* out);
 lqmpc_status lqmpc_gamma_tmv(lqmpc_ctx* ctx, const double* w, double* out);
 
 /* Form M = H + Gamma' diag(sigx) Gamma + diag(sigu) (Eq. 7) in the given
- * precision (LQMPC_FP64, LQMPC_MIXED_BF16, LQMPC_MIXED_TF32, LQMPC_FP32) and
- * return it as n x n doubles (full symmetric).  sigx: ns*N, sigu: n, >= 0. */
+ * precision (LQMPC_FP64, LQMPC_MIXED_BF16, LQMPC_MIXED_TF32, LQMPC_FP32; or
+ * LQMPC_FP32X2: the float-float Horner chains over the horizon that tier
+ * uses, available when the context forms FP64 matrices by the chains, else
+ * LQMPC_ERR_UNSUPPORTED) and return it as n x n doubles (full symmetric).
+ * sigx: ns*N, sigu: n, >= 0. */
 lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* sigu,
                             int precision, double* M);
 

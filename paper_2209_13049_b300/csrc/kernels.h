@@ -65,6 +65,9 @@ void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int
                      double shift = 0.0);
 double kkt_cost_syrk(int ns, int nu, int N);
 double kkt_cost_lyap(int ns, int nu, int N, long long nnzA, long long nnzB);
+// the same chains in float-float (the two-level FP32 tier's M; Sigma_x split into sig_ff first)
+void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
+                        cudaStream_t st, double shift);
 
 // kernels_chol.cu
 void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags, cudaStream_t st,

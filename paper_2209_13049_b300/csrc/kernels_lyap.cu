@@ -19,6 +19,8 @@
 // A' is available as CSR (the columns of A); B's nonzeros as per-column
 // lists.  For batches blockIdx.x runs over the largest (N, nu) and CTAs
 // outside an instance's own sizes return.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -71,13 +73,135 @@ __global__ void k_ly_chain(const Inst* __restrict__ insts, int flags, int max_nu
                 const int row = c1 * nu + a, cc = c * nu + col;
                 double v = s + I.H64[(size_t)row + (size_t)n * cc];
                 if (row == cc) v = (v + I.sigu[row]) * (1.0 + shift);   // shift: a retried factor
-                I.M64[(size_t)row + (size_t)n * cc] = v;
-                if (c1 < c) I.M64[(size_t)cc + (size_t)n * row] = v;
+                // within the diagonal block each pair is computed twice (by
+                // the CTAs of both columns): the lower one is written to both
+                if (c1 < c || row >= cc) I.M64[(size_t)row + (size_t)n * cc] = v;
+                if (c1 < c || row > cc) I.M64[(size_t)cc + (size_t)n * row] = v;
             }
         }
         // the next step overwrites the other buffer only; the dots above read
         // z0, which the step after it overwrites behind a barrier
     }
+}
+
+// The same chains in float-float on the FP32 pipes (FP64 runs at 1/64 of
+// its rate here): z as hi + lo planes in shared memory, A', B and G (G32 +
+// G32lo) as float-float pairs, Sigma_x split once per launch into sig_ff;
+// every multiply-add is an exact FP32 product (FMA) plus the cross terms,
+// summed by TwoSum.  About 2^-44 relative per operation, ~1e-12 after the
+// horizon's 50 steps: M for the two-level FP32 tier, whose E = M - L1 L1'
+// needs M far below FP32 rounding, not at FP64's.
+namespace {
+__device__ __forceinline__ void ffc_mac(float& ah, float& al, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    const float s = ah + p;
+    const float z = s - ah;
+    al += ((ah - (s - z)) + (p - z)) + e;
+    ah = s;
+}
+}  // namespace
+
+__global__ void k_sig_split(const Inst* __restrict__ insts, int flags) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int sx = I.SX;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < sx; k += gridDim.x * blockDim.x) {
+        const double v = I.sigx[k];
+        const float h = (float)v;
+        I.sig_ff[k] = h;
+        I.sig_ff[sx + k] = (float)(v - (double)h);
+    }
+}
+
+__global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max_nu, double shift) {
+    const Inst& I = insts[blockIdx.y];
+    if (skip_instance(I, flags)) return;
+    const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg, sx = I.SX;
+    const int c = blockIdx.x / max_nu, col = blockIdx.x % max_nu;
+    if (c >= N || col >= nu) return;
+    extern __shared__ float zf[];
+    float *z0h = zf, *z0l = zf + ns, *z1h = zf + 2 * ns, *z1l = zf + 3 * ns;
+    const int nnzA = I.at_ptr[ns], nnzB = I.bc_ptr[nu];
+    const float *ah = I.at_ff, *al = I.at_ff + nnzA;
+    // z <- A' z_old + Sigma_{c+d} G_d[:, col]  (scaled term only when d >= 0)
+    auto step = [&](const float* inh, const float* inl, float* outh, float* outl, int d) {
+        const float* sh = I.sig_ff + (size_t)(c + (d >= 0 ? d : 0)) * ns;
+        const float* sl = sh + sx;
+        const size_t go = (size_t)ldg * ((N - 1 - (d >= 0 ? d : 0)) * nu + col);
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            float th = 0.f, tl = 0.f;
+            if (d >= 0) ffc_mac(th, tl, sh[i], sl[i], I.G32[go + i], I.G32lo[go + i]);
+            for (int p = I.at_ptr[i]; p < I.at_ptr[i + 1]; ++p) {
+                const int q = I.at_idx[p];
+                ffc_mac(th, tl, ah[p], al[p], inh[q], inl[q]);
+            }
+            outh[i] = th;
+            outl[i] = tl;
+        }
+        __syncthreads();
+    };
+    {
+        const float* sh = I.sig_ff + (size_t)(N - 1) * ns;
+        const float* sl = sh + sx;
+        const size_t go = (size_t)ldg * (c * nu + col);   // G_{N-1-c}
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            float th = 0.f, tl = 0.f;
+            ffc_mac(th, tl, sh[i], sl[i], I.G32[go + i], I.G32lo[go + i]);
+            z0h[i] = th;
+            z0l[i] = tl;
+        }
+        __syncthreads();
+    }
+    for (int d = N - 2 - c; d >= 0; --d) {
+        step(z0h, z0l, z1h, z1l, d);
+        float* t = z0h; z0h = z1h; z1h = t;
+        t = z0l; z0l = z1l; z1l = t;
+    }
+    const float *bh = I.bc_ff, *bl = I.bc_ff + nnzB;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c1 = c; c1 >= 0; --c1) {
+        if (c1 < c) {
+            step(z0h, z0l, z1h, z1l, -1);
+            float* t = z0h; z0h = z1h; z1h = t;
+            t = z0l; z0l = z1l; z1l = t;
+        }
+        for (int a = warp; a < nu; a += nw) {
+            float th = 0.f, tl = 0.f;
+            for (int p = I.bc_ptr[a] + lane; p < I.bc_ptr[a + 1]; p += 32) {
+                const int q = I.bc_idx[p];
+                ffc_mac(th, tl, bh[p], bl[p], z0h[q], z0l[q]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, th, o), ol = __shfl_xor_sync(0xffffffffu, tl, o);
+                const float s2 = th + oh;
+                const float z = s2 - th;
+                tl += ((th - (s2 - z)) + (oh - z)) + ol;
+                th = s2;
+            }
+            if (lane == 0) {
+                const int row = c1 * nu + a, cc = c * nu + col;
+                double v = ((double)th + (double)tl) + I.H64[(size_t)row + (size_t)n * cc];
+                if (row == cc) v = (v + I.sigu[row]) * (1.0 + shift);
+                // within the diagonal block each pair is computed twice (by
+                // the CTAs of both columns): the lower one is written to both
+                if (c1 < c || row >= cc) I.M64[(size_t)row + (size_t)n * cc] = v;
+                if (c1 < c || row > cc) I.M64[(size_t)cc + (size_t)n * row] = v;
+            }
+        }
+    }
+}
+
+void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
+                        cudaStream_t st, double shift) {
+    LQ_LAUNCH(k_sig_split<<<dim3(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), 256, 0, st>>>(d_insts, flags));
+    const size_t smem = 4 * sizeof(float) * (size_t)max_ns;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_ly_chain_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LQ_LAUNCH(k_ly_chain_ff<<<dim3(max_N * max_nu, count), 256, smem, st>>>(d_insts, flags, max_nu, shift));
 }
 
 void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int flags,

@@ -222,6 +222,8 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     const size_t G = (size_t)I.ldg * n;
     auto at_ptr = c.take<int>(ns + 1); auto at_idx = c.take<int>(nnzA); auto at_val = c.take<double>(nnzA);
     auto bc_ptr = c.take<int>(nu + 1); auto bc_idx = c.take<int>(nnzB); auto bc_val = c.take<double>(nnzB);
+    auto at_ff = c.take<float>(2 * (size_t)nnzA); auto bc_ff = c.take<float>(2 * (size_t)nnzB);
+    auto sig_ff = c.take<float>(2 * (size_t)I.SX);
     auto a_ptr = c.take<int>(ns + 1); auto a_idx = c.take<int>(nnzA); auto a_val = c.take<double>(nnzA);
     auto q_ptr = c.take<int>(ns + 1); auto q_idx = c.take<int>(nnzQ); auto q_val = c.take<double>(nnzQ);
     auto qf_ptr = c.take<int>(ns + 1); auto qf_idx = c.take<int>(nnzQf); auto qf_val = c.take<double>(nnzQf);
@@ -295,6 +297,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
         I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
+        I.at_ff = at_ff; I.bc_ff = bc_ff; I.sig_ff = sig_ff;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
         I.Xlo32 = Xlo32; I.XloT32 = XloT32; I.r32lo = r32lo;
@@ -541,7 +544,7 @@ void kkt_form(const Batch& b, int prec, SyrkTimer* tm = nullptr, double shift = 
             // factored, then the factor of I + X1 E X1' and the combined inverse
             rec(c0->evk[2]);
             if (b.lyap) {
-                launch_kkt_lyap(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, sel, b.st, 0.0);
+                launch_kkt_lyap_ff(b.d_insts, b.count, b.max_ns, b.max_nu, b.max_N, b.max_sx, sel, b.st, 0.0);
             } else {
                 launch_syrk_cc(b.d_insts, b.count, b.max_n, b.cc_splits, 1, 0, nullptr, nullptr, sel, b.st);
                 launch_syrk_reduce(b.d_insts, b.count, b.max_n, b.cc_splits, 0, 1, 0, 1, sel, nullptr, b.st, 0.0);
@@ -1168,6 +1171,18 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     ok = ok && up(I.at_ptr, at_ptr.data(), sizeof(int) * (ns + 1)) && up(I.at_idx, at_idx.data(), sizeof(int) * nnzA) &&
          up(I.at_val, at_val.data(), sizeof(double) * nnzA) && up(I.bc_ptr, bc_ptr.data(), sizeof(int) * (nu + 1)) &&
          up(I.bc_idx, bc_idx.data(), sizeof(int) * nnzB) && up(I.bc_val, bc_val.data(), sizeof(double) * nnzB);
+    {   // float-float splits (hi plane, then lo plane) for the float-float Horner chains
+        auto split = [](const std::vector<double>& v) {
+            std::vector<float> f(2 * v.size());
+            for (size_t k = 0; k < v.size(); ++k) {
+                f[k] = (float)v[k];
+                f[v.size() + k] = (float)(v[k] - (double)f[k]);
+            }
+            return f;
+        };
+        const std::vector<float> af = split(at_val), bf = split(bc_val);
+        ok = ok && up(I.at_ff, af.data(), sizeof(float) * af.size()) && up(I.bc_ff, bf.data(), sizeof(float) * bf.size());
+    }
     {
         std::vector<int> plan = syrk_tc_make_plan(ns, nu, N);
         ok = ok && up(I.tc_plan, plan.data(), sizeof(int) * plan.size());
@@ -1609,10 +1624,11 @@ static lqmpc_status download_matrix(lqmpc_ctx* ctx, bool fp64, double* out, bool
 
 lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* sigu, int precision,
                             double* M) {
-    if (!ctx || !sigx || !sigu || !M || precision < 0 || precision > 3) return LQMPC_ERR_ARG;
+    if (!ctx || !sigx || !sigu || !M || precision < 0 || precision > 4) return LQMPC_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     if ((precision == LQMPC_MIXED_BF16 || precision == LQMPC_MIXED_TF32) && !ctx->tc_ok)
         return LQMPC_ERR_UNSUPPORTED;
+    if (precision == LQMPC_FP32X2 && !ctx->lyap) return LQMPC_ERR_UNSUPPORTED;
     lqmpc_status s = upload_sigma(ctx, sigx, sigu);
     if (s) return s;
     s = reset_scal(ctx);
@@ -1626,6 +1642,8 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
     if (precision == LQMPC_FP64) {
         launch_syrk_cc(b.d_insts, 1, I.n, b.cc_splits, 1, 0, nullptr, nullptr, F_NONE, b.st);
         launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
+    } else if (precision == LQMPC_FP32X2) {
+        launch_kkt_lyap_ff(b.d_insts, 1, I.ns, I.nu, I.N, I.SX, F_NONE, b.st, 0.0);
     } else if (precision == LQMPC_FP32) {
         launch_syrk_cc(b.d_insts, 1, I.n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
         launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st);
@@ -1635,7 +1653,7 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(b.st));
-    return download_matrix(ctx, precision == LQMPC_FP64, M, false);
+    return download_matrix(ctx, precision == LQMPC_FP64 || precision == LQMPC_FP32X2, M, false);
 }
 
 lqmpc_status lqmpc_form_kkt_noalloc(lqmpc_ctx* ctx, const double* sigx, const double* sigu, double* M) {

@@ -81,8 +81,11 @@ def _sigmas(p, seed, spread=2.0):
 
 
 @pytest.mark.parametrize("precision,rel", [("fp64", 1e-12), ("fp32", None), ("tf32", 4 * 2.0**-11),
-                                           ("bf16", 4 * 2.0**-8)])
+                                           ("bf16", 4 * 2.0**-8), ("fp32x2", 1e-10)])
 def test_kkt_matrix_matches_oracle(case, precision, rel):
+    """fp32x2: the float-float Horner chains of the two-level tier, a few
+    2^-44 per operation over the horizon's steps: bounded by 1e-10 of the
+    absolute sum, far below FP32 rounding (E = M - L1 L1' needs that)."""
     p, s, Gam, H = case
     sigx, sigu = _sigmas(p, 2)
     M = s.form_kkt(sigx, sigu, precision)
