@@ -109,7 +109,8 @@ struct Inst {
     float* ffv;                       // 2 x n: float-float split of the Gamma operand (hi, lo)
     const int* at_ptr; const int* at_idx; const double* at_val;   // A' in CSR (the columns of A)
     const int* bc_ptr; const int* bc_idx; const double* bc_val;   // nonzeros of B per column
-    const float* at_ff; const float* bc_ff;   // the same values split hi + lo (hi plane, then lo plane)
+    const int* at_pack;               // A' nonzeros packed as (column index, hi bits, lo bits, 0): float-float chains
+    const float* bc_ff;               // B's nonzeros split hi + lo (hi plane, then lo plane)
     float* sig_ff;                    // Sigma_x split hi + lo (SX each) for the float-float Horner chains
     float* XinvT32;                   // its transpose (coalesced rows)
     float* Tinv32;                    // n x n scratch of the inversion

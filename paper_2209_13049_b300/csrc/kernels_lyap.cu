@@ -122,24 +122,26 @@ __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg, sx = I.SX;
     const int c = blockIdx.x / max_nu, col = blockIdx.x % max_nu;
     if (c >= N || col >= nu) return;
-    extern __shared__ float zf[];
-    float *z0h = zf, *z0l = zf + ns, *z1h = zf + 2 * ns, *z1l = zf + 3 * ns;
-    const int nnzA = I.at_ptr[ns], nnzB = I.bc_ptr[nu];
-    const float *ah = I.at_ff, *al = I.at_ff + nnzA;
+    extern __shared__ float2 zf2[];    // z as (hi, lo) pairs, two buffers
+    float2* z0 = zf2;
+    float2* z1 = zf2 + ns;
+    // A' packed per nonzero as (column index, hi, lo): one 16-byte load each
+    const int4* ap = reinterpret_cast<const int4*>(I.at_pack);
     // z <- A' z_old + Sigma_{c+d} G_d[:, col]  (scaled term only when d >= 0)
-    auto step = [&](const float* inh, const float* inl, float* outh, float* outl, int d) {
+    auto step = [&](const float2* zin, float2* zout, int d) {
         const float* sh = I.sig_ff + (size_t)(c + (d >= 0 ? d : 0)) * ns;
         const float* sl = sh + sx;
         const size_t go = (size_t)ldg * ((N - 1 - (d >= 0 ? d : 0)) * nu + col);
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
             float th = 0.f, tl = 0.f;
             if (d >= 0) ffc_mac(th, tl, sh[i], sl[i], I.G32[go + i], I.G32lo[go + i]);
-            for (int p = I.at_ptr[i]; p < I.at_ptr[i + 1]; ++p) {
-                const int q = I.at_idx[p];
-                ffc_mac(th, tl, ah[p], al[p], inh[q], inl[q]);
+            const int p1 = I.at_ptr[i + 1];
+            for (int p = I.at_ptr[i]; p < p1; ++p) {
+                const int4 a = ap[p];
+                const float2 z = zin[a.x];
+                ffc_mac(th, tl, __int_as_float(a.y), __int_as_float(a.z), z.x, z.y);
             }
-            outh[i] = th;
-            outl[i] = tl;
+            zout[i] = make_float2(th, tl);
         }
         __syncthreads();
     };
@@ -150,29 +152,27 @@ __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
             float th = 0.f, tl = 0.f;
             ffc_mac(th, tl, sh[i], sl[i], I.G32[go + i], I.G32lo[go + i]);
-            z0h[i] = th;
-            z0l[i] = tl;
+            z0[i] = make_float2(th, tl);
         }
         __syncthreads();
     }
     for (int d = N - 2 - c; d >= 0; --d) {
-        step(z0h, z0l, z1h, z1l, d);
-        float* t = z0h; z0h = z1h; z1h = t;
-        t = z0l; z0l = z1l; z1l = t;
+        step(z0, z1, d);
+        float2* t = z0; z0 = z1; z1 = t;
     }
+    const int nnzB = I.bc_ptr[nu];
     const float *bh = I.bc_ff, *bl = I.bc_ff + nnzB;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int c1 = c; c1 >= 0; --c1) {
         if (c1 < c) {
-            step(z0h, z0l, z1h, z1l, -1);
-            float* t = z0h; z0h = z1h; z1h = t;
-            t = z0l; z0l = z1l; z1l = t;
+            step(z0, z1, -1);
+            float2* t = z0; z0 = z1; z1 = t;
         }
         for (int a = warp; a < nu; a += nw) {
             float th = 0.f, tl = 0.f;
             for (int p = I.bc_ptr[a] + lane; p < I.bc_ptr[a + 1]; p += 32) {
-                const int q = I.bc_idx[p];
-                ffc_mac(th, tl, bh[p], bl[p], z0h[q], z0l[q]);
+                const float2 z = z0[I.bc_idx[p]];
+                ffc_mac(th, tl, bh[p], bl[p], z.x, z.y);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -198,7 +198,7 @@ __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max
 void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
                         cudaStream_t st, double shift) {
     LQ_LAUNCH(k_sig_split<<<dim3(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), 256, 0, st>>>(d_insts, flags));
-    const size_t smem = 4 * sizeof(float) * (size_t)max_ns;
+    const size_t smem = 2 * sizeof(float2) * (size_t)max_ns;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ly_chain_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     LQ_LAUNCH(k_ly_chain_ff<<<dim3(max_N * max_nu, count), 256, smem, st>>>(d_insts, flags, max_nu, shift));

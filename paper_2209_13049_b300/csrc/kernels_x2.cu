@@ -43,9 +43,7 @@ namespace lqmpc {
 
 namespace {
 
-constexpr int kXb = 32;          // tile of the residual kernel
-constexpr int kGb = 64;          // tile of the FP32 products
-constexpr int kGk = 16;          // K step of the FP32 products
+constexpr int kXb = 32;          // tile edge (and K step) of every kernel here
 
 __device__ __forceinline__ float* x2_s1(const Inst& I) { return I.Tinv32; }
 __device__ __forceinline__ float* x2_s2a(const Inst& I) { return reinterpret_cast<float*>(I.M64); }
@@ -188,18 +186,18 @@ __global__ void __launch_bounds__(256) k_x2_trimul(const Inst* __restrict__ inst
     }
 }
 
-// FP32 products of the two-level preconditioner, C = A B over 64 x 64 output
+// FP32 products of the two-level preconditioner, C = A B over 32 x 32 output
 // tiles (column-major n x n), K limited to where the operands are nonzero:
 //   mode 0: S2a = G = X1 E                 A = X1 (Xinv32, k <= i), B = E (S1); all tiles
 //   mode 1: M32 = A2 = G X1' + W W'        A = G (S2a), B = X1' (XinvT32, k <= j), then
 //                                          A = W (S2b, k <= i), B = W' (k <= j); lower tiles
-// 256 threads, 4 x 4 entries each.
+// 256 threads, four entries each (row tid % 32, columns tid / 32 + 8 q), K in
+// steps of 32 staged through shared memory with coalesced loads.
 __global__ void __launch_bounds__(256) k_x2_gemm(const Inst* __restrict__ insts, int flags, int mode) {
-    __shared__ __align__(16) float As[kGk][kGb + 4];
-    __shared__ __align__(16) float Bs[kGk][kGb + 4];
+    __shared__ float As[kXb][kXb + 1], Bs[kXb][kXb + 1];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
-    const int n = I.n, nt = (n + kGb - 1) / kGb;
+    const int n = I.n, nt = (n + kXb - 1) / kXb;
     int ti, tj;
     if (mode == 0) {
         if ((int)blockIdx.x >= nt * nt) return;
@@ -209,54 +207,48 @@ __global__ void __launch_bounds__(256) k_x2_gemm(const Inst* __restrict__ insts,
         if ((int)blockIdx.x >= nt * (nt + 1) / 2) return;
         lower_tile(blockIdx.x, ti, tj);
     }
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;   // rows ty*4 .. +3, columns tx*4 .. +3
-    float acc[4][4] = {};
+    const int r = threadIdx.x % kXb, cb = threadIdx.x / kXb;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     // pass 0: X1 E (mode 0) or G X1' (mode 1); pass 1 (mode 1): W W'
     for (int pass = 0; pass < (mode == 0 ? 1 : 2); ++pass) {
         const float* A = mode == 0 ? I.Xinv32 : (pass == 0 ? x2_s2a(I) : x2_s2b(I));
-        const int k1 = min(n, ((mode == 0 ? ti : tj) + 1) * kGb);
+        const int kend = min(n, ((mode == 0 ? ti : tj) + 1) * kXb);
         const bool a_lower = mode == 0 || pass == 1;   // A(i, k) = 0 for k > i
-        for (int kb = 0; kb < k1; kb += kGk) {
-            for (int e = threadIdx.x; e < kGb * kGk; e += blockDim.x) {
-                const int rr = e % kGb, kk = e / kGb, i = ti * kGb + rr, k = kb + kk;
-                float a = 0.f;
-                if (i < n && k < k1 && (!a_lower || k <= i)) a = A[(size_t)i + (size_t)n * k];
-                As[kk][rr] = a;
-            }
-            for (int e = threadIdx.x; e < kGb * kGk; e += blockDim.x) {
-                const int kk = e % kGk, cc = e / kGk, j = tj * kGb + cc, k = kb + kk;
-                float bv = 0.f;
-                if (j < n && k < k1) {
-                    if (mode == 0) bv = x2_s1(I)[(size_t)k + (size_t)n * j];
-                    else if (k <= j) bv = pass == 0 ? I.XinvT32[(size_t)k + (size_t)n * j]
-                                                    : x2_s2b(I)[(size_t)j + (size_t)n * k];
+        for (int k0 = 0; k0 < kend; k0 += kXb) {
+            for (int e = threadIdx.x; e < kXb * kXb; e += blockDim.x) {
+                const int rr = e % kXb, kk = e / kXb, i = ti * kXb + rr, k = k0 + kk;
+                As[rr][kk] = (i < n && k < kend && (!a_lower || k <= i)) ? A[(size_t)i + (size_t)n * k] : 0.f;
+                if (mode == 1 && pass == 1) {   // W'(k, j) = W(j, k): j fastest
+                    const int jj = e % kXb, k2 = k0 + e / kXb, j = tj * kXb + jj;
+                    Bs[e / kXb][jj] = (j < n && k2 < kend && k2 <= j) ? x2_s2b(I)[(size_t)j + (size_t)n * k2] : 0.f;
+                } else {                        // B(k, j) column-major: k fastest
+                    const int j = tj * kXb + kk;   // here kk runs over columns, rr over k
+                    const int k2 = k0 + rr;
+                    float bv = 0.f;
+                    if (j < n && k2 < kend) {
+                        if (mode == 0) bv = x2_s1(I)[(size_t)k2 + (size_t)n * j];
+                        else if (k2 <= j) bv = I.XinvT32[(size_t)k2 + (size_t)n * j];
+                    }
+                    Bs[rr][kk] = bv;
                 }
-                Bs[kk][cc] = bv;
             }
             __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < kXb; ++kk) {
+                const float a = As[r][kk];
 #pragma unroll
-            for (int kk = 0; kk < kGk; ++kk) {
-                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-                const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+                for (int q = 0; q < 4; ++q) acc[q] = fmaf(a, Bs[kk][cb + 8 * q], acc[q]);
             }
             __syncthreads();
         }
     }
+    const int i = ti * kXb + r;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int i = ti * kGb + ty * 4 + u;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int j = tj * kGb + tx * 4 + v;
-            if (i >= n || j >= n) continue;
-            if (mode == 0) x2_s2a(I)[(size_t)i + (size_t)n * j] = acc[u][v];
-            else if (j <= i) I.M32[(size_t)i + (size_t)n * j] = acc[u][v];
-        }
+    for (int q = 0; q < 4; ++q) {
+        const int j = tj * kXb + cb + 8 * q;
+        if (i >= n || j >= n) continue;
+        if (mode == 0) x2_s2a(I)[(size_t)i + (size_t)n * j] = acc[q];
+        else if (j <= i) I.M32[(size_t)i + (size_t)n * j] = acc[q];
     }
 }
 
@@ -290,12 +282,12 @@ void launch_x2_round(const Inst* d_insts, int count, int max_n, int flags, cudaS
 }
 
 void launch_x2_refine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st) {
-    const int nt = (max_n + kXb - 1) / kXb, gt = (max_n + kGb - 1) / kGb;
+    const int nt = (max_n + kXb - 1) / kXb;
     const int cblocks = std::min(1024, ((max_n * max_n) + 255) / 256);
     LQ_LAUNCH(k_x2_resid<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags));
     LQ_LAUNCH(k_x2_trimul<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 0));
-    LQ_LAUNCH(k_x2_gemm<<<dim3(gt * gt, count), 256, 0, st>>>(d_insts, flags, 0));
-    LQ_LAUNCH(k_x2_gemm<<<dim3(gt * (gt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 1));
+    LQ_LAUNCH(k_x2_gemm<<<dim3(nt * nt, count), 256, 0, st>>>(d_insts, flags, 0));
+    LQ_LAUNCH(k_x2_gemm<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 1));
     LQ_LAUNCH(k_x2_copy<<<dim3(cblocks, count), 256, 0, st>>>(d_insts, flags, 0));
 }
 

@@ -222,7 +222,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     const size_t G = (size_t)I.ldg * n;
     auto at_ptr = c.take<int>(ns + 1); auto at_idx = c.take<int>(nnzA); auto at_val = c.take<double>(nnzA);
     auto bc_ptr = c.take<int>(nu + 1); auto bc_idx = c.take<int>(nnzB); auto bc_val = c.take<double>(nnzB);
-    auto at_ff = c.take<float>(2 * (size_t)nnzA); auto bc_ff = c.take<float>(2 * (size_t)nnzB);
+    auto at_pack = c.take<int>(4 * (size_t)nnzA); auto bc_ff = c.take<float>(2 * (size_t)nnzB);
     auto sig_ff = c.take<float>(2 * (size_t)I.SX);
     auto a_ptr = c.take<int>(ns + 1); auto a_idx = c.take<int>(nnzA); auto a_val = c.take<double>(nnzA);
     auto q_ptr = c.take<int>(ns + 1); auto q_idx = c.take<int>(nnzQ); auto q_val = c.take<double>(nnzQ);
@@ -297,7 +297,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ffv = ffv;
         I.at_ptr = at_ptr; I.at_idx = at_idx; I.at_val = at_val;
         I.bc_ptr = bc_ptr; I.bc_idx = bc_idx; I.bc_val = bc_val;
-        I.at_ff = at_ff; I.bc_ff = bc_ff; I.sig_ff = sig_ff;
+        I.at_pack = at_pack; I.bc_ff = bc_ff; I.sig_ff = sig_ff;
         I.pp = pp; I.qq = qq; I.dxs = dxs;
         I.gpart = gpart; I.r32 = r32; I.syrk_ws = syrk_ws; I.syrk_ws_bytes = ws;
         I.Xlo32 = Xlo32; I.XloT32 = XloT32; I.r32lo = r32lo;
@@ -1181,7 +1181,14 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
             return f;
         };
         const std::vector<float> af = split(at_val), bf = split(bc_val);
-        ok = ok && up(I.at_ff, af.data(), sizeof(float) * af.size()) && up(I.bc_ff, bf.data(), sizeof(float) * bf.size());
+        std::vector<int> pack(4 * (size_t)nnzA, 0);
+        for (int k = 0; k < nnzA; ++k) {
+            pack[4 * (size_t)k] = at_idx[k];
+            memcpy(&pack[4 * (size_t)k + 1], &af[k], sizeof(float));
+            memcpy(&pack[4 * (size_t)k + 2], &af[nnzA + k], sizeof(float));
+        }
+        ok = ok && up(I.at_pack, pack.data(), sizeof(int) * pack.size()) &&
+             up(I.bc_ff, bf.data(), sizeof(float) * bf.size());
     }
     {
         std::vector<int> plan = syrk_tc_make_plan(ns, nu, N);
