@@ -162,6 +162,17 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
 // F_N_LE_512 / F_N_GT_512 keep only the instances with n <= 512 / n > 512 (the
 // cluster Cholesky's limit: a batch then factors its small instances in
 // clusters and only its large ones with the grid-cooperative kernel).
+// Blocks per instance of a grid-stride kernel: `nb` fills the GPU for one
+// instance; in a batch the instances share it, so each gets a share of about
+// 4096 CTAs in all (at least `lo`): the launch stays a few waves and the CTAs
+// of instances a launch skips cost little.
+inline int per_instance_blocks(int nb, int count, int lo = 4) {
+    if (count <= 1) return nb;
+    int share = (4096 + count - 1) / count;
+    if (share < lo) share = lo;
+    return nb < share ? nb : share;
+}
+
 constexpr int kPrecTwoLevel = 4;   // Scal::prec_cur of the two-level FP32 tier (LQMPC_FP32X2)
 
 enum Flags : int { F_NONE = 0, F_FORCE = 1, F_SKIP_REFINED = 2, F_PENDING = 4, F_N_LE_512 = 16, F_N_GT_512 = 32 };

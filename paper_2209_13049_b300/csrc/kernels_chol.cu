@@ -724,7 +724,7 @@ void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, i
                        cudaStream_t st, int tail) {
     // one warp per row (column), two warps per CTA: every SM takes part
     int nb = (max_n + 1) / 2;
-    nb = nb > 8192 ? 8192 : nb;
+    nb = per_instance_blocks(nb > 8192 ? 8192 : nb, count);
     LQ_LAUNCH(k_prec_lower<<<dim3(nb, count), 64, 0, st>>>(d_insts, in_role, flags));
     LQ_LAUNCH(k_prec_upper<<<dim3(nb, count), 64, 0, st>>>(d_insts, out_role, flags, tail));
 }

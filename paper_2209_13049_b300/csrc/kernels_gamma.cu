@@ -609,7 +609,7 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
         LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
     LQ_LAUNCH(k_gamma_mv_ff<<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
     int nb = (max_ns * max_N + 255) / 256;
-    nb = nb > 4096 ? 4096 : nb;
+    nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
     LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits, fuse));
 }
 
@@ -624,7 +624,7 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
     const int tiles = ((max_n + kFfBM - 1) / kFfBM) * (NV * ((max_N + kFfBN - 1) / kFfBN));
     const int splits = gamma_tmv_ff_splits(count, max_ns, max_N, max_n, NV);
     int nb = (NV * max_n + 1) / 2;   // two warps (two outputs) per CTA: every SM takes part
-    nb = nb > 8192 ? 8192 : nb;
+    nb = per_instance_blocks(nb > 8192 ? 8192 : nb, count);
     int npre = (max_ns * max_N + 255) / 256;
     npre = npre > 4096 ? 4096 : npre;
     if (!(fuse & kFuseInSplit))

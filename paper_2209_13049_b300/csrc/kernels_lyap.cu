@@ -197,7 +197,8 @@ __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max
 
 void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
                         cudaStream_t st, double shift) {
-    LQ_LAUNCH(k_sig_split<<<dim3(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), 256, 0, st>>>(d_insts, flags));
+    LQ_LAUNCH(k_sig_split<<<dim3(per_instance_blocks(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), count), 256,
+                                0, st>>>(d_insts, flags));
     const size_t smem = 2 * sizeof(float2) * (size_t)max_ns;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ly_chain_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -299,7 +299,7 @@ void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int 
 void launch_pcg_matvec_ff(const Inst* d_insts, int count, int max_n, int splits, int mode, int sel,
                           cudaStream_t st) {
     const int wpb = 2;   // two rows per CTA: every SM takes part
-    const int nb = nblk(max_n, wpb, kMaxParts);
+    const int nb = per_instance_blocks(nblk(max_n, wpb, kMaxParts), count);
     LQ_LAUNCH(k_pcg_matvec_ff<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel, splits));
 }
 
@@ -308,7 +308,7 @@ void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) 
 }
 
 void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st) {
-    int nb = nblk(max_total, 256, kMaxParts);
+    int nb = per_instance_blocks(nblk(max_total, 256, kMaxParts), count);
     LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts, sel));
 }
 

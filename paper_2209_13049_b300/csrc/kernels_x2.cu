@@ -277,13 +277,13 @@ __global__ void k_x2_copy(const Inst* __restrict__ insts, int flags, int what) {
 }
 
 void launch_x2_round(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st, double shift) {
-    const int blocks = std::min(1024, ((max_n * max_n) + 255) / 256);
+    const int blocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
     LQ_LAUNCH(k_x2_round<<<dim3(blocks, count), 256, 0, st>>>(d_insts, flags, shift));
 }
 
 void launch_x2_refine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st) {
     const int nt = (max_n + kXb - 1) / kXb;
-    const int cblocks = std::min(1024, ((max_n * max_n) + 255) / 256);
+    const int cblocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
     LQ_LAUNCH(k_x2_resid<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags));
     LQ_LAUNCH(k_x2_trimul<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 0));
     LQ_LAUNCH(k_x2_gemm<<<dim3(nt * nt, count), 256, 0, st>>>(d_insts, flags, 0));
@@ -293,7 +293,7 @@ void launch_x2_refine(const Inst* d_insts, int count, int max_n, int flags, cuda
 
 void launch_x2_combine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st) {
     const int nt = (max_n + kXb - 1) / kXb;
-    const int cblocks = std::min(1024, ((max_n * max_n) + 255) / 256);
+    const int cblocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
     LQ_LAUNCH(k_x2_trimul<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 1));
     LQ_LAUNCH(k_x2_copy<<<dim3(cblocks, count), 256, 0, st>>>(d_insts, flags, 1));
 }
