@@ -63,6 +63,7 @@ struct Scal {
     int kkt_pending;    // the current KKT solve of this instance is not settled yet
     int refine_budget;  // conjugate-gradient steps allowed for the current right-hand side
     int arrive;         // CTAs of the current launch that finished (last_arrival), 0 between launches
+    int pcg_loops;      // passes of the device-side conjugate-gradient loop in the latest solve (instance 0)
 };
 
 // Device descriptor of one instance (all pointers are device memory).
@@ -127,7 +128,8 @@ struct Inst {
     size_t syrk_ws_bytes;
     const int* tc_plan;               // tensor-core SYRK: per lower tile (splits, first partial)
     double* part;                     // kParts x kMaxParts reduction partials
-    unsigned* bar;                    // grid-barrier state (2 words), queued Cholesky tickets (2 words)
+    unsigned* bar;                    // grid-barrier state (2 words), queued Cholesky tickets (2 words),
+                                      // device-side conjugate-gradient loop count (1 word)
     int* pflags;                      // dataflow Cholesky: epoch, finished tasks, flag per (block column, row block)
     const int* ftasks;                // queued dataflow Cholesky: task list of this instance alone
     Scal* sc;

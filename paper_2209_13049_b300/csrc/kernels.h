@@ -99,6 +99,9 @@ void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int 
 
 // kernels_refine.cu (preconditioned conjugate gradients on M du = b; `sel`
 // is the launch predicate that picks the instances of the solve)
+// loop control of the device-side conjugate-gradient loop (while node of a captured graph)
+void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset,
+                     cudaStream_t st);
 void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, int budget_mid,
                       cudaStream_t st);
 void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st);

@@ -172,6 +172,35 @@ __device__ void pcg_test(const Inst& I, double rn) {
     }
 }
 
+// Control of the device-side conjugate-gradient loop (the while node of a
+// captured graph): go on while some selected instance's refinement is
+// neither converged nor failed (nor its factor failed), for at most `cap`
+// passes.  reset: the pass count restarts (the launch after the initial
+// residual).  The pass count is left in instance 0's Scal for the host.
+__global__ void k_pcg_more(const Inst* __restrict__ insts, int count, int selr, cudaGraphConditionalHandle h,
+                           int cap, int reset) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < count; q += blockDim.x) {
+        const Inst& I = insts[q];
+        if (!skip_instance(I, selr) && !I.sc->info) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned* loops = insts[0].bar + 4;
+        const unsigned k = reset ? 0u : *loops + 1u;
+        *loops = k;
+        insts[0].sc->pcg_loops = (int)k;
+        cudaGraphSetConditional(h, (any && k < (unsigned)cap) ? 1u : 0u);
+    }
+}
+
+void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset,
+                     cudaStream_t st) {
+    LQ_LAUNCH(k_pcg_more<<<1, 256, 0, st>>>(d_insts, count, selr, h, cap, reset));
+}
+
 // p = z, rz = r'z (one block per instance).
 __global__ void k_pcg_pinit(const Inst* __restrict__ insts, int sel) {
     __shared__ double red[32];

@@ -116,7 +116,8 @@ namespace lqmpc {
 // as the descriptor array it was captured with.
 struct GraphSeg {
     cudaGraphExec_t exec = nullptr;
-    unsigned long long kernels = 0;   // kernel launches one replay performs
+    unsigned long long kernels = 0;   // kernel launches one replay performs (before any loop)
+    unsigned long long pass_kernels = 0;   // kernel launches of one pass of its device-side loop
     bool bad = false;                 // capture or instantiation failed: launch directly
 };
 struct GraphCache {
@@ -273,7 +274,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     size_t ws = std::max(ws_cc, ws_tc);
     auto syrk_ws = c.take<unsigned char>(ws);
     auto part = c.take<double>((size_t)kParts * kMaxParts);
-    auto bar = c.take<unsigned>(4);
+    auto bar = c.take<unsigned>(6);
     auto sc = c.take<Scal>(1);
     auto trace = c.take<double>((size_t)(max_iter + 1) * kTraceW);
     if (kAssign) {
@@ -393,9 +394,91 @@ void seg_run(const Batch& b, int key, F&& body) {
     if (cudaGraphLaunch(g.exec, b.st) == cudaSuccess) note_launches((int)g.kernels);
 }
 
+// The conjugate-gradient loop as one graph: the start (`first`, ending with a
+// loop-control launch that restarts the pass count) and a while node whose
+// body is `pass` (two steps) plus the loop control, which stops when no
+// selected instance is still refining or after `cap` passes.  The host reads
+// the instance flags once, after the whole loop.  Returns false (nothing
+// launched) when graphs are off or the graph could not be built; the caller
+// then runs the loop from the host.
+template <class F1, class F2>
+bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, F1&& first, F2&& pass) {
+    if (!b.gc || !graphs_enabled()) return false;
+    GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];
+    if (g.bad) return false;
+    if (!g.exec) {
+        auto fail = [&](const char* what, cudaError_t e) {
+            if (getenv("LQMPC_DEBUG"))
+                fprintf(stderr, "lqmpc: conjugate-gradient loop graph: %s (%s); host loop instead\n", what,
+                        cudaGetErrorString(e));
+            cudaGetLastError();
+            g.bad = true;
+            return false;
+        };
+        const unsigned long long k0 = lqmpc_kernel_launches();
+        cudaError_t e = cudaStreamBeginCapture(b.st, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return fail("capture", e);
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t graph = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraphConditionalHandle h = 0;
+        e = cudaStreamGetCaptureInfo(b.st, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            first();
+            launch_pcg_more(b.d_insts, b.count, selr, h, cap, 1, b.st);
+            e = cudaStreamGetCaptureInfo(b.st, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+        }
+        cudaGraphNode_t wnode = nullptr;
+        cudaGraph_t body = nullptr;
+        if (e == cudaSuccess) {
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &cp);
+            if (e == cudaSuccess) {
+                body = cp.conditional.phGraph_out[0];
+                e = cudaStreamUpdateCaptureDependencies(b.st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+            }
+        }
+        cudaGraph_t done = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(b.st, &done);
+        if (e == cudaSuccess) e = e2;
+        const unsigned long long n_first = lqmpc_kernel_launches() - k0;
+        unsigned long long n_pass = 0;
+        if (e == cudaSuccess) {   // the loop body, captured into the while node's graph
+            const unsigned long long k1 = lqmpc_kernel_launches();
+            e = cudaStreamBeginCaptureToGraph(b.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                pass();
+                launch_pcg_more(b.d_insts, b.count, selr, h, cap, 0, b.st);
+                cudaGraph_t bg = nullptr;
+                e = cudaStreamEndCapture(b.st, &bg);
+            }
+            n_pass = lqmpc_kernel_launches() - k1;
+        }
+        note_launches(-(int)(lqmpc_kernel_launches() - k0));   // captured, not run
+        if (e == cudaSuccess && done) e = cudaGraphInstantiate(&g.exec, done, 0);
+        if (done) cudaGraphDestroy(done);
+        if (e != cudaSuccess || !g.exec) {
+            g.exec = nullptr;
+            return fail("build", e);
+        }
+        g.kernels = n_first;
+        g.pass_kernels = n_pass;
+    }
+    if (cudaGraphLaunch(g.exec, b.st) != cudaSuccess) return false;
+    note_launches((int)g.kernels);
+    return true;
+}
+
 enum SegKey {
     SEG_HEAD = 1, SEG_HEAD_R = 2, SEG_HEAD_SIDE = 3, SEG_HEAD_CHECK = 4, SEG_FORM = 10 /* + precision */,
-    SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31, SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50
+    SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31, SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50,
+    SEG_PCG_LOOP = 60 /* + 100 with the FP64 preconditioner */
 };
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
@@ -650,13 +733,14 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         }
     };
     const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
-    seg_run(b, SEG_PCG0 + kp, [&]() {
+    // start: ||b||, du = P^{-1} b, the initial residual r = b - M du (and
+    // Gamma du), z = P^{-1} r and the first direction
+    auto first = [&]() {
         launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, budget_mid, b.st);
         prec(R_B, R_DU, sel);
-        // initial residual r = b - M du and Gamma du
         pcg_apply_m(b, R_DU, 0, sel, selr, true, false);
         prec(R_RHO, R_DCORR, selr, 1);
-    });
+    };
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and
     // the new direction (harmless after the last step: every kernel is
     // predicated on the instance's refinement flags)
@@ -666,10 +750,22 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         if (!with_next) return;
         prec(R_RHO, R_DCORR, selr, 2);
     };
-    // The host looks at the flags after the initial residual and after every
-    // second step, and stops launching once every unfinished instance has
-    // converged or failed (one read per look; the last one leaves each h_scal
-    // holding the outcome).
+    // With graphs the whole loop runs on the device (a while node, two steps
+    // per pass) and the host reads the flags once at the end; otherwise the
+    // host looks at them after the start and after every second step, and
+    // stops launching once every unfinished instance has converged or failed
+    // (the last read leaves each h_scal holding the outcome).
+    {
+        const int key = SEG_PCG_LOOP + kp;
+        if (pcg_loop_graph(b, key, selr, (refine_max + 1) / 2, first, [&]() { step(true); step(true); })) {
+            lqmpc_status st = read_scals(b);
+            if (st != LQMPC_OK) return st;
+            const GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];
+            note_launches((int)(g.pass_kernels * (unsigned long long)b.ctxs[0]->h_scal->pcg_loops));
+            return LQMPC_OK;
+        }
+    }
+    seg_run(b, SEG_PCG0 + kp, first);
     auto pending = [&]() {
         for (auto* c : b.ctxs)
             if (host_selected(*c->h_scal, selr) && !c->h_scal->info) return true;

@@ -1,6 +1,7 @@
 """Captured CUDA graphs of the fixed launch sequences of an iteration replay
 exactly the kernels a direct launch sequence runs: same results bit for bit
-and the same kernel count (child processes, graphs on and off)."""
+and the same kernels, plus the device-side conjugate-gradient loop's own
+control launches (child processes, graphs on and off)."""
 import json
 import os
 import subprocess
@@ -59,5 +60,9 @@ def test_graph_replay_equals_direct_launches():
     assert "graph capture" not in err_on and "capture unavailable" not in err_on, err_on[-2000:]
     for key in ("fp64", "bf16", "fp32"):
         assert on[key]["u"] == off[key]["u"], key
-        assert on[key]["launches"] == off[key]["launches"], key
+        # with graphs the conjugate-gradient loop runs on the device: the same
+        # kernels plus one loop-control launch at its start and one per pass
+        # of two steps (one per KKT solve and per two steps: under 10% here)
+        extra = on[key]["launches"] - off[key]["launches"]
+        assert 0 <= extra <= 0.1 * off[key]["launches"], (key, on[key]["launches"], off[key]["launches"])
     assert on["batch"]["u"] == off["batch"]["u"]
