@@ -109,8 +109,10 @@ __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts,
 // M[j,k] = base[j,k] + sum_s partial_s[max, min] + [j==k] sigu[j].
 // base_mode 0: H (FP64 or FP32 copy), 1: Rbar (block diagonal from R), 2: none.
 // Tout = double writes M64, float writes M32.  TP is the partial type,
-// TILE the tile edge of the partial layout.
-template <typename TP, typename Tout, int TILE, bool COLMAJOR = false>
+// TILE the tile edge of the partial layout.  LOWER: the lower triangle only
+// (the FP32 factorisations read nothing else), with FP32 partials summed in
+// float-float (TwoSum) rather than by a dependent chain of FP64 adds.
+template <typename TP, typename Tout, int TILE, bool COLMAJOR = false, bool LOWER = false>
 __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int base_mode,
                               int add_sigu, int force, Tout* out_override, double shift) {
     const Inst& I = insts[blockIdx.y];
@@ -123,6 +125,7 @@ __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int ba
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (size_t)gridDim.x * blockDim.x) {
         int j = (int)(q % n), k = (int)(q / n);
+        if (LOWER && j < k) continue;
         int p = j > k ? j : k, m = j > k ? k : j;
         int a = p / TILE, b = m / TILE;
         int t = a * (a + 1) / 2 + b;
@@ -131,7 +134,19 @@ __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int ba
         const TP* src = ws + (size_t)first * TILE * TILE +
                         (COLMAJOR ? (m % TILE) * TILE + (p % TILE) : (p % TILE) * TILE + (m % TILE));
         double acc = 0.0;
-        for (int s = 0; s < cnt; ++s) acc += (double)src[(size_t)s * TILE * TILE];
+        if (LOWER && sizeof(TP) == 4) {
+            float sh = 0.f, sl = 0.f;
+            for (int s = 0; s < cnt; ++s) {
+                const float x = (float)src[(size_t)s * TILE * TILE];
+                const float t = sh + x;
+                const float z = t - sh;
+                sl += (sh - (t - z)) + (x - z);
+                sh = t;
+            }
+            acc = (double)sh + (double)sl;
+        } else {
+            for (int s = 0; s < cnt; ++s) acc += (double)src[(size_t)s * TILE * TILE];
+        }
         double base = 0.0;
         if (base_mode == 0) base = sizeof(Tout) == 8 ? I.H64[q] : (double)I.H32[q];
         else if (base_mode == 1) {
@@ -193,7 +208,7 @@ void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, i
         else LQ_LAUNCH(k_syrk_reduce<float, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     } else {                     // FP32 partials, 128-tiles, column-major (tensor-core SYRK)
         if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
-        else LQ_LAUNCH(k_syrk_reduce<float, float, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
+        else LQ_LAUNCH(k_syrk_reduce<float, float, 128, true, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     }
 }
 

@@ -1718,6 +1718,10 @@ static lqmpc_status download_matrix(lqmpc_ctx* ctx, bool fp64, double* out, bool
         std::vector<float> t(nn);
         CK(cudaMemcpy(t.data(), I.M32, sizeof(float) * nn, cudaMemcpyDeviceToHost));
         for (size_t q = 0; q < nn; ++q) out[q] = t[q];
+        // the FP32 formations may write the lower triangle only: mirror it
+        if (!lower_only)
+            for (int k = 0; k < I.n; ++k)
+                for (int j = 0; j < k; ++j) out[j + (size_t)I.n * k] = out[k + (size_t)I.n * j];
     }
     if (lower_only)
         for (int k = 0; k < I.n; ++k)
