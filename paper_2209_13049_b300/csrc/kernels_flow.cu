@@ -403,6 +403,11 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
     if (next) {
         form_t(false, 1);
         solve_store(j + 1);
+        // L_{j+1,j} out before L_jj and X_jj: its release then waits on its
+        // own stores only (the CTA barrier orders them before thread 0's
+        // release)
+        __syncthreads();
+        if (threadIdx.x == 0) st_flag_release(flg + j * nt + j + 1, ep);
     }
     for (int c = warp; c < kn; c += 8) {
         if (lane < kn && lane >= c) {
@@ -413,13 +418,8 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
         }
     }
     for (int e = threadIdx.x; e < kFb * kFb; e += blockDim.x) Xs[e] = Dv[e >> 5][e & 31];
-    // the CTA barrier orders every thread's stores before thread 0's
-    // release of the flags
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (next) st_flag_release(flg + j * nt + j + 1, ep);
-        st_flag_release(flg + j * nt + j, ep);
-    }
+    if (threadIdx.x == 0) st_flag_release(flg + j * nt + j, ep);
     // the rest of the column
     for (int p = j + 2; p < nt; ++p) {
         gather(p);
@@ -626,6 +626,8 @@ __device__ __forceinline__ void flowq_factor(const Inst& I, int j, int ep, const
     if (next) {
         form_t_q(T, s.As, s.Red, false, kn, 1);
         solve_store_q(T, Dv, M, n, r0, kn, j + 1);
+        __syncthreads();   // L_{j+1,j} out before L_jj and X_jj (a shorter release)
+        if (threadIdx.x == 0) st_flag_release(flg + j * nt + j + 1, ep);
     }
     for (int c = warp; c < kn; c += 8) {
         if (lane < kn && lane >= c) {
@@ -636,10 +638,7 @@ __device__ __forceinline__ void flowq_factor(const Inst& I, int j, int ep, const
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (next) st_flag_release(flg + j * nt + j + 1, ep);
-        st_flag_release(flg + j * nt + j, ep);
-    }
+    if (threadIdx.x == 0) st_flag_release(flg + j * nt + j, ep);
     // the rest of the column
     for (int p = j + 2; p < nt; ++p) {
         const int p0 = kFb * p, pr = min(kFb, n - p0);
