@@ -233,14 +233,17 @@ __device__ __forceinline__ double block_reduce(double v, double* smem32) {
 // call it (the launch predicates are uniform per instance).
 __device__ __forceinline__ bool last_arrival(Scal* S) {
     __shared__ int last;
-    __threadfence();
+    // the CTA barrier orders every thread's writes before thread 0's
+    // acquire-release count; the last CTA's acquire then sees every other
+    // CTA's writes, and the second barrier passes that on to its threads
     __syncthreads();
     if (threadIdx.x == 0) {
-        last = atomicAdd(&S->arrive, 1) == (int)gridDim.x - 1;
+        int old;
+        asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], 1;" : "=r"(old) : "l"(&S->arrive) : "memory");
+        last = old == (int)gridDim.x - 1;
         if (last) atomicExch(&S->arrive, 0);
     }
     __syncthreads();
-    if (last) __threadfence();
     return last;
 }
 

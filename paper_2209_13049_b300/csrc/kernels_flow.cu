@@ -43,7 +43,14 @@ __device__ __forceinline__ int ld_flag(const int* p) { return *(const volatile i
 __device__ __forceinline__ void st_flag_release(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// Flag load with acquire semantics at GPU scope: synchronises with the
+// writer's release without a full fence (which would also wait for this
+// thread's own outstanding stores).
+__device__ __forceinline__ int ld_flag_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // 16-byte global -> shared copy through L2 only (other CTAs' data is read
 // after their flag), zero-filled past `bytes` (0..16).
@@ -112,7 +119,7 @@ __device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k
         int idx = -1;
         if (lane < cnt) idx = (k0 + lane) * nt + p;
         else if (lane == cnt && extra >= 0) idx = extra;
-        bool ok = idx < 0 || ld_flag(flg + idx) == ep;
+        bool ok = idx < 0 || ld_flag_acquire(flg + idx) == ep;
         uint32_t it = 0;
         while (!__all_sync(0xffffffffu, ok)) {
             // give up after the bound, or at once after a wait anywhere gave up
@@ -123,9 +130,8 @@ __device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k
                 break;
             }
             __nanosleep(64);
-            if (!ok) ok = ld_flag(flg + idx) == ep;
+            if (!ok) ok = ld_flag_acquire(flg + idx) == ep;
         }
-        fence_acquire();
     }
     if (W == 0) __syncthreads();
     else bar_w17();
