@@ -476,15 +476,12 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ 
         }
         __syncthreads();
     }
-    // the last CTA to finish advances the epoch (every CTA has read it by then)
+    // the last CTA to finish advances the epoch (every CTA has read it by
+    // then; the next launch reads it after this one's end, so no fence)
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(done, 1) == nt - 1) {
-            atomicExch(done, 0);
-            __threadfence();
-            atomicAdd(epoch, 1);
-        }
+    if (threadIdx.x == 0 && atomicAdd(done, 1) == nt - 1) {
+        atomicExch(done, 0);
+        atomicAdd(epoch, 1);
     }
 }
 
@@ -770,14 +767,13 @@ __global__ void __launch_bounds__(256, 1) k_potrf_flowq(const Inst* __restrict__
         else flowq_factor(I, j, ep, s, T, D, Dv, warm);
         warm = false;
         // the instance's last task to finish advances its epoch (every task
-        // of it has read the epoch by then)
+        // of it has read the epoch by then; later launches read it after this
+        // one's end, so no fence)
         __syncthreads();
         if (threadIdx.x == 0) {
             const int nt = (I.n + kFb - 1) / kFb;
-            __threadfence();
             if (atomicAdd(I.pflags + 1, 1) == 2 * nt - 2) {
                 atomicExch(I.pflags + 1, 0);
-                __threadfence();
                 atomicAdd(I.pflags, 1);
             }
         }
