@@ -122,14 +122,17 @@ __device__ __forceinline__ void wait_flags(const int* flg, int nt, int k0, int k
         bool ok = idx < 0 || ld_flag_acquire(flg + idx) == ep;
         uint32_t it = 0;
         while (!__all_sync(0xffffffffu, ok)) {
-            // give up after the bound, or at once after a wait anywhere gave up
-            int stop = 0;
-            if (lane == 0) stop = (++it > kFlowSpin) || (ld_flag(err) & 4);
-            if (__shfl_sync(0xffffffffu, stop, 0)) {
-                if (lane == 0) atomicOr(err, 4);
-                break;
+            // give up after the bound, or soon after a wait anywhere gave up
+            // (looked at every 64 polls, off the short waits' path)
+            if ((++it & 63) == 0) {
+                int stop = 0;
+                if (lane == 0) stop = (it > kFlowSpin) || (ld_flag(err) & 4);
+                if (__shfl_sync(0xffffffffu, stop, 0)) {
+                    if (lane == 0) atomicOr(err, 4);
+                    break;
+                }
             }
-            __nanosleep(64);
+            if (it > 256) __nanosleep(64);   // spin first: the wait is usually short
             if (!ok) ok = ld_flag_acquire(flg + idx) == ep;
         }
     }
