@@ -40,7 +40,7 @@ GOLD = os.path.join(ROOT, "tests", "golden", "heat2d_g32_nu10_N50.npz")
 NS, NU, N = 1024, 10, 50
 # DRAM bytes (read + write) of one k_potrf_flow launch on this workload from the
 # ncu capture summarised in profiles/ (None until captured for this kernel version)
-POTRF_FLOW_TRAFFIC = 764928
+POTRF_FLOW_TRAFFIC = 765696
 DTYPES = {
     "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, FP64 "
             "refinement and fallback",
