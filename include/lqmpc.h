@@ -273,7 +273,8 @@ lqmpc_status lqmpc_form_kkt_noalloc(lqmpc_ctx* ctx, const double* sigx, const do
 
 /* Form M as above, Cholesky-factor it and solve M x = b (mixed precisions
  * with FP64 iterative refinement).  L (nullable) receives the lower factor
- * as n x n doubles (upper triangle zero).  refine_steps (nullable) receives
+ * as n x n doubles (upper triangle zero); with LQMPC_FP32X2 that is the
+ * second-level factor L2 of L1^-1 M L1^-T.  refine_steps (nullable) receives
  * the refinement steps taken.  Returns LQMPC_ERR_NOT_PD if a pivot is not
  * positive, LQMPC_ERR_STALL if refinement did not reach refine_tol. */
 lqmpc_status lqmpc_kkt_solve(lqmpc_ctx* ctx, const double* sigx, const double* sigu,
