@@ -4,10 +4,10 @@ FP64 oracle matrix, over sizes spanning one to seventeen 32-wide block
 columns with ragged ends (a single instance of n <= 544 takes the dataflow
 factorisation).
 
-Tolerances.  The factor is judged by its backward error, element-wise:
+Tolerances.  The factor is checked by its backward error, element-wise:
 |L L' - M| <= 8 (n + 2) 2^-24 (|L| |L'|) + the FP32-accurate formation error
 of M (4 2^-24 (sqrt(K) + 2) of the absolute sum, K = ns N terms).  The
-inverse is judged by the conjugate gradients it preconditions: started from
+inverse is checked by the conjugate gradients it preconditions: started from
 L^-T L^-1 b, FP64 products with M must reach a 2e-10 relative residual in a
 few steps (an FP32-accurate inverse contracts the error by about
 cond(M) 2^-24 per step; a wrong block of it would not).
