@@ -42,10 +42,12 @@ NS, NU, N = 1024, 10, 50
 # ncu capture summarised in profiles/ (None until captured for this kernel version)
 POTRF_FLOW_TRAFFIC = 765696
 DTYPES = {
-    "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, FP64 "
-            "refinement and fallback",
-    "bf16": "mixed: BF16 tcgen05 formation (FP32 accumulate), FP32 Cholesky, FP64 refinement and fallback",
-    "tf32": "mixed: TF32 tcgen05 formation (FP32 accumulate), FP32 Cholesky, FP64 refinement and fallback",
+    "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, two-level "
+            "FP32 tier near the end, FP64-accurate refinement, FP64 fallback",
+    "bf16": "mixed: BF16 tcgen05 formation (FP32 accumulate), FP32 Cholesky, two-level FP32 tier, FP64-accurate "
+            "refinement, FP64 fallback",
+    "tf32": "mixed: TF32 tcgen05 formation (FP32 accumulate), FP32 Cholesky, two-level FP32 tier, FP64-accurate "
+            "refinement, FP64 fallback",
     "fp64": "f64",
 }
 
