@@ -22,8 +22,13 @@ __device__ __forceinline__ T* kkt_mat(const Inst& I) {
 }
 
 // Grid-wide barrier for the cooperative factorisation kernel (all CTAs are
-// co-resident by the cooperative launch).  The spin is bounded: a barrier
-// that gives up raises Scal::err bit 2 and lets the kernel return.
+// co-resident by the cooperative launch): thread 0 of each CTA arrives with an
+// acquire-release add on the counter (its CTA's writes were ordered before it
+// by the CTA barrier), the last one resets the counter and advances the
+// generation word with a release add, the others poll the generation with
+// acquire loads (spinning first, then sleeping between polls).  The spin is
+// bounded: a barrier that gives up raises Scal::err bit 2 and lets the kernel
+// return.
 constexpr unsigned kBarLimit = 1u << 24;
 
 __device__ bool grid_barrier(unsigned* bar, int* err) {
@@ -31,22 +36,21 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned* gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        unsigned g, arrived;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(bar) : "memory");
+        if (arrived + 1u == gridDim.x) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(bar), "r"(0u) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(bar + 1), "r"(1u) : "memory");
         } else {
-            unsigned it = 0;
-            while (*gen == g) {
+            unsigned it = 0, cur;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(bar + 1) : "memory");
+                if (cur != g) break;
                 if (++it > kBarLimit) { ok = 0; atomicOr(err, 2); break; }
-                __nanosleep(64);
+                if (it > 256) __nanosleep(32);
             }
         }
-        __threadfence();
         ok_sh = ok;
     }
     __syncthreads();
@@ -227,6 +231,192 @@ __device__ void update_tile(const Inst& I, int k, int p, int q, T (*Lp)[kNb + 1]
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// FP64 panel and update work.  An FP64 warp instruction holds one SM
+// sub-partition's FP64 pipe for about 60 cycles on this part, so the layout
+// above (one warp factors and inverts the 32 x 32 diagonal block, ~1000 FP64
+// instructions on one sub-partition) took ~80 us per panel.  Here the factor
+// runs on warps 0-3, one per sub-partition: warp w holds the columns
+// c = w (mod 4), lane = row, and pivot j is taken by warp j % 4 as soon as
+// column j has column j-1's update; the other warps wait for column j on a
+// named barrier (producer bar.arrive, consumers bar.sync) while the producer
+// goes on with its other columns.  Warps 4-7 take part in the same barriers
+// and solve the panel's row tile against the columns as they appear
+// (L_pk = A_pk L_kk^{-T} by right-looking substitution), so no inverse of the
+// diagonal block is formed.
+
+// d = sqrt(v), rd = 1/d: the FP32 seed r = rsqrtf(v) and one third-order
+// step of the series (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3) with
+// e = 1 - v r^2 (|e| <= 2^-21 from the seed, so the dropped terms are below
+// 2^-62): three dependent FP64 operations instead of two Newton steps' six.
+__device__ __forceinline__ void pivot64(double v, double& d, double& rd) {
+    const float vf = (float)v;
+    if (vf > 1e-30f && vf < 1e30f) {
+        const double r = (double)rsqrtf(vf);
+        const double e = fma(-v * r, r, 1.0);
+        const double q = fma(0.375, e, 0.5);
+        rd = fma(r * e, q, r);
+        d = v * rd;
+    } else {
+        d = sqrt(v);
+        rd = 1.0 / d;
+    }
+}
+
+__device__ __forceinline__ void named_bar_sync256(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void named_bar_arrive256(int id) { asm volatile("bar.arrive %0, 256;" ::"r"(id) : "memory"); }
+
+// Warps 0-3: factor the diagonal block of panel k (rows/columns k0.., kn of
+// them, identity padding) into Ld = L_kk (zero above the diagonal) and
+// rdg = 1 / diag(L_kk), column j published on named barrier 1 + j % 4 (all
+// 256 threads take part).  The first failing pivot (k0 + j + 1) goes to
+// *fail_sh (zeroed by the caller); the steps after it go on (on NaNs) so that
+// every barrier is met.  Barrier ids are reused every four steps: a warp
+// can publish column j + 4 only after every warp has passed column j.
+__device__ void factor_diag64(const double* M, int n, int k0, int kn, double (*Ld)[kNb + 1], double* rdg,
+                              int* fail_sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double a[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const int c = 4 * s + w;
+        double v = (c == lane) ? 1.0 : 0.0;
+        if (lane < kn && c < kn && c <= lane) v = M[(size_t)(k0 + lane) + (size_t)n * (k0 + c)];
+        a[s] = v;
+    }
+    // column J of L from the owner's register a[J / 4]
+#define LQ_PRODUCE64(J)                                                                   \
+    {                                                                                     \
+        const double djj = __shfl_sync(0xffffffffu, a[(J) >> 2], (J));                    \
+        double d, rd;                                                                     \
+        pivot64(djj, d, rd);                                                              \
+        const bool bad = !(djj > 0.0);                                                    \
+        const double l = lane > (J) ? a[(J) >> 2] * rd : (lane == (J) ? d : 0.0);         \
+        a[(J) >> 2] = l;                                                                  \
+        Ld[lane][(J)] = l;                                                                \
+        if (lane == 0) {                                                                  \
+            rdg[(J)] = rd;                                                                \
+            if (bad && *fail_sh == 0) *fail_sh = k0 + (J) + 1;                            \
+        }                                                                                 \
+        __syncwarp();                                                                     \
+        named_bar_arrive256(1 + ((J) & 3));                                               \
+    }
+    if (w == 0) LQ_PRODUCE64(0)
+#pragma unroll
+    for (int j = 0; j < kNb; ++j) {
+        if (w != (j & 3)) named_bar_sync256(1 + (j & 3));
+        const double li = Ld[lane][j];
+        if (j + 1 < kNb && w == ((j + 1) & 3)) {
+            a[(j + 1) >> 2] = fma(-li, Ld[j + 1][j], a[(j + 1) >> 2]);
+            LQ_PRODUCE64(j + 1)
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+            if (4 * s + w > j + 1) a[s] = fma(-li, Ld[4 * s + w][j], a[s]);
+    }
+#undef LQ_PRODUCE64
+}
+
+// Panel k, row tile p, FP64: every CTA of the panel factors the diagonal
+// block (warps 0-3); p == k stores L_kk (parked as in panel_tile); p > k has
+// warps 4-7 solve X L_kk' = A_pk row by row while the columns of L_kk appear:
+// lane = (row rho of the warp's 8, column class g = lane % 4) holds columns
+// c = g (mod 4) of its row; at column j, x_j = a_j / L_jj is final and is
+// subtracted, times L_cj, from every later column.
+__device__ void panel_tile64(const Inst& I, int k, int p, double (*Ld)[kNb + 1], double* rdg, int* fail_sh) {
+    double* M = I.M64;
+    const int n = I.n, k0 = k * kNb, kn = min(kNb, n - k0), p0 = p * kNb;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) *fail_sh = 0;
+    __syncthreads();
+    const int g = lane & 3, r = 8 * (w - 4) + (lane >> 2);
+    double x[8];
+    if (w < 4) {
+        factor_diag64(M, n, k0, kn, Ld, rdg, fail_sh);
+    } else if (p == k) {
+#pragma unroll
+        for (int j = 0; j < kNb; ++j) named_bar_sync256(1 + (j & 3));
+    } else {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int c = 4 * s + g;
+            x[s] = (p0 + r < n && c < kn) ? M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < kNb; ++j) {
+            named_bar_sync256(1 + (j & 3));
+            const double xj = __shfl_sync(0xffffffffu, x[j >> 2], (lane & ~3) | (j & 3)) * rdg[j];
+            // L_cj = 0 for c < j (groups with 4s + 3 < j are skipped whole);
+            // c = j is overwritten by x_j below
+#pragma unroll
+            for (int s = 0; s < 8; ++s)
+                if (4 * s + 3 >= j) x[s] = fma(-xj, Ld[4 * s + g][j], x[s]);
+            if (g == (j & 3)) x[j >> 2] = xj;
+        }
+    }
+    __syncthreads();
+    const int fail = *fail_sh;
+    if (fail) {
+        if (p == k && tid == 0) atomicCAS(&I.sc->info, 0, fail);
+        return;
+    }
+    if (p == k) {
+        const int nt = (n + kNb - 1) / kNb;
+        double* park = reinterpret_cast<double*>(I.ldiag) + (size_t)(k % 2) * kNb * kNb;
+        if (k > 0) {
+            const double* prev = reinterpret_cast<const double*>(I.ldiag) + (size_t)((k - 1) % 2) * kNb * kNb;
+            const int q0 = k0 - kNb;
+            for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+                const int rr = e % kNb, c = e / kNb;
+                if (c <= rr) M[(size_t)(q0 + rr) + (size_t)n * (q0 + c)] = prev[e];
+            }
+        }
+        for (int e = tid; e < kNb * kNb; e += blockDim.x) {
+            const int rr = e % kNb, c = e / kNb;
+            if (rr < kn && c < kn && c <= rr) {
+                if (k + 1 < nt) park[e] = Ld[rr][c];
+                else M[(size_t)(k0 + rr) + (size_t)n * (k0 + c)] = Ld[rr][c];
+            }
+        }
+    } else if (w >= 4) {
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int c = 4 * s + g;
+            if (p0 + r < n && c < kn) M[(size_t)(p0 + r) + (size_t)n * (k0 + c)] = x[s];
+        }
+    }
+    __syncthreads();
+}
+
+// A_pq -= L_pk L_qk' on one 16 x 16 quadrant (quad = 2 * row half + column
+// half) of the trailing tile (p, q), FP64: four work items per tile so that
+// a panel's update spreads over four times as many SMs.  The quadrant above
+// the diagonal of a diagonal tile is skipped.
+__device__ void update_quad64(const Inst& I, int k, int p, int q, int quad, double (*Lp)[kNb + 1],
+                              double (*Lq)[kNb + 1]) {
+    double* M = I.M64;
+    const int n = I.n, k0 = k * kNb, kn = min(kNb, n - k0);
+    const int rh = quad >> 1, ch = quad & 1;
+    if (p == q && rh < ch) return;
+    const int r0 = p * kNb + 16 * rh, c0 = q * kNb + 16 * ch;
+    for (int e = threadIdx.x; e < 16 * kNb; e += blockDim.x) {
+        const int r = e % 16, c = e / 16;
+        Lp[r][c] = (r0 + r < n && c < kn) ? M[(size_t)(r0 + r) + (size_t)n * (k0 + c)] : 0.0;
+        Lq[r][c] = (c0 + r < n && c < kn) ? M[(size_t)(c0 + r) + (size_t)n * (k0 + c)] : 0.0;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int c = 0; c < kNb; c += 2) {
+        s0 = fma(Lp[ty][c], Lq[tx][c], s0);
+        s1 = fma(Lp[ty][c + 1], Lq[tx][c + 1], s1);
+    }
+    const int row = r0 + ty, col = c0 + tx;
+    if (row < n && col < n && col <= row) M[(size_t)row + (size_t)n * col] -= s0 + s1;
+    __syncthreads();
+}
+
 // C (32 x 32 tile) = sum_{j in [j0, j1)} A_j B_j for tiles read from global
 // column-major n x n matrices: A_j = tile (ar, j) of Amat, B_j = tile (j, bc)
 // of Bmat (zero outside [0, n)).  The next pair of tiles is fetched into
@@ -297,7 +487,9 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
     __shared__ T S1[kNb][kNb + 1];
     __shared__ T S2[kNb][kNb + 1];
     __shared__ T S3[kNb][kNb + 1];
+    __shared__ T rdg[kNb];
     __shared__ int fail_sh;
+    constexpr int kSub = sizeof(T) == 8 ? 4 : 1;   // update work items per trailing tile
     unsigned* bar = insts[0].bar;
     int* err = &insts[0].sc->err;
     for (int k = 0; k < max_nt; ++k) {
@@ -319,7 +511,11 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
             }
             const Inst& I = insts[q];
             T* X = (want_inv && sizeof(T) == 4) ? (T*)I.Xinv32 : nullptr;
-            if (!I.sc->info) panel_tile<T>(I, k, k + rem, S1, S2, S3, &fail_sh, X);
+            if (I.sc->info) continue;
+            if constexpr (sizeof(T) == 8)
+                panel_tile64(I, k, k + rem, S1, rdg, &fail_sh);
+            else
+                panel_tile<T>(I, k, k + rem, S1, S2, S3, &fail_sh, X);
         }
         if (!grid_barrier(bar, err)) return;
         // update phase
@@ -327,23 +523,28 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
         for (int q = 0; q < count; ++q) {
             const Inst& I = insts[q];
             const int m = (I.n + kNb - 1) / kNb - k - 1;
-            if (!skip_instance(I, flags) && m > 0) total += m * (m + 1) / 2;
+            if (!skip_instance(I, flags) && m > 0) total += kSub * (m * (m + 1) / 2);
         }
         for (int item = blockIdx.x; item < total; item += gridDim.x) {
             int q = 0, rem = item;
             for (;; ++q) {
                 const Inst& I = insts[q];
                 const int m = (I.n + kNb - 1) / kNb - k - 1;
-                const int c = (!skip_instance(I, flags) && m > 0) ? m * (m + 1) / 2 : 0;
+                const int c = (!skip_instance(I, flags) && m > 0) ? kSub * (m * (m + 1) / 2) : 0;
                 if (rem < c) break;
                 rem -= c;
             }
             const Inst& I = insts[q];
             if (I.sc->info) continue;
+            const int sub = rem % kSub;
+            rem /= kSub;
             int a = 0;
             while ((a + 1) * (a + 2) / 2 <= rem) ++a;
             const int b = rem - a * (a + 1) / 2;
-            update_tile<T>(I, k, k + 1 + a, k + 1 + b, S1, S2);
+            if constexpr (sizeof(T) == 8)
+                update_quad64(I, k, k + 1 + a, k + 1 + b, sub, S1, S2);
+            else
+                update_tile<T>(I, k, k + 1 + a, k + 1 + b, S1, S2);
         }
         if (!grid_barrier(bar, err)) return;
     }
@@ -704,8 +905,10 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
         flags |= F_N_GT_512;   // the small instances are factored; the rest follow
         if (flowq_ok && launch_potrf_flowq(d_insts, d_tasks, ntasks, max_n, flags, st)) return;
     }
-    long long work = (long long)count * (nt * (nt + 1) / 2 > nt ? nt * (nt + 1) / 2 : nt);
-    long long cap = (long long)occ[fp64 ? 1 : 0] * sms;
+    long long work = (long long)count * (nt * (nt + 1) / 2 > nt ? nt * (nt + 1) / 2 : nt) * (fp64 ? 4 : 1);
+    // FP64: one CTA per SM, so that the panel's CTAs (each factoring the
+    // diagonal block on four sub-partitions' FP64 pipes) never share an SM
+    long long cap = fp64 ? (long long)sms : (long long)occ[0] * sms;
     int grid = (int)(work < cap ? work : cap);
     if (grid < 1) grid = 1;
     void* args[] = {(void*)&d_insts, (void*)&count, (void*)&nt, (void*)&flags, (void*)&want_inv};

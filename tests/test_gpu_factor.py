@@ -77,6 +77,28 @@ def test_fp32_factor_backward_error(case):
     assert np.all(err <= bound), float((err / bound).max())
 
 
+U64 = 2.0 ** -53
+
+
+def test_fp64_factor_backward_error(case):
+    """FP64 Cholesky of M (grid-cooperative kernel: four-warp diagonal factor
+    with the third-order pivot, unit-triangular inverse of the diagonal block,
+    quadrant updates): backward error of L L' within the FP64 rounding bound
+    of the factorisation plus the FP64 formation of M."""
+    p, s, sigx, sigu, M, absm = case
+    b = np.random.default_rng(14).standard_normal(p.n)
+    r = s.kkt_solve(sigx, sigu, b, "fp64", want_L=True)
+    L = np.tril(r["L"])
+    assert np.all(np.isfinite(L)) and np.all(np.diag(L) > 0)
+    err = np.abs(L @ L.T - M)
+    bound = 8 * (p.n + 2) * U64 * (np.abs(L) @ np.abs(L).T) + 4 * U64 * (np.sqrt(p.ns * p.N) + 2) * absm
+    assert np.all(err <= bound), float((err / bound).max())
+    x_ref = np.linalg.solve(M, b)
+    # forward error <= cond(M) x backward error of the factor and the formation
+    fwd = 10 * np.linalg.cond(M) * (p.n + np.sqrt(p.ns * p.N) + 2) * U64 * np.max(np.abs(x_ref))
+    assert np.max(np.abs(r["x"] - x_ref)) <= fwd
+
+
 def test_fp32_inverse_preconditions_in_few_steps(case):
     p, s, sigx, sigu, M, _ = case
     b = np.random.default_rng(13).standard_normal(p.n)
