@@ -239,11 +239,29 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
                  : "memory");
 }
+// 4-byte asynchronous copy (zero-filled when !valid; src must then still be
+// a valid address, it is not read).
+__device__ __forceinline__ void cp4(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Gamma v: block (m-tile of states, r-tile, split of the column range).  G
+// Split plan of Gamma v: r-tile t holds rows N - 16 (t + 1) .. N - 16 t - 1
+// (aligned to the horizon's end), needs the columns from kbeg on (nk K-tiles
+// of 32) and gives them to S = min(nk, kFfMaxSplits) CTAs, so that every CTA
+// of the launch gets one K-tile (two past 512 columns) whatever its r-tile.
+__host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kbeg, int& nk, int& S) {
+    const int r1 = N - kFfBN * t;
+    kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
+    nk = (n - kbeg + kFfBK - 1) / kFfBK;
+    S = nk < kFfMaxSplits ? nk : kFfMaxSplits;
+}
+
+// Gamma v: block (r-tile, m-tile of states, split of the column range).  G
 // tiles stream through a double-buffered shared-memory ring (cp.async); the
 // input comes split into float-float by k_ff_prep_v.
 __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
@@ -252,17 +270,21 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
     const int mt = (ns + kFfBM - 1) / kFfBM, nt = (N + kFfBN - 1) / kFfBN;
-    const int tile = blockIdx.x / splits, split = blockIdx.x % splits;
-    if (tile >= mt * nt) return;
     // r tiles aligned to the horizon's end (rows r0 .. r1-1, r0 may be
     // negative): the partial tile holds the first stages, which need only the
-    // last columns
-    const int m0 = (tile % mt) * kFfBM, r1 = N - kFfBN * (tile / mt), r0 = r1 - kFfBN;
+    // last columns (col >= off_{r1-1})
+    int rem = blockIdx.x, t = 0, kbeg = 0, nk = 0, S = 1;
+    for (;; ++t) {
+        if (t >= nt) return;
+        mv_ff_rtile(t, N, nu, n, kbeg, nk, S);
+        if (rem < mt * S) break;
+        rem -= mt * S;
+    }
+    const int split = rem % S;
+    const int m0 = (rem / S) * kFfBM, r1 = N - kFfBN * t, r0 = r1 - kFfBN;
     const double* v = role_ptr(I, in_role);
-    // columns needed by this r-tile: col >= off_{r1-1}
-    const int kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
-    const int nk = (n - kbeg + kFfBK - 1) / kFfBK;
-    const int k0t = nk * split / splits, k1t = nk * (split + 1) / splits;
+    const int k0t = nk * split / S, k1t = nk * (split + 1) / S;
+    (void)splits;
     __shared__ __align__(16) float Gs[2][2][kFfBK][kFfBM];          // [buffer][hi, lo][col][state]
     __shared__ float Vs[2][2][kFfBK][kFfBN + 1];                   // [buffer][hi, lo][col][r]
     (void)v;
@@ -277,16 +299,14 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             cp16(&Gs[buf][0][kk][4 * q], I.G32 + off, ok);
             cp16(&Gs[buf][1][kk][4 * q], I.G32lo + off, ok);
         }
+        // the Toeplitz-gathered input tile, asynchronous like the G tiles
         for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
             const int kk = e / kFfBN, rr = e % kFfBN;
             const int col = c0 + kk, r = r0 + rr;
-            float h = 0.f, l = 0.f;
-            if (col < n && r >= 0) {
-                const int t = col - (N - 1 - r) * nu;
-                if (t >= 0) { h = vsp[t]; l = vsp[n + t]; }
-            }
-            Vs[buf][0][kk][rr] = h;
-            Vs[buf][1][kk][rr] = l;
+            const int t = (col < n && r >= 0) ? col - (N - 1 - r) * nu : -1;
+            const bool ok = t >= 0;
+            cp4(&Vs[buf][0][kk][rr], vsp + (ok ? t : 0), ok);
+            cp4(&Vs[buf][1][kk][rr], vsp + n + (ok ? t : 0), ok);
         }
         cp_commit();
     };
@@ -339,10 +359,14 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     double* out = role_ptr(I, out_role);
+    (void)splits;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
+        // the splits of row r's r-tile (the split plan of k_gamma_mv_ff)
+        int kbeg, nk, S;
+        mv_ff_rtile((I.N - 1 - k / I.ns) / kFfBN, I.N, I.nu, I.n, kbeg, nk, S);
         double s = 0.0;
 #pragma unroll 4
-        for (int q = 0; q < splits; ++q) s += I.gpart[(size_t)q * I.SX + k];
+        for (int q = 0; q < S; ++q) s += I.gpart[(size_t)q * I.SX + k];
         out[k] = s;
         if (fuse & kFuseOutDxs) I.dxs[k] = s;
         if (fuse & kFuseOutW) {
@@ -428,14 +452,10 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         for (int e = threadIdx.x; e < kFfBK * kFfBN; e += kFfThreads) {
             const int rr = e / kFfBK, kk = e % kFfBK;
             const int r = r_lo + rr, i = i0 + kk;
-            float h = 0.f, l = 0.f;
-            if (r >= 0 && i < ns) {
-                const size_t q = (size_t)r * ns + i;
-                h = I.ffw[(size_t)(2 * vec_t) * I.SX + q];
-                l = I.ffw[(size_t)(2 * vec_t + 1) * I.SX + q];
-            }
-            Ws[buf][0][kk][rr] = h;
-            Ws[buf][1][kk][rr] = l;
+            const bool ok = r >= 0 && i < ns;
+            const size_t q = ok ? (size_t)r * ns + i : 0;
+            cp4(&Ws[buf][0][kk][rr], I.ffw + (size_t)(2 * vec_t) * I.SX + q, ok);
+            cp4(&Ws[buf][1][kk][rr], I.ffw + (size_t)(2 * vec_t + 1) * I.SX + q, ok);
         }
         cp_commit();
     };
@@ -603,11 +623,24 @@ static int ff_splits(int tiles, int nk) {
 
 void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
                         int out_role, int flags, cudaStream_t st, int fuse) {
-    const int tiles = ((max_ns + kFfBM - 1) / kFfBM) * ((max_N + kFfBN - 1) / kFfBN);
-    const int splits = ff_splits(tiles * count, (max_n + kFfBK - 1) / kFfBK);
+    // CTAs: sum over r-tiles of m-tiles x splits (exact for one instance; for
+    // a batch a bound over its instances, the surplus CTAs return at once)
+    const int mt = (max_ns + kFfBM - 1) / kFfBM, nt = (max_N + kFfBN - 1) / kFfBN;
+    int ctas = 0;
+    if (count == 1) {
+        for (int t = 0; t < nt; ++t) {
+            int kbeg, nk, S;
+            mv_ff_rtile(t, max_N, max_n / max_N, max_n, kbeg, nk, S);
+            ctas += mt * S;
+        }
+    } else {
+        const int nkmax = (max_n + kFfBK - 1) / kFfBK;
+        ctas = mt * nt * (nkmax < kFfMaxSplits ? nkmax : kFfMaxSplits);
+    }
+    const int splits = 0;
     if (!(fuse & kFuseInSplit))
         LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
-    LQ_LAUNCH(k_gamma_mv_ff<<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
+    LQ_LAUNCH(k_gamma_mv_ff<<<dim3(ctas, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
     int nb = (max_ns * max_N + 255) / 256;
     nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
     LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits, fuse));
