@@ -64,38 +64,57 @@ __global__ void k_gstack_cast(const Inst* __restrict__ insts) {
 }
 
 // out[r*ns + i] = sum_{t < (r+1) nu} G[i, (N-1-r) nu + t] v[t]   (out = Gamma v).
-// Each thread owns one state i and RB consecutive row blocks; a G element
+// Each lane owns one state i and RB consecutive row blocks; a G element
 // loaded once serves every row block of the group (each is the same column
-// window shifted by nu).
-template <int RB>
-__global__ void k_gamma_mv(const Inst* __restrict__ insts, int in_role, int out_role, int flags) {
+// window shifted by nu).  The KS warps of a CTA take consecutive slices of
+// the column range and their partial sums are added in warp order
+// (deterministic): an FP64 multiply-add holds one sub-partition's FP64 pipe
+// for ~60 cycles on this part, so one warp per 32 states left most of each
+// SM's four FP64 pipes idle behind a 500-long dependent chain.
+template <int RB, int KS>
+__global__ void __launch_bounds__(32 * KS) k_gamma_mv(const Inst* __restrict__ insts, int in_role, int out_role,
+                                                      int flags) {
+    __shared__ double red[KS][RB][32];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const double* v = role_ptr(I, in_role);
     double* out = role_ptr(I, out_role);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
     const int r0 = blockIdx.z * RB;
-    if (i >= I.ns || r0 >= I.N) return;
+    if (r0 >= I.N) return;
+    const bool valid = i < I.ns;
     const int nu = I.nu, N = I.N, n = I.n;
     const int rlast = min(r0 + RB, N) - 1;
     double acc[RB];
 #pragma unroll
     for (int q = 0; q < RB; ++q) acc[q] = 0.0;
     const int col0 = (N - 1 - rlast) * nu;       // smallest window start in the group
-    const double* g = I.G64 + i;
-    for (int col = col0; col < n; ++col) {
-        double gv = g[(size_t)I.ldg * col];
+    const int c_beg = col0 + (n - col0) * w / KS, c_end = col0 + (n - col0) * (w + 1) / KS;
+    const double* g = I.G64 + (valid ? i : 0);
+    if (valid) {
+        for (int col = c_beg; col < c_end; ++col) {
+            const double gv = g[(size_t)I.ldg * col];
 #pragma unroll
-        for (int q = 0; q < RB; ++q) {
-            int r = r0 + q;
-            int off = (N - 1 - r) * nu;
-            int t = col - off;
-            if (r <= rlast && t >= 0) acc[q] += gv * __ldg(v + t);
+            for (int q = 0; q < RB; ++q) {
+                const int r = r0 + q;
+                const int t = col - (N - 1 - r) * nu;
+                if (r <= rlast && t >= 0) acc[q] += gv * __ldg(v + t);
+            }
         }
     }
 #pragma unroll
-    for (int q = 0; q < RB; ++q)
-        if (r0 + q <= rlast) out[(size_t)(r0 + q) * I.ns + i] = acc[q];
+    for (int q = 0; q < RB; ++q) red[w][q][lane] = acc[q];
+    __syncthreads();
+    if (w == 0 && valid) {
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            double s = red[0][q][lane];
+#pragma unroll
+            for (int k = 1; k < KS; ++k) s += red[k][q][lane];
+            if (r0 + q <= rlast) out[(size_t)(r0 + q) * I.ns + i] = s;
+        }
+    }
 }
 
 // Gamma' w, two-level.  Stage 1: block (t, chunk, rgroup) computes, for input
@@ -587,9 +606,9 @@ void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st) {
 
 void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int in_role,
                      int out_role, int flags, cudaStream_t st) {
-    constexpr int RB = 4;
+    constexpr int RB = 4, KS = 8;
     dim3 grid((max_ns + 31) / 32, count, (max_N + RB - 1) / RB);
-    LQ_LAUNCH(k_gamma_mv<RB><<<grid, 32, 0, st>>>(d_insts, in_role, out_role, flags));
+    LQ_LAUNCH(k_gamma_mv<RB, KS><<<grid, 32 * KS, 0, st>>>(d_insts, in_role, out_role, flags));
 }
 
 size_t gamma_tmv_part_doubles(int ns, int n, int N) {
