@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(32 * KS) k_gamma_mv(const Inst* __restrict__ i
 // FP64 throughput per SM is low on this part, so the work must be spread.
 constexpr int kTmvChunk = 128;
 constexpr int kTmvRg = 8;
-constexpr int kTmvMaxNu = 32;
+constexpr int kTmvMaxNu = 16;
 
 __host__ __device__ inline int tmv_groups(int N) { return (N + kTmvRg - 1) / kTmvRg; }
 
