@@ -63,7 +63,8 @@ class _Problem(ctypes.Structure):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("tau", ctypes.c_double)]
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("tau", ctypes.c_double),
+                ("u_init", ctypes.c_void_p), ("mu0", ctypes.c_double)]
 
 
 class _Stats(ctypes.Structure):
@@ -101,8 +102,9 @@ def _csr(m, n):
 
 
 def ipm_solve(plant, x0, *, tol: float = 1e-8, max_iter: int = 100, tau: float = 0.995,
-              want_trace: bool = False):
-    """Run the oracle IPM.  Returns dict(u, x, z, stats, trace)."""
+              want_trace: bool = False, u_init=None, mu0: float = 0.0):
+    """Run the oracle IPM (cold, or warm-started from the guess u_init with
+    complementarity mu0).  Returns dict(u, x, z, stats, trace)."""
     ns, nu, N = plant.ns, plant.nu, plant.N
     n = nu * N
     keep = []
@@ -116,7 +118,9 @@ def ipm_solve(plant, x0, *, tol: float = 1e-8, max_iter: int = 100, tau: float =
     pb = _Problem(ns, nu, N, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(B),
                   _ptr(q[0]), _ptr(q[1]), _ptr(q[2]), _ptr(qf[0]), _ptr(qf[1]), _ptr(qf[2]),
                   _ptr(R), _ptr(vecs[0]), _ptr(vecs[1]), _ptr(vecs[2]), _ptr(vecs[3]))
-    op = _Options(tol, max_iter, tau)
+    ui = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64).reshape(n)
+    keep.append(ui)
+    op = _Options(tol, max_iter, tau, _ptr(ui), mu0)
     xb = np.ascontiguousarray(x0, dtype=np.float64)
     u = np.zeros(n)
     x = np.zeros(ns * N)

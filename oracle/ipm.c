@@ -30,6 +30,9 @@
  * Readings where the paper is silent (listed again in the design notes):
  *  - initial point: u0 = box midpoint, x0 = rollout, s0 = max(slack, 1),
  *    z0 = 1, lambda0 from the adjoint recursion (zero state-stationarity);
+ *  - warm start (not in the paper; the learned warm start starts from a
+ *    guess): u0 = the guess moved inside the input box by 1% of the range,
+ *    s0 = max(slack, 1e-2), z0 = mu0 / s0, lambda0 as above;
  *  - Mehrotra sigma = (mu_aff / mu)^3, fraction to boundary tau = 0.995;
  *  - stop when max(||r_d||/(1+||h||), ||r_p||/(1+||d||), mu) <= tol, with
  *    h = Gamma' Qbar Phi xbar and d the condensed constraint right-hand side
@@ -419,23 +422,39 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
         }
     }
 
-    /* initial point */
+    /* initial point.  Cold: u = box midpoints, s = max(slack, 1), z = 1.
+     * Warm (u_init given): u = the guess moved inside the box by a margin,
+     * s = max(slack, 1e-2), z = mu0 / s (complementarity mu0 on every pair). */
+    const double* ui = op ? op->u_init : NULL;
+    const double mu0 = (op && op->mu0 > 0.0) ? op->mu0 : 1e-2;
+    const double sfl = ui ? 1e-2 : 1.0;
     for (int t = 0; t < N; ++t)
-        for (int j = 0; j < nu; ++j) u[t * nu + j] = mid_of_box(pb->ul[j], pb->uu[j]);
+        for (int j = 0; j < nu; ++j) {
+            if (!ui) { u[t * nu + j] = mid_of_box(pb->ul[j], pb->uu[j]); continue; }
+            double lo = pb->ul[j], hi = pb->uu[j], v = ui[t * nu + j];
+            int fl = isfinite(lo), fh = isfinite(hi);
+            double margin = (fl && fh) ? 0.01 * (hi - lo) : 0.01;
+            if (fl && v < lo + margin) v = lo + margin;
+            if (fh && v > hi - margin) v = hi - margin;
+            if (fl && fh && hi - lo <= 2.0 * margin) v = 0.5 * (lo + hi);
+            u[t * nu + j] = v;
+        }
     rollout(&c, xbar, u, x);
+#define DUAL0(sv) (ui ? mu0 / (sv) : 1.0)
     for (int t = 1; t <= N; ++t)
         for (int i = 0; i < ns; ++i) {
             size_t k = (size_t)(t - 1) * ns + i;
             double xi = x[(size_t)t * ns + i];
-            s1[k] = c.f1[i] ? fmax(pb->xu[i] - xi, 1.0) : 1.0; z1[k] = c.f1[i] ? 1.0 : 0.0;
-            s2[k] = c.f2[i] ? fmax(xi - pb->xl[i], 1.0) : 1.0; z2[k] = c.f2[i] ? 1.0 : 0.0;
+            s1[k] = c.f1[i] ? fmax(pb->xu[i] - xi, sfl) : 1.0; z1[k] = c.f1[i] ? DUAL0(s1[k]) : 0.0;
+            s2[k] = c.f2[i] ? fmax(xi - pb->xl[i], sfl) : 1.0; z2[k] = c.f2[i] ? DUAL0(s2[k]) : 0.0;
         }
     for (int t = 0; t < N; ++t)
         for (int j = 0; j < nu; ++j) {
             int k = t * nu + j;
-            s3[k] = c.f3[j] ? fmax(pb->uu[j] - u[k], 1.0) : 1.0; z3[k] = c.f3[j] ? 1.0 : 0.0;
-            s4[k] = c.f4[j] ? fmax(u[k] - pb->ul[j], 1.0) : 1.0; z4[k] = c.f4[j] ? 1.0 : 0.0;
+            s3[k] = c.f3[j] ? fmax(pb->uu[j] - u[k], sfl) : 1.0; z3[k] = c.f3[j] ? DUAL0(s3[k]) : 0.0;
+            s4[k] = c.f4[j] ? fmax(u[k] - pb->ul[j], sfl) : 1.0; z4[k] = c.f4[j] ? DUAL0(s4[k]) : 0.0;
         }
+#undef DUAL0
     /* lambda0: zero state stationarity, lam_t = Q x_t + z1 - z2 + A' lam_{t+1} */
     for (size_t k = 0; k < SX; ++k) q[k] = z1[k] - z2[k];
     adjoint(&c, x, q, NULL, lam);

@@ -29,7 +29,12 @@ typedef struct {
     const double *xl, *xu, *ul, *uu;
 } orc_problem;
 
-typedef struct { double tol; int max_iter; double tau; } orc_options;
+/* u_init (nullable, nu*N): warm start from this input sequence instead of
+ * the box midpoints (the learned warm start; the paper starts cold): clipped
+ * into the input box with a margin of 1% of each two-sided range (1e-2 from
+ * a one-sided bound), every slack s0 = max(slack, 1e-2) and every dual
+ * z0 = mu0 / s0 (mu0 <= 0 selects 1e-2). */
+typedef struct { double tol; int max_iter; double tau; const double* u_init; double mu0; } orc_options;
 
 typedef struct {
     int iters, status, m;
