@@ -129,6 +129,57 @@ def heat2d(g: int, nu: int, N: int, *, alpha: float = ALPHA, r: float = 0.1) -> 
                  kind="heat2d", meta={"alpha": alpha, "g": g})
 
 
+# Table I of the paper (3-D copper cube): time step, mesh size, density,
+# specific heat, conductivity, weights and bounds
+CUBE_DT, CUBE_DW = 0.1, 0.02
+CUBE_RHO, CUBE_CP, CUBE_K = 8960.0, 386.0, 400.0
+CUBE_XL, CUBE_XU, CUBE_UL, CUBE_UU, CUBE_XHAT = 200.0, 550.0, 300.0, 500.0, 300.0
+CUBE_SETPOINT = 400.0
+
+
+def heat3d_cube(g: int, T: int, *, setpoint: float = CUBE_SETPOINT) -> Plant:
+    """The paper's 3-D temperature control problem (Section V-A, Eq. 8,
+    Table I) on a g x g x g interior grid with horizon T.
+
+    Explicit Euler in time and the 7-point finite-difference Laplacian in
+    space give A = I + a*L3 with a = dt*k/(rho*cp*dw^2); the six faces are
+    Dirichlet boundaries whose temperatures are the nu = 6 inputs (the
+    boundary is not a state), so an interior node next to face f gets
+    B[node, f] = a.  The set point d of Eq. 8 is not given in the paper; it is
+    the constant `setpoint` (K), and the problem is written in deviations
+    from it (x - d, u - d), the form of Eq. 1, which has no linear cost terms:
+    the uniform state at d with every face at d is a fixed point of the
+    discretised dynamics (each row of [A B] sums to one), Q = q*I and
+    R = r*I with q = 10 dw^2 and r = dw^2/10 weigh the deviations, and the
+    bounds of Table I move by -d.  Node (i, j, l) is state (i*g + j)*g + l;
+    faces are i = 0, i = g-1, j = 0, j = g-1, l = 0, l = g-1 in that order.
+    """
+    ns = g ** 3
+    a = CUBE_DT * CUBE_K / (CUBE_RHO * CUBE_CP * CUBE_DW ** 2)
+    L1 = _laplacian_1d(g)
+    I = sp.identity(g, format="csr")
+    L3 = (sp.kron(sp.kron(I, I), L1) + sp.kron(sp.kron(I, L1), I) + sp.kron(sp.kron(L1, I), I)).tocsr()
+    A = (sp.identity(ns, format="csr") + a * L3).tocsr()
+    B = np.zeros((ns, 6))
+    idx = np.arange(ns)
+    i, j, l = idx // (g * g), (idx // g) % g, idx % g
+    for f, on in enumerate((i == 0, i == g - 1, j == 0, j == g - 1, l == 0, l == g - 1)):
+        B[on, f] += a
+    q, r = 10.0 * CUBE_DW ** 2, 0.1 * CUBE_DW ** 2
+    Q = q * sp.identity(ns, format="csr")
+    d = setpoint
+    return Plant(ns, 6, T, A, B, Q, r * np.eye(6), Q.copy(),
+                 (CUBE_XL - d) * np.ones(ns), (CUBE_XU - d) * np.ones(ns),
+                 (CUBE_UL - d) * np.ones(6), (CUBE_UU - d) * np.ones(6),
+                 kind="heat3d_cube", meta={"alpha": a, "g": g, "setpoint": d})
+
+
+def x0_cube(g: int, setpoint: float = CUBE_SETPOINT) -> np.ndarray:
+    """The cube's initial temperature (Table I: 300 K everywhere) as a
+    deviation from the set point."""
+    return (CUBE_XHAT - setpoint) * np.ones(g ** 3)
+
+
 def x0_uniform(ns: int, seed: int, lo: float = -0.8, hi: float = 0.8) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return rng.uniform(lo, hi, size=ns)

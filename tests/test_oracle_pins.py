@@ -301,3 +301,32 @@ def test_planted_sign_error_is_caught_by_brute_force():
     bad.A = np.array([[1.0, -0.5], [0.0, 1.0]])
     r = oracle.ipm_solve(bad, x0, tol=1e-12)
     assert np.max(np.abs(r["u"] - ubf)) > 1e-4
+
+
+def test_cube_plant_follows_table_1_and_the_oracle_meets_kkt():
+    """The 3-D cube generator against Table I's constants (a = dt k /
+    (rho cp dw^2), six face inputs, q = 10 dw^2, r = dw^2 / 10) and the fixed
+    point of the deviation form (the uniform set-point state with every face
+    at the set point stays put); the oracle's solution of a small cube meets
+    the KKT conditions of Eq. 5."""
+    from paper_2209_13049_b300 import inputs
+    p = inputs.heat3d_cube(3, 12)
+    a = 0.1 * 400.0 / (8960.0 * 386.0 * 0.02 ** 2)
+    assert abs(p.meta["alpha"] - a) <= 1e-15
+    A = p.dense("A")
+    assert np.allclose(np.diag(A), 1.0 - 6 * a)
+    centre = (1 * 3 + 1) * 3 + 1                     # the one node with no face neighbour
+    assert np.all(p.B[centre] == 0.0)
+    assert np.allclose(p.B.sum(axis=0), 9 * a)      # nine nodes touch each face
+    assert np.allclose(A.sum(axis=1) + p.B.sum(axis=1), 1.0)
+    assert np.allclose(p.dense("Q"), 10 * 0.02 ** 2 * np.eye(27))
+    assert np.allclose(p.R, 0.1 * 0.02 ** 2 * np.eye(6))
+    assert np.allclose(p.xl, -200.0) and np.allclose(p.uu, 100.0)
+    x0 = inputs.x0_cube(3)
+    assert np.allclose(x0, -100.0)
+    r = oracle.ipm_solve(p, x0, tol=1e-11)
+    assert r["status"] == 0
+    k = oracle.kkt_check(p, x0, r["u"], r["z"])
+    assert k["primal_violation"] <= 1e-9 and k["dual_min"] >= 0.0
+    scale = 1.0 + float(np.max(np.abs(p.R @ r["u"].reshape(-1, 6).T)))
+    assert k["stationarity"] <= 1e-9 * scale and k["complementarity"] <= 1e-8
