@@ -56,6 +56,7 @@ def test_setup_rejects_bad_arguments_without_device_work(lib):
     assert code == 1 and not h.value
     assert lib.lqmpc_solve(None, None, None, None) == 1
     assert lib.lqmpc_solve_batch(None, 0, None, None, None) == 1
+    assert lib.lqmpc_solve_batch_warm(None, 0, None, None, 0.0, None, None) == 1
     lib.lqmpc_free(None)
 
 
@@ -77,4 +78,5 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text
+                assert "import baseline" not in text and "from baseline" not in text
                 assert "liboracle" not in text and "oracle.h" not in text
