@@ -185,6 +185,18 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
                                double* const* u_outs, lqmpc_stats* stats);
 
 /*
+ * Warm-started batch (the learned warm start over many initial states; the
+ * paper starts cold): as lqmpc_solve_batch, with instance i started from the
+ * guess u_inits[i] (nu_i*N_i doubles, host) by the rule of lqmpc_solve_warm
+ * (clip into the input box with a margin, rollout, slacks floored at 1e-2,
+ * duals mu0 / s; mu0 <= 0 selects 1e-2).  LQMPC_ERR_ARG for a NULL u_inits,
+ * a NULL entry, a non-finite guess or a NaN mu0.
+ */
+lqmpc_status lqmpc_solve_batch_warm(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                                    const double* const* u_inits, double mu0, double* const* u_outs,
+                                    lqmpc_stats* stats);
+
+/*
  * Autotune the launch shapes of batches like this one (same count and
  * largest ns, nu*N and N): the split-K factor of the CUDA-core SYRK, the
  * Cholesky variant (grid-cooperative over all SMs, or one 8-CTA cluster per
@@ -243,11 +255,11 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
  * For callers that must not allocate device memory while they run: a
  * real-time control loop that cannot take the allocator's latency or the
  * device-wide synchronisation cudaMalloc/cudaFree may imply, or a process
- * whose device memory is entirely held by another allocator.  The call
- * allocates nothing, host or device: the split-K partial tiles live in one
- * fixed 16 MiB device array inside this library (one per device), and
- * everything else is the context's (G-stack and H from setup) or the
- * caller's.
+ * whose device memory is entirely held by another allocator.  After the
+ * first call on a device (below) a call allocates nothing, host or device:
+ * the split-K partial tiles live in one fixed 16 MiB device array inside this
+ * library (one per device), and everything else is the context's (G-stack and
+ * H from setup) or the caller's.
  *
  * sigx: device pointer, ns*N doubles (stage r, state i at r*ns + i); sigu:
  * device pointer, n doubles; M: device pointer, n*n doubles, receives the
@@ -256,9 +268,14 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
  * The work is enqueued on the context's stream and the call returns without
  * waiting: synchronise that stream before reading M.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * outside any stream capture.  All calls on a device share the array, so
+ * The first call on a device sets that device up, with it current: it loads
+ * this entry point's two kernels onto the device (under CUDA's default lazy
+ * module loading, that is when the driver places the 16 MiB array in device
+ * memory, and it may synchronise the device), looks up the array's address
+ * (cudaGetSymbolAddress) and reads the SM count.  Make that first call
+ * during set-up, before the loop that must not allocate, and outside any
+ * stream capture (with CUDA_MODULE_LOADING=EAGER the array is placed when the
+ * CUDA context is created instead).  All calls on a device share the array, so
  * calls whose work overlaps in time (different streams, or different host
  * threads) race and corrupt each other's results: order them.  No part of
  * the array needs to start at zero (every partial is written before it is

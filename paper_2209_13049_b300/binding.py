@@ -29,7 +29,8 @@ EXPORTS = ["lqmpc_default_options", "lqmpc_status_str", "lqmpc_setup", "lqmpc_se
            "lqmpc_form_kkt", "lqmpc_kkt_solve", "lqmpc_get_trace", "lqmpc_get_duals",
            "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc", "lqmpc_solve_warm", "lqmpc_mlp_create",
            "lqmpc_mlp_set_bounds", "lqmpc_mlp_get_params", "lqmpc_mlp_set_params", "lqmpc_mlp_grad",
-           "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free", "lqmpc_autotune"]
+           "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free", "lqmpc_autotune",
+           "lqmpc_solve_batch_warm"]
 
 
 class LqmpcError(RuntimeError):
@@ -84,6 +85,8 @@ def load(path: str = LIB_PATH):
         f.argtypes = [P, P, P, ctypes.POINTER(Stats)]
     lib.lqmpc_solve_batch.restype = I
     lib.lqmpc_solve_batch.argtypes = [P, I, P, P, P]
+    lib.lqmpc_solve_batch_warm.restype = I
+    lib.lqmpc_solve_batch_warm.argtypes = [P, I, P, P, D, P, P]
     lib.lqmpc_free.restype = None
     lib.lqmpc_free.argtypes = [P]
     for name in ("lqmpc_get_gstack", "lqmpc_get_hessian", "lqmpc_get_duals"):
@@ -301,8 +304,9 @@ def autotune(solvers, cache_path=None):
                                  None if cache_path is None else str(cache_path).encode()), "lqmpc_autotune")
 
 
-def solve_batch(solvers, x0s, check: bool = True):
-    """Solve every (solver, x0) pair in one lockstep batch (lqmpc_solve_batch)."""
+def solve_batch(solvers, x0s, check: bool = True, u_inits=None, mu0: float = 0.0):
+    """Solve every (solver, x0) pair in one lockstep batch (lqmpc_solve_batch);
+    with u_inits, every instance starts from its guess (lqmpc_solve_batch_warm)."""
     lib = load()
     k = len(solvers)
     x0a = [_f64(x) for x in x0s]
@@ -311,10 +315,19 @@ def solve_batch(solvers, x0s, check: bool = True):
     xp = (ctypes.c_void_p * k)(*[x.ctypes.data for x in x0a])
     up = (ctypes.c_void_p * k)(*[u.ctypes.data for u in us])
     stats = (Stats * k)()
-    code = lib.lqmpc_solve_batch(ctypes.cast(hs, ctypes.c_void_p), k, ctypes.cast(xp, ctypes.c_void_p),
-                                 ctypes.cast(up, ctypes.c_void_p), ctypes.cast(stats, ctypes.c_void_p))
+    if u_inits is None:
+        code = lib.lqmpc_solve_batch(ctypes.cast(hs, ctypes.c_void_p), k, ctypes.cast(xp, ctypes.c_void_p),
+                                     ctypes.cast(up, ctypes.c_void_p), ctypes.cast(stats, ctypes.c_void_p))
+        where = "lqmpc_solve_batch"
+    else:
+        ga = [_f64(g) for g in u_inits]
+        gp = (ctypes.c_void_p * k)(*[g.ctypes.data for g in ga])
+        code = lib.lqmpc_solve_batch_warm(ctypes.cast(hs, ctypes.c_void_p), k, ctypes.cast(xp, ctypes.c_void_p),
+                                          ctypes.cast(gp, ctypes.c_void_p), float(mu0),
+                                          ctypes.cast(up, ctypes.c_void_p), ctypes.cast(stats, ctypes.c_void_p))
+        where = "lqmpc_solve_batch_warm"
     if check and code != 0:
-        raise LqmpcError(code, "lqmpc_solve_batch")
+        raise LqmpcError(code, where)
     return us, [s.as_dict() for s in stats], code
 
 

@@ -1364,9 +1364,15 @@ lqmpc_status lqmpc_solve_warm(lqmpc_ctx* ctx, const double* x0, const double* u_
     return solve_common(ctx, x0, false, u_out, false, stats, u_init, mu0);
 }
 
-lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
-                               double* const* u_outs, lqmpc_stats* stats) {
+static lqmpc_status solve_batch_impl(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                                     const double* const* u_inits, double mu0, double* const* u_outs,
+                                     lqmpc_stats* stats) {
     if (!ctxs || count < 1 || !x0s || !u_outs) return LQMPC_ERR_ARG;
+    if (u_inits) {
+        if (std::isnan(mu0)) return LQMPC_ERR_ARG;
+        for (int i = 0; i < count; ++i)
+            if (!u_inits[i] || (ctxs[i] && !all_finite(u_inits[i], ctxs[i]->h.n))) return LQMPC_ERR_ARG;
+    }
     for (int i = 0; i < count; ++i)
         if (!ctxs[i] || !x0s[i] || !u_outs[i] || ctxs[i]->user_stream != ctxs[0]->user_stream ||
             ctxs[i]->device != ctxs[0]->device)
@@ -1424,6 +1430,13 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (cudaMemcpyAsync(ctxs[i]->h.xbar, x0s[i], sizeof(double) * ctxs[i]->h.ns, cudaMemcpyHostToDevice,
                             b.st) != cudaSuccess)
             s = LQMPC_ERR_CUDA;
+    if (u_inits) {      // warm start: every instance's guess where prepare() reads it
+        for (int i = 0; i < count && s == LQMPC_OK; ++i)
+            if (cudaMemcpyAsync(ctxs[i]->h.du_aff, u_inits[i], sizeof(double) * ctxs[i]->h.n,
+                                cudaMemcpyHostToDevice, b.st) != cudaSuccess)
+                s = LQMPC_ERR_CUDA;
+        b.warm_mu0 = mu0 > 0.0 ? mu0 : kWarmMu0;
+    }
     double tt = 0, tk = 0;
     {
         GraphCache gc;      // graphs of this call's descriptor array
@@ -1448,6 +1461,18 @@ lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* 
         if (si != LQMPC_OK && first == LQMPC_OK) first = si;
     }
     return first;
+}
+
+lqmpc_status lqmpc_solve_batch(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                               double* const* u_outs, lqmpc_stats* stats) {
+    return solve_batch_impl(ctxs, count, x0s, nullptr, 0.0, u_outs, stats);
+}
+
+lqmpc_status lqmpc_solve_batch_warm(lqmpc_ctx* const* ctxs, int count, const double* const* x0s,
+                                    const double* const* u_inits, double mu0, double* const* u_outs,
+                                    lqmpc_stats* stats) {
+    if (!u_inits) return LQMPC_ERR_ARG;
+    return solve_batch_impl(ctxs, count, x0s, u_inits, mu0, u_outs, stats);
 }
 
 lqmpc_status lqmpc_autotune(lqmpc_ctx* const* ctxs, int count, const char* cache_path) {
