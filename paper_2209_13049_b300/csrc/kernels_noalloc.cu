@@ -109,20 +109,35 @@ __global__ void k_kkt_scratch_reduce(const double* __restrict__ ws, int splits, 
     }
 }
 
-// Address of this device's scratch array, looked up once per device (the
-// device must be current).  nullptr with *err set if the lookup fails.
-static double* noalloc_scratch(int dev, cudaError_t* err) {
+// Per-device set-up, done once per device by the first call (the device must
+// be current): force this module's two kernels onto the device (with lazy
+// module loading that is also when the driver places the scratch array),
+// look up the array's device address and read the SM count.  nullptr with
+// *err set if any step fails.
+struct NaDevice {
+    double* scratch;
+    int sms;
+};
+
+static const NaDevice* noalloc_device(int dev, cudaError_t* err) {
     static std::mutex mu;
-    static double* ptrs[kNaMaxDevices] = {};
+    static NaDevice devs[kNaMaxDevices] = {};
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= kNaMaxDevices) { *err = cudaErrorInvalidDevice; return nullptr; }
-    if (!ptrs[dev]) {
+    NaDevice& d = devs[dev];
+    if (!d.scratch) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_syrk_scratch);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_kkt_scratch_reduce);
+        int sms = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) { *err = e; return nullptr; }
-        ptrs[dev] = static_cast<double*>(p);
+        d.sms = sms > 0 ? sms : 1;
+        d.scratch = static_cast<double*>(p);
     }
-    return ptrs[dev];
+    return &d;
 }
 
 int noalloc_max_n() {
@@ -139,13 +154,14 @@ int launch_form_kkt_noalloc(const double* G, int ldg, const double* H, const dou
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 2;
     cudaError_t err = cudaSuccess;
-    double* ws = noalloc_scratch(dev, &err);
-    if (!ws) return 2;
+    const NaDevice* nd = noalloc_device(dev, &err);
+    if (!nd) return 2;
+    double* ws = nd->scratch;
     const int nt = (n + kNaTile - 1) / kNaTile;
     const long long tiles = (long long)nt * (nt + 1) / 2;
     // about four CTAs per SM over the tiles, within the scratch and the K chunks
     const long long chunks = (long long)N * ((ns + kNaKc - 1) / kNaKc);
-    long long splits = (148 * 4 + tiles - 1) / tiles;
+    long long splits = ((long long)nd->sms * 4 + tiles - 1) / tiles;
     const long long fit = (long long)(kNaScratchDoubles / (tiles * kNaTileDoubles));
     if (splits > fit) splits = fit;
     if (splits > chunks) splits = chunks;
