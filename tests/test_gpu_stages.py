@@ -31,6 +31,9 @@ CASES = [
     ("heat2d_10_ragged", lambda: inputs.heat2d(10, 7, 23)),      # n = 161: ragged 128/64/32 tiles
     ("heat1d_300_N37", lambda: inputs.heat1d(300, 3, 37)),        # n = 111
     ("dense_q", lambda: inputs.random_small(9, 4, 33, 3, dense_q=True)),  # non-diagonal Q, n = 132
+    # more than 16 inputs: the Gamma' product takes its input columns in several passes
+    ("heat1d_60_nu20", lambda: inputs.heat1d(60, 20, 6)),         # n = 120, two full passes
+    ("heat1d_70_nu17", lambda: inputs.heat1d(70, 17, 5)),         # n = 85, a one-column second pass
 ]
 
 
