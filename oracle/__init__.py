@@ -59,7 +59,10 @@ class _Problem(ctypes.Structure):
                 ("qf_ptr", ctypes.c_void_p), ("qf_idx", ctypes.c_void_p), ("qf_val", ctypes.c_void_p),
                 ("R", ctypes.c_void_p),
                 ("xl", ctypes.c_void_p), ("xu", ctypes.c_void_p),
-                ("ul", ctypes.c_void_p), ("uu", ctypes.c_void_p)]
+                ("ul", ctypes.c_void_p), ("uu", ctypes.c_void_p),
+                ("S", ctypes.c_void_p), ("w", ctypes.c_void_p), ("nc", ctypes.c_int),
+                ("E", ctypes.c_void_p), ("F", ctypes.c_void_p), ("gl", ctypes.c_void_p),
+                ("gu", ctypes.c_void_p)]
 
 
 class _Options(ctypes.Structure):
@@ -101,6 +104,24 @@ def _csr(m, n):
             np.ascontiguousarray(m.data, dtype=np.float64))
 
 
+def _general_arrays(plant, ns, nu, N, nc):
+    """The optional data of Eq. 1 as C-ordered FP64 arrays (None when absent).
+    A feedback K is not the oracle's business: it reparametrises the inputs
+    (u = K x + v) without changing the problem or its minimiser."""
+    def col(m, r, c):
+        return None if m is None else np.asfortranarray(np.asarray(m, dtype=np.float64).reshape(r, c))
+    out = {"S": col(getattr(plant, "S", None), ns, nu),
+           "w": None if getattr(plant, "w", None) is None else
+           np.ascontiguousarray(np.asarray(plant.w, dtype=np.float64).reshape(N, ns)),
+           "E": None, "F": None, "gl": None, "gu": None}
+    if nc:
+        out["E"] = col(plant.E, nc, ns)
+        out["F"] = col(plant.F, nc, nu)
+        out["gl"] = np.ascontiguousarray(plant.gl, dtype=np.float64).reshape(nc)
+        out["gu"] = np.ascontiguousarray(plant.gu, dtype=np.float64).reshape(nc)
+    return out
+
+
 def ipm_solve(plant, x0, *, tol: float = 1e-8, max_iter: int = 100, tau: float = 0.995,
               want_trace: bool = False, u_init=None, mu0: float = 0.0):
     """Run the oracle IPM (cold, or warm-started from the guess u_init with
@@ -115,16 +136,21 @@ def ipm_solve(plant, x0, *, tol: float = 1e-8, max_iter: int = 100, tau: float =
     R = np.asfortranarray(np.asarray(plant.R, dtype=np.float64).reshape(nu, nu))
     vecs = [np.ascontiguousarray(v, dtype=np.float64) for v in (plant.xl, plant.xu, plant.ul, plant.uu)]
     keep += [a, q, qf, B, R, vecs]
+    nc = getattr(plant, "nc", 0)
+    gen = _general_arrays(plant, ns, nu, N, nc)
+    keep.append(gen)
     pb = _Problem(ns, nu, N, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), _ptr(B),
                   _ptr(q[0]), _ptr(q[1]), _ptr(q[2]), _ptr(qf[0]), _ptr(qf[1]), _ptr(qf[2]),
-                  _ptr(R), _ptr(vecs[0]), _ptr(vecs[1]), _ptr(vecs[2]), _ptr(vecs[3]))
+                  _ptr(R), _ptr(vecs[0]), _ptr(vecs[1]), _ptr(vecs[2]), _ptr(vecs[3]),
+                  _ptr(gen["S"]), _ptr(gen["w"]), nc, _ptr(gen["E"]), _ptr(gen["F"]), _ptr(gen["gl"]),
+                  _ptr(gen["gu"]))
     ui = None if u_init is None else np.ascontiguousarray(u_init, dtype=np.float64).reshape(n)
     keep.append(ui)
     op = _Options(tol, max_iter, tau, _ptr(ui), mu0)
     xb = np.ascontiguousarray(x0, dtype=np.float64)
     u = np.zeros(n)
     x = np.zeros(ns * N)
-    z = np.zeros(2 * ns * N + 2 * n)
+    z = np.zeros(2 * ns * N + 2 * n + 2 * nc * N)
     st = _Stats()
     tr = np.zeros((max_iter + 1, TRACE_W)) if want_trace else None
     rc = _lib().orc_ipm_solve(ctypes.byref(pb), _ptr(xb), ctypes.byref(op), _ptr(u), _ptr(x),

@@ -6,11 +6,13 @@
  * CPU-baseline leg use it.  It shares no code, header or constant with the
  * CUDA path.
  *
- * What it computes.  The problem is Eq. 1 of the paper with S = 0, E = F = 0
- * (n_c = 0), w = 0:
+ * What it computes.  The problem is Eq. 1 of the paper:
  *     min  1/2 sum_{t=1}^{N-1} x_t' Q x_t + 1/2 x_N' Qf x_N + 1/2 sum_{t=0}^{N-1} u_t' R u_t
- *     s.t. x_0 = xbar,  x_{t+1} = A x_t + B u_t,
- *          xl <= x_t <= xu (t = 1..N),  ul <= u_t <= uu (t = 0..N-1).
+ *          + sum_{t=0}^{N-1} x_t' S u_t
+ *     s.t. x_0 = xbar,  x_{t+1} = A x_t + B u_t + w_t,
+ *          gl <= E x_t + F u_t <= gu (t = 0..N-1),
+ *          xl <= x_t <= xu (t = 1..N),  ul <= u_t <= uu (t = 0..N-1),
+ * with S, w and the nc general constraints optional (absent: zero).
  * The bounds on x_0 are dropped because x_0 is fixed (Eq. 1e lists t = 0..T;
  * a fixed x_0 makes them constants).  The 1/2 follows Eq. 3a (Eq. 1a has none;
  * scaling does not move the minimiser).
@@ -53,7 +55,34 @@ typedef struct {
     int m;                      /* number of finite one-sided constraints */
     unsigned char *f1, *f2;     /* finite masks: xu, xl (per state) */
     unsigned char *f3, *f4;     /* finite masks: uu, ul (per input) */
+    int nc;                     /* general constraints per stage */
+    unsigned char *f5, *f6;     /* finite masks: gu, gl (per constraint row) */
 } ctx_t;
+
+/* out = E x + F u (nc rows; x may be NULL for x = 0) */
+static void cons_eval(const ctx_t* c, const double* x, const double* u, double* out) {
+    const orc_problem* pb = c->pb;
+    for (int r = 0; r < c->nc; ++r) {
+        double v = 0.0;
+        if (x)
+            for (int i = 0; i < c->ns; ++i) v += pb->E[r + (size_t)i * c->nc] * x[i];
+        for (int a = 0; a < c->nu; ++a) v += pb->F[r + (size_t)a * c->nc] * u[a];
+        out[r] = v;
+    }
+}
+
+/* xo += E' v (if xo), uo += F' v (if uo) */
+static void cons_tadd(const ctx_t* c, const double* v, double* xo, double* uo) {
+    const orc_problem* pb = c->pb;
+    for (int r = 0; r < c->nc; ++r) {
+        const double vr = v[r];
+        if (vr == 0.0) continue;
+        if (xo)
+            for (int i = 0; i < c->ns; ++i) xo[i] += pb->E[r + (size_t)i * c->nc] * vr;
+        if (uo)
+            for (int a = 0; a < c->nu; ++a) uo[a] += pb->F[r + (size_t)a * c->nc] * vr;
+    }
+}
 
 /* y += alpha * A x  (CSR) */
 static void csr_mv_add(int rows, const int* ptr, const int* idx, const double* val,
@@ -83,14 +112,15 @@ static double mid_of_box(double lo, double hi) {
     return 0.0;
 }
 
-/* x[0] = xbar; x[t+1] = A x[t] + B u[t] */
+/* x[0] = xbar; x[t+1] = A x[t] + B u[t] + w[t] */
 static void rollout(const ctx_t* c, const double* xbar, const double* u, double* x) {
     const orc_problem* pb = c->pb;
     int ns = c->ns, nu = c->nu;
     memcpy(x, xbar, sizeof(double) * ns);
     for (int t = 0; t < c->N; ++t) {
         double* xn = x + (size_t)(t + 1) * ns;
-        memset(xn, 0, sizeof(double) * ns);
+        if (pb->w) memcpy(xn, pb->w + (size_t)t * ns, sizeof(double) * ns);
+        else memset(xn, 0, sizeof(double) * ns);
         csr_mv_add(ns, pb->a_ptr, pb->a_idx, pb->a_val, x + (size_t)t * ns, 1.0, xn);
         for (int j = 0; j < nu; ++j) {
             double uj = u[t * nu + j];
@@ -143,13 +173,15 @@ typedef struct {
 
 /*
  * Backward Riccati sweep: P_N = Qf + diag(Sigma_x,N);
- * for t = N-1..0:  Hhat_t = R + diag(Sigma_u,t) + B' P_{t+1} B,
- *                  P_t = Q + diag(Sigma_x,t) + A' P_{t+1} A
- *                        - A' P_{t+1} B Hhat_t^{-1} B' P_{t+1} A   (t >= 1).
+ * for t = N-1..0:  Hhat_t = R + diag(Sigma_u,t) + F' Sigma_c,t F + B' P_{t+1} B,
+ *                  K'_t = A' P_{t+1} B + S + E' Sigma_c,t F     (bpat, ns x nu)
+ *                  P_t = Q + diag(Sigma_x,t) + E' Sigma_c,t E + A' P_{t+1} A
+ *                        - K'_t Hhat_t^{-1} K'_t'              (t >= 1).
+ * Sigma_c,t (sigc, nc per stage) weighs stage t's general constraint rows.
  * e_t is the dynamics residual (zero for a dynamics-feasible iterate).
  */
 static int riccati_factor(const ctx_t* c, const double* sigx, const double* sigu,
-                          const double* e, fact_t* f) {
+                          const double* sigc, const double* e, fact_t* f) {
     const orc_problem* pb = c->pb;
     int ns = c->ns, nu = c->nu, N = c->N;
     size_t nn = (size_t)ns * ns;
@@ -188,12 +220,25 @@ static int riccati_factor(const ctx_t* c, const double* sigx, const double* sigu
                 hc[a + b * nu] = v;
             }
         for (int a = 0; a < nu; ++a) hc[a + a * nu] += sigu[t * nu + a];
+        const double* sc = c->nc ? sigc + (size_t)t * c->nc : NULL;
+        for (int r = 0; sc && r < c->nc; ++r)          /* F' Sigma_c F */
+            for (int a = 0; a < nu; ++a)
+                for (int b = 0; b < nu; ++b)
+                    hc[a + b * nu] += pb->F[r + (size_t)a * c->nc] * sc[r] * pb->F[r + (size_t)b * c->nc];
         if (chol_small(nu, hc)) return ORC_ERR_NOT_PD;
         /* bpat[:, c] = ((PB)' A)' [:, c] = A' PB[:, c] */
         memset(bpat, 0, sizeof(double) * ns * nu);
         for (int j = 0; j < nu; ++j)
             csr_mtv_add(ns, pb->a_ptr, pb->a_idx, pb->a_val, f->PB + (size_t)j * ns, 1.0,
                         bpat + (size_t)j * ns);
+        if (pb->S)                                      /* cross term S */
+            for (size_t k = 0; k < (size_t)ns * nu; ++k) bpat[k] += pb->S[k];
+        for (int r = 0; sc && r < c->nc; ++r)          /* E' Sigma_c F */
+            for (int a = 0; a < nu; ++a) {
+                const double fa = sc[r] * pb->F[r + (size_t)a * c->nc];
+                if (fa == 0.0) continue;
+                for (int i = 0; i < ns; ++i) bpat[i + (size_t)a * ns] += pb->E[r + (size_t)i * c->nc] * fa;
+            }
         /* pe = P_{t+1} e_t */
         const double* et = e + (size_t)t * ns;
         memset(pe, 0, sizeof(double) * ns);
@@ -223,6 +268,14 @@ static int riccati_factor(const ctx_t* c, const double* sigx, const double* sigu
             for (int k = pb->q_ptr[r]; k < pb->q_ptr[r + 1]; ++k)
                 Pt[r + (size_t)pb->q_idx[k] * ns] += pb->q_val[k];
         for (int i = 0; i < ns; ++i) Pt[i + (size_t)i * ns] += sigx[(size_t)(t - 1) * ns + i];
+        for (int r = 0; sc && r < c->nc; ++r) {        /* E' Sigma_c E */
+            if (sc[r] == 0.0) continue;
+            for (int j = 0; j < ns; ++j) {
+                const double ej = sc[r] * pb->E[r + (size_t)j * c->nc];
+                if (ej == 0.0) continue;
+                for (int i = 0; i < ns; ++i) Pt[i + (size_t)j * ns] += pb->E[r + (size_t)i * c->nc] * ej;
+            }
+        }
         /* Y = Hhat^{-1} bpat'  (nu x ns), column j = Hhat^{-1} bpat[j, :]' */
         for (int j = 0; j < ns; ++j) {
             double* yj = f->Y + (size_t)j * nu;
@@ -335,6 +388,36 @@ static void adjoint(const ctx_t* c, const double* dx, const double* q, const dou
     }
 }
 
+/* The stage terms that couple x_t and u_t (t = 1..N-1 for the state rows,
+ * t = 0..N-1 for the inputs): qx_t += S u_t + E' (za_t - zb_t) and, when
+ * ru and x are given, ru_t += S' x_t + F' (za_t - zb_t) (x_0 = xbar; x holds
+ * x_0..x_N).  za, zb: nc per stage (NULL when nc = 0). */
+static void stage_terms(const ctx_t* c, const double* u, const double* za, const double* zb, double* qx,
+                        double* ru, const double* x) {
+    const orc_problem* pb = c->pb;
+    const int ns = c->ns, nu = c->nu, N = c->N, nc = c->nc;
+    double* dz = nc ? malloc(sizeof(double) * nc) : NULL;
+    for (int t = 0; t < N; ++t) {
+        double* qt = t >= 1 ? qx + (size_t)(t - 1) * ns : NULL;
+        if (pb->S && qt)
+            for (int a = 0; a < nu; ++a) {
+                const double ua = u[t * nu + a];
+                for (int i = 0; i < ns; ++i) qt[i] += pb->S[i + (size_t)a * ns] * ua;
+            }
+        if (ru && pb->S)
+            for (int a = 0; a < nu; ++a) {
+                double v = 0.0;
+                for (int i = 0; i < ns; ++i) v += pb->S[i + (size_t)a * ns] * x[(size_t)t * ns + i];
+                ru[t * nu + a] += v;
+            }
+        if (nc) {
+            for (int r = 0; r < nc; ++r) dz[r] = za[(size_t)t * nc + r] - zb[(size_t)t * nc + r];
+            cons_tadd(c, dz, qt, ru ? ru + t * nu : NULL);
+        }
+    }
+    free(dz);
+}
+
 static double vmaxabs(const double* v, size_t n) {
     double m = 0.0;
     for (size_t i = 0; i < n; ++i) { double a = fabs(v[i]); if (a > m || a != a) m = a; }
@@ -362,6 +445,14 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
         c.f3[j] = isfinite(pb->uu[j]) != 0; c.f4[j] = isfinite(pb->ul[j]) != 0;
         c.m += N * (c.f3[j] + c.f4[j]);
     }
+    c.nc = (pb->nc > 0 && pb->E && pb->F && pb->gl && pb->gu) ? pb->nc : 0;
+    const int nc = c.nc;
+    const size_t CX = (size_t)N * nc;   /* general constraint rows, stage t at t*nc */
+    c.f5 = malloc(nc + 1); c.f6 = malloc(nc + 1);
+    for (int r = 0; r < nc; ++r) {
+        c.f5[r] = isfinite(pb->gu[r]) != 0; c.f6[r] = isfinite(pb->gl[r]) != 0;
+        c.m += N * (c.f5[r] + c.f6[r]);
+    }
 
     /* variables */
     double* u = calloc(n, sizeof(double));
@@ -378,6 +469,12 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
     double *ds1 = calloc(SX, 8), *ds2 = calloc(SX, 8), *ds3 = calloc(n, 8), *ds4 = calloc(n, 8);
     double *dz1 = calloc(SX, 8), *dz2 = calloc(SX, 8), *dz3 = calloc(n, 8), *dz4 = calloc(n, 8);
     double *rc1 = calloc(SX, 8), *rc2 = calloc(SX, 8), *rc3 = calloc(n, 8), *rc4 = calloc(n, 8);
+    /* general constraints: value c_t = E x_t + F u_t, slacks/duals (upper 5,
+     * lower 6), residuals, steps, Sigma_c and the per-stage linear terms */
+    double *cv = calloc(CX + 1, 8), *s5 = calloc(CX + 1, 8), *z5 = calloc(CX + 1, 8), *s6 = calloc(CX + 1, 8);
+    double *z6 = calloc(CX + 1, 8), *rp5 = calloc(CX + 1, 8), *rp6 = calloc(CX + 1, 8), *rc5 = calloc(CX + 1, 8);
+    double *rc6 = calloc(CX + 1, 8), *ds5 = calloc(CX + 1, 8), *dz5 = calloc(CX + 1, 8), *ds6 = calloc(CX + 1, 8);
+    double *dz6 = calloc(CX + 1, 8), *sigc = calloc(CX + 1, 8), *wc = calloc(CX + 1, 8), *dcv = calloc(CX + 1, 8);
     double* work = calloc(2 * (size_t)ns + nu + n + 8, 8);
     double* tmp = calloc(XT, 8);
     fact_t f;
@@ -409,7 +506,28 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                 for (int i = 0; i < ns; ++i) v += ba[i] * lt[i];
                 if (fabs(v) > hm) hm = fabs(v);
             }
+        if (pb->S) {                     /* + S' y_t (y_0 = xbar) */
+            hm = 0.0;
+            for (int t = 0; t < N; ++t)
+                for (int a = 0; a < nu; ++a) {
+                    const double* ba = pb->B + (size_t)a * ns;
+                    const double* lt = lam + (size_t)(t + 1) * ns;
+                    const double* sa = pb->S + (size_t)a * ns;
+                    const double* yt = x + (size_t)t * ns;
+                    double v = 0.0, vs = 0.0;
+                    for (int i = 0; i < ns; ++i) v += ba[i] * lt[i];
+                    for (int i = 0; i < ns; ++i) vs += sa[i] * yt[i];
+                    if (fabs(v + vs) > hm) hm = fabs(v + vs);
+                }
+        }
         hnorm = hm;
+        for (int t = 0; t < N && nc; ++t) {   /* general rows at u = 0: E y_t */
+            cons_eval(&c, x + (size_t)t * ns, u, cv);
+            for (int r2 = 0; r2 < nc; ++r2) {
+                if (c.f5[r2] && fabs(pb->gu[r2] - cv[r2]) > dnorm) dnorm = fabs(pb->gu[r2] - cv[r2]);
+                if (c.f6[r2] && fabs(cv[r2] - pb->gl[r2]) > dnorm) dnorm = fabs(cv[r2] - pb->gl[r2]);
+            }
+        }
         for (int t = 1; t <= N; ++t)
             for (int i = 0; i < ns; ++i) {
                 double y = x[(size_t)t * ns + i];
@@ -454,9 +572,19 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
             s3[k] = c.f3[j] ? fmax(pb->uu[j] - u[k], sfl) : 1.0; z3[k] = c.f3[j] ? DUAL0(s3[k]) : 0.0;
             s4[k] = c.f4[j] ? fmax(u[k] - pb->ul[j], sfl) : 1.0; z4[k] = c.f4[j] ? DUAL0(s4[k]) : 0.0;
         }
+    for (int t = 0; t < N && nc; ++t) {
+        cons_eval(&c, x + (size_t)t * ns, u + (size_t)t * nu, cv + (size_t)t * nc);
+        for (int r2 = 0; r2 < nc; ++r2) {
+            size_t k = (size_t)t * nc + r2;
+            s5[k] = c.f5[r2] ? fmax(pb->gu[r2] - cv[k], sfl) : 1.0; z5[k] = c.f5[r2] ? DUAL0(s5[k]) : 0.0;
+            s6[k] = c.f6[r2] ? fmax(cv[k] - pb->gl[r2], sfl) : 1.0; z6[k] = c.f6[r2] ? DUAL0(s6[k]) : 0.0;
+        }
+    }
 #undef DUAL0
-    /* lambda0: zero state stationarity, lam_t = Q x_t + z1 - z2 + A' lam_{t+1} */
+    /* lambda0: zero state stationarity, lam_t = Q x_t + z1 - z2 + S u_t
+     * + E'(z5 - z6) + A' lam_{t+1} */
     for (size_t k = 0; k < SX; ++k) q[k] = z1[k] - z2[k];
+    stage_terms(&c, u, z5, z6, q, NULL, NULL);
     adjoint(&c, x, q, NULL, lam);
 
     for (it = 0;; ++it) {
@@ -486,11 +614,15 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                 for (int i = 0; i < ns; ++i) v += ba[i] * lt[i];
                 ru[t * nu + a] = v + z3[t * nu + a] - z4[t * nu + a];
             }
-        /* r_dyn,t = A x_t + B u_t - x_{t+1} */
+        /* + S u_t + E'(z5 - z6) (states), S' x_t + F'(z5 - z6) (inputs) */
+        stage_terms(&c, u, z5, z6, rx, ru, x);
+        /* r_dyn,t = A x_t + B u_t + w_t - x_{t+1} */
         for (int t = 0; t < N; ++t) {
             double* rt = rdyn + (size_t)t * ns;
             const double* xt1 = x + (size_t)(t + 1) * ns;
             for (int i = 0; i < ns; ++i) rt[i] = -xt1[i];
+            if (pb->w)
+                for (int i = 0; i < ns; ++i) rt[i] += pb->w[(size_t)t * ns + i];
             csr_mv_add(ns, pb->a_ptr, pb->a_idx, pb->a_val, x + (size_t)t * ns, 1.0, rt);
             for (int a = 0; a < nu; ++a) {
                 double ua = u[t * nu + a];
@@ -519,6 +651,17 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                 if (fabs(rp4[k]) > rpmax) rpmax = fabs(rp4[k]);
                 sz += (c.f3[j] ? s3[k] * z3[k] : 0.0) + (c.f4[j] ? s4[k] * z4[k] : 0.0);
             }
+        for (int t = 0; t < N && nc; ++t) {   /* general rows: c_t + s5 - gu, -c_t + s6 + gl */
+            cons_eval(&c, x + (size_t)t * ns, u + (size_t)t * nu, cv + (size_t)t * nc);
+            for (int r2 = 0; r2 < nc; ++r2) {
+                size_t k = (size_t)t * nc + r2;
+                rp5[k] = c.f5[r2] ? cv[k] + s5[k] - pb->gu[r2] : 0.0;
+                rp6[k] = c.f6[r2] ? -cv[k] + s6[k] + pb->gl[r2] : 0.0;
+                if (fabs(rp5[k]) > rpmax) rpmax = fabs(rp5[k]);
+                if (fabs(rp6[k]) > rpmax) rpmax = fabs(rp6[k]);
+                sz += (c.f5[r2] ? s5[k] * z5[k] : 0.0) + (c.f6[r2] ? s6[k] * z6[k] : 0.0);
+            }
+        }
         double rdmax = vmaxabs(ru, n);
         double rxm = vmaxabs(rx, SX);
         if (rxm > rdmax || rxm != rxm) rdmax = rxm;
@@ -537,7 +680,8 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
         /* --- Sigma = S^{-1} Z (Eq. 6), per state and input row --- */
         for (size_t k = 0; k < SX; ++k) sigx[k] = z1[k] / s1[k] + z2[k] / s2[k];
         for (int k = 0; k < n; ++k) sigu[k] = z3[k] / s3[k] + z4[k] / s4[k];
-        int fs = riccati_factor(&c, sigx, sigu, rdyn, &f);
+        for (size_t k = 0; k < CX; ++k) sigc[k] = z5[k] / s5[k] + z6[k] / s6[k];
+        int fs = riccati_factor(&c, sigx, sigu, sigc, rdyn, &f);
         if (fs) { status = fs; break; }
 
         double alpha_aff = 1.0, sigma = 0.0, alpha = 1.0;
@@ -547,6 +691,7 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
             if (pass == 0) {
                 for (size_t k = 0; k < SX; ++k) { rc1[k] = s1[k] * z1[k]; rc2[k] = s2[k] * z2[k]; }
                 for (int k = 0; k < n; ++k) { rc3[k] = s3[k] * z3[k]; rc4[k] = s4[k] * z4[k]; }
+                for (size_t k = 0; k < CX; ++k) { rc5[k] = s5[k] * z5[k]; rc6[k] = s6[k] * z6[k]; }
             } else {
                 double smu = sigma * mu;
                 for (int t = 1; t <= N; ++t)
@@ -561,6 +706,11 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                         rc3[k] = c.f3[j] ? s3[k] * z3[k] + ds3[k] * dz3[k] - smu : 0.0;
                         rc4[k] = c.f4[j] ? s4[k] * z4[k] + ds4[k] * dz4[k] - smu : 0.0;
                     }
+                for (size_t k = 0; k < CX; ++k) {
+                    const int r2 = (int)(k % nc);
+                    rc5[k] = c.f5[r2] ? s5[k] * z5[k] + ds5[k] * dz5[k] - smu : 0.0;
+                    rc6[k] = c.f6[r2] ? s6[k] * z6[k] + ds6[k] * dz6[k] - smu : 0.0;
+                }
             }
             /* linear terms after eliminating ds, dz:
              * q = r_x + S1^{-1}(Z1 rp1 - rc1) - S2^{-1}(Z2 rp2 - rc2), likewise r. */
@@ -568,8 +718,32 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                 q[k] = rx[k] + (z1[k] * rp1[k] - rc1[k]) / s1[k] - (z2[k] * rp2[k] - rc2[k]) / s2[k];
             for (int k = 0; k < n; ++k)
                 r[k] = ru[k] + (z3[k] * rp3[k] - rc3[k]) / s3[k] - (z4[k] * rp4[k] - rc4[k]) / s4[k];
+            if (nc) {   /* general rows: q_t += E' wc_t (t >= 1), r_t += F' wc_t */
+                for (size_t k = 0; k < CX; ++k)
+                    wc[k] = (z5[k] * rp5[k] - rc5[k]) / s5[k] - (z6[k] * rp6[k] - rc6[k]) / s6[k];
+                for (int t = 0; t < N; ++t)
+                    cons_tadd(&c, wc + (size_t)t * nc, t >= 1 ? q + (size_t)(t - 1) * ns : NULL, r + t * nu);
+            }
             riccati_solve(&c, &f, q, r, rdyn, dx, du, work);
-            adjoint(&c, dx, q, sigx, dlam);
+            if (pb->S || nc) {
+                /* the LQ subproblem's costate also carries the stage
+                 * couplings: S du_t + E' Sigma_c,t (E dx_t + F du_t) */
+                memcpy(tmp, q, sizeof(double) * SX);
+                for (int t = 0; t < N && nc; ++t) {
+                    cons_eval(&c, dx + (size_t)t * ns, du + t * nu, dcv + (size_t)t * nc);
+                    for (int r2 = 0; r2 < nc; ++r2) wc[(size_t)t * nc + r2] = sigc[(size_t)t * nc + r2] * dcv[(size_t)t * nc + r2];
+                    if (t >= 1) cons_tadd(&c, wc + (size_t)t * nc, tmp + (size_t)(t - 1) * ns, NULL);
+                }
+                if (pb->S)
+                    for (int t = 1; t < N; ++t)
+                        for (int a = 0; a < nu; ++a) {
+                            const double da = du[t * nu + a];
+                            for (int i = 0; i < ns; ++i) tmp[(size_t)(t - 1) * ns + i] += pb->S[i + (size_t)a * ns] * da;
+                        }
+                adjoint(&c, dx, tmp, sigx, dlam);
+            } else {
+                adjoint(&c, dx, q, sigx, dlam);
+            }
             /* dlam is the costate of the LQ subproblem: it satisfies the
              * linearised state stationarity Qt dx + q + A' dlam_{t+1} - dlam_t = 0. */
             /* ds = -rp - C d(x,u);  dz = -(rc + z ds)/s */
@@ -590,6 +764,16 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                     if (c.f4[j]) { ds4[k] = -rp4[k] + du[k]; dz4[k] = -(rc4[k] + z4[k] * ds4[k]) / s4[k]; }
                     else { ds4[k] = 0; dz4[k] = 0; }
                 }
+            for (int t = 0; t < N && nc; ++t) {
+                cons_eval(&c, dx + (size_t)t * ns, du + t * nu, dcv + (size_t)t * nc);
+                for (int r2 = 0; r2 < nc; ++r2) {
+                    size_t k = (size_t)t * nc + r2;
+                    if (c.f5[r2]) { ds5[k] = -rp5[k] - dcv[k]; dz5[k] = -(rc5[k] + z5[k] * ds5[k]) / s5[k]; }
+                    else { ds5[k] = 0; dz5[k] = 0; }
+                    if (c.f6[r2]) { ds6[k] = -rp6[k] + dcv[k]; dz6[k] = -(rc6[k] + z6[k] * ds6[k]) / s6[k]; }
+                    else { ds6[k] = 0; dz6[k] = 0; }
+                }
+            }
             /* largest step to the boundary of s >= 0, z >= 0 */
             double amax = INFINITY;
 #define RATIO(v, dv) do { if ((dv) < 0.0) { double rr = -(v) / (dv); if (rr < amax) amax = rr; } } while (0)
@@ -600,6 +784,10 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
             for (int k = 0; k < n; ++k) {
                 RATIO(s3[k], ds3[k]); RATIO(z3[k], dz3[k]);
                 RATIO(s4[k], ds4[k]); RATIO(z4[k], dz4[k]);
+            }
+            for (size_t k = 0; k < CX; ++k) {
+                RATIO(s5[k], ds5[k]); RATIO(z5[k], dz5[k]);
+                RATIO(s6[k], ds6[k]); RATIO(z6[k], dz6[k]);
             }
 #undef RATIO
             if (pass == 0) {
@@ -617,6 +805,11 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
                         if (c.f3[j]) szaff += (s3[k] + alpha_aff * ds3[k]) * (z3[k] + alpha_aff * dz3[k]);
                         if (c.f4[j]) szaff += (s4[k] + alpha_aff * ds4[k]) * (z4[k] + alpha_aff * dz4[k]);
                     }
+                for (size_t k = 0; k < CX; ++k) {
+                    const int r2 = (int)(k % nc);
+                    if (c.f5[r2]) szaff += (s5[k] + alpha_aff * ds5[k]) * (z5[k] + alpha_aff * dz5[k]);
+                    if (c.f6[r2]) szaff += (s6[k] + alpha_aff * ds6[k]) * (z6[k] + alpha_aff * dz6[k]);
+                }
                 double mu_aff = c.m > 0 ? szaff / c.m : 0.0;
                 sigma = mu > 0.0 ? pow(mu_aff / mu, 3.0) : 0.0;
             } else {
@@ -639,6 +832,10 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
             s3[k] += alpha * ds3[k]; s4[k] += alpha * ds4[k];
             z3[k] += alpha * dz3[k]; z4[k] += alpha * dz4[k];
         }
+        for (size_t k = 0; k < CX; ++k) {
+            s5[k] += alpha * ds5[k]; s6[k] += alpha * ds6[k];
+            z5[k] += alpha * dz5[k]; z6[k] += alpha * dz6[k];
+        }
     }
 
     if (u_out) memcpy(u_out, u, sizeof(double) * n);
@@ -646,6 +843,10 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
     if (z_out) {
         memcpy(z_out, z1, 8 * SX); memcpy(z_out + SX, z2, 8 * SX);
         memcpy(z_out + 2 * SX, z3, 8 * (size_t)n); memcpy(z_out + 2 * SX + n, z4, 8 * (size_t)n);
+        if (CX) {
+            memcpy(z_out + 2 * SX + 2 * (size_t)n, z5, 8 * CX);
+            memcpy(z_out + 2 * SX + 2 * (size_t)n + CX, z6, 8 * CX);
+        }
     }
     if (st) {
         st->iters = it; st->status = status; st->mu = mu;
@@ -653,7 +854,9 @@ int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* 
         st->hnorm = hnorm; st->dnorm = dnorm; st->m = c.m;
     }
 
-    free(c.f1); free(c.f2); free(c.f3); free(c.f4);
+    free(c.f1); free(c.f2); free(c.f3); free(c.f4); free(c.f5); free(c.f6);
+    free(cv); free(s5); free(z5); free(s6); free(z6); free(rp5); free(rp6); free(rc5); free(rc6);
+    free(ds5); free(dz5); free(ds6); free(dz6); free(sigc); free(wc); free(dcv);
     free(u); free(x); free(lam); free(s1); free(s2); free(z1); free(z2);
     free(s3); free(s4); free(z3); free(z4); free(rx); free(ru); free(rdyn);
     free(rp1); free(rp2); free(rp3); free(rp4); free(sigx); free(sigu); free(q); free(r);

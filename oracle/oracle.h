@@ -2,10 +2,10 @@
  * Oracle interface (test infrastructure only: the tests, the smoke check and
  * the benchmark's CPU-baseline leg may call it; the product path never does).
  *
- * Plain FP64 CPU implementation of the box-constrained LQ-MPC problem of the
- * paper's Eq. 1 (S = 0, n_c = 0, w = 0) solved by Mehrotra's predictor-
- * corrector method on the uncondensed problem, each Newton step by a backward
- * Riccati recursion.  Matrices A, Q, Qf are CSR (row pointers, column indices,
+ * Plain FP64 CPU implementation of the LQ-MPC problem of the paper's Eq. 1
+ * (cross term S, disturbance w, general constraints E, F, box bounds) solved
+ * by Mehrotra's predictor-corrector method on the uncondensed problem, each
+ * Newton step by a backward Riccati recursion.  Matrices A, Q, Qf are CSR (row pointers, column indices,
  * values); B (ns x nu) and R (nu x nu) are dense column-major.  Bounds may be
  * +-INFINITY (the constraint is then absent).
  */
@@ -27,6 +27,15 @@ typedef struct {
     const int* qf_ptr; const int* qf_idx; const double* qf_val;
     const double* R;
     const double *xl, *xu, *ul, *uu;
+    /* General data of Eq. 1, each optional (NULL / nc = 0: absent):
+     *   S  (ns x nu, column-major): cross term x_t' S u_t of the stage cost, t = 0..N-1
+     *   w  (N x ns, w_t at w + t*ns): x_{t+1} = A x_t + B u_t + w_t
+     *   E (nc x ns), F (nc x nu), column-major, gl, gu (nc, +-INFINITY allowed):
+     *       gl <= E x_t + F u_t <= gu for t = 0..N-1 (x_0 = xbar) */
+    const double* S;
+    const double* w;
+    int nc;
+    const double *E, *F, *gl, *gu;
 } orc_problem;
 
 /* u_init (nullable, nu*N): warm start from this input sequence instead of
@@ -42,7 +51,8 @@ typedef struct {
 } orc_stats;
 
 /* u_out: nu*N (u_t at t*nu); x_out: ns*N states x_1..x_N (nullable);
- * z_out: duals [z_xu (ns*N), z_xl (ns*N), z_uu (n), z_ul (n)] (nullable);
+ * z_out: duals [z_xu (ns*N), z_xl (ns*N), z_uu (n), z_ul (n), z_gu (nc*N),
+ * z_gl (nc*N)] (nullable);
  * trace: (max_iter+1) x ORC_TRACE_W (nullable).  Returns an ORC_* status. */
 int orc_ipm_solve(const orc_problem* pb, const double* xbar, const orc_options* op,
                   double* u_out, double* x_out, double* z_out, orc_stats* st, double* trace);

@@ -59,10 +59,29 @@ class Plant:
     uu: np.ndarray
     kind: str = "custom"
     meta: dict = field(default_factory=dict)
+    # general data of Eq. 1 (None: absent): cross term S (ns x nu), disturbance
+    # w (N x ns), general constraints gl <= E x_t + F u_t <= gu (E: nc x ns,
+    # F: nc x nu), and a stabilising feedback K (nu x ns) for the elimination
+    # u_t = K x_t + v_t (Section II; it changes the arithmetic, not u*)
+    S: Optional[np.ndarray] = None
+    w: Optional[np.ndarray] = None
+    E: Optional[np.ndarray] = None
+    F: Optional[np.ndarray] = None
+    gl: Optional[np.ndarray] = None
+    gu: Optional[np.ndarray] = None
+    K: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:
         return self.nu * self.N
+
+    @property
+    def nc(self) -> int:
+        return 0 if self.E is None else int(np.asarray(self.E).shape[0])
+
+    @property
+    def general(self) -> bool:
+        return any(v is not None for v in (self.S, self.w, self.E, self.K))
 
     def dense(self, name: str) -> np.ndarray:
         m = getattr(self, name)

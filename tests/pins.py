@@ -46,24 +46,94 @@ def dense_qp(plant, x0):
     return Gam, y, H, h
 
 
+def dense_qp_general(plant, x0):
+    """Dense reduced QP of Eq. 1 with its general data, written out directly:
+    x_t = y_t + Gamma_t u (y the free response, disturbance included, x_0 =
+    xbar), the cost 1/2 sum x'Q x + 1/2 sum u'R u + sum_t x_t' S u_t expanded
+    in u, and the general rows E x_t + F u_t as rows in u with offsets.
+    Returns Gam, y, H, h and the general rows [(g, lo, hi)]."""
+    ns, nu, N = plant.ns, plant.nu, plant.N
+    n = nu * N
+    Ad = plant.dense("A")
+    B = np.asarray(plant.B, dtype=np.float64)
+    w = np.zeros((N, ns)) if plant.w is None else np.asarray(plant.w, dtype=np.float64).reshape(N, ns)
+    cols = []
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        cols.append(simulate(Ad, B, np.zeros(ns), e, N).reshape(-1))
+    Gam = np.array(cols).T
+    x = np.asarray(x0, dtype=np.float64)
+    y = []
+    for t in range(N):
+        x = Ad @ x + w[t]
+        y.append(x)
+    y = np.concatenate(y)
+    Q, Qf, R = plant.dense("Q"), plant.dense("Qf"), np.asarray(plant.R)
+    H = np.kron(np.eye(N), R)
+    h = np.zeros(n)
+    for t in range(N):
+        W = Qf if t == N - 1 else Q
+        Gt = Gam[t * ns:(t + 1) * ns]
+        H += Gt.T @ W @ Gt
+        h += Gt.T @ W @ y[t * ns:(t + 1) * ns]
+
+    def state(t):        # x_t = off + G u  (t = 0..N)
+        if t == 0:
+            return np.asarray(x0, dtype=np.float64), np.zeros((ns, n))
+        return y[(t - 1) * ns:t * ns], Gam[(t - 1) * ns:t * ns]
+
+    def sel(t):          # u_t = P u
+        P = np.zeros((nu, n))
+        P[:, t * nu:(t + 1) * nu] = np.eye(nu)
+        return P
+
+    if plant.S is not None:
+        S = np.asarray(plant.S, dtype=np.float64).reshape(ns, nu)
+        for t in range(N):
+            off, G = state(t)
+            P = sel(t)
+            C = G.T @ S @ P
+            H += C + C.T
+            h += P.T @ S.T @ off
+    rows = []
+    if plant.E is not None:
+        E = np.asarray(plant.E, dtype=np.float64).reshape(-1, ns)
+        F = np.asarray(plant.F, dtype=np.float64).reshape(-1, nu)
+        for t in range(N):
+            off, G = state(t)
+            Gr = E @ G + F @ sel(t)
+            o = E @ off
+            for r in range(E.shape[0]):
+                rows.append((Gr[r], plant.gl[r] - o[r], plant.gu[r] - o[r]))
+    return Gam, y, H, h, rows
+
+
 def brute_force(plant, x0, tol=1e-9):
     """Unique minimiser of the strictly convex QP by enumerating every
     active-set pattern of the two-sided rows (free / at upper / at lower),
     solving the equality-constrained KKT system densely and keeping the
     pattern that is primal and dual feasible.  Tiny instances only."""
-    Gam, y, H, h = dense_qp(plant, x0)
+    if getattr(plant, "general", False):
+        Gam, y, H, h, grows = dense_qp_general(plant, x0)
+    else:
+        Gam, y, H, h = dense_qp(plant, x0)
+        grows = []
     ns, nu, N = plant.ns, plant.nu, plant.N
     n = nu * N
     rows = []   # (row vector g, lower bound, upper bound) for lo <= g u <= hi
     for t in range(N):
         for i in range(ns):
             k = t * ns + i
-            rows.append((Gam[k], plant.xl[i] - y[k], plant.xu[i] - y[k]))
+            if np.isfinite(plant.xl[i]) or np.isfinite(plant.xu[i]):
+                rows.append((Gam[k], plant.xl[i] - y[k], plant.xu[i] - y[k]))
     for t in range(N):
         for c in range(nu):
             e = np.zeros(n)
             e[t * nu + c] = 1.0
-            rows.append((e, plant.ul[c], plant.uu[c]))
+            if np.isfinite(plant.ul[c]) or np.isfinite(plant.uu[c]):
+                rows.append((e, plant.ul[c], plant.uu[c]))
+    rows += grows
     choices = []
     for (_, lo, hi) in rows:
         ch = [0]

@@ -330,3 +330,109 @@ def test_cube_plant_follows_table_1_and_the_oracle_meets_kkt():
     assert k["primal_violation"] <= 1e-9 and k["dual_min"] >= 0.0
     scale = 1.0 + float(np.max(np.abs(p.R @ r["u"].reshape(-1, 6).T)))
     assert k["stationarity"] <= 1e-9 * scale and k["complementarity"] <= 1e-8
+
+
+# ------------------------------------------------- general data of Eq. 1
+
+
+def _general(seed, ns=2, nu=1, N=3, nc=2, xb=np.inf, ub=0.6, cross=True, dist=True, cons=True):
+    """Random plant with the general data of Eq. 1: a cross term S with the
+    joint stage weight [Q S; S' R] positive definite, a disturbance w, and nc
+    general rows E x_t + F u_t."""
+    rng = np.random.default_rng(seed)
+    p = inputs.random_small(ns, nu, N, seed, xb=1.0, ub=ub, dense_q=True)
+    Mj = rng.standard_normal((ns + nu, ns + nu))
+    W = Mj @ Mj.T / (ns + nu) + 0.3 * np.eye(ns + nu)
+    p.Q, p.R = W[:ns, :ns], W[ns:, ns:]
+    if cross:
+        p.S = W[:ns, ns:].copy()
+    if dist:
+        p.w = 0.3 * rng.standard_normal((N, ns))
+    if cons:
+        p.E = rng.standard_normal((nc, ns))
+        p.F = rng.standard_normal((nc, nu))
+        p.gl = -rng.uniform(0.2, 0.6, nc)
+        p.gu = rng.uniform(0.2, 0.6, nc)
+    p.xl, p.xu = np.full(ns, -xb), np.full(ns, xb)
+    return p
+
+
+def test_general_data_unconstrained_equals_dense_minimiser():
+    """No finite bound or row: the oracle's optimum with S and w equals
+    -H^-1 h of the dense QP written out independently (a dropped cross term,
+    a transposed S or a disturbance at the wrong stage changes it)."""
+    for seed in range(4):
+        p = _general(seed, ns=3, nu=2, N=5, ub=np.inf, cons=False)
+        x0 = np.random.default_rng(seed).uniform(-1, 1, 3)
+        _, _, H, h, _ = pins.dense_qp_general(p, x0)
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        assert r["status"] == 0 and r["stats"]["m"] == 0
+        np.testing.assert_allclose(r["u"], -np.linalg.solve(H, h), rtol=0, atol=1e-10)
+
+
+def test_general_constraints_match_brute_force():
+    """General rows gl <= E x_t + F u_t <= gu (t = 0..N-1, the first on the
+    fixed x_0) with binding rows, cross term and disturbance, against the
+    brute-force active-set optimum."""
+    found, active = 0, 0
+    for seed in range(30):
+        p = _general(seed)
+        x0 = np.random.default_rng(200 + seed).uniform(-0.5, 0.5, 2)
+        bf = pins.brute_force(p, x0)
+        if bf is None:
+            continue
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        assert r["status"] == 0, seed
+        np.testing.assert_allclose(r["u"], bf[0], rtol=0, atol=1e-8)
+        found += 1
+        active += len(bf[1])
+        if found == 6:
+            break
+    assert found == 6 and active >= 6
+
+
+def test_cross_term_and_disturbance_with_state_bounds_match_brute_force():
+    found = 0
+    for seed in range(30):
+        p = _general(50 + seed, xb=0.5, cons=False)
+        x0 = np.random.default_rng(300 + seed).uniform(-0.4, 0.4, 2)
+        bf = pins.brute_force(p, x0)
+        if bf is None or not bf[1]:
+            continue
+        r = oracle.ipm_solve(p, x0, tol=1e-12)
+        assert r["status"] == 0
+        np.testing.assert_allclose(r["u"], bf[0], rtol=0, atol=1e-8)
+        found += 1
+        if found == 4:
+            break
+    assert found == 4
+
+
+def test_general_rows_kkt_and_duals():
+    """At the oracle's optimum the general rows hold, their duals are
+    nonnegative and complementary to the row slacks, and rows that cut the
+    unconstrained optimum bind (nc = nu with F invertible: every row value is
+    reachable, so the problem is feasible)."""
+    p = _general(7, ns=4, nu=2, N=6, nc=2, ub=np.inf)
+    x0 = np.random.default_rng(1).uniform(-0.5, 0.5, 4)
+    _, _, H, h, _ = pins.dense_qp_general(p, x0)
+    u0 = -np.linalg.solve(H, h).reshape(p.N, p.nu)
+    xs, c0 = x0.copy(), []
+    for t in range(p.N):
+        c0.append(p.E @ xs + p.F @ u0[t])
+        xs = p.dense("A") @ xs + p.B @ u0[t] + p.w[t]
+    c0 = np.array(c0)
+    p.gu = c0.max(axis=0) - 0.3 * np.ptp(c0, axis=0)
+    p.gl = np.full(p.nc, -np.inf)
+    r = oracle.ipm_solve(p, x0, tol=1e-12)
+    assert r["status"] == 0
+    n, SX, nc = p.n, p.ns * p.N, p.nc
+    z5 = r["z"][2 * SX + 2 * n:2 * SX + 2 * n + nc * p.N].reshape(p.N, nc)
+    z6 = r["z"][2 * SX + 2 * n + nc * p.N:].reshape(p.N, nc)
+    xs = np.vstack([x0, r["x"][:-1]])
+    u = r["u"].reshape(p.N, p.nu)
+    c = xs @ p.E.T + u @ p.F.T
+    assert np.all(c <= p.gu + 1e-9)
+    assert z5.min() >= 0 and np.all(z6 == 0.0)
+    assert np.max(np.abs(z5 * (p.gu - c))) <= 1e-9
+    assert z5.max() > 1e-3                       # rows bind
