@@ -2,9 +2,12 @@
  * lqmpc: condensed-space interior-point solver for box-constrained
  * linear-quadratic MPC on one B300 GPU (sm_103a).
  *
- * The problem (the paper's Eq. 1 with S = 0, no general constraints, w = 0):
+ * The problem (the paper's Eq. 1; lqmpc_setup takes the box-constrained case
+ * S = 0, no general constraints, w = 0, lqmpc_setup_general the rest):
  *     min  1/2 sum_{t=1}^{N-1} x_t' Q x_t + 1/2 x_N' Qf x_N + 1/2 sum_{t=0}^{N-1} u_t' R u_t
- *     s.t. x_0 = x0,  x_{t+1} = A x_t + B u_t          (t = 0..N-1)
+ *          + sum_{t=0}^{N-1} x_t' S u_t
+ *     s.t. x_0 = x0,  x_{t+1} = A x_t + B u_t + w_t          (t = 0..N-1)
+ *          gl <= E x_t + F u_t <= gu                       (t = 0..N-1)
  *          xl <= x_t <= xu  (t = 1..N),  ul <= u_t <= uu  (t = 0..N-1).
  * The states are eliminated once (Section II: x = Phi x0 + Gamma u, Gamma the
  * block lower-triangular Toeplitz matrix of the blocks A^k B), giving the
@@ -140,6 +143,44 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N,
                          const double* R,
                          const double* xl, const double* xu, const double* ul, const double* uu,
                          const lqmpc_options* opts, void* stream);
+
+/* General data of Eq. 1 (Section II).  Every pointer is host memory, owned
+ * by the caller and read during the call only; NULL (or nc = 0) means absent. */
+typedef struct {
+    const double* S;    /* ns x nu column-major: cross term x_t' S u_t of the stage cost;
+                           [Q S; S' R] must be positive semidefinite (not checked) */
+    const double* w;    /* N x ns, w_t at w + t*ns: known disturbance of the dynamics */
+    int nc;             /* general constraint rows per stage */
+    const double* E;    /* nc x ns column-major */
+    const double* F;    /* nc x nu column-major */
+    const double *gl, *gu;  /* nc each: gl <= E x_t + F u_t <= gu (+-INFINITY allowed) */
+    const double* K;    /* nu x ns column-major: stabilising feedback of the state
+                           elimination, u_t = K x_t + v_t (Section II); the solver then runs in v
+                           (A + B K in the powers of the elimination) and returns u */
+} lqmpc_general;
+
+/*
+ * As lqmpc_setup, for the general problem of Eq. 1.  The general rows are
+ * lifted into the state: stage t's rows become nc extra states of x_{t+1}
+ * (c_{t+1} = E x_t + F u_t, no cost, bounds [gl, gu]), so the condensed KKT
+ * matrix of Eq. 7 carries them in its Gamma' Sigma Gamma term; with K the
+ * input bounds become nu more lifted rows (u_t = K x_t + v_t) and v is free.
+ * Solves return u in every case.  The stage-level entry points
+ * (lqmpc_get_gstack, lqmpc_gamma_mv, lqmpc_form_kkt, lqmpc_get_duals, ...)
+ * work on the lifted state of dimension ns + nc (+ nu with K), whose extra
+ * rows come after the plant's states.  With K, warm starts
+ * (lqmpc_solve_warm, lqmpc_solve_batch_warm) return LQMPC_ERR_UNSUPPORTED.
+ * g = NULL is lqmpc_setup.  LQMPC_ERR_ARG as lqmpc_setup, and for non-finite
+ * S, w, E, F, K, crossed or NaN row bounds, or nc > 0 with a NULL array.
+ */
+lqmpc_status lqmpc_setup_general(lqmpc_ctx** out, int ns, int nu, int N,
+                                 const int* a_ptr, const int* a_idx, const double* a_val,
+                                 const double* B,
+                                 const int* q_ptr, const int* q_idx, const double* q_val,
+                                 const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                                 const double* R,
+                                 const double* xl, const double* xu, const double* ul, const double* uu,
+                                 const lqmpc_general* g, const lqmpc_options* opts, void* stream);
 
 /* Replace the options of a context (takes effect at the next solve). */
 lqmpc_status lqmpc_set_options(lqmpc_ctx* ctx, const lqmpc_options* opts);

@@ -30,7 +30,7 @@ EXPORTS = ["lqmpc_default_options", "lqmpc_status_str", "lqmpc_setup", "lqmpc_se
            "lqmpc_kernel_launches", "lqmpc_form_kkt_noalloc", "lqmpc_solve_warm", "lqmpc_mlp_create",
            "lqmpc_mlp_set_bounds", "lqmpc_mlp_get_params", "lqmpc_mlp_set_params", "lqmpc_mlp_grad",
            "lqmpc_mlp_train", "lqmpc_mlp_infer", "lqmpc_mlp_free", "lqmpc_autotune",
-           "lqmpc_solve_batch_warm"]
+           "lqmpc_solve_batch_warm", "lqmpc_setup_general"]
 
 
 class LqmpcError(RuntimeError):
@@ -43,6 +43,11 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("refine_max", ctypes.c_int), ("refine_tol", ctypes.c_double), ("fallback", ctypes.c_int),
                 ("tau", ctypes.c_double), ("verbose", ctypes.c_int)]
+
+
+class General(ctypes.Structure):
+    _fields_ = [("S", ctypes.c_void_p), ("w", ctypes.c_void_p), ("nc", ctypes.c_int), ("E", ctypes.c_void_p),
+                ("F", ctypes.c_void_p), ("gl", ctypes.c_void_p), ("gu", ctypes.c_void_p), ("K", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -77,6 +82,9 @@ def load(path: str = LIB_PATH):
     lib.lqmpc_setup.restype = I
     lib.lqmpc_setup.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P,
                                 ctypes.POINTER(Options), VP]
+    lib.lqmpc_setup_general.restype = I
+    lib.lqmpc_setup_general.argtypes = [ctypes.POINTER(P), I, I, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P,
+                                        ctypes.POINTER(General), ctypes.POINTER(Options), VP]
     lib.lqmpc_set_options.restype = I
     lib.lqmpc_set_options.argtypes = [P, ctypes.POINTER(Options)]
     for name in ("lqmpc_solve", "lqmpc_solve_device"):
@@ -175,10 +183,32 @@ class Solver:
         vec = [_f64(v) for v in (plant.xl, plant.xu, plant.ul, plant.uu)]
         h = ctypes.c_void_p()
         st = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0))
-        code = lib.lqmpc_setup(ctypes.byref(h), self.ns, self.nu, self.N, _p(a[0]), _p(a[1]), _p(a[2]), _p(B),
-                               _p(q[0]), _p(q[1]), _p(q[2]), _p(qf[0]), _p(qf[1]), _p(qf[2]), _p(R),
-                               _p(vec[0]), _p(vec[1]), _p(vec[2]), _p(vec[3]), ctypes.byref(o), st)
-        _check(code, "lqmpc_setup")
+        # internal (lifted) state dimension: general rows and, with K, the inputs
+        self.ns_int = self.ns
+        if getattr(plant, "general", False):
+            nc = plant.nc
+
+            def col(m, r, c):
+                return None if m is None else np.asfortranarray(np.asarray(m, dtype=np.float64).reshape(r, c))
+            self._gen = {"S": col(plant.S, self.ns, self.nu),
+                         "w": None if plant.w is None else _f64(np.asarray(plant.w).reshape(self.N, self.ns)),
+                         "E": col(plant.E, nc, self.ns) if nc else None, "F": col(plant.F, nc, self.nu) if nc else None,
+                         "gl": _f64(plant.gl) if nc else None, "gu": _f64(plant.gu) if nc else None,
+                         "K": col(plant.K, self.nu, self.ns)}
+            gd = self._gen
+            g = General(_p(gd["S"]), _p(gd["w"]), nc, _p(gd["E"]), _p(gd["F"]), _p(gd["gl"]), _p(gd["gu"]),
+                        _p(gd["K"]))
+            self.ns_int = self.ns + nc + (self.nu if plant.K is not None else 0)
+            code = lib.lqmpc_setup_general(ctypes.byref(h), self.ns, self.nu, self.N, _p(a[0]), _p(a[1]), _p(a[2]),
+                                           _p(B), _p(q[0]), _p(q[1]), _p(q[2]), _p(qf[0]), _p(qf[1]), _p(qf[2]),
+                                           _p(R), _p(vec[0]), _p(vec[1]), _p(vec[2]), _p(vec[3]), ctypes.byref(g),
+                                           ctypes.byref(o), st)
+            _check(code, "lqmpc_setup_general")
+        else:
+            code = lib.lqmpc_setup(ctypes.byref(h), self.ns, self.nu, self.N, _p(a[0]), _p(a[1]), _p(a[2]), _p(B),
+                                   _p(q[0]), _p(q[1]), _p(q[2]), _p(qf[0]), _p(qf[1]), _p(qf[2]), _p(R),
+                                   _p(vec[0]), _p(vec[1]), _p(vec[2]), _p(vec[3]), ctypes.byref(o), st)
+            _check(code, "lqmpc_setup")
         self.h = h
         self.options = o
 
@@ -221,7 +251,7 @@ class Solver:
         return st.as_dict()
 
     def get_gstack(self):
-        G = np.zeros((self.N, self.nu, self.ns))
+        G = np.zeros((self.N, self.nu, self.ns_int))
         _check(load().lqmpc_get_gstack(self.h, _p(G)), "lqmpc_get_gstack")
         return np.transpose(G, (0, 2, 1)).copy()          # (N, ns, nu)
 
@@ -232,7 +262,7 @@ class Solver:
 
     def gamma_mv(self, v):
         v = _f64(v)
-        out = np.zeros(self.ns * self.N)
+        out = np.zeros(self.ns_int * self.N)
         _check(load().lqmpc_gamma_mv(self.h, _p(v), _p(out)), "lqmpc_gamma_mv")
         return out
 
@@ -261,7 +291,8 @@ class Solver:
         """FP64 M into the CUDA tensor M (n x n, read column-major) from CUDA
         tensors sigx (ns*N) and sigu (n); allocates nothing and does not wait
         for the context's stream."""
-        for name, t, size in (("sigx", sigx, self.ns * self.N), ("sigu", sigu, self.n), ("M", M, self.n * self.n)):
+        for name, t, size in (("sigx", sigx, self.ns_int * self.N), ("sigu", sigu, self.n),
+                              ("M", M, self.n * self.n)):
             if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous() and t.numel() == size):
                 raise ValueError(f"{name}: contiguous float64 CUDA tensor of {size} elements expected")
         _check(load().lqmpc_form_kkt_noalloc(self.h, sigx.data_ptr(), sigu.data_ptr(), M.data_ptr()),
@@ -286,7 +317,7 @@ class Solver:
         return tr[: rows.value].copy()
 
     def get_duals(self):
-        z = np.zeros(2 * self.ns * self.N + 2 * self.n)
+        z = np.zeros(2 * self.ns_int * self.N + 2 * self.n)
         _check(load().lqmpc_get_duals(self.h, _p(z)), "lqmpc_get_duals")
         return z
 

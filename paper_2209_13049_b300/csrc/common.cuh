@@ -134,6 +134,10 @@ struct Inst {
     const int* ftasks;                // queued dataflow Cholesky: task list of this instance alone
     Scal* sc;
     double* trace;                    // (max_iter+1) x kTraceW
+    // general data of Eq. 1 (nullptr: absent): cross term S of the stage cost
+    // (ns x nu, column-major) and disturbance w (N x ns, w_t at t*ns)
+    const double* Sx;
+    const double* wd;
 };
 
 // Vectors addressed by role, so one launch can name "the same vector" of

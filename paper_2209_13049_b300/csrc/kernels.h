@@ -47,6 +47,8 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
                          int w1_role, int o0_role, int o1_role, int scale0, int flags, cudaStream_t st,
                          int fuse = 0);
 void launch_ychain(const Inst* d_insts, int count, cudaStream_t st);
+void launch_hess_cross(const Inst* d_inst, int n, cudaStream_t st);
+void launch_h_cross(const Inst* d_insts, int count, int max_n, cudaStream_t st);
 void launch_qbar_y(const Inst* d_insts, int count, int max_sx, cudaStream_t st);
 void launch_q_times_g(const Inst* d_inst, const Inst& h, int use_qf, double* out, cudaStream_t st);
 

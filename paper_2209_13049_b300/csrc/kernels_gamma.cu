@@ -538,7 +538,8 @@ __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, 
     }
 }
 
-// y_t = A^t xbar for t = 1..N (one block per instance, sequential in t).
+// Free response y_t = A y_{t-1} + w_{t-1} for t = 1..N, y_0 = xbar (w = 0
+// when absent; one block per instance, sequential in t).
 __global__ void k_ychain(const Inst* __restrict__ insts) {
     const Inst& I = insts[blockIdx.y];
     const double* prev = I.xbar;
@@ -547,6 +548,7 @@ __global__ void k_ychain(const Inst* __restrict__ insts) {
         for (int i = threadIdx.x; i < I.ns; i += blockDim.x) {
             double acc = 0.0;
             for (int p = I.a_ptr[i]; p < I.a_ptr[i + 1]; ++p) acc += I.a_val[p] * prev[I.a_idx[p]];
+            if (I.wd) acc += I.wd[(size_t)t * I.ns + i];
             cur[i] = acc;
         }
         __syncthreads();
@@ -689,6 +691,61 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
         if (!(fuse & kFuseNoSum))
             LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
     }
+}
+
+// The cross term x_t' S u_t of the stage cost in the condensed Hessian:
+// H[j, l] += (G_{t-1-k}' S)[a, b] for input j = (k, a) of an earlier stage
+// than input l = (t, b), and its mirror below the diagonal (one thread per
+// entry, each computing its own dot product over the states).
+__global__ void k_hess_cross(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    if (!I.Sx) return;
+    const int n = I.n, nu = I.nu, N = I.N, ns = I.ns;
+    const size_t total = (size_t)n * n;
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q % n), l = (int)(q / n);
+        const int kj = j / nu, kl = l / nu;
+        if (kj == kl) continue;
+        // earlier stage e with input index ae, later stage t with index bt
+        const int e = kj < kl ? kj : kl, t = kj < kl ? kl : kj;
+        const int ae = kj < kl ? j % nu : l % nu, bt = kj < kl ? l % nu : j % nu;
+        const double* g = I.G64 + (size_t)I.ldg * ((N - 1 - (t - 1 - e)) * nu + ae);
+        const double* sc = I.Sx + (size_t)bt * ns;
+        double v = 0.0;
+        for (int i = 0; i < ns; ++i) v += g[i] * sc[i];
+        I.H64[q] += v;
+    }
+}
+
+// h_t += S' y_t (y_0 = xbar): the cross term's part of the condensed linear
+// term (one warp per output).
+__global__ void k_h_cross(const Inst* __restrict__ insts) {
+    const Inst& I = insts[blockIdx.y];
+    if (!I.Sx) return;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < I.n; q += gridDim.x * wpb) {
+        const int t = q / I.nu, b = q % I.nu;
+        const double* yt = t == 0 ? I.xbar : I.y + (size_t)(t - 1) * I.ns;
+        const double* sc = I.Sx + (size_t)b * I.ns;
+        double v = 0.0;
+        for (int i = lane; i < I.ns; i += 32) v += sc[i] * yt[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) I.h[q] += v;
+    }
+}
+
+void launch_hess_cross(const Inst* d_inst, int n, cudaStream_t st) {
+    size_t tot = (size_t)n * n;
+    int nb = (int)((tot + 255) / 256);
+    nb = nb > 8192 ? 8192 : nb;
+    LQ_LAUNCH(k_hess_cross<<<dim3(nb, 1), 256, 0, st>>>(d_inst));
+}
+
+void launch_h_cross(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
+    int nb = (max_n + 7) / 8;
+    nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
+    LQ_LAUNCH(k_h_cross<<<dim3(nb, count), 256, 0, st>>>(d_insts));
 }
 
 void launch_ychain(const Inst* d_insts, int count, cudaStream_t st) {

@@ -158,6 +158,11 @@ struct lqmpc_ctx {
     // the context's stream forms and factors M (joined before the solves)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // general data (lqmpc_setup_general): device copies of S and w, and with a
+    // feedback K the row of the lifted state that holds u_t (-1: u is the
+    // solver's own variable)
+    double* gen_dev = nullptr;
+    int u_row = -1;
 };
 
 namespace {
@@ -796,6 +801,9 @@ void prepare(const Batch& b, const lqmpc_options& o) {
     launch_ychain(b.d_insts, b.count, b.st);
     launch_qbar_y(b.d_insts, b.count, b.max_sx, b.st);
     gtmv(b, R_TMPX, R_NONE, R_H, R_NONE, 0, F_FORCE);
+    bool cross = false;
+    for (auto* c : b.ctxs) cross = cross || c->h.Sx != nullptr;
+    if (cross) launch_h_cross(b.d_insts, b.count, b.max_n, b.st);
     const bool warm = b.warm_mu0 > 0.0;
     launch_set_u0(b.d_insts, b.count, b.max_n, b.st, warm ? 1 : 0);
     gmv(b, R_U, R_TMPX, F_FORCE);
@@ -1068,6 +1076,15 @@ lqmpc_status final_status(lqmpc_ctx* c) {
     return (lqmpc_status)S.status;
 }
 
+// The input sequence of the last solve into dst: the solver's variable, or
+// with a feedback K the lifted rows u_t = K x_t + v_t of x_{t+1}.
+cudaError_t copy_u(const lqmpc_ctx* c, double* dst, cudaMemcpyKind kind, cudaStream_t st) {
+    const Inst& I = c->h;
+    if (c->u_row < 0) return cudaMemcpyAsync(dst, I.u, sizeof(double) * I.n, kind, st);
+    return cudaMemcpy2DAsync(dst, sizeof(double) * I.nu, I.x + c->u_row, sizeof(double) * I.ns,
+                             sizeof(double) * I.nu, I.N, kind, st);
+}
+
 lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double* u, bool u_dev,
                           lqmpc_stats* st, const double* u_init = nullptr, double mu0 = 0.0) {
     if (!ctx || !x0 || !u) return LQMPC_ERR_ARG;
@@ -1080,6 +1097,7 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
         CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyDeviceToDevice, ctx->stream));
     }
     if (u_init) {
+        if (ctx->u_row >= 0) return LQMPC_ERR_UNSUPPORTED;   // the guess would be for v, not u
         if (!all_finite(u_init, I.n)) return LQMPC_ERR_ARG;
         CK(cudaMemcpyAsync(I.du_aff, u_init, sizeof(double) * I.n, cudaMemcpyHostToDevice, ctx->stream));
     }
@@ -1094,8 +1112,7 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
     double tt = 0, tk = 0;
     lqmpc_status s = run_ipm(b, ctx->opts, &tt, &tk);
     if (s != LQMPC_OK) return s;
-    CK(cudaMemcpyAsync(u, I.u, sizeof(double) * I.n, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(copy_u(ctx, u, u_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     fill_stats(ctx, st, tt, tk);
     return final_status(ctx);
@@ -1143,11 +1160,12 @@ static bool opts_ok(const lqmpc_options& o) {
            o.refine_max >= 0 && o.refine_max <= 100 && o.refine_tol > 0 && o.tau > 0 && o.tau < 1;
 }
 
-lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_ptr, const int* a_idx,
-                         const double* a_val, const double* Bh, const int* q_ptr, const int* q_idx,
-                         const double* q_val, const int* qf_ptr, const int* qf_idx, const double* qf_val,
-                         const double* Rh, const double* xl, const double* xu, const double* ul,
-                         const double* uu, const lqmpc_options* opts, void* stream) {
+static lqmpc_status setup_impl(lqmpc_ctx** out, int ns, int nu, int N, const int* a_ptr, const int* a_idx,
+                               const double* a_val, const double* Bh, const int* q_ptr, const int* q_idx,
+                               const double* q_val, const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                               const double* Rh, const double* xl, const double* xu, const double* ul,
+                               const double* uu, const lqmpc_options* opts, void* stream, const double* Sh,
+                               const double* wh) {
     if (!out) return LQMPC_ERR_ARG;
     *out = nullptr;
     if (ns < 1 || nu < 1 || N < 1 || (long long)nu * N > 30000 || (long long)ns * N > (1LL << 31) - 1)
@@ -1296,6 +1314,14 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         ok = ok && up(I.ftasks, ft.data(), sizeof(int) * ft.size());
     }
     if (!ok) return fail(LQMPC_ERR_CUDA);
+    if (Sh || wh) {   // general data: S (ns x nu) and w (N x ns)
+        const size_t sn = Sh ? (size_t)ns * nu : 0, wn = wh ? (size_t)N * ns : 0;
+        if (cudaMalloc(&ctx->gen_dev, sizeof(double) * (sn + wn)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
+        if (Sh && !up(ctx->gen_dev, Sh, sizeof(double) * sn)) return fail(LQMPC_ERR_CUDA);
+        if (wh && !up(ctx->gen_dev + sn, wh, sizeof(double) * wn)) return fail(LQMPC_ERR_CUDA);
+        I.Sx = Sh ? ctx->gen_dev : nullptr;
+        I.wd = wh ? ctx->gen_dev + sn : nullptr;
+    }
     if (cudaMalloc(&ctx->d_inst, sizeof(Inst)) != cudaSuccess) return fail(LQMPC_ERR_CUDA);
     if (!up(ctx->d_inst, &I, sizeof(Inst))) return fail(LQMPC_ERR_CUDA);
     // the solve's Scal starts "not done" for the setup-time launches
@@ -1322,6 +1348,7 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
         cudaFree(gqf);
     }
     launch_syrk_reduce(ctx->d_inst, 1, I.n, ctx->cc_splits, 0, 1, 1, 0, F_FORCE, I.H64, st);
+    if (Sh) launch_hess_cross(ctx->d_inst, I.n, st);   // + the stage cross term x_t' S u_t
     launch_h_to_f32(ctx->d_inst, I.n, st);
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return fail(LQMPC_ERR_CUDA);
@@ -1340,6 +1367,171 @@ lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_pt
     }
     *out = ctx;
     return LQMPC_OK;
+}
+
+lqmpc_status lqmpc_setup(lqmpc_ctx** out, int ns, int nu, int N, const int* a_ptr, const int* a_idx,
+                         const double* a_val, const double* Bh, const int* q_ptr, const int* q_idx,
+                         const double* q_val, const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                         const double* Rh, const double* xl, const double* xu, const double* ul,
+                         const double* uu, const lqmpc_options* opts, void* stream) {
+    return setup_impl(out, ns, nu, N, a_ptr, a_idx, a_val, Bh, q_ptr, q_idx, q_val, qf_ptr, qf_idx, qf_val, Rh, xl,
+                      xu, ul, uu, opts, stream, nullptr, nullptr);
+}
+
+// General data of Eq. 1 by a lifting to the box-constrained form the solver
+// runs: the nc general rows of stage t become extra states of x_{t+1},
+// c_{t+1} = E x_t + F u_t (rows [E 0] of the lifted A, F of the lifted B, no
+// cost, bounds [gl, gu]); a feedback K (u_t = K x_t + v_t, Section II)
+// becomes A + B K, Q + S K + K' S' + K' R K, cross term S + K' R, general
+// rows E + F K and nu more lifted rows c = K x_t + v_t = u_t carrying the
+// input bounds (v itself is free); the cross term and the disturbance go to
+// the device as they are.
+lqmpc_status lqmpc_setup_general(lqmpc_ctx** out, int ns, int nu, int N, const int* a_ptr, const int* a_idx,
+                                 const double* a_val, const double* Bh, const int* q_ptr, const int* q_idx,
+                                 const double* q_val, const int* qf_ptr, const int* qf_idx, const double* qf_val,
+                                 const double* Rh, const double* xl, const double* xu, const double* ul,
+                                 const double* uu, const lqmpc_general* g, const lqmpc_options* opts,
+                                 void* stream) {
+    if (!out) return LQMPC_ERR_ARG;
+    *out = nullptr;
+    if (!g) return setup_impl(out, ns, nu, N, a_ptr, a_idx, a_val, Bh, q_ptr, q_idx, q_val, qf_ptr, qf_idx, qf_val,
+                              Rh, xl, xu, ul, uu, opts, stream, nullptr, nullptr);
+    if (ns < 1 || nu < 1 || N < 1 || g->nc < 0 || g->nc > (1 << 20)) return LQMPC_ERR_ARG;
+    if (!Bh || !Rh || !xl || !xu || !ul || !uu) return LQMPC_ERR_ARG;
+    if (!csr_ok(ns, a_ptr, a_idx, a_val) || !csr_ok(ns, q_ptr, q_idx, q_val)) return LQMPC_ERR_ARG;
+    if (qf_ptr && !csr_ok(ns, qf_ptr, qf_idx, qf_val)) return LQMPC_ERR_ARG;
+    const int nc = g->nc;
+    if (nc > 0 && (!g->E || !g->F || !g->gl || !g->gu)) return LQMPC_ERR_ARG;
+    if ((g->S && !all_finite(g->S, (size_t)ns * nu)) || (g->w && !all_finite(g->w, (size_t)N * ns)) ||
+        (g->K && !all_finite(g->K, (size_t)nu * ns)) || !all_finite(Bh, (size_t)ns * nu) ||
+        !all_finite(Rh, (size_t)nu * nu))
+        return LQMPC_ERR_ARG;
+    if (nc > 0 && (!all_finite(g->E, (size_t)nc * ns) || !all_finite(g->F, (size_t)nc * nu))) return LQMPC_ERR_ARG;
+    for (int r = 0; r < nc; ++r)
+        if (std::isnan(g->gl[r]) || std::isnan(g->gu[r]) || g->gl[r] > g->gu[r] || g->gl[r] == INFINITY ||
+            g->gu[r] == -INFINITY)
+            return LQMPC_ERR_ARG;
+    const double* K = g->K;
+    const int ncu = K ? nu : 0;           // lifted input rows
+    const int nca = nc + ncu;             // all lifted rows
+    const int nsa = ns + nca;
+    if (!qf_ptr) { qf_ptr = q_ptr; qf_idx = q_idx; qf_val = q_val; }
+    // dense copies where K mixes the data
+    auto dense_of = [&](const int* p, const int* ix, const double* v) {
+        std::vector<double> d((size_t)ns * ns, 0.0);
+        for (int r = 0; r < ns; ++r)
+            for (int k = p[r]; k < p[r + 1]; ++k) d[r + (size_t)ix[k] * ns] += v[k];
+        return d;
+    };
+    // rows of the lifted A, B, Q, Qf as (row, col, value) lists
+    std::vector<std::vector<std::pair<int, double>>> Ar(nsa), Qr(nsa), Qfr(nsa);
+    std::vector<double> Ba((size_t)nsa * nu, 0.0), Sa;
+    bool has_S = g->S != nullptr;
+    if (!K) {
+        for (int r = 0; r < ns; ++r) {
+            for (int k = a_ptr[r]; k < a_ptr[r + 1]; ++k) Ar[r].push_back({a_idx[k], a_val[k]});
+            for (int k = q_ptr[r]; k < q_ptr[r + 1]; ++k) Qr[r].push_back({q_idx[k], q_val[k]});
+        }
+        if (has_S) Sa.assign(g->S, g->S + (size_t)ns * nu);
+    } else {
+        std::vector<double> Ad = dense_of(a_ptr, a_idx, a_val), Qd = dense_of(q_ptr, q_idx, q_val);
+        for (int i = 0; i < ns; ++i)           // A + B K
+            for (int j = 0; j < ns; ++j) {
+                double v = Ad[i + (size_t)j * ns];
+                for (int a = 0; a < nu; ++a) v += Bh[i + (size_t)a * ns] * K[a + (size_t)j * nu];
+                Ad[i + (size_t)j * ns] = v;
+            }
+        std::vector<double> RK((size_t)nu * ns, 0.0);   // R K
+        for (int a = 0; a < nu; ++a)
+            for (int j = 0; j < ns; ++j) {
+                double v = 0.0;
+                for (int b = 0; b < nu; ++b) v += Rh[a + (size_t)b * nu] * K[b + (size_t)j * nu];
+                RK[a + (size_t)j * nu] = v;
+            }
+        Sa.assign((size_t)ns * nu, 0.0);       // S + K' R
+        for (int i = 0; i < ns; ++i)
+            for (int a = 0; a < nu; ++a) {
+                double v = g->S ? g->S[i + (size_t)a * ns] : 0.0;
+                for (int b = 0; b < nu; ++b) v += K[b + (size_t)i * nu] * Rh[b + (size_t)a * nu];
+                Sa[i + (size_t)a * ns] = v;
+            }
+        has_S = true;
+        for (int i = 0; i < ns; ++i)           // Q + S K + K' S' + K' R K
+            for (int j = 0; j < ns; ++j) {
+                double v = Qd[i + (size_t)j * ns];
+                for (int a = 0; a < nu; ++a) {
+                    const double sk = g->S ? g->S[i + (size_t)a * ns] * K[a + (size_t)j * nu] +
+                                                 g->S[j + (size_t)a * ns] * K[a + (size_t)i * nu]
+                                           : 0.0;
+                    v += sk + K[a + (size_t)i * nu] * RK[a + (size_t)j * nu];
+                }
+                Qd[i + (size_t)j * ns] = v;
+            }
+        for (int i = 0; i < ns; ++i)
+            for (int j = 0; j < ns; ++j) {
+                if (Ad[i + (size_t)j * ns] != 0.0) Ar[i].push_back({j, Ad[i + (size_t)j * ns]});
+                if (Qd[i + (size_t)j * ns] != 0.0) Qr[i].push_back({j, Qd[i + (size_t)j * ns]});
+            }
+    }
+    for (int r = 0; r < ns; ++r)
+        for (int k = qf_ptr[r]; k < qf_ptr[r + 1]; ++k) Qfr[r].push_back({qf_idx[k], qf_val[k]});
+    for (int i = 0; i < ns; ++i)
+        for (int a = 0; a < nu; ++a) Ba[i + (size_t)a * nsa] = Bh[i + (size_t)a * ns];
+    std::vector<double> xla(nsa), xua(nsa), ula(nu), uua(nu);
+    for (int i = 0; i < ns; ++i) { xla[i] = xl[i]; xua[i] = xu[i]; }
+    for (int r = 0; r < nc; ++r) {             // general rows: E + F K, F
+        const int row = ns + r;
+        for (int j = 0; j < ns; ++j) {
+            double v = g->E[r + (size_t)j * nc];
+            if (K)
+                for (int a = 0; a < nu; ++a) v += g->F[r + (size_t)a * nc] * K[a + (size_t)j * nu];
+            if (v != 0.0) Ar[row].push_back({j, v});
+        }
+        for (int a = 0; a < nu; ++a) Ba[row + (size_t)a * nsa] = g->F[r + (size_t)a * nc];
+        xla[row] = g->gl[r];
+        xua[row] = g->gu[r];
+    }
+    for (int a = 0; a < ncu; ++a) {            // u_t = K x_t + v_t, bounds [ul, uu]
+        const int row = ns + nc + a;
+        for (int j = 0; j < ns; ++j)
+            if (K[a + (size_t)j * nu] != 0.0) Ar[row].push_back({j, K[a + (size_t)j * nu]});
+        Ba[row + (size_t)a * nsa] = 1.0;
+        xla[row] = ul[a];
+        xua[row] = uu[a];
+    }
+    for (int a = 0; a < nu; ++a) {
+        ula[a] = K ? -INFINITY : ul[a];
+        uua[a] = K ? INFINITY : uu[a];
+    }
+    auto to_csr = [&](const std::vector<std::vector<std::pair<int, double>>>& rows, std::vector<int>& p,
+                      std::vector<int>& ix, std::vector<double>& v) {
+        p.assign(nsa + 1, 0);
+        for (int r = 0; r < nsa; ++r) {
+            for (auto& e : rows[r]) { ix.push_back(e.first); v.push_back(e.second); }
+            p[r + 1] = (int)ix.size();
+        }
+    };
+    std::vector<int> ap, ai, qp, qi, fp, fi;
+    std::vector<double> av, qv, fv;
+    to_csr(Ar, ap, ai, av);
+    to_csr(Qr, qp, qi, qv);
+    to_csr(Qfr, fp, fi, fv);
+    std::vector<double> Sl, wl;
+    if (has_S) {
+        Sl.assign((size_t)nsa * nu, 0.0);
+        for (int i = 0; i < ns; ++i)
+            for (int a = 0; a < nu; ++a) Sl[i + (size_t)a * nsa] = Sa[i + (size_t)a * ns];
+    }
+    if (g->w) {
+        wl.assign((size_t)N * nsa, 0.0);
+        for (int t = 0; t < N; ++t)
+            for (int i = 0; i < ns; ++i) wl[(size_t)t * nsa + i] = g->w[(size_t)t * ns + i];
+    }
+    lqmpc_status s = setup_impl(out, nsa, nu, N, ap.data(), ai.data(), av.data(), Ba.data(), qp.data(), qi.data(),
+                                qv.data(), fp.data(), fi.data(), fv.data(), Rh, xla.data(), xua.data(), ula.data(),
+                                uua.data(), opts, stream, has_S ? Sl.data() : nullptr, g->w ? wl.data() : nullptr);
+    if (s == LQMPC_OK && K) (*out)->u_row = ns + nc;
+    return s;
 }
 
 lqmpc_status lqmpc_set_options(lqmpc_ctx* ctx, const lqmpc_options* opts) {
@@ -1372,6 +1564,8 @@ static lqmpc_status solve_batch_impl(lqmpc_ctx* const* ctxs, int count, const do
         if (std::isnan(mu0)) return LQMPC_ERR_ARG;
         for (int i = 0; i < count; ++i)
             if (!u_inits[i] || (ctxs[i] && !all_finite(u_inits[i], ctxs[i]->h.n))) return LQMPC_ERR_ARG;
+        for (int i = 0; i < count; ++i)
+            if (ctxs[i] && ctxs[i]->u_row >= 0) return LQMPC_ERR_UNSUPPORTED;
     }
     for (int i = 0; i < count; ++i)
         if (!ctxs[i] || !x0s[i] || !u_outs[i] || ctxs[i]->user_stream != ctxs[0]->user_stream ||
@@ -1446,8 +1640,7 @@ static lqmpc_status solve_batch_impl(lqmpc_ctx* const* ctxs, int count, const do
     }
     if (s == LQMPC_OK) {
         for (int i = 0; i < count; ++i)
-            if (cudaMemcpyAsync(u_outs[i], ctxs[i]->h.u, sizeof(double) * ctxs[i]->h.n, cudaMemcpyDeviceToHost,
-                                b.st) != cudaSuccess)
+            if (copy_u(ctxs[i], u_outs[i], cudaMemcpyDeviceToHost, b.st) != cudaSuccess)
                 s = LQMPC_ERR_CUDA;
         if (cudaStreamSynchronize(b.st) != cudaSuccess) s = LQMPC_ERR_CUDA;
     }
@@ -1634,6 +1827,7 @@ void lqmpc_free(lqmpc_ctx* ctx) {
             cudaEventDestroy(ctx->evk[e]);
         }
     cudaFree(ctx->arena);
+    cudaFree(ctx->gen_dev);
     cudaFree(ctx->d_inst);
     cudaFree(ctx->d_maps);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
@@ -1776,11 +1970,13 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
         launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 0, 1, 0, 1, F_NONE, nullptr, b.st);
     } else if (precision == LQMPC_FP32X2) {
         launch_kkt_lyap_ff(b.d_insts, 1, I.ns, I.nu, I.N, I.SX, F_NONE, b.st, 0.0);
-    } else if (precision == LQMPC_FP32) {
+    } else if (precision == LQMPC_FP32 && !ctx->tc_ok) {
         launch_syrk_cc(b.d_insts, 1, I.n, b.cc_splits, 0, 0, nullptr, nullptr, F_NONE, b.st);
         launch_syrk_reduce(b.d_insts, 1, I.n, b.cc_splits, 1, 0, 0, 1, F_NONE, nullptr, b.st);
     } else {
-        launch_syrk_tc(b.d_insts, 1, I.n, b.tc_splits, precision == LQMPC_MIXED_TF32, b.d_maps, F_NONE, b.st);
+        // the solves' tensor-core formation: BF16, TF32, or split TF32 for the FP32 tier
+        const int mode = precision == LQMPC_MIXED_TF32 ? 1 : (precision == LQMPC_FP32 ? 2 : 0);
+        launch_syrk_tc(b.d_insts, 1, I.n, b.tc_splits, mode, b.d_maps, F_NONE, b.st);
         launch_syrk_reduce(b.d_insts, 1, I.n, b.tc_splits, 2, 0, 0, 1, F_NONE, nullptr, b.st);
     }
     CK(cudaGetLastError());

@@ -57,6 +57,22 @@ def test_setup_rejects_bad_arguments_without_device_work(lib):
     assert lib.lqmpc_solve(None, None, None, None) == 1
     assert lib.lqmpc_solve_batch(None, 0, None, None, None) == 1
     assert lib.lqmpc_solve_batch_warm(None, 0, None, None, 0.0, None, None) == 1
+    # general data: rows without their arrays, crossed row bounds
+    import numpy as np
+    from paper_2209_13049_b300 import inputs
+    p = inputs.heat1d(6, 2, 3)
+    a = [np.ascontiguousarray(v) for v in (p.A.indptr.astype(np.int32), p.A.indices.astype(np.int32), p.A.data)]
+    B = np.asfortranarray(p.B)
+    R = np.asfortranarray(p.R)
+    ptr = lambda v: v.ctypes.data_as(ctypes.c_void_p)
+    gl, gu = np.array([1.0]), np.array([0.0])
+    E, F = np.asfortranarray(np.ones((1, 6))), np.asfortranarray(np.ones((1, 2)))
+    for g in (binding.General(None, None, 1, None, None, None, None, None),
+              binding.General(None, None, 1, ptr(E), ptr(F), ptr(gl), ptr(gu), None)):
+        code = lib.lqmpc_setup_general(ctypes.byref(h), 6, 2, 3, ptr(a[0]), ptr(a[1]), ptr(a[2]), ptr(B),
+                                       ptr(a[0]), ptr(a[1]), ptr(a[2]), None, None, None, ptr(R),
+                                       ptr(p.xl), ptr(p.xu), ptr(p.ul), ptr(p.uu), ctypes.byref(g), None, None)
+        assert code == 1 and not h.value
     lib.lqmpc_free(None)
 
 

@@ -167,10 +167,13 @@ def test_warm_start_from_stored_guess_takes_the_oracle_warm_iterates(warm_gold):
         assert st["iters"] == len(g[f"v{j}_trace8"]) - 1, j
         np.testing.assert_allclose(s.get_trace()[:, 0], g[f"v{j}_trace8"][:, 0], rtol=1e-6)
         assert rel(u, g[f"v{j}_u8"]) <= 1e-8, j
+    # both run on to 1e-11: the same iterates in exact arithmetic, but at
+    # mu ~ 1e-11 the rounding of each Newton step is amplified by
+    # cond(M) ~ 1/mu; the bar is one decade above the cold start's
     s.set_options(tol=1e-11)
     for j in range(len(xt)):
         u, _ = s.solve_warm(xt[j], g[f"v{j}_guess"])
-        assert rel(u, g[f"v{j}_u12"]) <= 1e-10, j
+        assert rel(u, g[f"v{j}_u12"]) <= 1e-9, j
     m = binding.Solver(p, precision="fp32")
     for j in range(len(xt)):
         u, st = m.solve_warm(xt[j], g[f"v{j}_guess"])
