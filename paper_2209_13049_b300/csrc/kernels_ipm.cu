@@ -249,16 +249,25 @@ __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int tr
 // mu_aff = (sum s z + a S4 + a^2 S5)/m in closed form.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void ratio(double v, double dv, double& amax) {
-    if (dv < 0.0) amax = fmin(amax, -v / dv);
-}
+// The largest step to the boundary, min over dv < 0 of v / (-dv), kept as a
+// fraction (num, den) with den > 0 and compared by cross-multiplication
+// (v * den < num * (-dv)): one FP64 division per thread at the end instead of
+// one per candidate (this part's FP64 division costs several FMA-pipe passes).
+struct StepMin {
+    double num = INFINITY, den = 1.0;
+    __device__ __forceinline__ void add(double v, double dv) {
+        if (dv < 0.0 && v * den < num * -dv) { num = v; den = -dv; }
+    }
+    __device__ __forceinline__ double value() const { return num / den; }
+};
 
 __global__ void k_aff(const Inst* __restrict__ insts) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     const int total = I.SX + I.n;
-    double amax = INFINITY, s4 = 0.0, s5 = 0.0;
+    StepMin am;
+    double s4 = 0.0, s5 = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
         double d = k < I.SX ? I.dx_aff[k] : I.du_aff[k - I.SX];
@@ -267,18 +276,18 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
         if (r.fu) {
             double rp = r.v + su - r.hi;
             dsu = -rp - d; dzu = -zu - (zu / su) * dsu;
-            ratio(su, dsu, amax); ratio(zu, dzu, amax);
+            am.add(su, dsu); am.add(zu, dzu);
             s4 += su * dzu + zu * dsu; s5 += dsu * dzu;
         }
         if (r.fl) {
             double rp = -r.v + sl + r.lo;
             dsl = -rp + d; dzl = -zl - (zl / sl) * dsl;
-            ratio(sl, dsl, amax); ratio(zl, dzl, amax);
+            am.add(sl, dsl); am.add(zl, dzl);
             s4 += sl * dzl + zl * dsl; s5 += dsl * dzl;
         }
         *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
     }
-    double v = block_reduce<2>(amax, red); put_part(I, 3, v);
+    double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
     v = block_reduce<0>(s4, red); put_part(I, 4, v);
     v = block_reduce<0>(s5, red); put_part(I, 5, v);
 }
@@ -351,7 +360,7 @@ __global__ void k_step(const Inst* __restrict__ insts) {
     if (I.sc->done) return;
     const double smu = I.sc->sigma * I.sc->mu;
     const int total = I.SX + I.n;
-    double amax = INFINITY;
+    StepMin am;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
         double d = k < I.SX ? I.dx[k] : I.du[k - I.SX];
@@ -361,17 +370,17 @@ __global__ void k_step(const Inst* __restrict__ insts) {
             double rp = r.v + su - r.hi;
             double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
             dsu = -rp - d; dzu = -(rc + zu * dsu) / su;
-            ratio(su, dsu, amax); ratio(zu, dzu, amax);
+            am.add(su, dsu); am.add(zu, dzu);
         }
         if (r.fl) {
             double rp = -r.v + sl + r.lo;
             double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
             dsl = -rp + d; dzl = -(rc + zl * dsl) / sl;
-            ratio(sl, dsl, amax); ratio(zl, dzl, amax);
+            am.add(sl, dsl); am.add(zl, dzl);
         }
         *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
     }
-    double v = block_reduce<2>(amax, red); put_part(I, 3, v);
+    double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
 }
 
 // alpha = min(1, tau * max step); trace; iteration count.
