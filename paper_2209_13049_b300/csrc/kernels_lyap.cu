@@ -195,6 +195,18 @@ __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max
     }
 }
 
+// Threads per chain CTA: the two z buffers take 16 ns bytes of shared memory,
+// so a large ns leaves room for only one or two CTAs per SM; those get more
+// threads (each thread owns fewer rows of z), so the SM keeps about 32 warps
+// in flight to hide the latency of the sparse A' gathers and the FMA chains.
+// The rows a thread owns change, not the arithmetic of any row: the result
+// is the same bit for bit.
+static int chain_threads(size_t smem) {
+    const size_t per_sm = 227 * 1024;
+    const size_t ctas = per_sm / (smem + 1024);
+    return ctas >= 4 ? 256 : (ctas >= 2 ? 512 : 1024);
+}
+
 void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
                         cudaStream_t st, double shift) {
     LQ_LAUNCH(k_sig_split<<<dim3(per_instance_blocks(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), count), 256,
@@ -202,14 +214,16 @@ void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, 
     const size_t smem = 2 * sizeof(float2) * (size_t)max_ns;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ly_chain_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LQ_LAUNCH(k_ly_chain_ff<<<dim3(max_N * max_nu, count), 256, smem, st>>>(d_insts, flags, max_nu, shift));
+    LQ_LAUNCH(k_ly_chain_ff<<<dim3(max_N * max_nu, count), chain_threads(smem), smem, st>>>(d_insts, flags, max_nu,
+                                                                                           shift));
 }
 
 void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int flags,
                      cudaStream_t st, double shift) {
     const size_t smem = 2 * sizeof(double) * (size_t)max_ns;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ly_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LQ_LAUNCH(k_ly_chain<<<dim3(max_N * max_nu, count), 256, smem, st>>>(d_insts, flags, max_nu, shift));
+    LQ_LAUNCH(k_ly_chain<<<dim3(max_N * max_nu, count), chain_threads(smem), smem, st>>>(d_insts, flags, max_nu,
+                                                                                        shift));
 }
 
 // Multiply-add counts of the two ways to form Gamma' Sigma Gamma (the SYRK
