@@ -12,10 +12,10 @@
 // one side gives Gamma' D Gamma), done in shared memory by four transform
 // warps between the TMA arrival and the MMA issue.
 //
-// Warp roles (192 threads): warp 0 TMA producer, warp 1 TMEM allocator and
-// single-thread MMA issuer, warps 2-5 scale transform and epilogue
-// (tcgen05.ld of the 128 x 128 FP32 accumulator, coalesced column-major store
-// of the partial tile).  Every mbarrier wait is bounded; a wait that gives up
+// Warp roles (64 + 32 kScaleWarps threads): warp 0 TMA producer, warp 1 TMEM
+// allocator and single-thread MMA issuer, warps 2 .. the scale transform,
+// warps 2-5 also the epilogue (tcgen05.ld of the 128 x 128 FP32 accumulator,
+// coalesced column-major store of the partial tile).  Every mbarrier wait is bounded; a wait that gives up
 // marks the CTA aborted, drains its own TMA copies (bounded), frees TMEM and
 // reports Scal::err.
 #include <cuda.h>
@@ -37,6 +37,11 @@ template <int MODE> struct TcCfg {
     static constexpr int kStages = MODE == 2 ? 3 : 6;
 };
 constexpr int kStagesMax = 6;
+// scale-transform warps (warps 2 .. 2 + kScaleWarps - 1; the first four also
+// run the epilogue): each of the B tile's 128 rows is scaled by
+// kScaleWarps / 4 threads
+constexpr int kScaleWarps = 8;
+constexpr int kTcThreads = 64 + 32 * kScaleWarps;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -149,7 +154,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ insts, const CUtensorMap* maps,
+__global__ void __launch_bounds__(kTcThreads, 1) k_syrk_tc(const Inst* __restrict__ insts, const CUtensorMap* maps,
                                                      int splits, int flags) {
     constexpr bool TF32 = MODE != 0;
     constexpr int kStages = TcCfg<MODE>::kStages;
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&bar_full[s]), 1);
-            mbar_init(smem_u32(&bar_scaled[s]), 128);
+            mbar_init(smem_u32(&bar_scaled[s]), 32 * kScaleWarps);
             mbar_init(smem_u32(&bar_empty[s]), 1);
         }
         mbar_init(smem_u32(&bar_acc), 1);
@@ -277,7 +282,9 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
         }
     } else {
         // ---------------- scale transform: B tile row t *= D_r[i0 + K]
-        const int t = threadIdx.x - 64;   // 0..127, one B-tile row each
+        constexpr int kParts = kScaleWarps / 4, kChunks = 8 / kParts;   // 16-byte chunks per thread
+        const int t = (threadIdx.x - 64) & 127;   // B-tile row
+        const int lc0 = ((threadIdx.x - 64) >> 7) * kChunks;
         for (int q = 0; q < nq; ++q) {
             const int s = q % kStages, round = q / kStages;
             if (!mbar_wait(smem_u32(&bar_full[s]), round & 1, abort_flag)) break;
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 // B = D (B_hi + B_lo), re-split into TF32 hi + FP32 lo
                 unsigned char* rowl = rowp + kTileBytes;
 #pragma unroll
-                for (int lc = 0; lc < 8; ++lc) {
+                for (int lc = lc0; lc < lc0 + kChunks; ++lc) {
                     const int p = lc ^ (t & 7);
                     float4* ch = reinterpret_cast<float4*>(rowp + p * 16);
                     float4* cl = reinterpret_cast<float4*>(rowl + p * 16);
@@ -308,7 +315,7 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
                 }
             } else {
 #pragma unroll
-            for (int lc = 0; lc < 8; ++lc) {
+            for (int lc = lc0; lc < lc0 + kChunks; ++lc) {
                 const int p = lc ^ (t & 7);
                 uint4* cp = reinterpret_cast<uint4*>(rowp + p * 16);
                 uint4 v = *cp;
@@ -332,7 +339,9 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(smem_u32(&bar_scaled[s]));
         }
-        // ---------------- epilogue: TMEM -> partial tile (column-major)
+        // ---------------- epilogue: TMEM -> partial tile (column-major), warps 2-5
+        if (warp >= 6) goto done;
+        {
         float* ws = (float*)I.syrk_ws + (size_t)blockIdx.x * kTcTile * kTcTile;
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
@@ -350,8 +359,9 @@ __global__ void __launch_bounds__(192, 1) k_syrk_tc(const Inst* __restrict__ ins
 #pragma unroll
             for (int j = 0; j < 32; ++j) ws[(size_t)(cb + j) * kTcTile + row] = v[j];
         }
+        }
     }
-
+done:
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (abort_sh) {
@@ -469,15 +479,15 @@ void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int m
     if (mode == 1) {
         const size_t smem = (size_t)TcCfg<1>::kStages * TcCfg<1>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<1><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(k_syrk_tc<1><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
     } else if (mode == 2) {
         const size_t smem = (size_t)TcCfg<2>::kStages * TcCfg<2>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<2><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(k_syrk_tc<2><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
     } else {
         const size_t smem = (size_t)TcCfg<0>::kStages * TcCfg<0>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<0><<<grid, 192, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(k_syrk_tc<0><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
     }
 }
 
