@@ -96,6 +96,7 @@ struct Inst {
     double *s1, *z1, *s2, *z2;        // SX: upper / lower state bound slacks and duals
     double *s3, *z3, *s4, *z4;        // n:  upper / lower input bound slacks and duals
     double *sigx, *sigu;              // SX, n
+    double *sgu, *sgl;                // SX + n: z/s of each row's upper and lower family (rows as row_view)
     float* sigx32;                    // N x ldg: FP32 Sigma_x, row r at r*ldg, zero padding
     double *wz, *wx;                  // SX: vectors for Gamma' products
     double *wzu, *wxu;                // n

@@ -167,6 +167,7 @@ __global__ void k_resid(const Inst* __restrict__ insts) {
         double rpu = r.fu ? r.v + su - r.hi : 0.0;
         double rpl = r.fl ? -r.v + sl + r.lo : 0.0;
         double sgu = zu / su, sgl = zl / sl;
+        I.sgu[k] = sgu; I.sgl[k] = sgl;   // for the affine step (no second division)
         rpmax = fmax(rpmax, fmax(fabs(rpu), fabs(rpl)));
         if (r.fu) sz += su * zu;
         if (r.fl) sz += sl * zl;
@@ -275,13 +276,13 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
         double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
         if (r.fu) {
             double rp = r.v + su - r.hi;
-            dsu = -rp - d; dzu = -zu - (zu / su) * dsu;
+            dsu = -rp - d; dzu = -zu - I.sgu[k] * dsu;
             am.add(su, dsu); am.add(zu, dzu);
             s4 += su * dzu + zu * dsu; s5 += dsu * dzu;
         }
         if (r.fl) {
             double rp = -r.v + sl + r.lo;
-            dsl = -rp + d; dzl = -zl - (zl / sl) * dsl;
+            dsl = -rp + d; dzl = -zl - I.sgl[k] * dsl;
             am.add(sl, dsl); am.add(zl, dzl);
             s4 += sl * dzl + zl * dsl; s5 += dsl * dzl;
         }

@@ -248,6 +248,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto s3 = c.take<double>(n); auto z3 = c.take<double>(n);
     auto s4 = c.take<double>(n); auto z4 = c.take<double>(n);
     auto sigx = c.take<double>(SX); auto sigu = c.take<double>(n);
+    auto sgu = c.take<double>((size_t)SX + n); auto sgl = c.take<double>((size_t)SX + n);
     auto sigx32 = c.take<float>((size_t)I.N * I.ldg);
     auto wz = c.take<double>(SX); auto wx = c.take<double>(SX);
     auto wzu = c.take<double>(n); auto wxu = c.take<double>(n);
@@ -290,7 +291,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.G64 = G64; I.G32 = G32; I.G32lo = G32lo; I.G16 = G16; I.Gt = Gt; I.Gtlo = Gtlo; I.H64 = H64; I.H32 = H32;
         I.xbar = xbar; I.y = y; I.h = h; I.u = u; I.x = x;
         I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
-        I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32;
+        I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32; I.sgu = sgu; I.sgl = sgl;
         I.wz = wz; I.wx = wx; I.wzu = wzu; I.wxu = wxu; I.gz = gz; I.gw = gw;
         I.rd = rd; I.b = b; I.du = du; I.dx = dx; I.du_aff = du_aff; I.dx_aff = dx_aff;
         I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;

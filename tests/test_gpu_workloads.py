@@ -77,7 +77,23 @@ def test_c3_mixed_matches_oracle(c3, precision):
     s.set_options(tol=1e-11)
     u12, st12 = s.solve(x0)
     assert st12["status"] == 0
-    assert rel(u12, g["heat2d_100_s0_u12"]) <= 1e-6
+    if precision == "fp32":
+        # follows the oracle's iterates to the same stop
+        assert rel(u12, g["heat2d_100_s0_u12"]) <= 1e-6
+    else:
+        # The BF16 tier's inexact Newton steps leave the dual residual a
+        # little above the oracle's near the end, so it stops two iterations
+        # later at a smaller mu.  This optimum is degenerate (state bounds
+        # active with vanishing multipliers): u converges like sqrt(mu), and
+        # the oracle's own 1e-11 stop lies ~2.4e-6 from its 1e-12 stop.  Two
+        # valid stops at tol 1e-11 are compared within sqrt(tol), and the
+        # result must satisfy the optimality conditions on its own.
+        assert rel(u12, g["heat2d_100_s0_u12"]) <= np.sqrt(1e-11)
+        k = oracle.kkt_check(p, x0, u12, s.get_duals())
+        assert k["primal_violation"] <= 1e-9
+        assert k["dual_min"] >= 0.0
+        assert k["stationarity"] <= 1e-8
+        assert k["complementarity"] <= 1e-8
 
 
 def test_c3_kkt_conditions_with_the_oracle_checker(c3):
