@@ -484,6 +484,7 @@ __device__ void store_tile(T* Mat, int n, int tr, int tc, const T acc[4], T scal
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ insts, int count, int max_nt,
                                                     int flags, int want_inv) {
+    pdl_wait();
     __shared__ T S1[kNb][kNb + 1];
     __shared__ T S2[kNb][kNb + 1];
     __shared__ T S3[kNb][kNb + 1];
@@ -625,6 +626,7 @@ __device__ __forceinline__ void ffp_warp_sum(float& sh, float& sl) {
 }
 
 __global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     const double* r = role_ptr(I, in_role);
@@ -670,6 +672,7 @@ __global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int fl
 // tail (conjugate-gradient direction from z, run by the instance's last CTA):
 // 1 p = z and r'z; 2 beta = r'z_new / r'z_old, p = z + beta p.
 __global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags, int tail) {
+    pdl_wait();
     __shared__ double red[32];
     __shared__ double beta_sh;
     const Inst& I = insts[blockIdx.y];
@@ -735,6 +738,7 @@ constexpr int solve_threads() { return sizeof(T) == 8 ? 256 : 512; }
 template <typename T>
 __global__ void __launch_bounds__(solve_threads<T>()) k_chol_solve(const Inst* __restrict__ insts, int in_role,
                                                                int out_role, int flags) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* y = (T*)smem_raw;
     __shared__ double red[32];
@@ -928,8 +932,8 @@ void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, i
     // one warp per row (column), two warps per CTA: every SM takes part
     int nb = (max_n + 1) / 2;
     nb = per_instance_blocks(nb > 8192 ? 8192 : nb, count);
-    LQ_LAUNCH(k_prec_lower<<<dim3(nb, count), 64, 0, st>>>(d_insts, in_role, flags));
-    LQ_LAUNCH(k_prec_upper<<<dim3(nb, count), 64, 0, st>>>(d_insts, out_role, flags, tail));
+    LQ_LAUNCH(lq_pdl(k_prec_lower, dim3(nb, count), 64, 0, st, d_insts, in_role, flags));
+    LQ_LAUNCH(lq_pdl(k_prec_upper, dim3(nb, count), 64, 0, st, d_insts, out_role, flags, tail));
 }
 
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,
@@ -938,11 +942,11 @@ void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int 
     if (fp64) {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_chol_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_chol_solve<double><<<dim3(1, count), solve_threads<double>(), smem, st>>>(d_insts, in_role, out_role, flags));
+        LQ_LAUNCH(lq_pdl(k_chol_solve<double>, dim3(1, count), solve_threads<double>(), smem, st, d_insts, in_role, out_role, flags));
     } else {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(k_chol_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_chol_solve<float><<<dim3(1, count), solve_threads<float>(), smem, st>>>(d_insts, in_role, out_role, flags));
+        LQ_LAUNCH(lq_pdl(k_chol_solve<float>, dim3(1, count), solve_threads<float>(), smem, st, d_insts, in_role, out_role, flags));
     }
 }
 

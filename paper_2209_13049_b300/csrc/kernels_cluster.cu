@@ -111,6 +111,7 @@ __device__ __forceinline__ void tile_copy2(T* d0, const T* s0, T* d1, const T* s
 template <typename T, bool INV>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(256, 1)
     k_potrf_cluster(const Inst* __restrict__ insts, int flags) {
+    pdl_wait();
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const Inst& I = insts[blockIdx.x / kCl];

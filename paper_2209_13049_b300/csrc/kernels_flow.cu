@@ -279,6 +279,7 @@ __device__ __noinline__ int factor_diag_block(const float* T, float* D, float* D
 }  // namespace
 
 __global__ void __launch_bounds__(256, 1) k_potrf_flow(const Inst* __restrict__ insts, int flags) {
+    pdl_wait();
     const Inst& I = insts[0];
     if (skip_instance(I, flags)) return;           // the same decision in every CTA
     extern __shared__ __align__(16) float fsm[];
@@ -736,6 +737,7 @@ __device__ __forceinline__ void flowq_inverse(const Inst& I, int j, int ep, cons
 // 32 x 32 and the partial sums.
 __global__ void __launch_bounds__(256, 1) k_potrf_flowq(const Inst* __restrict__ insts, const int* __restrict__ tasks,
                                                         int ntasks, int max_nt, int C, int flags) {
+    pdl_wait();
     extern __shared__ __align__(16) float fsm[];
     __shared__ float T[kFb][kFb + 1], D[kFb][kFb + 1], Dv[kFb][kFb + 1];
     __shared__ int task_sh, ep_sh;

@@ -18,6 +18,7 @@ namespace lqmpc {
 
 // G_0 = B into its column block (N-1)*nu.
 __global__ void k_gstack_init(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const int total = I.ns * I.nu;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
@@ -28,6 +29,7 @@ __global__ void k_gstack_init(const Inst* __restrict__ insts) {
 
 // G_k = A G_{k-1} (CSR A).  One thread per (row i, input c).
 __global__ void k_gstack_step(const Inst* __restrict__ insts, int k) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (k >= I.N) return;
     const int total = I.ns * I.nu;
@@ -44,6 +46,7 @@ __global__ void k_gstack_step(const Inst* __restrict__ insts, int k) {
 
 // Working copies of the G-stack in FP32 and BF16 (padding rows stay zero).
 __global__ void k_gstack_cast(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const size_t total = (size_t)I.ldg * I.n;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -74,6 +77,7 @@ __global__ void k_gstack_cast(const Inst* __restrict__ insts) {
 template <int RB, int KS>
 __global__ void __launch_bounds__(32 * KS) k_gamma_mv(const Inst* __restrict__ insts, int in_role, int out_role,
                                                       int flags) {
+    pdl_wait();
     __shared__ double red[KS][RB][32];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
@@ -133,6 +137,7 @@ __host__ __device__ inline int tmv_groups(int N) { return (N + kTmvRg - 1) / kTm
 template <int NV>
 __global__ void __launch_bounds__(kTmvChunk) k_gamma_tmv_part(const Inst* __restrict__ insts, int w0_role,
                                                               int w1_role, int scale0, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(kTmvChunk) k_gamma_tmv_part(const Inst* __rest
 
 template <int NV>
 __global__ void k_gamma_tmv_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int nchunks = (I.ns + kTmvChunk - 1) / kTmvChunk;
@@ -285,6 +291,7 @@ __host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kb
 // input comes split into float-float by k_ff_prep_v.
 __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
                                                             int out_role, int flags, int splits) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
@@ -375,6 +382,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
 // of Sigma_x out (the operand of a following Gamma' (Sigma_x .)), with
 // kFuseOutDxs also a copy into dxs.
 __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, int flags, int splits, int fuse) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     double* out = role_ptr(I, out_role);
@@ -399,6 +407,7 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
 
 // Float-float split of the Gamma operand, once per product.
 __global__ void k_ff_prep_v(const Inst* __restrict__ insts, int in_role, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const double* v = role_ptr(I, in_role);
@@ -409,6 +418,7 @@ __global__ void k_ff_prep_v(const Inst* __restrict__ insts, int in_role, int fla
 // Float-float split of the Gamma' operands (w0 scaled by Sigma_x when
 // scale0), once per product instead of once per tile that reads them.
 __global__ void k_ff_prep_w(const Inst* __restrict__ insts, int w0_role, int w1_role, int scale0, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const double* w0 = role_ptr(I, w0_role);
@@ -434,6 +444,7 @@ __global__ void k_ff_prep_w(const Inst* __restrict__ insts, int w0_role, int w1_
 template <int NV>
 __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restrict__ insts, int w0_role,
                                                              int w1_role, int scale0, int flags, int splits) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
@@ -528,6 +539,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
 template <int NV>
 __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags,
                                    int splits) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -541,6 +553,7 @@ __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, 
 // Free response y_t = A y_{t-1} + w_{t-1} for t = 1..N, y_0 = xbar (w = 0
 // when absent; one block per instance, sequential in t).
 __global__ void k_ychain(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const double* prev = I.xbar;
     for (int t = 0; t < I.N; ++t) {
@@ -558,6 +571,7 @@ __global__ void k_ychain(const Inst* __restrict__ insts) {
 
 // w = Qbar y (Q on blocks 0..N-2, Qf on block N-1), CSR, into tmpx.
 __global__ void k_qbar_y(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < I.SX; k += gridDim.x * blockDim.x) {
         int r = k / I.ns, i = k % I.ns;
@@ -574,6 +588,7 @@ __global__ void k_qbar_y(const Inst* __restrict__ insts) {
 
 // Dense-Q operand for H: GQ = Q * G (columns of the G-stack), or Qf * G.
 __global__ void k_q_times_g(const Inst* __restrict__ insts, int use_qf, double* out) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const int* ptr = use_qf ? I.qf_ptr : I.q_ptr;
     const int* idx = use_qf ? I.qf_idx : I.q_idx;
@@ -598,19 +613,19 @@ void launch_gstack(const Inst* d_inst, const Inst& h, cudaStream_t st) {
     int tot = h.ns * h.nu;
     int nb = (tot + 255) / 256;
     nb = nb > 4096 ? 4096 : nb;
-    LQ_LAUNCH(k_gstack_init<<<dim3(nb, 1), 256, 0, st>>>(d_inst));
-    LQ_LAUNCH(for (int k = 1; k < h.N; ++k) k_gstack_step<<<dim3(nb, 1), 256, 0, st>>>(d_inst, k));
+    LQ_LAUNCH(lq_pdl(k_gstack_init, dim3(nb, 1), 256, 0, st, d_inst));
+    LQ_LAUNCH(for (int k = 1; k < h.N; ++k) lq_pdl(k_gstack_step, dim3(nb, 1), 256, 0, st, d_inst, k));
     size_t tot2 = (size_t)h.ldg * h.n;
     int nb2 = (int)((tot2 + 255) / 256);
     nb2 = nb2 > 8192 ? 8192 : nb2;
-    LQ_LAUNCH(k_gstack_cast<<<dim3(nb2, 1), 256, 0, st>>>(d_inst));
+    LQ_LAUNCH(lq_pdl(k_gstack_cast, dim3(nb2, 1), 256, 0, st, d_inst));
 }
 
 void launch_gamma_mv(const Inst* d_insts, int count, int max_ns, int max_N, int in_role,
                      int out_role, int flags, cudaStream_t st) {
     constexpr int RB = 4, KS = 8;
     dim3 grid((max_ns + 31) / 32, count, (max_N + RB - 1) / RB);
-    LQ_LAUNCH(k_gamma_mv<RB, KS><<<grid, 32 * KS, 0, st>>>(d_insts, in_role, out_role, flags));
+    LQ_LAUNCH(lq_pdl(k_gamma_mv<RB, KS>, grid, 32 * KS, 0, st, d_insts, in_role, out_role, flags));
 }
 
 size_t gamma_tmv_part_doubles(int ns, int n, int N) {
@@ -627,11 +642,11 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
     dim3 grid(max_N * tmv_groups(max_N), count, nchunks);
     int nbs = (max_n + 255) / 256;
     if (w1_role != R_NONE) {
-        LQ_LAUNCH(k_gamma_tmv_part<2><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
-        LQ_LAUNCH(k_gamma_tmv_sum<2><<<dim3(nbs, count), 256, 0, st>>>(d_insts, o0_role, o1_role, flags));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_part<2>, grid, kTmvChunk, 0, st, d_insts, w0_role, w1_role, scale0, flags));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_sum<2>, dim3(nbs, count), 256, 0, st, d_insts, o0_role, o1_role, flags));
     } else {
-        LQ_LAUNCH(k_gamma_tmv_part<1><<<grid, kTmvChunk, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags));
-        LQ_LAUNCH(k_gamma_tmv_sum<1><<<dim3(nbs, count), 256, 0, st>>>(d_insts, o0_role, R_NONE, flags));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_part<1>, grid, kTmvChunk, 0, st, d_insts, w0_role, R_NONE, scale0, flags));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_sum<1>, dim3(nbs, count), 256, 0, st, d_insts, o0_role, R_NONE, flags));
     }
 }
 
@@ -660,11 +675,11 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
     }
     const int splits = 0;
     if (!(fuse & kFuseInSplit))
-        LQ_LAUNCH(k_ff_prep_v<<<dim3((max_n + 255) / 256, count), 256, 0, st>>>(d_insts, in_role, flags));
-    LQ_LAUNCH(k_gamma_mv_ff<<<dim3(ctas, count), kFfThreads, 0, st>>>(d_insts, in_role, out_role, flags, splits));
+        LQ_LAUNCH(lq_pdl(k_ff_prep_v, dim3((max_n + 255) / 256, count), 256, 0, st, d_insts, in_role, flags));
+    LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags, splits));
     int nb = (max_ns * max_N + 255) / 256;
     nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
-    LQ_LAUNCH(k_gamma_mv_ff_sum<<<dim3(nb, count), 256, 0, st>>>(d_insts, out_role, flags, splits, fuse));
+    LQ_LAUNCH(lq_pdl(k_gamma_mv_ff_sum, dim3(nb, count), 256, 0, st, d_insts, out_role, flags, splits, fuse));
 }
 
 int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV) {
@@ -682,14 +697,14 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
     int npre = (max_ns * max_N + 255) / 256;
     npre = npre > 4096 ? 4096 : npre;
     if (!(fuse & kFuseInSplit))
-        LQ_LAUNCH(k_ff_prep_w<<<dim3(npre, count), 256, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags));
+        LQ_LAUNCH(lq_pdl(k_ff_prep_w, dim3(npre, count), 256, 0, st, d_insts, w0_role, w1_role, scale0, flags));
     if (NV == 2) {
-        LQ_LAUNCH(k_gamma_tmv_ff<2><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, w1_role, scale0, flags, splits));
-        LQ_LAUNCH(k_gamma_tmv_ff_sum<2><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, o1_role, flags, splits));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff<2>, dim3(tiles * splits, count), kFfThreads, 0, st, d_insts, w0_role, w1_role, scale0, flags, splits));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<2>, dim3(nb, count), 64, 0, st, d_insts, o0_role, o1_role, flags, splits));
     } else {
-        LQ_LAUNCH(k_gamma_tmv_ff<1><<<dim3(tiles * splits, count), kFfThreads, 0, st>>>(d_insts, w0_role, R_NONE, scale0, flags, splits));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff<1>, dim3(tiles * splits, count), kFfThreads, 0, st, d_insts, w0_role, R_NONE, scale0, flags, splits));
         if (!(fuse & kFuseNoSum))
-            LQ_LAUNCH(k_gamma_tmv_ff_sum<1><<<dim3(nb, count), 64, 0, st>>>(d_insts, o0_role, R_NONE, flags, splits));
+            LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<1>, dim3(nb, count), 64, 0, st, d_insts, o0_role, R_NONE, flags, splits));
     }
 }
 
@@ -698,6 +713,7 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
 // than input l = (t, b), and its mirror below the diagonal (one thread per
 // entry, each computing its own dot product over the states).
 __global__ void k_hess_cross(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (!I.Sx) return;
     const int n = I.n, nu = I.nu, N = I.N, ns = I.ns;
@@ -720,6 +736,7 @@ __global__ void k_hess_cross(const Inst* __restrict__ insts) {
 // h_t += S' y_t (y_0 = xbar): the cross term's part of the condensed linear
 // term (one warp per output).
 __global__ void k_h_cross(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (!I.Sx) return;
     const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -739,30 +756,30 @@ void launch_hess_cross(const Inst* d_inst, int n, cudaStream_t st) {
     size_t tot = (size_t)n * n;
     int nb = (int)((tot + 255) / 256);
     nb = nb > 8192 ? 8192 : nb;
-    LQ_LAUNCH(k_hess_cross<<<dim3(nb, 1), 256, 0, st>>>(d_inst));
+    LQ_LAUNCH(lq_pdl(k_hess_cross, dim3(nb, 1), 256, 0, st, d_inst));
 }
 
 void launch_h_cross(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
     int nb = (max_n + 7) / 8;
     nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
-    LQ_LAUNCH(k_h_cross<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_h_cross, dim3(nb, count), 256, 0, st, d_insts));
 }
 
 void launch_ychain(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_ychain<<<dim3(1, count), 1024, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_ychain, dim3(1, count), 1024, 0, st, d_insts));
 }
 
 void launch_qbar_y(const Inst* d_insts, int count, int max_sx, cudaStream_t st) {
     int nb = (max_sx + 255) / 256;
     nb = nb > 4096 ? 4096 : nb;
-    LQ_LAUNCH(k_qbar_y<<<dim3(nb, count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_qbar_y, dim3(nb, count), 256, 0, st, d_insts));
 }
 
 void launch_q_times_g(const Inst* d_inst, const Inst& h, int use_qf, double* out, cudaStream_t st) {
     size_t tot = (size_t)h.ns * h.n;
     int nb = (int)((tot + 255) / 256);
     nb = nb > 8192 ? 8192 : nb;
-    LQ_LAUNCH(k_q_times_g<<<dim3(nb, 1), 256, 0, st>>>(d_inst, use_qf, out));
+    LQ_LAUNCH(lq_pdl(k_q_times_g, dim3(nb, 1), 256, 0, st, d_inst, use_qf, out));
 }
 
 }  // namespace lqmpc

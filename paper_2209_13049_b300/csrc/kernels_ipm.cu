@@ -61,6 +61,7 @@ __device__ __forceinline__ void put_part(const Inst& I, int slot, double v) {
 // ---------------------------------------------------------------------------
 
 __global__ void k_set_u0(const Inst* __restrict__ insts, int warm) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x) {
         int c = j % I.nu;
@@ -85,6 +86,7 @@ __global__ void k_set_u0(const Inst* __restrict__ insts, int warm) {
 // Cold start: s = max(slack, 1), z = 1.  Warm start (mu0 > 0): s =
 // max(slack, smin), z = mu0 / s, a start centred at complementarity mu0.
 __global__ void k_init_slacks(const Inst* __restrict__ insts, double mu0, double smin) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     const bool warm = mu0 > 0.0;
@@ -124,6 +126,7 @@ __global__ void k_init_slacks(const Inst* __restrict__ insts, double mu0, double
 
 __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double tol, double tau,
                            int max_iter, double refine_tol, int prec) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     double c = 0, d = 0, h = 0;
@@ -156,6 +159,7 @@ __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double to
 // ---------------------------------------------------------------------------
 
 __global__ void k_resid(const Inst* __restrict__ insts) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -190,6 +194,7 @@ __global__ void k_resid(const Inst* __restrict__ insts) {
 // the design notes).  One warp per input row; H column j = row j (symmetric).
 // Partial: slot 2 max|r_d|.
 __global__ void k_rd(const Inst* __restrict__ insts) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -213,6 +218,7 @@ __global__ void k_rd(const Inst* __restrict__ insts) {
 
 // Stop test and trace.  nb1: partial count of k_resid, nb2: of k_rd.
 __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int trace_on) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -263,6 +269,7 @@ struct StepMin {
 };
 
 __global__ void k_aff(const Inst* __restrict__ insts) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -295,6 +302,7 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
 
 // alpha_aff = min(1, max step); mu_aff; sigma = (mu_aff/mu)^3 (Mehrotra).
 __global__ void k_aff_fin(const Inst* __restrict__ insts, int nb) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -322,6 +330,7 @@ __global__ void k_aff_fin(const Inst* __restrict__ insts, int nb) {
 // Corrector: r_c = s.z + ds_aff.dz_aff - sigma mu; w = (r_c - z r_p)/s per
 // family; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).
 __global__ void k_corr(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     const double smu = I.sc->sigma * I.sc->mu;
@@ -347,6 +356,7 @@ __global__ void k_corr(const Inst* __restrict__ insts) {
 
 // b = -r_d + Gamma' wx + wxu
 __global__ void k_rhs(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < I.n; j += gridDim.x * blockDim.x)
@@ -356,6 +366,7 @@ __global__ void k_rhs(const Inst* __restrict__ insts) {
 // Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with r_c from the
 // stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.
 __global__ void k_step(const Inst* __restrict__ insts) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -386,6 +397,7 @@ __global__ void k_step(const Inst* __restrict__ insts) {
 
 // alpha = min(1, tau * max step); trace; iteration count.
 __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -406,6 +418,7 @@ __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on)
 
 // One step length for every variable (u, x, s, z).
 __global__ void k_update(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const Scal* S = I.sc;
     if (S->done) return;
@@ -421,6 +434,7 @@ __global__ void k_update(const Inst* __restrict__ insts) {
 }
 
 __global__ void k_iter_inc(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (threadIdx.x == 0 && !I.sc->done) I.sc->iter += 1;
 }
@@ -438,48 +452,48 @@ void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n,
                        double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0,
                        double smin) {
     int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(k_init_slacks<<<dim3(nb, count), 256, 0, st>>>(d_insts, mu0, smin));
-    LQ_LAUNCH(k_init_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, tol, tau, max_iter, refine_tol, prec));
+    LQ_LAUNCH(lq_pdl(k_init_slacks, dim3(nb, count), 256, 0, st, d_insts, mu0, smin));
+    LQ_LAUNCH(lq_pdl(k_init_fin, dim3(1, count), 256, 0, st, d_insts, nb, tol, tau, max_iter, refine_tol, prec));
 }
 
 void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm) {
-    LQ_LAUNCH(k_set_u0<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts, warm));
+    LQ_LAUNCH(lq_pdl(k_set_u0, dim3(ew_blocks(max_n, 256), count), 256, 0, st, d_insts, warm));
 }
 
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
                         cudaStream_t st, bool do_resid, bool do_rd, int rd_parts) {
     int nb1 = ew_blocks(max_total, 256);
-    if (do_resid) LQ_LAUNCH(k_resid<<<dim3(nb1, count), 256, 0, st>>>(d_insts));
+    if (do_resid) LQ_LAUNCH(lq_pdl(k_resid, dim3(nb1, count), 256, 0, st, d_insts));
     int wpb = 8;
     int nb2 = (max_n + wpb - 1) / wpb;
     nb2 = nb2 > kMaxParts ? kMaxParts : nb2;
     if (do_rd) {
-        if (rd_parts & 1) LQ_LAUNCH(k_rd<<<dim3(nb2, count), wpb * 32, 0, st>>>(d_insts));
-        if (rd_parts & 2) LQ_LAUNCH(k_check<<<dim3(1, count), 256, 0, st>>>(d_insts, nb1, nb2, trace_on));
+        if (rd_parts & 1) LQ_LAUNCH(lq_pdl(k_rd, dim3(nb2, count), wpb * 32, 0, st, d_insts));
+        if (rd_parts & 2) LQ_LAUNCH(lq_pdl(k_check, dim3(1, count), 256, 0, st, d_insts, nb1, nb2, trace_on));
     }
 }
 
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(k_aff<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_aff_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb));
+    LQ_LAUNCH(lq_pdl(k_aff, dim3(nb, count), 256, 0, st, d_insts));
+    LQ_LAUNCH(lq_pdl(k_aff_fin, dim3(1, count), 256, 0, st, d_insts, nb));
 }
 
 void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
-    LQ_LAUNCH(k_corr<<<dim3(ew_blocks(max_total, 256), count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_corr, dim3(ew_blocks(max_total, 256), count), 256, 0, st, d_insts));
 }
 
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
-    LQ_LAUNCH(k_rhs<<<dim3(ew_blocks(max_n, 256), count), 256, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_rhs, dim3(ew_blocks(max_n, 256), count), 256, 0, st, d_insts));
 }
 
 void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
                         cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(k_step<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_step_fin<<<dim3(1, count), 256, 0, st>>>(d_insts, nb, trace_on));
-    LQ_LAUNCH(k_update<<<dim3(nb, count), 256, 0, st>>>(d_insts));
-    LQ_LAUNCH(k_iter_inc<<<dim3(1, count), 32, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_step, dim3(nb, count), 256, 0, st, d_insts));
+    LQ_LAUNCH(lq_pdl(k_step_fin, dim3(1, count), 256, 0, st, d_insts, nb, trace_on));
+    LQ_LAUNCH(lq_pdl(k_update, dim3(nb, count), 256, 0, st, d_insts));
+    LQ_LAUNCH(lq_pdl(k_iter_inc, dim3(1, count), 32, 0, st, d_insts));
 }
 
 }  // namespace lqmpc

@@ -27,6 +27,7 @@
 namespace lqmpc {
 
 __global__ void k_ly_chain(const Inst* __restrict__ insts, int flags, int max_nu, double shift) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg;
@@ -105,6 +106,7 @@ __device__ __forceinline__ void ffc_mac(float& ah, float& al, float xh, float xl
 }  // namespace
 
 __global__ void k_sig_split(const Inst* __restrict__ insts, int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int sx = I.SX;
@@ -117,6 +119,7 @@ __global__ void k_sig_split(const Inst* __restrict__ insts, int flags) {
 }
 
 __global__ void k_ly_chain_ff(const Inst* __restrict__ insts, int flags, int max_nu, double shift) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int ns = I.ns, nu = I.nu, N = I.N, n = I.n, ldg = I.ldg, sx = I.SX;
@@ -209,12 +212,11 @@ static int chain_threads(size_t smem) {
 
 void launch_kkt_lyap_ff(const Inst* d_insts, int count, int max_ns, int max_nu, int max_N, int max_sx, int flags,
                         cudaStream_t st, double shift) {
-    LQ_LAUNCH(k_sig_split<<<dim3(per_instance_blocks(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), count), 256,
-                                0, st>>>(d_insts, flags));
+    LQ_LAUNCH(lq_pdl(k_sig_split, dim3(per_instance_blocks(std::max(1, std::min(1024, (max_sx + 255) / 256)), count), count), 256, 0, st, d_insts, flags));
     const size_t smem = 2 * sizeof(float2) * (size_t)max_ns;
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(k_ly_chain_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LQ_LAUNCH(k_ly_chain_ff<<<dim3(max_N * max_nu, count), chain_threads(smem), smem, st>>>(d_insts, flags, max_nu,
+    LQ_LAUNCH(lq_pdl(k_ly_chain_ff, dim3(max_N * max_nu, count), chain_threads(smem), smem, st, d_insts, flags, max_nu,
                                                                                            shift));
 }
 
@@ -222,7 +224,7 @@ void launch_kkt_lyap(const Inst* d_insts, int count, int max_ns, int max_nu, int
                      cudaStream_t st, double shift) {
     const size_t smem = 2 * sizeof(double) * (size_t)max_ns;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k_ly_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    LQ_LAUNCH(k_ly_chain<<<dim3(max_N * max_nu, count), chain_threads(smem), smem, st>>>(d_insts, flags, max_nu,
+    LQ_LAUNCH(lq_pdl(k_ly_chain, dim3(max_N * max_nu, count), chain_threads(smem), smem, st, d_insts, flags, max_nu,
                                                                                         shift));
 }
 

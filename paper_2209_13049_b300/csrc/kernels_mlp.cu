@@ -134,6 +134,7 @@ template <int EPI>
 __global__ void __launch_bounds__(192, 1) k_mlp_gemm(const __grid_constant__ CUtensorMap mapA,
                                                      const __grid_constant__ CUtensorMap mapB, int K,
                                                      GemmEpi ep) {
+    pdl_wait();
     extern __shared__ __align__(1024) unsigned char gsm[];
     __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], accb;
     __shared__ uint32_t tbase;
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(192, 1) k_mlp_gemm(const __grid_constant__ CUt
 __global__ void k_mlp_gather(const float* __restrict__ Xs, const float* __restrict__ Us, const int* __restrict__ idx,
                              int B, int ldt, int nin, int inp, int nout, int outp, __nv_bfloat16* __restrict__ X,
                              __nv_bfloat16* __restrict__ XT, float* __restrict__ T) {
+    pdl_wait();
     const int r = blockIdx.y;
     const bool real = r < B;
     const size_t src = real ? (size_t)idx[r] : 0;
@@ -320,6 +322,7 @@ __global__ void k_mlp_gather(const float* __restrict__ Xs, const float* __restri
 
 // Bias gradient: db[f] = sum over the batch of G^T[f, :] (one warp per feature).
 __global__ void k_mlp_colsum(const __nv_bfloat16* __restrict__ GT, int F, int Bp, int ldt, float* __restrict__ db) {
+    pdl_wait();
     const int f = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (f >= F) return;
     float s = 0.0f;
@@ -334,6 +337,7 @@ __global__ void k_mlp_adam(float* __restrict__ w, const float* __restrict__ g, f
                            float* __restrict__ v, size_t count, float lr, float b1, float b2, float eps,
                            const int* __restrict__ tstep, int rows, int cols, __nv_bfloat16* __restrict__ wb,
                            __nv_bfloat16* __restrict__ wbt) {
+    pdl_wait();
     const float t = (float)*tstep;   // steps taken including this one
     const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
@@ -356,6 +360,7 @@ __global__ void k_mlp_adam(float* __restrict__ w, const float* __restrict__ g, f
 // BF16 working copies of one weight matrix from its FP32 master.
 __global__ void k_mlp_cast(const float* __restrict__ w, int rows, int cols, __nv_bfloat16* __restrict__ wb,
                            __nv_bfloat16* __restrict__ wbt) {
+    pdl_wait();
     const size_t count = (size_t)rows * cols;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / cols), c = (int)(i % cols);
@@ -367,6 +372,7 @@ __global__ void k_mlp_cast(const float* __restrict__ w, int rows, int cols, __nv
 
 // FP64 inputs (count x nin) to the BF16 input tile (Bp x inp, zero padding).
 __global__ void k_mlp_load_x(const double* __restrict__ x, int count, int nin, int inp, __nv_bfloat16* __restrict__ X) {
+    pdl_wait();
     const int r = blockIdx.y;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < inp; c += gridDim.x * blockDim.x)
         X[(size_t)r * inp + c] = __float2bfloat16_rn((r < count && c < nin) ? (float)x[(size_t)r * nin + c] : 0.0f);
@@ -374,6 +380,7 @@ __global__ void k_mlp_load_x(const double* __restrict__ x, int count, int nin, i
 
 // out += sum of the per-CTA partials (fixed order).
 __global__ void k_mlp_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+    pdl_wait();
     __shared__ double red[32];
     double s = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
@@ -413,7 +420,7 @@ static void gemm_launch(const void* mapA, const void* mapB, int M, int N, int K,
     cudaFuncSetAttribute(k_mlp_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const CUtensorMap& a = *reinterpret_cast<const CUtensorMap*>(mapA);
     const CUtensorMap& b = *reinterpret_cast<const CUtensorMap*>(mapB);
-    LQ_LAUNCH(k_mlp_gemm<EPI><<<dim3(N / kGT, M / kGT), 192, smem, st>>>(a, b, K, ep));
+    LQ_LAUNCH(lq_pdl(k_mlp_gemm<EPI>, dim3(N / kGT, M / kGT), 192, smem, st, a, b, K, ep));
 }
 
 void mlp_gemm(int epi, const void* mapA, const void* mapB, int M, int N, int K, const GemmEpi& ep, cudaStream_t st) {
@@ -428,36 +435,37 @@ void mlp_gemm(int epi, const void* mapA, const void* mapB, int M, int N, int K, 
 
 void mlp_gather(const float* Xs, const float* Us, const int* idx, int B, int Bp, int ldt, int nin, int inp, int nout,
                 int outp, __nv_bfloat16* X, __nv_bfloat16* XT, float* T, cudaStream_t st) {
-    LQ_LAUNCH(k_mlp_gather<<<dim3(4, Bp), 256, 0, st>>>(Xs, Us, idx, B, ldt, nin, inp, nout, outp, X, XT, T));
+    LQ_LAUNCH(lq_pdl(k_mlp_gather, dim3(4, Bp), 256, 0, st, Xs, Us, idx, B, ldt, nin, inp, nout, outp, X, XT, T));
 }
 
 void mlp_colsum(const __nv_bfloat16* GT, int F, int Bp, int ldt, float* db, cudaStream_t st) {
-    LQ_LAUNCH(k_mlp_colsum<<<(F + 7) / 8, 256, 0, st>>>(GT, F, Bp, ldt, db));
+    LQ_LAUNCH(lq_pdl(k_mlp_colsum, (F + 7) / 8, 256, 0, st, GT, F, Bp, ldt, db));
 }
 
 void mlp_adam(float* w, const float* g, float* m, float* v, size_t count, float lr, float b1, float b2, float eps,
               const int* tstep, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wbt, cudaStream_t st) {
     int nb = (int)((count + 255) / 256);
     nb = nb > 2048 ? 2048 : nb;
-    LQ_LAUNCH(k_mlp_adam<<<nb, 256, 0, st>>>(w, g, m, v, count, lr, b1, b2, eps, tstep, rows, cols, wb, wbt));
+    LQ_LAUNCH(lq_pdl(k_mlp_adam, nb, 256, 0, st, w, g, m, v, count, lr, b1, b2, eps, tstep, rows, cols, wb, wbt));
 }
 
-__global__ void k_mlp_tick(int* tstep) { *tstep += 1; }
+__global__ void k_mlp_tick(int* tstep) {
+    pdl_wait(); *tstep += 1; }
 
-void mlp_tick(int* tstep, cudaStream_t st) { LQ_LAUNCH(k_mlp_tick<<<1, 1, 0, st>>>(tstep)); }
+void mlp_tick(int* tstep, cudaStream_t st) { LQ_LAUNCH(lq_pdl(k_mlp_tick, 1, 1, 0, st, tstep)); }
 
 void mlp_cast(const float* w, int rows, int cols, __nv_bfloat16* wb, __nv_bfloat16* wbt, cudaStream_t st) {
     int nb = (int)(((size_t)rows * cols + 255) / 256);
     nb = nb > 2048 ? 2048 : nb;
-    LQ_LAUNCH(k_mlp_cast<<<nb, 256, 0, st>>>(w, rows, cols, wb, wbt));
+    LQ_LAUNCH(lq_pdl(k_mlp_cast, nb, 256, 0, st, w, rows, cols, wb, wbt));
 }
 
 void mlp_load_x(const double* x, int count, int nin, int inp, int Bp, __nv_bfloat16* X, cudaStream_t st) {
-    LQ_LAUNCH(k_mlp_load_x<<<dim3(4, Bp), 256, 0, st>>>(x, count, nin, inp, X));
+    LQ_LAUNCH(lq_pdl(k_mlp_load_x, dim3(4, Bp), 256, 0, st, x, count, nin, inp, X));
 }
 
 void mlp_sum(const double* part, int n, double* out, cudaStream_t st) {
-    LQ_LAUNCH(k_mlp_sum<<<1, 256, 0, st>>>(part, n, out));
+    LQ_LAUNCH(lq_pdl(k_mlp_sum, 1, 256, 0, st, part, n, out));
 }
 
 }  // namespace lqmpc

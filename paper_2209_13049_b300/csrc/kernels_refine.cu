@@ -32,6 +32,7 @@ __device__ __forceinline__ bool pcg_skip(const Inst& I, int sel) {
 // budget and FP32 factors the middle one: replacing such a factor by the next
 // tier is cheaper than iterating with it).
 __global__ void k_pcg_begin(const Inst* __restrict__ insts, int sel, int budget_hi, int budget_lo, int budget_mid) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
@@ -54,6 +55,7 @@ __device__ void pcg_test(const Inst& I, double rn);
 __device__ void pcg_alpha(const Inst& I, double pq);
 
 __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
@@ -97,6 +99,7 @@ __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) 
 // In the conjugate-gradient steps the last CTA's tail also leaves nothing
 // else to do: alpha is formed there as in k_pcg_matvec.
 __global__ void k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int sel, int splits) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
@@ -179,6 +182,7 @@ __device__ void pcg_test(const Inst& I, double rn) {
 // residual).  The pass count is left in instance 0's Scal for the host.
 __global__ void k_pcg_more(const Inst* __restrict__ insts, int count, int selr, cudaGraphConditionalHandle h,
                            int cap, int reset) {
+    pdl_wait();
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -198,11 +202,12 @@ __global__ void k_pcg_more(const Inst* __restrict__ insts, int count, int selr, 
 
 void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset,
                      cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_more<<<1, 256, 0, st>>>(d_insts, count, selr, h, cap, reset));
+    LQ_LAUNCH(lq_pdl(k_pcg_more, 1, 256, 0, st, d_insts, count, selr, h, cap, reset));
 }
 
 // p = z, rz = r'z (one block per instance).
 __global__ void k_pcg_pinit(const Inst* __restrict__ insts, int sel) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
@@ -226,6 +231,7 @@ __device__ void pcg_alpha(const Inst& I, double pq) {
 // du += alpha p, r -= alpha q (input rows), dxs += alpha (Gamma p) (state
 // rows).  Partial max|r| in slot 7; the last CTA runs the convergence test.
 __global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
+    pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
@@ -254,6 +260,7 @@ __global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
 
 // beta = r'z_new / r'z_old; p = z + beta p (one block per instance).
 __global__ void k_pcg_beta(const Inst* __restrict__ insts, int sel) {
+    pdl_wait();
     __shared__ double red[32];
     __shared__ double beta_sh;
     const Inst& I = insts[blockIdx.y];
@@ -274,6 +281,7 @@ __global__ void k_pcg_beta(const Inst* __restrict__ insts, int sel) {
 // dst = src over the instance's SX (len_kind 0) or n (len_kind 1) entries.
 __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst_role, int len_kind,
                            int flags) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const double* s = role_ptr(I, src_role);
@@ -285,6 +293,7 @@ __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst
 // dst += src over the instance's n entries (instances not done).
 // Every unfinished instance needs a KKT solve.
 __global__ void k_kkt_begin(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.x];
     if (threadIdx.x == 0) I.sc->kkt_pending = I.sc->done ? 0 : 1;
 }
@@ -294,6 +303,7 @@ __global__ void k_kkt_begin(const Inst* __restrict__ insts) {
 // low-precision one whose refinement converged.  The rest stay pending for
 // the host: escalation to a more accurate factor, or a final status.
 __global__ void k_kkt_settle(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.x];
     Scal* S = I.sc;
     if (threadIdx.x != 0 || S->done || !S->kkt_pending || S->info) return;
@@ -301,6 +311,7 @@ __global__ void k_kkt_settle(const Inst* __restrict__ insts) {
 }
 
 __global__ void k_vec_add(const Inst* __restrict__ insts, int src_role, int dst_role) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     const double* s = role_ptr(I, src_role);
@@ -315,52 +326,52 @@ static int nblk(int len, int th, int cap) {
 
 void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, int budget_mid,
                       cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_begin<<<dim3(1, count), 256, 0, st>>>(d_insts, sel, budget_hi, budget_lo, budget_mid));
+    LQ_LAUNCH(lq_pdl(k_pcg_begin, dim3(1, count), 256, 0, st, d_insts, sel, budget_hi, budget_lo, budget_mid));
 }
 
 // mode 0: r = b - M du and its convergence test; mode 1: q = M p and alpha.
 void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int sel, cudaStream_t st) {
     int wpb = 8;
     int nb = nblk(max_n, wpb, kMaxParts);
-    LQ_LAUNCH(k_pcg_matvec<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel));
+    LQ_LAUNCH(lq_pdl(k_pcg_matvec, dim3(nb, count), wpb * 32, 0, st, d_insts, mode, sel));
 }
 
 void launch_pcg_matvec_ff(const Inst* d_insts, int count, int max_n, int splits, int mode, int sel,
                           cudaStream_t st) {
     const int wpb = 2;   // two rows per CTA: every SM takes part
     const int nb = per_instance_blocks(nblk(max_n, wpb, kMaxParts), count);
-    LQ_LAUNCH(k_pcg_matvec_ff<<<dim3(nb, count), wpb * 32, 0, st>>>(d_insts, mode, sel, splits));
+    LQ_LAUNCH(lq_pdl(k_pcg_matvec_ff, dim3(nb, count), wpb * 32, 0, st, d_insts, mode, sel, splits));
 }
 
 void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_pinit<<<dim3(1, count), 256, 0, st>>>(d_insts, sel));
+    LQ_LAUNCH(lq_pdl(k_pcg_pinit, dim3(1, count), 256, 0, st, d_insts, sel));
 }
 
 void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st) {
     int nb = per_instance_blocks(nblk(max_total, 256, kMaxParts), count);
-    LQ_LAUNCH(k_pcg_axpy<<<dim3(nb, count), 256, 0, st>>>(d_insts, sel));
+    LQ_LAUNCH(lq_pdl(k_pcg_axpy, dim3(nb, count), 256, 0, st, d_insts, sel));
 }
 
 void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st) {
-    LQ_LAUNCH(k_pcg_beta<<<dim3(1, count), 256, 0, st>>>(d_insts, sel));
+    LQ_LAUNCH(lq_pdl(k_pcg_beta, dim3(1, count), 256, 0, st, d_insts, sel));
 }
 
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
                      int len_kind, int force, cudaStream_t st) {
-    LQ_LAUNCH(k_vec_copy<<<dim3(nblk(max_len, 256, 4096), count), 256, 0, st>>>(d_insts, src_role, dst_role,
+    LQ_LAUNCH(lq_pdl(k_vec_copy, dim3(nblk(max_len, 256, 4096), count), 256, 0, st, d_insts, src_role, dst_role,
                                                                                  len_kind, force));
 }
 
 void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st) {
-    LQ_LAUNCH(k_vec_add<<<dim3(nblk(max_n, 256, 1024), count), 256, 0, st>>>(d_insts, src_role, dst_role));
+    LQ_LAUNCH(lq_pdl(k_vec_add, dim3(nblk(max_n, 256, 1024), count), 256, 0, st, d_insts, src_role, dst_role));
 }
 
 void launch_kkt_begin(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_kkt_begin<<<count, 32, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_kkt_begin, count, 32, 0, st, d_insts));
 }
 
 void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(k_kkt_settle<<<count, 32, 0, st>>>(d_insts));
+    LQ_LAUNCH(lq_pdl(k_kkt_settle, count, 32, 0, st, d_insts));
 }
 
 }  // namespace lqmpc

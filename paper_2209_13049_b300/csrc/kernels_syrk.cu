@@ -33,6 +33,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts, int mode,
                                                  const double* gq, const double* gqf, int splits,
                                                  int force) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, force)) return;
     if (!(force & F_FORCE) && mode == 0 && I.sc->info) return;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256) k_syrk_cc(const Inst* __restrict__ insts,
 template <typename TP, typename Tout, int TILE, bool COLMAJOR = false, bool LOWER = false>
 __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int base_mode,
                               int add_sigu, int force, Tout* out_override, double shift) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, force)) return;
     if (!(force & F_FORCE) && I.sc->info) return;
@@ -161,6 +163,7 @@ __global__ void k_syrk_reduce(const Inst* __restrict__ insts, int splits, int ba
 
 // H (FP64) to its FP32 copy.
 __global__ void k_h_to_f32(const Inst* __restrict__ insts) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const size_t total = (size_t)I.n * I.n;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -189,8 +192,8 @@ int syrk_cc_splits(int ns, int nu, int N) {
 void launch_syrk_cc(const Inst* d_insts, int count, int max_n, int splits, int fp64, int mode,
                     const double* gq, const double* gqf, int force, cudaStream_t st) {
     dim3 grid(syrk_cc_tiles(max_n) * splits, count);
-    if (fp64) LQ_LAUNCH(k_syrk_cc<double><<<grid, 256, 0, st>>>(d_insts, mode, gq, gqf, splits, force));
-    else LQ_LAUNCH(k_syrk_cc<float><<<grid, 256, 0, st>>>(d_insts, mode, gq, gqf, splits, force));
+    if (fp64) LQ_LAUNCH(lq_pdl(k_syrk_cc<double>, grid, 256, 0, st, d_insts, mode, gq, gqf, splits, force));
+    else LQ_LAUNCH(lq_pdl(k_syrk_cc<float>, grid, 256, 0, st, d_insts, mode, gq, gqf, splits, force));
 }
 
 void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, int part_kind,
@@ -201,14 +204,14 @@ void launch_syrk_reduce(const Inst* d_insts, int count, int max_n, int splits, i
     nb = nb > 4096 ? 4096 : nb;
     dim3 grid(nb, count);
     if (part_kind == 0) {        // FP64 partials, 64-tiles
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<double, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
-        else LQ_LAUNCH(k_syrk_reduce<double, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
+        if (out_fp64) LQ_LAUNCH(lq_pdl(k_syrk_reduce<double, double, 64>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(lq_pdl(k_syrk_reduce<double, float, 64>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     } else if (part_kind == 1) { // FP32 partials, 64-tiles
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
-        else LQ_LAUNCH(k_syrk_reduce<float, float, 64><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
+        if (out_fp64) LQ_LAUNCH(lq_pdl(k_syrk_reduce<float, double, 64>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(lq_pdl(k_syrk_reduce<float, float, 64>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     } else {                     // FP32 partials, 128-tiles, column-major (tensor-core SYRK)
-        if (out_fp64) LQ_LAUNCH(k_syrk_reduce<float, double, 128, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
-        else LQ_LAUNCH(k_syrk_reduce<float, float, 128, true, true><<<grid, 256, 0, st>>>(d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
+        if (out_fp64) LQ_LAUNCH(lq_pdl(k_syrk_reduce<float, double, 128, true>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (double*)out_override, shift));
+        else LQ_LAUNCH(lq_pdl(k_syrk_reduce<float, float, 128, true, true>, grid, 256, 0, st, d_insts, splits, base_mode, add_sigu, force, (float*)out_override, shift));
     }
 }
 
@@ -216,7 +219,7 @@ void launch_h_to_f32(const Inst* d_inst, int n, cudaStream_t st) {
     size_t total = (size_t)n * n;
     int nb = (int)((total + 255) / 256);
     nb = nb > 4096 ? 4096 : nb;
-    LQ_LAUNCH(k_h_to_f32<<<dim3(nb, 1), 256, 0, st>>>(d_inst));
+    LQ_LAUNCH(lq_pdl(k_h_to_f32, dim3(nb, 1), 256, 0, st, d_inst));
 }
 
 }  // namespace lqmpc

@@ -156,6 +156,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 template <int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_syrk_tc(const Inst* __restrict__ insts, const CUtensorMap* maps,
                                                      int splits, int flags) {
+    pdl_wait();
     constexpr bool TF32 = MODE != 0;
     constexpr int kStages = TcCfg<MODE>::kStages;
     constexpr int kStageBytes = TcCfg<MODE>::kStageBytes;
@@ -479,15 +480,15 @@ void launch_syrk_tc(const Inst* d_insts, int count, int max_n, int splits, int m
     if (mode == 1) {
         const size_t smem = (size_t)TcCfg<1>::kStages * TcCfg<1>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<1><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(lq_pdl(k_syrk_tc<1>, grid, kTcThreads, smem, st, d_insts, maps, splits, flags));
     } else if (mode == 2) {
         const size_t smem = (size_t)TcCfg<2>::kStages * TcCfg<2>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<2><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(lq_pdl(k_syrk_tc<2>, grid, kTcThreads, smem, st, d_insts, maps, splits, flags));
     } else {
         const size_t smem = (size_t)TcCfg<0>::kStages * TcCfg<0>::kStageBytes + 1024;
         cudaFuncSetAttribute(k_syrk_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        LQ_LAUNCH(k_syrk_tc<0><<<grid, kTcThreads, smem, st>>>(d_insts, maps, splits, flags));
+        LQ_LAUNCH(lq_pdl(k_syrk_tc<0>, grid, kTcThreads, smem, st, d_insts, maps, splits, flags));
     }
 }
 

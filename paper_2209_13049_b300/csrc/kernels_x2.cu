@@ -64,6 +64,7 @@ __device__ __forceinline__ void lower_tile(int t, int& ti, int& tj) {
 
 // M32 = fl(M64) on the lower triangle, the diagonal scaled by (1 + shift).
 __global__ void k_x2_round(const Inst* __restrict__ insts, int flags, double shift) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
     const int n = I.n;
@@ -82,6 +83,7 @@ __global__ void k_x2_round(const Inst* __restrict__ insts, int flags, double shi
 // entries each (row tid % 32, columns tid / 32 + 8 q); the products
 // L1(i, k) L1(j, k) are exact as p + e (FMA) and summed in float-float.
 __global__ void __launch_bounds__(256) k_x2_resid(const Inst* __restrict__ insts, int flags) {
+    pdl_wait();
     __shared__ float As[kXb][kXb + 1], Bs[kXb][kXb + 1];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(256) k_x2_resid(const Inst* __restrict__ insts
 //   mode 0: S2b = fl(W),  W = X1 L1    A = Xinv32, B = M32 (L1)
 //   mode 1: S2a + S2b = Y = X2 X1     A = Xinv32 (X2), B = S1 (X1)
 __global__ void __launch_bounds__(256) k_x2_trimul(const Inst* __restrict__ insts, int flags, int mode) {
+    pdl_wait();
     __shared__ float As[kXb][kXb + 1], Bs[kXb][kXb + 1];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
@@ -194,6 +197,7 @@ __global__ void __launch_bounds__(256) k_x2_trimul(const Inst* __restrict__ inst
 // 256 threads, four entries each (row tid % 32, columns tid / 32 + 8 q), K in
 // steps of 32 staged through shared memory with coalesced loads.
 __global__ void __launch_bounds__(256) k_x2_gemm(const Inst* __restrict__ insts, int flags, int mode) {
+    pdl_wait();
     __shared__ float As[kXb][kXb + 1], Bs[kXb][kXb + 1];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(256) k_x2_gemm(const Inst* __restrict__ insts,
 // what 0: S1 = Xinv32 (keep X1); 1: Xinv32 / Xlo32 = Y (lower), XinvT32 /
 // XloT32 = Y' (upper) from S2a / S2b
 __global__ void k_x2_copy(const Inst* __restrict__ insts, int flags, int what) {
+    pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     const int n = I.n;
@@ -278,24 +283,24 @@ __global__ void k_x2_copy(const Inst* __restrict__ insts, int flags, int what) {
 
 void launch_x2_round(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st, double shift) {
     const int blocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
-    LQ_LAUNCH(k_x2_round<<<dim3(blocks, count), 256, 0, st>>>(d_insts, flags, shift));
+    LQ_LAUNCH(lq_pdl(k_x2_round, dim3(blocks, count), 256, 0, st, d_insts, flags, shift));
 }
 
 void launch_x2_refine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st) {
     const int nt = (max_n + kXb - 1) / kXb;
     const int cblocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
-    LQ_LAUNCH(k_x2_resid<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags));
-    LQ_LAUNCH(k_x2_trimul<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 0));
-    LQ_LAUNCH(k_x2_gemm<<<dim3(nt * nt, count), 256, 0, st>>>(d_insts, flags, 0));
-    LQ_LAUNCH(k_x2_gemm<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 1));
-    LQ_LAUNCH(k_x2_copy<<<dim3(cblocks, count), 256, 0, st>>>(d_insts, flags, 0));
+    LQ_LAUNCH(lq_pdl(k_x2_resid, dim3(nt * (nt + 1) / 2, count), 256, 0, st, d_insts, flags));
+    LQ_LAUNCH(lq_pdl(k_x2_trimul, dim3(nt * (nt + 1) / 2, count), 256, 0, st, d_insts, flags, 0));
+    LQ_LAUNCH(lq_pdl(k_x2_gemm, dim3(nt * nt, count), 256, 0, st, d_insts, flags, 0));
+    LQ_LAUNCH(lq_pdl(k_x2_gemm, dim3(nt * (nt + 1) / 2, count), 256, 0, st, d_insts, flags, 1));
+    LQ_LAUNCH(lq_pdl(k_x2_copy, dim3(cblocks, count), 256, 0, st, d_insts, flags, 0));
 }
 
 void launch_x2_combine(const Inst* d_insts, int count, int max_n, int flags, cudaStream_t st) {
     const int nt = (max_n + kXb - 1) / kXb;
     const int cblocks = per_instance_blocks(std::min(1024, ((max_n * max_n) + 255) / 256), count);
-    LQ_LAUNCH(k_x2_trimul<<<dim3(nt * (nt + 1) / 2, count), 256, 0, st>>>(d_insts, flags, 1));
-    LQ_LAUNCH(k_x2_copy<<<dim3(cblocks, count), 256, 0, st>>>(d_insts, flags, 1));
+    LQ_LAUNCH(lq_pdl(k_x2_trimul, dim3(nt * (nt + 1) / 2, count), 256, 0, st, d_insts, flags, 1));
+    LQ_LAUNCH(lq_pdl(k_x2_copy, dim3(cblocks, count), 256, 0, st, d_insts, flags, 1));
 }
 
 }  // namespace lqmpc

@@ -65,7 +65,7 @@ void prof_stop(cudaStream_t st, cudaEvent_t e0, const char* what) {
     cudaEventRecord(e1, st);
     g_prof_recs.push_back({what, e0, e1});
 }
-// Print and clear the per-kernel table (kernel name = text before "<<<").
+// Print and clear the per-kernel table (kernel name = lq_pdl's first argument).
 static void prof_report(const char* title) {
     if (g_prof != 1 || g_prof_recs.empty()) return;
     cudaDeviceSynchronize();
@@ -76,7 +76,19 @@ static void prof_report(const char* title) {
         float ms = 0;
         cudaEventElapsedTime(&ms, r.a, r.b);
         std::string nm(r.what);
-        size_t k = nm.find("<<<");
+        size_t k = nm.find("lq_pdl(");
+        if (k != std::string::npos) {       // the kernel: lq_pdl's first argument
+            nm = nm.substr(k + 7);
+            int depth = 0;
+            size_t e = 0;
+            for (; e < nm.size(); ++e) {
+                if (nm[e] == '<') ++depth;
+                else if (nm[e] == '>') --depth;
+                else if (nm[e] == ',' && depth == 0) break;
+            }
+            nm = nm.substr(0, e);
+        }
+        k = nm.find("<<<");
         if (k != std::string::npos) nm = nm.substr(0, k);
         bool found = false;
         for (auto& a : aggs)
@@ -107,6 +119,16 @@ void check_launch(cudaStream_t st, const char* what, const char* file, int line)
         fflush(stderr);
     }
 }
+// Programmatic dependent launch of the library's kernels (LQMPC_PDL=0: off).
+bool pdl_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = getenv("LQMPC_PDL");
+        on = (e && e[0] == '0') ? 0 : 1;
+    }
+    return on == 1;
+}
+
 }  // namespace lqmpc
 
 namespace lqmpc {
