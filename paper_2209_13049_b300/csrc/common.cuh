@@ -94,6 +94,9 @@ struct Scal {
     int refine_budget;  // conjugate-gradient steps allowed for the current right-hand side
     int arrive;         // CTAs of the current launch that finished (last_arrival), 0 between launches
     int pcg_loops;      // passes of the device-side conjugate-gradient loop in the latest solve (instance 0)
+    int pcg_pass_total[2];  // passes of the loop graphs since the solve began (instance 0; [FP64 preconditioner])
+    int spec_fail;      // a KKT solve of this iteration stayed pending while the host was not looking:
+                        // the step and update are skipped and the host repeats the iteration
 };
 
 // Device descriptor of one instance (all pointers are device memory).

@@ -102,7 +102,7 @@ void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int 
 // kernels_refine.cu (preconditioned conjugate gradients on M du = b; `sel`
 // is the launch predicate that picks the instances of the solve)
 // loop control of the device-side conjugate-gradient loop (while node of a captured graph)
-void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset,
+void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset, int slot,
                      cudaStream_t st);
 void launch_pcg_begin(const Inst* d_insts, int count, int sel, int budget_hi, int budget_lo, int budget_mid,
                       cudaStream_t st);
@@ -115,7 +115,7 @@ void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st);
 void launch_pcg_step_update(const Inst* d_insts, int count, int max_total, int sel, cudaStream_t st);
 void launch_pcg_beta(const Inst* d_insts, int count, int sel, cudaStream_t st);
 void launch_kkt_begin(const Inst* d_insts, int count, cudaStream_t st);
-void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st);
+void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st, int mark);
 void launch_vec_copy(const Inst* d_insts, int count, int max_len, int src_role, int dst_role,
                      int len_kind, int force, cudaStream_t st);
 void launch_vec_add(const Inst* d_insts, int count, int max_n, int src_role, int dst_role, cudaStream_t st);

@@ -163,6 +163,10 @@ __global__ void k_resid(const Inst* __restrict__ insts) {
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
+    // An iteration starts with no failed solve and no failed pivot (a repeat
+    // of an iteration whose solve failed unseen starts afresh); the first
+    // kernel of the iteration on the main stream, before any KKT launch.
+    if (blockIdx.x == 0 && threadIdx.x == 0) { I.sc->spec_fail = 0; I.sc->info = 0; }
     const int total = I.SX + I.n;
     double rpmax = 0.0, sz = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -364,12 +368,15 @@ __global__ void k_rhs(const Inst* __restrict__ insts) {
 }
 
 // Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with r_c from the
-// stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.
+// stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.  This
+// and the rest of the step (k_step_fin, k_update, k_iter_inc) skip an
+// instance whose KKT solve of the iteration failed unseen (Scal::spec_fail):
+// the iterate stays as it was and the host repeats the iteration.
 __global__ void k_step(const Inst* __restrict__ insts) {
     pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
-    if (I.sc->done) return;
+    if (I.sc->done || I.sc->spec_fail) return;
     const double smu = I.sc->sigma * I.sc->mu;
     const int total = I.SX + I.n;
     StepMin am;
@@ -401,7 +408,7 @@ __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on)
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
-    if (S->done) return;
+    if (S->done || S->spec_fail) return;
     double a = INFINITY;
     for (int p = threadIdx.x; p < nb; p += blockDim.x) a = fmin(a, I.part[3 * kMaxParts + p]);
     a = block_reduce<2>(a, red);
@@ -421,7 +428,7 @@ __global__ void k_update(const Inst* __restrict__ insts) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
     const Scal* S = I.sc;
-    if (S->done) return;
+    if (S->done || S->spec_fail) return;
     const double al = S->alpha;
     const int total = I.SX + I.n;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -436,7 +443,7 @@ __global__ void k_update(const Inst* __restrict__ insts) {
 __global__ void k_iter_inc(const Inst* __restrict__ insts) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
-    if (threadIdx.x == 0 && !I.sc->done) I.sc->iter += 1;
+    if (threadIdx.x == 0 && !I.sc->done && !I.sc->spec_fail) I.sc->iter += 1;
 }
 
 // ---------------------------------------------------------------------------

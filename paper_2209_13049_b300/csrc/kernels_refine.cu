@@ -181,7 +181,7 @@ __device__ void pcg_test(const Inst& I, double rn) {
 // passes.  reset: the pass count restarts (the launch after the initial
 // residual).  The pass count is left in instance 0's Scal for the host.
 __global__ void k_pcg_more(const Inst* __restrict__ insts, int count, int selr, cudaGraphConditionalHandle h,
-                           int cap, int reset) {
+                           int cap, int reset, int slot) {
     pdl_wait();
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
@@ -196,13 +196,14 @@ __global__ void k_pcg_more(const Inst* __restrict__ insts, int count, int selr, 
         const unsigned k = reset ? 0u : *loops + 1u;
         *loops = k;
         insts[0].sc->pcg_loops = (int)k;
+        if (!reset) insts[0].sc->pcg_pass_total[slot] += 1;
         cudaGraphSetConditional(h, (any && k < (unsigned)cap) ? 1u : 0u);
     }
 }
 
 void launch_pcg_more(const Inst* d_insts, int count, int selr, cudaGraphConditionalHandle h, int cap, int reset,
-                     cudaStream_t st) {
-    LQ_LAUNCH(lq_pdl(k_pcg_more, 1, 256, 0, st, d_insts, count, selr, h, cap, reset));
+                     int slot, cudaStream_t st) {
+    LQ_LAUNCH(lq_pdl(k_pcg_more, 1, 256, 0, st, d_insts, count, selr, h, cap, reset, slot));
 }
 
 // p = z, rz = r'z (one block per instance).
@@ -295,19 +296,24 @@ __global__ void k_vec_copy(const Inst* __restrict__ insts, int src_role, int dst
 __global__ void k_kkt_begin(const Inst* __restrict__ insts) {
     pdl_wait();
     const Inst& I = insts[blockIdx.x];
-    if (threadIdx.x == 0) I.sc->kkt_pending = I.sc->done ? 0 : 1;
+    // an instance whose predictor failed unseen (spec_fail) skips the corrector
+    if (threadIdx.x == 0) I.sc->kkt_pending = (I.sc->done || I.sc->spec_fail) ? 0 : 1;
 }
 
 // Settle the pending KKT solves: an FP64 solve that met no failing pivot (a
 // refinement of it that did not converge keeps its best iterate), or a
 // low-precision one whose refinement converged.  The rest stay pending for
-// the host: escalation to a more accurate factor, or a final status.
-__global__ void k_kkt_settle(const Inst* __restrict__ insts) {
+// the host: escalation to a more accurate factor, or a final status.  With
+// `mark` (the host reads the outcome only at the end of the iteration) a
+// solve left pending also sets spec_fail, so that the iteration's step and
+// update are skipped.
+__global__ void k_kkt_settle(const Inst* __restrict__ insts, int mark) {
     pdl_wait();
     const Inst& I = insts[blockIdx.x];
     Scal* S = I.sc;
-    if (threadIdx.x != 0 || S->done || !S->kkt_pending || S->info) return;
-    if (S->prec_cur == 0 || S->refine_ok) S->kkt_pending = 0;
+    if (threadIdx.x != 0 || S->done || !S->kkt_pending) return;
+    if (!S->info && (S->prec_cur == 0 || S->refine_ok)) S->kkt_pending = 0;
+    else if (mark) S->spec_fail = 1;
 }
 
 __global__ void k_vec_add(const Inst* __restrict__ insts, int src_role, int dst_role) {
@@ -370,8 +376,8 @@ void launch_kkt_begin(const Inst* d_insts, int count, cudaStream_t st) {
     LQ_LAUNCH(lq_pdl(k_kkt_begin, count, 32, 0, st, d_insts));
 }
 
-void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st) {
-    LQ_LAUNCH(lq_pdl(k_kkt_settle, count, 32, 0, st, d_insts));
+void launch_kkt_settle(const Inst* d_insts, int count, cudaStream_t st, int mark) {
+    LQ_LAUNCH(lq_pdl(k_kkt_settle, count, 32, 0, st, d_insts, mark));
 }
 
 }  // namespace lqmpc

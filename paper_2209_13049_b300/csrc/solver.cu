@@ -355,6 +355,10 @@ struct Batch {
     cudaStream_t side = nullptr;    // ctxs[0]'s side stream and events (nullptr: no overlap)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_pending = false;      // head work on the side stream not joined yet
+    // launches of the conjugate-gradient loop graphs' bodies (counted from
+    // the passes the device reports, [FP64 preconditioner])
+    unsigned seen_pass[2] = {0u, 0u};
+    unsigned long long pass_kernels[2] = {0ull, 0ull};
 };
 
 // ---- autotuned launch shapes, keyed by batch signature (count and the
@@ -373,12 +377,23 @@ std::string batch_key(const Batch& b) {
     return k;
 }
 
+static bool env_is(const char* k, char c) {
+    const char* e = getenv(k);
+    return e && e[0] == c;
+}
+
+// KKT solves launched without a host read after each (LQMPC_UNSEEN=0: off).
+static bool unseen_enabled() {
+    static int on = -1;
+    if (on < 0) on = env_is("LQMPC_UNSEEN", '0') ? 0 : 1;
+    return on == 1;
+}
+
 // Off under the per-launch debug modes (they synchronise or record events per
 // launch) or with LQMPC_GRAPH=0.
 bool graphs_enabled() {
     static int on = -1;
     if (on < 0) {
-        auto env_is = [](const char* k, char c) { const char* e = getenv(k); return e && e[0] == c; };
         on = !(env_is("LQMPC_GRAPH", '0') || env_is("LQMPC_PROFILE", '1') || env_is("LQMPC_CHECK", '1'));
     }
     return on == 1;
@@ -430,7 +445,7 @@ void seg_run(const Batch& b, int key, F&& body) {
 // launched) when graphs are off or the graph could not be built; the caller
 // then runs the loop from the host.
 template <class F1, class F2>
-bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, F1&& first, F2&& pass) {
+bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, int slot, F1&& first, F2&& pass) {
     if (!b.gc || !graphs_enabled()) return false;
     GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];
     if (g.bad) return false;
@@ -455,7 +470,7 @@ bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, F1&& first, F2&&
         if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
         if (e == cudaSuccess) {
             first();
-            launch_pcg_more(b.d_insts, b.count, selr, h, cap, 1, b.st);
+            launch_pcg_more(b.d_insts, b.count, selr, h, cap, 1, slot, b.st);
             e = cudaStreamGetCaptureInfo(b.st, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
         }
         cudaGraphNode_t wnode = nullptr;
@@ -482,7 +497,7 @@ bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, F1&& first, F2&&
             e = cudaStreamBeginCaptureToGraph(b.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
                 pass();
-                launch_pcg_more(b.d_insts, b.count, selr, h, cap, 0, b.st);
+                launch_pcg_more(b.d_insts, b.count, selr, h, cap, 0, slot, b.st);
                 cudaGraph_t bg = nullptr;
                 e = cudaStreamEndCapture(b.st, &bg);
             }
@@ -734,6 +749,12 @@ bool host_selected(const Scal& S, int sel) {
 lqmpc_status read_scals(Batch& b) {
     for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
     CK(cudaStreamSynchronize(b.st));
+    const Scal& S0 = *b.ctxs[0]->h_scal;
+    for (int k = 0; k < 2; ++k) {
+        const unsigned now = (unsigned)S0.pcg_pass_total[k];
+        note_launches((int)(b.pass_kernels[k] * (now - b.seen_pass[k])));
+        b.seen_pass[k] = now;
+    }
     return LQMPC_OK;
 }
 
@@ -743,7 +764,7 @@ lqmpc_status read_scals(Batch& b) {
 // flags every second step and stops launching once every unfinished instance
 // has converged or failed; afterwards each h_scal holds the outcome.
 lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int sel = F_NONE,
-                             int budget_lo = -1, int budget_mid = -1) {
+                             int budget_lo = -1, int budget_mid = -1, bool unseen = false) {
     if (budget_lo < 0) budget_lo = refine_max;
     if (budget_mid < 0) budget_mid = refine_max;
     const int selr = sel | F_SKIP_REFINED;
@@ -784,13 +805,11 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     // stops launching once every unfinished instance has converged or failed
     // (the last read leaves each h_scal holding the outcome).
     {
-        const int key = SEG_PCG_LOOP + kp;
-        if (pcg_loop_graph(b, key, selr, (refine_max + 1) / 2, first, [&]() { step(true); step(true); })) {
-            lqmpc_status st = read_scals(b);
-            if (st != LQMPC_OK) return st;
-            const GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];
-            note_launches((int)(g.pass_kernels * (unsigned long long)b.ctxs[0]->h_scal->pcg_loops));
-            return LQMPC_OK;
+        const int key = SEG_PCG_LOOP + kp, slot = prec64 ? 1 : 0;
+        if (pcg_loop_graph(b, key, selr, (refine_max + 1) / 2, slot, first, [&]() { step(true); step(true); })) {
+            b.pass_kernels[slot] = b.gc->segs[2 * key + (b.ff ? 1 : 0)].pass_kernels;
+            if (unseen) return LQMPC_OK;   // the outcome is read with the iteration's end
+            return read_scals(b);
         }
     }
     seg_run(b, SEG_PCG0 + kp, first);
@@ -852,6 +871,33 @@ void write_scal(Batch& b, lqmpc_ctx* c) {
     cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
 }
 
+// Form and factor M in precision p (FP32, FP32X2 or FP64) for the instances
+// `sel` picks, retried with a relative diagonal shift where a pivot fails
+// (an FP64 pivot can fail on rounding when Sigma spans more decades than FP64
+// resolves); a shifted FP64 factor is only a preconditioner, so its solves
+// are refined (polish).  The host reads the instances after each attempt.
+lqmpc_status kkt_form_retried(Batch& b, int p, SyrkTimer* tm, int sel, bool& polish) {
+    const double shifts32[3] = {0.0, 1e-6, 1e-4}, shifts64[3] = {0.0, 1e-12, 1e-9};
+    const double* shifts = p == LQMPC_FP64 ? shifts64 : shifts32;
+    for (int a = 0; a < 3; ++a) {
+        if (a > 0 && p == LQMPC_FP64) polish = true;
+        kkt_form(b, p, tm, shifts[a], sel);
+        join_head(b);
+        lqmpc_status st = read_scals(b);
+        if (st != LQMPC_OK) return st;
+        bool fail = false;
+        for (auto* c : b.ctxs)
+            if (host_selected(*c->h_scal, sel) && c->h_scal->info) fail = true;
+        if (!fail || a == 2) break;
+        for (auto* c : b.ctxs)
+            if (host_selected(*c->h_scal, sel) && c->h_scal->info) {
+                c->h_scal->info = 0;
+                write_scal(b, c);
+            }
+    }
+    return LQMPC_OK;
+}
+
 // Solve M du = b for every unfinished instance, each with its own factor
 // precision (Scal::prec_cur).  Rounds: form and factor M for the instances
 // that need it (all of them unless `formed`; later only the escalated ones),
@@ -867,11 +913,51 @@ void write_scal(Batch& b, lqmpc_ctx* c) {
 // change only the preconditioner: the conjugate gradients with FP64 products
 // still converge to the exact solution.  The other instances keep their
 // precision: one instance's trouble does not move a whole batch to FP64.
-lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* tm, bool& polish) {
+lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* tm, bool& polish,
+                      bool unseen = false) {
     launch_kkt_begin(b.d_insts, b.count, b.st);
     for (auto* c : b.ctxs) c->h_scal->kkt_pending = c->h_scal->done ? 0 : 1;   // the same on the host copy
     const int budget_lo = std::min(o.refine_max, kLowPrecSteps);
     const int budget_mid = o.fallback ? std::min(o.refine_max, kFp32Steps) : o.refine_max;
+    if (unseen) {
+        // One round, read by the host only at the end of the iteration: the
+        // same launches as a round that meets no failing pivot and no
+        // refinement that fails; a solve that does fail is marked on the
+        // device (spec_fail) and its instance's iteration is repeated.
+        int present = 0;
+        for (auto* c : b.ctxs)
+            if (!c->h_scal->done) present |= 1 << c->h_scal->prec_cur;
+        // The factors of the last iterations (FP32X2, FP64) meet failing
+        // pivots often enough to be read and retried at once.
+        if (!formed)
+            for (int p = 0; p < 5; ++p) {
+                if (!((present >> p) & 1)) continue;
+                const int sel = F_PENDING | prec_sel(1 << p);
+                if (p == LQMPC_FP32X2 || p == LQMPC_FP64) {
+                    lqmpc_status st = kkt_form_retried(b, p, tm, sel, polish);
+                    if (st != LQMPC_OK) return st;
+                } else {
+                    kkt_form(b, p, tm, 0.0, sel);
+                }
+            }
+        join_head(b);
+        if (present & 1) {
+            const int sel = F_PENDING | prec_sel(1);
+            if (!polish) kkt_solve_fp64(b, sel);
+            else {
+                lqmpc_status st = kkt_solve_mixed(b, o.refine_max, true, sel, -1, -1, true);
+                if (st != LQMPC_OK) return st;
+            }
+        }
+        if (present & 0x1E) {
+            lqmpc_status st = kkt_solve_mixed(b, o.refine_max, false, F_PENDING | prec_sel(0x1E), budget_lo,
+                                              budget_mid, true);
+            if (st != LQMPC_OK) return st;
+        }
+        launch_kkt_settle(b.d_insts, b.count, b.st, 1);
+        for (auto* c : b.ctxs) c->h_scal->kkt_pending = 0;
+        return LQMPC_OK;
+    }
     for (int round = 0; round < 4; ++round) {
         int present = 0;   // precisions among the pending instances
         for (auto* c : b.ctxs) {
@@ -890,28 +976,8 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
                     kkt_form(b, p, tm, 0.0, sel);
                     continue;
                 }
-                // FP32 and FP64 factors are retried with a relative diagonal
-                // shift (an FP64 pivot can fail on rounding when Sigma spans
-                // more decades than FP64 resolves); a shifted FP64 factor is
-                // only a preconditioner, so its solves are refined.
-                const double shifts32[3] = {0.0, 1e-6, 1e-4}, shifts64[3] = {0.0, 1e-12, 1e-9};
-                const double* shifts = p == LQMPC_FP64 ? shifts64 : shifts32;
-                for (int a = 0; a < 3; ++a) {
-                    if (a > 0 && p == LQMPC_FP64) polish = true;
-                    kkt_form(b, p, tm, shifts[a], sel);
-                    join_head(b);
-                    lqmpc_status st = read_scals(b);
-                    if (st != LQMPC_OK) return st;
-                    bool fail = false;
-                    for (auto* c : b.ctxs)
-                        if (host_selected(*c->h_scal, sel) && c->h_scal->info) fail = true;
-                    if (!fail || a == 2) break;
-                    for (auto* c : b.ctxs)
-                        if (host_selected(*c->h_scal, sel) && c->h_scal->info) {
-                            c->h_scal->info = 0;
-                            write_scal(b, c);
-                        }
-                }
+                lqmpc_status st = kkt_form_retried(b, p, tm, sel, polish);
+                if (st != LQMPC_OK) return st;
             }
         }
         join_head(b);
@@ -934,7 +1000,7 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
         }
         // settle on the device and, from the host copies the solves just read
         // (or that no solve since has changed), the same decision here
-        launch_kkt_settle(b.d_insts, b.count, b.st);
+        launch_kkt_settle(b.d_insts, b.count, b.st, 0);
         for (auto* c : b.ctxs) {
             Scal& S = *c->h_scal;
             if (!S.done && S.kkt_pending && !S.info && (S.prec_cur == LQMPC_FP64 || S.refine_ok)) S.kkt_pending = 0;
@@ -974,7 +1040,13 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         if (st != LQMPC_OK) return st;
     }
     double kkt_ms = 0.0;
-    for (int it = 0; it <= o.max_iter; ++it) {
+    // With graphs the host reads the instance state once per iteration and
+    // launches the KKT solves unseen (see kkt_step); after an iteration in
+    // which some instance's solve failed, that iteration is repeated with the
+    // host looking after every solve.  Repeats do not count against max_iter.
+    bool unseen = graphs_enabled() && unseen_enabled();
+    int repeats = 0;
+    for (int it = 0; it <= o.max_iter + repeats; ++it) {
         SyrkTimer tm;
         // residuals, Sigma, stop test
         // An FP64 formation is costly even for instances it then skips: when
@@ -1010,7 +1082,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         for (auto* c : b.ctxs)
             if (!c->h_scal->done && it > 0 && c->h_scal->mu < 1e3 * o.tol) polish = true;
         // predictor: form and factor M, solve M du_aff = b
-        lqmpc_status s = kkt_step(b, o, false, &tm, polish);
+        lqmpc_status s = kkt_step(b, o, false, &tm, polish, unseen);
         if (s != LQMPC_OK) return s;
         seg_run(b, SEG_PRED_TAIL, [&]() {
             launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
@@ -1022,7 +1094,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             launch_rhs(b.d_insts, b.count, b.max_n, b.st);
         });
         // corrector: same factor
-        s = kkt_step(b, o, true, &tm, polish);
+        s = kkt_step(b, o, true, &tm, polish, unseen);
         if (s != LQMPC_OK) return s;
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
@@ -1040,16 +1112,31 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             c0->t_cc += ms; c0->n_cc++;
             if (tm.cc64) { c0->t_cc64 += ms; c0->n_cc64++; }
         }
-        bool all_done = true;
+        bool all_done = true, failed = false;
         for (auto* c : b.ctxs) {
             if (c->h_scal->err) return LQMPC_ERR_TIMEOUT;
             if (!c->h_scal->done) all_done = false;
+            if (!c->h_scal->done && c->h_scal->spec_fail) failed = true;
         }
+        if (getenv("LQMPC_DEBUG"))
+            for (auto* c : b.ctxs) {
+                const Scal& S = *c->h_scal;
+                fprintf(stderr, "lqmpc it %d%s: iter %d prec %d spec_fail %d info %d refine ok/fail %d/%d iter_steps %d pending %d fallbacks %d mu %.3e\n",
+                        it, unseen ? " (unseen)" : "", S.iter, S.prec_cur, S.spec_fail, S.info, S.refine_ok, S.refine_fail,
+                        S.refine_iter, S.kkt_pending, S.fallbacks, S.mu);
+            }
         if (all_done) break;
+        // An instance whose solve failed unseen repeats the iteration (its
+        // iterate was left as it was) with the host looking after every
+        // solve: the failing round then runs again and the escalation or the
+        // shifted retries follow as without the unseen rounds, so the results
+        // are the same.
+        if (unseen && failed) ++repeats;
+        unseen = graphs_enabled() && unseen_enabled() && !failed;
         // an FP32 instance whose solves grew costly moves on to the two-level tier
         for (auto* c : b.ctxs) {
             Scal& S = *c->h_scal;
-            if (o.fallback && !S.done && S.prec_cur == LQMPC_FP32 && S.refine_iter > kFp32IterSteps) {
+            if (o.fallback && !S.done && !S.spec_fail && S.prec_cur == LQMPC_FP32 && S.refine_iter > kFp32IterSteps) {
                 S.prec_cur = LQMPC_FP32X2;
                 S.fallbacks += 1;
                 write_scal(b, c);
