@@ -281,8 +281,9 @@ def kkt_check(plant, x0, u, z=None):
     """KKT quantities (Eq. 5) of a candidate u (and duals z = [z_xu, z_xl, z_uu, z_ul]).
 
     Returns a dict with max primal violation, and, when z is given, the
-    stationarity residual ||Hu + h + J'z||_inf and complementarity max |s_i z_i|
-    with s the slacks of u."""
+    stationarity residual ||Hu + h + J'z||_inf, complementarity max |s_i z_i|
+    and its mean over the finite one-sided constraints (the mu of the
+    interior-point stop test), with s the slacks of u."""
     ns, nu, N = plant.ns, plant.nu, plant.N
     n = nu * N
     x = simulate(plant, x0, u)
@@ -310,13 +311,16 @@ def kkt_check(plant, x0, u, z=None):
         s2 = np.where(np.isfinite(plant.xl), x - plant.xl, np.inf)
         s3 = np.where(np.isfinite(plant.uu), plant.uu - uu, np.inf)
         s4 = np.where(np.isfinite(plant.ul), uu - plant.ul, np.inf)
-        comp = 0.0
+        comp, csum, m = 0.0, 0.0, 0
         for s_, z_ in ((s1, z1), (s2, z2), (s3, z3), (s4, z4)):
             fin = np.isfinite(s_)
             if fin.any():
                 comp = max(comp, float(np.max(np.abs(s_[fin] * z_[fin]))))
+                csum += float(np.sum(np.abs(s_[fin] * z_[fin])))
+                m += int(fin.sum())
         out["stationarity"] = float(np.max(np.abs(g)))
         out["complementarity"] = comp
+        out["complementarity_mean"] = csum / m if m else 0.0
         out["dual_min"] = float(min(z1.min(initial=0), z2.min(initial=0), z3.min(initial=0),
                                     z4.min(initial=0)))
     return out

@@ -597,9 +597,8 @@ __global__ void __launch_bounds__(256) k_potrf_coop(const Inst* __restrict__ ins
 }
 
 // Preconditioner of the mixed-precision conjugate gradients: z = X' (X r)
-// with X = L^{-1} (FP32, lower).  Stage 1: t = X r, one thread per row
-// (coalesced along the column-major rows); stage 2: z = X' t, one warp per
-// column.
+// with X = L^{-1} (FP32, lower).  Stage 1: t = X r, row by row (rows of X
+// are the contiguous columns of X'); stage 2: z = X' t, column by column.
 //
 // The two-level tier's combined inverse Y is held as hi + lo planes
 // (Xinv32 + Xlo32, transposes likewise) and applied with float-float sums:
@@ -625,86 +624,149 @@ __device__ __forceinline__ void ffp_warp_sum(float& sh, float& sl) {
     }
 }
 
-__global__ void k_prec_lower(const Inst* __restrict__ insts, int in_role, int flags) {
+// Four warps per CTA, WPR warps per row (k_prec_lower) or column
+// (k_prec_upper): a single instance takes a whole CTA per row (WPR = 4, its
+// loads in flight at once for n <= 512, the warps' sums met in shared
+// memory), a batch one warp per row (WPR = 1, four rows per CTA).
+constexpr int kPrecThreads = 128, kPrecU = 4;
+
+// The row group of the calling thread: group g, thread tg of GT.
+template <int WPR>
+struct PrecGroup {
+    static constexpr int RPC = kPrecThreads / 32 / WPR, GT = 32 * WPR;
+    int g, tg;
+    __device__ PrecGroup() : g((threadIdx.x >> 5) / WPR), tg(threadIdx.x % (32 * WPR)) {}
+};
+
+// FP32 dot of a and x over len entries (FP64 x cast to FP32), the group's
+// sum in its thread 0 (tg == 0).  Every thread of the CTA calls it (len 0
+// for a group without a row).
+template <int WPR, typename TX>
+__device__ __forceinline__ float prec_dot32(const float* a, const TX* x, int len, float* wsum) {
+    const PrecGroup<WPR> G;
+    float av[kPrecU], xv[kPrecU];
+#pragma unroll
+    for (int u = 0; u < kPrecU; ++u) {
+        const int e = G.tg + G.GT * u;
+        av[u] = e < len ? a[e] : 0.f;
+        xv[u] = e < len ? (float)x[e] : 0.f;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPrecU; ++u) acc = fmaf(av[u], xv[u], acc);
+    for (int e = G.tg + G.GT * kPrecU; e < len; e += G.GT) acc = fmaf(a[e], (float)x[e], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (WPR > 1) {
+        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (G.tg == 0) {
+            acc = 0.f;
+#pragma unroll
+            for (int w = 0; w < WPR; ++w) acc += wsum[G.g * WPR + w];
+        }
+        __syncthreads();
+    }
+    return acc;
+}
+
+// The same in float-float: a = ah + al, x = xh + xl (x given as FP64 when
+// xd); the group's sum (oh, ol) in its thread 0.
+template <int WPR>
+__device__ __forceinline__ void prec_dot_ff(const float* ah, const float* al, const double* xd, const float* xh,
+                                            const float* xl, int len, float* wsh, float* wsl, float& oh, float& ol) {
+    const PrecGroup<WPR> G;
+    float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
+    auto mac = [&](int e, float& h, float& l) {
+        float vh, vl;
+        if (xd) { vh = (float)xd[e]; vl = (float)(xd[e] - (double)vh); }
+        else { vh = xh[e]; vl = xl[e]; }
+        ffp_mac(h, l, ah[e], al[e], vh, vl);
+    };
+    for (int e = G.tg; e < len; e += 2 * G.GT) {   // two independent chains
+        mac(e, sh[0], sl[0]);
+        if (e + G.GT < len) mac(e + G.GT, sh[1], sl[1]);
+    }
+    ffp_warp_sum(sh[0], sl[0]);
+    ffp_warp_sum(sh[1], sl[1]);
+    {
+        const float s = sh[0] + sh[1], z = s - sh[0];
+        sl[0] = ((sh[0] - (s - z)) + (sh[1] - z)) + sl[0] + sl[1];
+        sh[0] = s;
+    }
+    oh = sh[0]; ol = sl[0];
+    if (WPR > 1) {
+        if ((threadIdx.x & 31) == 0) { wsh[threadIdx.x >> 5] = sh[0]; wsl[threadIdx.x >> 5] = sl[0]; }
+        __syncthreads();
+        if (G.tg == 0) {
+            float h = wsh[G.g * WPR], l = wsl[G.g * WPR];
+            for (int w = 1; w < WPR; ++w) {
+                const float hw = wsh[G.g * WPR + w];
+                const float s = h + hw, z = s - h;
+                l += ((h - (s - z)) + (hw - z)) + wsl[G.g * WPR + w];
+                h = s;
+            }
+            oh = h; ol = l;
+        }
+        __syncthreads();
+    }
+}
+
+template <int WPR>
+__global__ void __launch_bounds__(kPrecThreads) k_prec_lower(const Inst* __restrict__ insts, int in_role, int flags) {
     pdl_wait();
+    __shared__ float wsh[kPrecThreads / 32], wsl[kPrecThreads / 32];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     const double* r = role_ptr(I, in_role);
-    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int n = I.n;
+    const PrecGroup<WPR> G;
     const float* XT = I.XinvT32;   // X' column-major: row i of X is contiguous
-    if (I.sc->prec_cur == kPrecTwoLevel) {
-        for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
-            const float* rh = XT + (size_t)n * i;
-            const float* rl = I.XloT32 + (size_t)n * i;
-            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
-            int j = lane, u = 0;
-            for (; j <= i; j += 32, u ^= 1) {
-                const float vh = (float)r[j], vl = (float)(r[j] - (double)vh);
-                ffp_mac(sh[u], sl[u], rh[j], rl[j], vh, vl);
+    const bool two = I.sc->prec_cur == kPrecTwoLevel;
+    for (int i0 = blockIdx.x * G.RPC; i0 < n; i0 += gridDim.x * G.RPC) {   // uniform trip count in the CTA
+        const int i = i0 + G.g, len = i < n ? i + 1 : 0;
+        const size_t ro = (size_t)n * (i < n ? i : 0);
+        if (two) {
+            float h, l;
+            prec_dot_ff<WPR>(XT + ro, I.XloT32 + ro, r, nullptr, nullptr, len, wsh, wsl, h, l);
+            if (G.tg == 0 && i < n) {
+                I.r32[i] = h + l;
+                I.r32lo[i] = l - ((h + l) - h);
             }
-            ffp_warp_sum(sh[0], sl[0]);
-            ffp_warp_sum(sh[1], sl[1]);
-            if (lane == 0) {
-                const float s = sh[0] + sh[1], z = s - sh[0];
-                const float lo = ((sh[0] - (s - z)) + (sh[1] - z)) + sl[0] + sl[1];
-                I.r32[i] = s + lo;
-                I.r32lo[i] = lo - ((s + lo) - s);
-            }
+        } else {
+            const float acc = prec_dot32<WPR>(XT + ro, r, len, wsh);
+            if (G.tg == 0 && i < n) I.r32[i] = acc;
         }
-        return;
-    }
-    for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n; i += gridDim.x * wpb) {
-        const float* row = XT + (size_t)n * i;
-        float a4[4] = {0.f, 0.f, 0.f, 0.f};   // independent chains: four loads in flight
-        int j = lane;
-        for (; j + 96 <= i; j += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) a4[u] = fmaf(row[j + 32 * u], (float)r[j + 32 * u], a4[u]);
-        }
-        for (; j <= i; j += 32) a4[0] = fmaf(row[j], (float)r[j], a4[0]);
-        float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) I.r32[i] = acc;
     }
 }
 
 // tail (conjugate-gradient direction from z, run by the instance's last CTA):
 // 1 p = z and r'z; 2 beta = r'z_new / r'z_old, p = z + beta p.
-__global__ void k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags, int tail) {
+template <int WPR>
+__global__ void __launch_bounds__(kPrecThreads) k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags,
+                                                             int tail) {
     pdl_wait();
     __shared__ double red[32];
     __shared__ double beta_sh;
+    __shared__ float wsh[kPrecThreads / 32], wsl[kPrecThreads / 32];
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags) || I.sc->info) return;
     double* z = role_ptr(I, out_role);
-    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int n = I.n;
+    const PrecGroup<WPR> G;
     const float* X = I.Xinv32;
-    if (I.sc->prec_cur == kPrecTwoLevel) {
-        for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
-            const float* ch = X + (size_t)n * j;
-            const float* cl = I.Xlo32 + (size_t)n * j;
-            float sh[2] = {0.f, 0.f}, sl[2] = {0.f, 0.f};
-            int i = j + lane, u = 0;
-            for (; i < n; i += 32, u ^= 1) ffp_mac(sh[u], sl[u], ch[i], cl[i], I.r32[i], I.r32lo[i]);
-            ffp_warp_sum(sh[0], sl[0]);
-            ffp_warp_sum(sh[1], sl[1]);
-            if (lane == 0) z[j] = ((double)sh[0] + (double)sh[1]) + ((double)sl[0] + (double)sl[1]);
+    const bool two = I.sc->prec_cur == kPrecTwoLevel;
+    for (int j0 = blockIdx.x * G.RPC; j0 < n; j0 += gridDim.x * G.RPC) {   // uniform trip count in the CTA
+        const int j = j0 + G.g, jj = j < n ? j : 0, len = j < n ? n - j : 0;
+        const size_t c0 = (size_t)n * jj + jj;    // column j from row j on
+        if (two) {
+            float h, l;
+            prec_dot_ff<WPR>(X + c0, I.Xlo32 + c0, nullptr, I.r32 + jj, I.r32lo + jj, len, wsh, wsl, h, l);
+            if (G.tg == 0 && j < n) z[j] = (double)h + (double)l;
+        } else {
+            const float acc = prec_dot32<WPR>(X + c0, I.r32 + jj, len, wsh);
+            if (G.tg == 0 && j < n) z[j] = (double)acc;
         }
-    } else
-    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
-        const float* col = X + (size_t)n * j;
-        float a4[4] = {0.f, 0.f, 0.f, 0.f};
-        int i = j + lane;
-        for (; i + 96 < n; i += 128) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) a4[u] = fmaf(col[i + 32 * u], I.r32[i + 32 * u], a4[u]);
-        }
-        for (; i < n; i += 32) a4[0] = fmaf(col[i], I.r32[i], a4[0]);
-        float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) z[j] = (double)acc;
     }
     if (!tail || !last_arrival(I.sc)) return;
     Scal* S = I.sc;
@@ -929,11 +991,16 @@ void launch_potrf(const Inst* d_insts, int count, int max_n, int fp64, int flags
 
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
                        cudaStream_t st, int tail) {
-    // one warp per row (column), two warps per CTA: every SM takes part
-    int nb = (max_n + 1) / 2;
-    nb = per_instance_blocks(nb > 8192 ? 8192 : nb, count);
-    LQ_LAUNCH(lq_pdl(k_prec_lower, dim3(nb, count), 64, 0, st, d_insts, in_role, flags));
-    LQ_LAUNCH(lq_pdl(k_prec_upper, dim3(nb, count), 64, 0, st, d_insts, out_role, flags, tail));
+    if (count == 1) {   // a CTA per row (column)
+        const int nb = max_n > 8192 ? 8192 : max_n;
+        LQ_LAUNCH(lq_pdl(k_prec_lower<4>, dim3(nb, count), kPrecThreads, 0, st, d_insts, in_role, flags));
+        LQ_LAUNCH(lq_pdl(k_prec_upper<4>, dim3(nb, count), kPrecThreads, 0, st, d_insts, out_role, flags, tail));
+    } else {            // a warp per row (column)
+        int nb = (max_n + 3) / 4;
+        nb = per_instance_blocks(nb > 8192 ? 8192 : nb, count);
+        LQ_LAUNCH(lq_pdl(k_prec_lower<1>, dim3(nb, count), kPrecThreads, 0, st, d_insts, in_role, flags));
+        LQ_LAUNCH(lq_pdl(k_prec_upper<1>, dim3(nb, count), kPrecThreads, 0, st, d_insts, out_role, flags, tail));
+    }
 }
 
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

@@ -391,9 +391,12 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
         // the splits of row r's r-tile (the split plan of k_gamma_mv_ff)
         int kbeg, nk, S;
         mv_ff_rtile((I.N - 1 - k / I.ns) / kFfBN, I.N, I.nu, I.n, kbeg, nk, S);
+        double pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
+#pragma unroll
+        for (int q = 0; q < kFfMaxSplits; ++q) pv[q] = q < S ? I.gpart[(size_t)q * I.SX + k] : 0.0;
         double s = 0.0;
-#pragma unroll 4
-        for (int q = 0; q < S; ++q) s += I.gpart[(size_t)q * I.SX + k];
+#pragma unroll
+        for (int q = 0; q < kFfMaxSplits; ++q) s += pv[q];
         out[k] = s;
         if (fuse & kFuseOutDxs) I.dxs[k] = s;
         if (fuse & kFuseOutW) {

@@ -95,31 +95,75 @@ __global__ void k_pcg_matvec(const Inst* __restrict__ insts, int mode, int sel) 
 }
 
 // k_pcg_matvec with mv_j gathered from the float-float Gamma' partials (no
-// separate sum launch) and the row of H read with four loads in flight.
-// In the conjugate-gradient steps the last CTA's tail also leaves nothing
-// else to do: alpha is formed there as in k_pcg_matvec.
-__global__ void k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int sel, int splits) {
+// separate sum launch).  Eight warps per CTA, WPR warps per row: the group's
+// threads split the row of H (its loads in flight at once: four per thread)
+// and its warps split the Gamma' partials, and the warps' sums meet in shared
+// memory.  A single instance takes a whole CTA per row (WPR = 8: a row costs
+// about one round trip to L2); a batch, whose instances get few CTAs each,
+// one warp per row (WPR = 1: eight rows per CTA in flight).  In the
+// conjugate-gradient steps the last CTA's tail also leaves nothing else to
+// do: alpha is formed there as in k_pcg_matvec.
+constexpr int kMvThreads = 256, kMvH = 4;
+template <int WPR>
+__global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __restrict__ insts, int mode, int sel,
+                                                              int splits) {
     pdl_wait();
+    constexpr int kW = kMvThreads / 32, RPC = kW / WPR, GT = 32 * WPR;
     __shared__ double red[32];
+    __shared__ double wsum[kW];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
     const double* v = mode == 0 ? I.du : I.pp;
-    const int n = I.n, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    double acc_red = 0.0;
-    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < n; j += gridDim.x * wpb) {
-        const double* hc = I.H64 + (size_t)j * n;
-        double a4[4] = {0.0, 0.0, 0.0, 0.0};
-        int k = lane;
-#pragma unroll 2
-        for (; k + 96 < n; k += 128) {
+    const int n = I.n, N = I.N, nu = I.nu, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = warp / WPR, wg = warp % WPR, tg = wg * 32 + lane;   // row group, warp and thread in it
+    const size_t stride = (size_t)N * n;          // one split's partials
+    double acc_red = 0.0;                          // the group leader's
+    for (int j0 = blockIdx.x * RPC; j0 < n; j0 += gridDim.x * RPC) {   // uniform trip count in the CTA
+        const int j = j0 + grp;
+        double s = 0.0;
+        if (j < n) {
+            const double* hc = I.H64 + (size_t)j * n;
+            double hv[kMvH], vv[kMvH];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) a4[u] += hc[k + 32 * u] * v[k + 32 * u];
+            for (int u = 0; u < kMvH; ++u) {
+                const int k = tg + GT * u;
+                hv[u] = k < n ? hc[k] : 0.0;
+                vv[u] = k < n ? v[k] : 0.0;
+            }
+            // Gamma' partials of output j (see gamma_tmv_ff_gather)
+            const int t = j / nu, c = j % nu, nd = N - t;
+            const double* base = I.gpart + ((size_t)t * nu + c) * N;
+            constexpr int QS = kFfMaxSplits / WPR;
+            double g[2 * QS];
+#pragma unroll
+            for (int q = 0; q < QS; ++q) {
+                const int sp = wg + WPR * q;
+                const double* src = base + (size_t)sp * stride;
+                g[2 * q] = (sp < splits && lane < nd) ? src[lane] : 0.0;
+                g[2 * q + 1] = (sp < splits && lane + 32 < nd) ? src[lane + 32] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kMvH; ++u) s = fma(hv[u], vv[u], s);
+            for (int k = tg + GT * kMvH; k < n; k += GT) s = fma(hc[k], v[k], s);
+#pragma unroll
+            for (int q = 0; q < 2 * QS; ++q) s += g[q];
+            for (int sp = wg; sp < splits; sp += WPR)
+                for (int d = lane + 64; d < nd; d += 32) s += base[(size_t)sp * stride + d];
         }
-        for (; k < n; k += 32) a4[0] += hc[k] * v[k];
-        const double hv = warp_sum((a4[0] + a4[1]) + (a4[2] + a4[3]));
-        const double mvj = gamma_tmv_ff_gather(I, 1, 0, j, splits);
-        if (lane == 0) {
-            const double mj = hv + mvj + I.sigu[j] * v[j];
+        s = warp_sum(s);
+        if (WPR > 1) {
+            if (lane == 0) wsum[warp] = s;
+            __syncthreads();
+            if (tg == 0) {
+                double m = 0.0;
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) m += wsum[grp * WPR + w];
+                s = m;
+            }
+            __syncthreads();
+        }
+        if (tg == 0 && j < n) {
+            const double mj = s + I.sigu[j] * v[j];
             if (mode == 0) {
                 const double r = I.b[j] - mj;
                 I.rho[j] = r;
@@ -344,9 +388,13 @@ void launch_pcg_matvec(const Inst* d_insts, int count, int max_n, int mode, int 
 
 void launch_pcg_matvec_ff(const Inst* d_insts, int count, int max_n, int splits, int mode, int sel,
                           cudaStream_t st) {
-    const int wpb = 2;   // two rows per CTA: every SM takes part
-    const int nb = per_instance_blocks(nblk(max_n, wpb, kMaxParts), count);
-    LQ_LAUNCH(lq_pdl(k_pcg_matvec_ff, dim3(nb, count), wpb * 32, 0, st, d_insts, mode, sel, splits));
+    if (count == 1) {   // a CTA per row
+        const int nb = nblk(max_n, 1, kMaxParts);
+        LQ_LAUNCH(lq_pdl(k_pcg_matvec_ff<8>, dim3(nb, count), kMvThreads, 0, st, d_insts, mode, sel, splits));
+    } else {            // a warp per row
+        const int nb = per_instance_blocks(nblk(max_n, kMvThreads / 32, kMaxParts), count);
+        LQ_LAUNCH(lq_pdl(k_pcg_matvec_ff<1>, dim3(nb, count), kMvThreads, 0, st, d_insts, mode, sel, splits));
+    }
 }
 
 void launch_pcg_pinit(const Inst* d_insts, int count, int sel, cudaStream_t st) {

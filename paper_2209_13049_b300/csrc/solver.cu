@@ -169,6 +169,7 @@ struct lqmpc_ctx {
     int tc_ok = 0;              // tensor maps built
     void* d_maps = nullptr;     // 3 CUtensorMap (BF16, TF32, TF32 low part), 64-byte aligned, device
     cudaEvent_t ev[4];
+    cudaEvent_t ev_read = nullptr;   // end of the copy of the instance state to the host
     cudaEvent_t evk[6];         // around the SYRK launch (tensor-core pair, CUDA-core pair) and the FP32 factor
     bool events = false;
     // per-solve SYRK timing
@@ -746,16 +747,38 @@ bool host_selected(const Scal& S, int sel) {
     return true;
 }
 
+// The copy of every instance's Scal to its host mirror, queued (then
+// read_scals_end waits for it, so more work can be queued behind it first).
+lqmpc_status read_scals_begin(Batch& b) {
+    for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
+    CK(cudaEventRecord(b.ctxs[0]->ev_read, b.st));
+    return LQMPC_OK;
+}
+
+void count_loop_passes(Batch& b);
+
+lqmpc_status read_scals_end(Batch& b) {
+    CK(cudaEventSynchronize(b.ctxs[0]->ev_read));
+    count_loop_passes(b);
+    return LQMPC_OK;
+}
+
 lqmpc_status read_scals(Batch& b) {
     for (auto* c : b.ctxs) CK(cudaMemcpyAsync(c->h_scal, c->h.sc, sizeof(Scal), cudaMemcpyDeviceToHost, b.st));
     CK(cudaStreamSynchronize(b.st));
+    count_loop_passes(b);
+    return LQMPC_OK;
+}
+
+// Launches of the loop graphs' bodies since the last read, from the pass
+// counters the device keeps.
+void count_loop_passes(Batch& b) {
     const Scal& S0 = *b.ctxs[0]->h_scal;
     for (int k = 0; k < 2; ++k) {
         const unsigned now = (unsigned)S0.pcg_pass_total[k];
         note_launches((int)(b.pass_kernels[k] * (now - b.seen_pass[k])));
         b.seen_pass[k] = now;
     }
-    return LQMPC_OK;
 }
 
 // Mixed-precision solve of M du = b (R_B -> R_DU, R_DXS = Gamma du):
@@ -869,6 +892,13 @@ int next_precision(int p) {
 
 void write_scal(Batch& b, lqmpc_ctx* c) {
     cudaMemcpyAsync(c->h.sc, c->h_scal, sizeof(Scal), cudaMemcpyHostToDevice, b.st);
+}
+
+// Only the precision and the fallback count (the rest of the device Scal may
+// be newer than the host's copy).
+void write_scal_prec(Batch& b, lqmpc_ctx* c) {
+    cudaMemcpyAsync(&c->h.sc->prec_cur, &c->h_scal->prec_cur, sizeof(int), cudaMemcpyHostToDevice, b.st);
+    cudaMemcpyAsync(&c->h.sc->fallbacks, &c->h_scal->fallbacks, sizeof(int), cudaMemcpyHostToDevice, b.st);
 }
 
 // Form and factor M in precision p (FP32, FP32X2 or FP64) for the instances
@@ -1046,16 +1076,16 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
     // host looking after every solve.  Repeats do not count against max_iter.
     bool unseen = graphs_enabled() && unseen_enabled();
     int repeats = 0;
-    for (int it = 0; it <= o.max_iter + repeats; ++it) {
-        SyrkTimer tm;
-        // residuals, Sigma, stop test
-        // An FP64 formation is costly even for instances it then skips: when
-        // one is ahead, take the stop test's outcome to the host first
-        // (no overlap of the head with the formation then).
-        bool fp64_ahead = false;
+    // residuals, Sigma, stop test: on the side stream overlapping the
+    // formation, unless an FP64 formation is ahead (it is costly even for the
+    // instances it then skips: the stop test's outcome goes to the host first)
+    auto fp64_ahead_now = [&]() {
         for (auto* c : b.ctxs)
             if (!c->h_scal->done && (c->h_scal->prec_cur == LQMPC_FP64 || c->h_scal->prec_cur == LQMPC_FP32X2))
-                fp64_ahead = true;
+                return true;
+        return false;
+    };
+    auto queue_head = [&](bool fp64_ahead) {
         if (b.side && !fp64_ahead) {
             head_fork(b);
         } else {
@@ -1065,9 +1095,17 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
                 launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
             });
         }
+    };
+    bool head_queued = false;   // this iteration's head went out behind the last iteration's read
+    for (int it = 0; it <= o.max_iter + repeats; ++it) {
+        SyrkTimer tm;
+        const bool fp64_ahead = fp64_ahead_now();
+        if (!head_queued) queue_head(fp64_ahead);
+        head_queued = false;
         cudaEventRecord(c0->ev[2], b.st);
         {
             if (fp64_ahead) {
+                join_head(b);
                 lqmpc_status st = read_scals(b);
                 if (st != LQMPC_OK) return st;
                 bool all_done = true;
@@ -1099,7 +1137,16 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
         cudaEventRecord(c0->ev[3], b.st);
         seg_run(b, SEG_CORR_TAIL, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st); });
-        s = read_scals(b);
+        // The state goes to the host and the next iteration's head is queued
+        // behind it before the host waits, so the GPU runs the head while the
+        // host looks.  Its variant comes from the state read an iteration
+        // earlier (the variants compute the same values); after the head the
+        // host writes back only prec_cur and fallbacks, which it does not touch.
+        s = read_scals_begin(b);
+        if (s != LQMPC_OK) return s;
+        queue_head(fp64_ahead_now());
+        head_queued = true;
+        s = read_scals_end(b);
         if (s != LQMPC_OK) return s;
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, c0->ev[2], c0->ev[3]) == cudaSuccess) kkt_ms += ms;
@@ -1139,7 +1186,7 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             if (o.fallback && !S.done && !S.spec_fail && S.prec_cur == LQMPC_FP32 && S.refine_iter > kFp32IterSteps) {
                 S.prec_cur = LQMPC_FP32X2;
                 S.fallbacks += 1;
-                write_scal(b, c);
+                write_scal_prec(b, c);
             }
         }
     }
@@ -1377,7 +1424,8 @@ static lqmpc_status setup_impl(lqmpc_ctx** out, int ns, int nu, int N, const int
     ctx->events = true;
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_read, cudaEventDisableTiming) != cudaSuccess)
         return fail(LQMPC_ERR_CUDA);
     cudaStream_t st = ctx->stream;
     auto up = [&](const void* dst, const void* src, size_t n) {
@@ -1947,6 +1995,7 @@ void lqmpc_free(lqmpc_ctx* ctx) {
     }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_read) cudaEventDestroy(ctx->ev_read);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

@@ -123,7 +123,8 @@ def batch256():
 def test_batch256_fp32_matches_oracle_on_sampled_instances(batch256):
     """The whole uneven 256-instance batch in the FP32 tier, autotuned, as
     bench.py runs it; the sampled instances against the oracle at the same
-    1e-8 stop and both at 1e-11."""
+    1e-8 stop, and at 1e-11 within the degenerate band plus the optimality
+    conditions."""
     inst, sample, g = batch256
     solvers = [binding.Solver(p, precision="fp32") for p, _ in inst]
     x0s = [x for _, x in inst]
@@ -138,7 +139,22 @@ def test_batch256_fp32_matches_oracle_on_sampled_instances(batch256):
     us12, stats12, code = binding.solve_batch(solvers, x0s, check=False)
     for k in sample:
         assert stats12[k]["status"] == 0
-        assert rel(us12[k], g[f"i{k}_u12"]) <= 1e-6, k
+        # At 1e-11 the batch's instances need not follow the oracle's iterates
+        # (rounding in the batched kernels can change where a refinement
+        # escalates), and on degenerate instances two valid stops differ by
+        # O(sqrt(tol)): instance 0 (20 x 20 plate) converges, in every tier
+        # pushed further, to a point 4.4e-6 from the oracle's own 1e-11
+        # stop.  So the stop is compared within 3 sqrt(tol), and the result
+        # must satisfy the optimality conditions on its own: the stop test
+        # bounds the mean complementarity product (mu <= tol), one product
+        # can be up to m times that.
+        assert rel(us12[k], g[f"i{k}_u12"]) <= 3.0 * np.sqrt(1e-11), k
+        p, x0 = inst[k]
+        kc = oracle.kkt_check(p, x0, us12[k], solvers[k].get_duals())
+        assert kc["primal_violation"] <= 1e-9, k
+        assert kc["dual_min"] >= 0.0, k
+        assert kc["stationarity"] <= 1e-8, k
+        assert kc["complementarity_mean"] <= 1.01e-11, k
 
 
 def test_batch256_sampled_instances_fp64_single_solves(batch256):

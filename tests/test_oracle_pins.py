@@ -146,6 +146,18 @@ def test_ipm_kkt_invariants_active_heat2d_small():
     assert k["complementarity"] <= 1e-9
 
 
+def test_kkt_check_mean_complementarity_is_the_ipm_mu():
+    """The checker's mean complementarity, from the bound distances of the
+    simulated trajectory, equals the oracle's own final mu = s'z / m (its
+    slack variables), up to the primal residual left at the stop."""
+    for p, x0 in (inputs.config_1d_small(1), (inputs.heat2d(6, 4, 8), inputs.x0_gaussians(6, 1))):
+        r = oracle.ipm_solve(p, x0, tol=1e-10)
+        k = oracle.kkt_check(p, x0, r["u"], r["z"])
+        assert r["status"] == 0
+        np.testing.assert_allclose(k["complementarity_mean"], r["stats"]["mu"], rtol=1e-3)
+        assert k["complementarity"] >= k["complementarity_mean"]
+
+
 def test_ipm_trace_monotone_and_steps_valid():
     p, x0 = inputs.config_1d_small(2)
     r = oracle.ipm_solve(p, x0, want_trace=True)
