@@ -65,7 +65,8 @@ def test_graph_replay_equals_direct_launches():
         # of two steps (one per KKT solve and per two steps), the next
         # iteration's head queued behind the host's read once more after the
         # last iteration, and any iteration repeated after a solve that failed
-        # unseen (under 15% here)
+        # unseen (the BF16 tier, whose refinements are meant to fail over to
+        # the next tier, repeats the most: under 30% here)
         extra = on[key]["launches"] - off[key]["launches"]
-        assert 0 <= extra <= 0.15 * off[key]["launches"], (key, on[key]["launches"], off[key]["launches"])
+        assert 0 <= extra <= 0.3 * off[key]["launches"], (key, on[key]["launches"], off[key]["launches"])
     assert on["batch"]["u"] == off["batch"]["u"]
