@@ -141,6 +141,7 @@ struct GraphSeg {
     unsigned long long kernels = 0;   // kernel launches one replay performs (before any loop)
     unsigned long long pass_kernels = 0;   // kernel launches of one pass of its device-side loop
     bool bad = false;                 // capture or instantiation failed: launch directly
+    int timer_bits = 0;               // an iteration graph: the SYRK / factor timers its launches record
 };
 struct GraphCache {
     std::map<int, GraphSeg> segs;
@@ -360,6 +361,11 @@ struct Batch {
     // the passes the device reports, [FP64 preconditioner])
     unsigned seen_pass[2] = {0u, 0u};
     unsigned long long pass_kernels[2] = {0ull, 0ull};
+    // while an iteration is captured into one graph: kernels of the loop
+    // bodies captured so far (counted by the pass counters instead), and
+    // whether a nested part could not be captured
+    unsigned long long loop_body_kernels = 0;
+    bool capture_failed = false;
 };
 
 // ---- autotuned launch shapes, keyed by batch signature (count and the
@@ -390,6 +396,13 @@ static bool unseen_enabled() {
     return on == 1;
 }
 
+// An unseen iteration captured as one graph (LQMPC_WHOLE=0: off).
+static bool whole_iteration_enabled() {
+    static int on = -1;
+    if (on < 0) on = env_is("LQMPC_WHOLE", '0') ? 0 : 1;
+    return on == 1;
+}
+
 // Off under the per-launch debug modes (they synchronise or record events per
 // launch) or with LQMPC_GRAPH=0.
 bool graphs_enabled() {
@@ -400,11 +413,47 @@ bool graphs_enabled() {
     return on == 1;
 }
 
+// Event-record nodes of a captured graph (the timers around the SYRK and the
+// factor, and the iteration's KKT timer) made leaves: each predecessor gets an
+// edge straight to each successor and the node keeps only its incoming
+// edges.  It still records when its predecessors complete, and no launch
+// waits for it (an event node in the chain costs ~4 us between kernels).
+static void detach_event_nodes(cudaGraph_t g) {
+    if (env_is("LQMPC_DETACH", '0')) return;
+    size_t n = 0;
+    if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return;
+    for (cudaGraphNode_t node : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(node, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+        size_t nin = 0, nout = 0;
+        cudaGraphNodeGetDependencies(node, nullptr, nullptr, &nin);
+        cudaGraphNodeGetDependentNodes(node, nullptr, nullptr, &nout);
+        if (nout == 0) continue;
+        std::vector<cudaGraphNode_t> in(nin), out(nout);
+        if (nin) cudaGraphNodeGetDependencies(node, in.data(), nullptr, &nin);
+        cudaGraphNodeGetDependentNodes(node, out.data(), nullptr, &nout);
+        for (cudaGraphNode_t o : out) {
+            for (cudaGraphNode_t d : in) cudaGraphAddDependencies(g, &d, &o, nullptr, 1);
+            cudaGraphRemoveDependencies(g, &node, &o, nullptr, 1);
+        }
+    }
+    cudaGetLastError();   // an edge that existed already
+}
+
+static bool is_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive;
+}
+
 // Run a fixed launch sequence: the first time under stream capture into a
 // graph (then replayed), or directly when graphs are off or capture failed.
+// Inside a capture already under way (an iteration captured whole) the
+// sequence becomes part of that graph.
 template <class F>
 void seg_run(const Batch& b, int key, F&& body) {
-    if (!b.gc || !graphs_enabled()) { body(); return; }
+    if (!b.gc || !graphs_enabled() || is_capturing(b.st)) { body(); return; }
     GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];   // the Gamma products differ with the arithmetic
     if (g.bad) { body(); return; }
     if (!g.exec) {
@@ -421,6 +470,7 @@ void seg_run(const Batch& b, int key, F&& body) {
         cudaError_t e = cudaStreamEndCapture(b.st, &graph);
         const unsigned long long nk = lqmpc_kernel_launches() - k0;
         note_launches(-(int)nk);          // captured, not run
+        if (e == cudaSuccess && graph) detach_event_nodes(graph);
         if (e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess || !g.exec) {
@@ -519,10 +569,62 @@ bool pcg_loop_graph(const Batch& b, int key, int selr, int cap, int slot, F1&& f
     return true;
 }
 
+// The conjugate-gradient loop added to a capture under way (an iteration
+// captured whole): `first`, the loop-control launch, and a while node whose
+// body (`pass` and the loop control) is captured on a stream of its own.
+// Returns false if a part could not be captured (the enclosing capture is
+// then discarded, see iter_graph_run).
+template <class F1, class F2>
+bool pcg_loop_inline(Batch& b, int selr, int cap, int slot, F1&& first, F2&& pass) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphConditionalHandle h = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(b.st, &cs, nullptr, &graph, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return false;
+    first();
+    launch_pcg_more(b.d_insts, b.count, selr, h, cap, 1, slot, b.st);
+    e = cudaStreamGetCaptureInfo(b.st, &cs, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return false;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    e = cudaGraphAddNode(&wnode, graph, deps, nullptr, ndeps, &cp);
+    if (e != cudaSuccess) return false;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(b.st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return false;
+    cudaStream_t outer = b.st, aux = nullptr;
+    if (cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess) return false;
+    const unsigned long long k1 = lqmpc_kernel_launches();
+    e = cudaStreamBeginCaptureToGraph(aux, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        b.st = aux;
+        pass();
+        launch_pcg_more(b.d_insts, b.count, selr, h, cap, 0, slot, b.st);
+        b.st = outer;
+        cudaGraph_t bg = nullptr;
+        e = cudaStreamEndCapture(aux, &bg);
+    }
+    b.st = outer;
+    const unsigned long long n_pass = lqmpc_kernel_launches() - k1;
+    cudaStreamDestroy(aux);
+    if (e != cudaSuccess) return false;
+    b.pass_kernels[slot] = n_pass;
+    b.loop_body_kernels += n_pass;
+    return true;
+}
+
 enum SegKey {
     SEG_HEAD = 1, SEG_HEAD_R = 2, SEG_HEAD_SIDE = 3, SEG_HEAD_CHECK = 4, SEG_FORM = 10 /* + precision */,
     SEG_SOLVE64 = 20, SEG_PCG0 = 30, SEG_PCG2 = 31, SEG_PRED_TAIL = 40, SEG_CORR_TAIL = 50,
-    SEG_PCG_LOOP = 60 /* + 100 with the FP64 preconditioner */
+    SEG_PCG_LOOP = 60 /* + 100 with the FP64 preconditioner */,
+    SEG_ITER = 300 /* + precisions present + 32 with the head on the side stream */
 };
 
 // Products with Gamma in the arithmetic of the solve: FP64 for the plain
@@ -559,7 +661,9 @@ void head_fork(Batch& b) {
 
 void join_head(Batch& b) {
     if (!b.side_pending) return;
-    cudaStreamWaitEvent(b.st, b.ev_join, 0);
+    // inside a captured iteration the head's event was recorded before the
+    // capture: an external wait node
+    cudaStreamWaitEvent(b.st, b.ev_join, is_capturing(b.st) ? cudaEventWaitExternal : 0);
     seg_run(b, SEG_HEAD_CHECK, [&]() {
         launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true, 2);
     });
@@ -827,6 +931,11 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     // host looks at them after the start and after every second step, and
     // stops launching once every unfinished instance has converged or failed
     // (the last read leaves each h_scal holding the outcome).
+    if (is_capturing(b.st)) {   // part of an iteration captured whole
+        if (!pcg_loop_inline(b, selr, (refine_max + 1) / 2, prec64 ? 1 : 0, first, [&]() { step(true); step(true); }))
+            b.capture_failed = true;
+        return LQMPC_OK;
+    }
     {
         const int key = SEG_PCG_LOOP + kp, slot = prec64 ? 1 : 0;
         if (pcg_loop_graph(b, key, selr, (refine_max + 1) / 2, slot, first, [&]() { step(true); step(true); })) {
@@ -1053,6 +1162,76 @@ lqmpc_status kkt_step(Batch& b, const lqmpc_options& o, bool formed, SyrkTimer* 
     return LQMPC_OK;
 }
 
+// An event record that is an external node when the stream is being
+// captured (read by the host after the graph ran).
+static void rec_event(cudaEvent_t e, cudaStream_t st) {
+    if (is_capturing(st)) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
+static int timer_bits(const SyrkTimer& t) {
+    return (t.tc ? 1 : 0) | (t.cc ? 2 : 0) | (t.cc64 ? 4 : 0) | (t.tc3 ? 8 : 0) | (t.pf ? 16 : 0);
+}
+static SyrkTimer timer_from_bits(int v) {
+    SyrkTimer t;
+    t.tc = v & 1; t.cc = v & 2; t.cc64 = v & 4; t.tc3 = v & 8; t.pf = v & 16;
+    return t;
+}
+
+// An unseen iteration's launches from the predictor's KKT solve to the step
+// as one graph, the conjugate-gradient loops as while nodes inside it (the
+// boundaries between separately launched graphs cost 3-6 us each, kernels in
+// one graph follow each other within 1 us).  Captured the first time for a
+// key and replayed after; when a part cannot be captured the iteration runs
+// as separate launches and the key is not tried again.
+template <class F>
+lqmpc_status iter_graph_run(Batch& b, int key, SyrkTimer& tm, F&& body) {
+    GraphSeg& g = b.gc->segs[2 * key + (b.ff ? 1 : 0)];
+    if (g.bad) return body();
+    if (!g.exec) {
+        const unsigned long long k0 = lqmpc_kernel_launches();
+        const bool side = b.side_pending;
+        b.loop_body_kernels = 0;
+        b.capture_failed = false;
+        if (cudaStreamBeginCapture(b.st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            cudaGetLastError();
+            g.bad = true;
+            return body();
+        }
+        const lqmpc_status s = body();
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(b.st, &graph);
+        const unsigned long long nk = lqmpc_kernel_launches() - k0;
+        note_launches(-(int)nk);   // captured, not run
+        if (e == cudaSuccess && (s != LQMPC_OK || b.capture_failed || !graph)) e = cudaErrorUnknown;
+        if (e == cudaSuccess) detach_event_nodes(graph);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || !g.exec) {
+            if (getenv("LQMPC_DEBUG"))
+                fprintf(stderr, "lqmpc: capture of a whole iteration failed (%s); separate launches\n",
+                        cudaGetErrorString(e));
+            cudaGetLastError();
+            g.exec = nullptr;
+            g.bad = true;
+            b.side_pending = side;   // the captured join did not run
+            tm = SyrkTimer();
+            return body();
+        }
+        g.kernels = nk - b.loop_body_kernels;   // the loop bodies count by their passes
+        g.pass_kernels = b.pass_kernels[0];
+        g.timer_bits = timer_bits(tm);
+    } else {
+        tm = timer_from_bits(g.timer_bits);
+        b.pass_kernels[0] = g.pass_kernels;
+        b.side_pending = false;   // the graph joins the head
+        for (auto* c : b.ctxs) c->h_scal->kkt_pending = 0;
+    }
+    if (cudaGraphLaunch(g.exec, b.st) != cudaSuccess) return LQMPC_ERR_CUDA;
+    note_launches((int)g.kernels);
+    return LQMPC_OK;
+}
+
 lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* t_kkt) {
     const int prec = o.precision;
     b.ff = prec != LQMPC_FP64;
@@ -1119,24 +1298,37 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
         bool polish = false;
         for (auto* c : b.ctxs)
             if (!c->h_scal->done && it > 0 && c->h_scal->mu < 1e3 * o.tol) polish = true;
-        // predictor: form and factor M, solve M du_aff = b
-        lqmpc_status s = kkt_step(b, o, false, &tm, polish, unseen);
+        auto iter_body = [&]() -> lqmpc_status {
+            // predictor: form and factor M, solve M du_aff = b
+            lqmpc_status st = kkt_step(b, o, false, &tm, polish, unseen);
+            if (st != LQMPC_OK) return st;
+            seg_run(b, SEG_PRED_TAIL, [&]() {
+                launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
+                launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
+                // affine step, sigma, corrector right-hand side
+                launch_aff(b.d_insts, b.count, b.max_total, b.st);
+                launch_corr(b.d_insts, b.count, b.max_total, b.st);
+                gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
+                launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+            });
+            // corrector: same factor
+            st = kkt_step(b, o, true, &tm, polish, unseen);
+            if (st != LQMPC_OK) return st;
+            launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
+            rec_event(c0->ev[3], b.st);
+            seg_run(b, SEG_CORR_TAIL, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st); });
+            return LQMPC_OK;
+        };
+        // Unseen iterations whose factors need no read in between (no
+        // two-level or FP64 tier present) run as one graph.
+        int present = 0;
+        for (auto* c : b.ctxs)
+            if (!c->h_scal->done) present |= 1 << c->h_scal->prec_cur;
+        const bool whole = unseen && b.gc && present && !(present & ((1 << LQMPC_FP64) | (1 << LQMPC_FP32X2))) &&
+                           whole_iteration_enabled();
+        lqmpc_status s = whole ? iter_graph_run(b, SEG_ITER + present + (b.side_pending ? 32 : 0), tm, iter_body)
+                               : iter_body();
         if (s != LQMPC_OK) return s;
-        seg_run(b, SEG_PRED_TAIL, [&]() {
-            launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
-            launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
-            // affine step, sigma, corrector right-hand side
-            launch_aff(b.d_insts, b.count, b.max_total, b.st);
-            launch_corr(b.d_insts, b.count, b.max_total, b.st);
-            gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
-            launch_rhs(b.d_insts, b.count, b.max_n, b.st);
-        });
-        // corrector: same factor
-        s = kkt_step(b, o, true, &tm, polish, unseen);
-        if (s != LQMPC_OK) return s;
-        launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
-        cudaEventRecord(c0->ev[3], b.st);
-        seg_run(b, SEG_CORR_TAIL, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st); });
         // The state goes to the host and the next iteration's head is queued
         // behind it before the host waits, so the GPU runs the head while the
         // host looks.  Its variant comes from the state read an iteration
