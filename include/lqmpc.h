@@ -168,7 +168,9 @@ typedef struct {
  * Solves return u in every case.  The stage-level entry points
  * (lqmpc_get_gstack, lqmpc_gamma_mv, lqmpc_form_kkt, lqmpc_get_duals, ...)
  * work on the lifted state of dimension ns + nc (+ nu with K), whose extra
- * rows come after the plant's states.  With K, warm starts
+ * rows come after the plant's states; solves read x0 as the plant's ns states
+ * (the lifted rows start at zero: no column of the lifted A holds them).
+ * With K, warm starts
  * (lqmpc_solve_warm, lqmpc_solve_batch_warm) return LQMPC_ERR_UNSUPPORTED.
  * g = NULL is lqmpc_setup.  LQMPC_ERR_ARG as lqmpc_setup, and for non-finite
  * S, w, E, F, K, crossed or NaN row bounds, or nc > 0 with a NULL array.

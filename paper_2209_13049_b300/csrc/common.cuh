@@ -165,6 +165,7 @@ struct Inst {
     unsigned* bar;                    // grid-barrier state (2 words), queued Cholesky tickets (2 words),
                                       // device-side conjugate-gradient loop count (1 word)
     int* pflags;                      // dataflow Cholesky: epoch, finished tasks, flag per (block column, row block)
+    int* mvcnt;                       // float-float Gamma v: arrivals per (r-tile, state tile), 0 between launches
     const int* ftasks;                // queued dataflow Cholesky: task list of this instance alone
     Scal* sc;
     double* trace;                    // (max_iter+1) x kTraceW

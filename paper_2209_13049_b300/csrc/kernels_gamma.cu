@@ -288,9 +288,16 @@ __host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kb
 
 // Gamma v: block (r-tile, m-tile of states, split of the column range).  G
 // tiles stream through a double-buffered shared-memory ring (cp.async); the
-// input comes split into float-float by k_ff_prep_v.
+// input comes split into float-float by k_ff_prep_v.  Each block leaves its
+// split's partial tile.  With kFuseSumHere (batches) the last of the tile's
+// splits to arrive (a counter per tile, acquire-release like last_arrival)
+// sums them in split order, as k_gamma_mv_ff_sum does for one instance, and
+// writes the output with its fused uses (kFuseOutW, kFuseOutDxs).  For one
+// instance few CTAs arrive last, each summing eight outputs in turn, which
+// took longer than the separate sum launch it saves (C2: 15.7 -> 17.3 ms);
+// a batch has many more tiles (256 instances: 845 -> 833 ms).
 __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
-                                                            int out_role, int flags, int splits) {
+                                                            int out_role, int flags, int fuse) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
@@ -310,7 +317,6 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     const int m0 = (rem / S) * kFfBM, r1 = N - kFfBN * t, r0 = r1 - kFfBN;
     const double* v = role_ptr(I, in_role);
     const int k0t = nk * split / S, k1t = nk * (split + 1) / S;
-    (void)splits;
     __shared__ __align__(16) float Gs[2][2][kFfBK][kFfBM];          // [buffer][hi, lo][col][state]
     __shared__ float Vs[2][2][kFfBK][kFfBN + 1];                   // [buffer][hi, lo][col][r]
     (void)v;
@@ -375,7 +381,41 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
             if (i < ns && r >= 0) part[(size_t)r * ns + i] = (double)sh[a][b] + (double)sl[a][b];
         }
-    (void)out_role;
+    if (!(fuse & kFuseSumHere)) return;
+    __shared__ int last_sh;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int* cnt = I.mvcnt + (size_t)t * mt + m0 / kFfBM;
+        int old;
+        asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
+        last_sh = old == S - 1;
+        if (last_sh) atomicExch(cnt, 0);
+    }
+    __syncthreads();
+    if (!last_sh) return;
+    double* out = role_ptr(I, out_role);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
+            if (i >= ns || r < 0) continue;
+            const size_t k = (size_t)r * ns + i;
+            double pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
+#pragma unroll
+            for (int q = 0; q < kFfMaxSplits; ++q) pv[q] = q < S ? __ldcg(I.gpart + (size_t)q * I.SX + k) : 0.0;
+            double sum = 0.0;
+#pragma unroll
+            for (int q = 0; q < kFfMaxSplits; ++q) sum += pv[q];
+            out[k] = sum;
+            if (fuse & kFuseOutDxs) I.dxs[k] = sum;
+            if (fuse & kFuseOutW) {
+                float h, l;
+                split_ff(sum * I.sigx[k], h, l);
+                I.ffw[k] = h;
+                I.ffw[(size_t)I.SX + k] = l;
+            }
+        }
 }
 
 // out = sum of the split partials; with kFuseOutW also the float-float split
@@ -676,13 +716,17 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
         const int nkmax = (max_n + kFfBK - 1) / kFfBK;
         ctas = mt * nt * (nkmax < kFfMaxSplits ? nkmax : kFfMaxSplits);
     }
-    const int splits = 0;
     if (!(fuse & kFuseInSplit))
         LQ_LAUNCH(lq_pdl(k_ff_prep_v, dim3((max_n + 255) / 256, count), 256, 0, st, d_insts, in_role, flags));
-    LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags, splits));
-    int nb = (max_ns * max_N + 255) / 256;
-    nb = per_instance_blocks(nb > 4096 ? 4096 : nb, count);
-    LQ_LAUNCH(lq_pdl(k_gamma_mv_ff_sum, dim3(nb, count), 256, 0, st, d_insts, out_role, flags, splits, fuse));
+    if (count > 1) {   // the split-K sum by the last split of each tile
+        LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags,
+                         fuse | kFuseSumHere));
+    } else {
+        LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags, fuse));
+        const int nb = (max_ns * max_N + 255) / 256;
+        LQ_LAUNCH(lq_pdl(k_gamma_mv_ff_sum, dim3(nb > 4096 ? 4096 : nb, count), 256, 0, st, d_insts, out_role, flags,
+                         0, fuse));
+    }
 }
 
 int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV) {

@@ -187,6 +187,9 @@ struct lqmpc_ctx {
     // solver's own variable)
     double* gen_dev = nullptr;
     int u_row = -1;
+    // the caller's state dimension (x0 holds this many values); the lifted
+    // rows of lqmpc_setup_general come after it and start at zero
+    int ns_plant = 0;
 };
 
 namespace {
@@ -289,6 +292,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto rho = c.take<double>(n); auto dcorr = c.take<double>(n); auto mv = c.take<double>(n);
     auto ldiag = c.take<double>(2 * 32 * 32);
     auto pflags = c.take<int>(2 + 32 * 32);   // dataflow Cholesky: epoch, count, flag per row block
+    auto mvcnt = c.take<int>((size_t)((ns + 63) / 64) * ((I.N + 15) / 16));   // Gamma v tiles (64 states x 16 stages)
     auto ftasks = c.take<int>(64);
     auto ffw = c.take<float>(4 * (size_t)I.SX);
     auto ffv = c.take<float>(2 * (size_t)n);
@@ -322,7 +326,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
         I.ldiag = ldiag;
-        I.pflags = pflags;
+        I.pflags = pflags; I.mvcnt = mvcnt;
         I.ftasks = ftasks;
         I.ffw = ffw;
         I.ffv = ffv;
@@ -1439,12 +1443,14 @@ lqmpc_status solve_common(lqmpc_ctx* ctx, const double* x0, bool x0_dev, double*
     if (!ctx || !x0 || !u) return LQMPC_ERR_ARG;
     CK(cudaSetDevice(ctx->device));
     const Inst& I = ctx->h;
+    const int nsp = ctx->ns_plant;   // x0 holds the plant's states; lifted rows start at zero
     if (!x0_dev) {
-        if (!all_finite(x0, I.ns)) return LQMPC_ERR_ARG;
-        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyHostToDevice, ctx->stream));
+        if (!all_finite(x0, nsp)) return LQMPC_ERR_ARG;
+        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * nsp, cudaMemcpyHostToDevice, ctx->stream));
     } else {
-        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * I.ns, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(I.xbar, x0, sizeof(double) * nsp, cudaMemcpyDeviceToDevice, ctx->stream));
     }
+    if (I.ns > nsp) CK(cudaMemsetAsync(I.xbar + nsp, 0, sizeof(double) * (I.ns - nsp), ctx->stream));
     if (u_init) {
         if (ctx->u_row >= 0) return LQMPC_ERR_UNSUPPORTED;   // the guess would be for v, not u
         if (!all_finite(u_init, I.n)) return LQMPC_ERR_ARG;
@@ -1715,6 +1721,7 @@ static lqmpc_status setup_impl(lqmpc_ctx** out, int ns, int nu, int N, const int
             ctx->tc_ok = 1;
         }
     }
+    ctx->ns_plant = ns;   // lqmpc_setup_general sets the caller's dimension after this
     *out = ctx;
     return LQMPC_OK;
 }
@@ -1881,6 +1888,7 @@ lqmpc_status lqmpc_setup_general(lqmpc_ctx** out, int ns, int nu, int N, const i
                                 qv.data(), fp.data(), fi.data(), fv.data(), Rh, xla.data(), xua.data(), ula.data(),
                                 uua.data(), opts, stream, has_S ? Sl.data() : nullptr, g->w ? wl.data() : nullptr);
     if (s == LQMPC_OK && K) (*out)->u_row = ns + nc;
+    if (s == LQMPC_OK) (*out)->ns_plant = ns;
     return s;
 }
 
@@ -1929,7 +1937,7 @@ static lqmpc_status solve_batch_impl(lqmpc_ctx* const* ctxs, int count, const do
     batch_dims(b);
     lqmpc_options o = ctxs[0]->opts;
     for (int i = 0; i < count; ++i) {
-        if (!all_finite(x0s[i], ctxs[i]->h.ns)) return LQMPC_ERR_ARG;
+        if (!all_finite(x0s[i], ctxs[i]->ns_plant)) return LQMPC_ERR_ARG;
         if (ctxs[i]->opts.max_iter < o.max_iter) o.max_iter = ctxs[i]->opts.max_iter;
     }
     // tensor maps for the tensor-core formations (BF16, TF32 and the split-TF32
@@ -1970,10 +1978,14 @@ static lqmpc_status solve_batch_impl(lqmpc_ctx* const* ctxs, int count, const do
     if (!ftasks.empty() && cudaMemcpyAsync(d + count, ftasks.data(), sizeof(int) * ftasks.size(),
                                            cudaMemcpyHostToDevice, b.st) != cudaSuccess)
         s = LQMPC_ERR_CUDA;
-    for (int i = 0; i < count && s == LQMPC_OK; ++i)
-        if (cudaMemcpyAsync(ctxs[i]->h.xbar, x0s[i], sizeof(double) * ctxs[i]->h.ns, cudaMemcpyHostToDevice,
-                            b.st) != cudaSuccess)
+    for (int i = 0; i < count && s == LQMPC_OK; ++i) {
+        const int nsp = ctxs[i]->ns_plant, nsl = ctxs[i]->h.ns;   // plant states given, lifted rows zero
+        if (cudaMemcpyAsync(ctxs[i]->h.xbar, x0s[i], sizeof(double) * nsp, cudaMemcpyHostToDevice, b.st) !=
+                cudaSuccess ||
+            (nsl > nsp &&
+             cudaMemsetAsync(ctxs[i]->h.xbar + nsp, 0, sizeof(double) * (nsl - nsp), b.st) != cudaSuccess))
             s = LQMPC_ERR_CUDA;
+    }
     if (u_inits) {      // warm start: every instance's guess where prepare() reads it
         for (int i = 0; i < count && s == LQMPC_OK; ++i)
             if (cudaMemcpyAsync(ctxs[i]->h.du_aff, u_inits[i], sizeof(double) * ctxs[i]->h.n,

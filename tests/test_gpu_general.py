@@ -149,6 +149,27 @@ def test_general_and_plain_contexts_in_one_batch():
             assert rel(us[k], refs[k]) <= bar, (precision, k)
 
 
+def test_x0_is_read_for_the_plant_states_only():
+    """x0 holds the plant's ns states; the lifted rows (general rows, and the
+    inputs with K) start at zero and nothing past x0[ns-1] is read: an x0
+    that is a view into a buffer with NaN after it solves like a plain one."""
+    for with_k in (False, True):
+        p, x0 = random_general(8, with_k)
+        buf = np.full(p.ns + 64, np.nan)
+        buf[:p.ns] = x0
+        ref = binding.Solver(p, precision="fp64", tol=1e-10).solve(x0)[0]
+        for precision in ("fp64", "fp32"):
+            s = binding.Solver(p, precision=precision, tol=1e-10)
+            u, st = s.solve(buf[:p.ns])
+            assert st["status"] == 0
+            assert rel(u, ref) <= (1e-12 if precision == "fp64" else 1e-6)
+        solvers = [binding.Solver(p, precision="fp32", tol=1e-10) for _ in range(2)]
+        us, stats, code = binding.solve_batch(solvers, [buf[:p.ns], x0])
+        assert code == 0
+        for k in range(2):
+            assert rel(us[k], ref) <= 1e-6
+
+
 def test_general_setup_rejects_bad_rows():
     p, _ = heat1d_general()
     p.gl = np.array([0.3, -np.inf, -0.3])        # gl > gu in row 0
