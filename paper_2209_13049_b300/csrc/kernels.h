@@ -38,8 +38,12 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
 // of Sigma_x (Gamma v) for a following Gamma' product (kFuseOutW) and a copy
 // into dxs (kFuseOutDxs); the Gamma' product leaves its partials for a fused
 // consumer (kFuseNoSum); with kFuseSumHere the Gamma v product sums its own
-// split-K partials (no sum launch).
-enum FuseFlags : int { kFuseInSplit = 1, kFuseOutW = 2, kFuseOutDxs = 4, kFuseNoSum = 8, kFuseSumHere = 16 };
+// split-K partials (no sum launch); with kFuseRhs the sum of a one-vector
+// Gamma' w also forms the corrector's right-hand side b = -r_d + Gamma' w +
+// w_u (no k_rhs launch).
+enum FuseFlags : int {
+    kFuseInSplit = 1, kFuseOutW = 2, kFuseOutDxs = 4, kFuseNoSum = 8, kFuseSumHere = 16, kFuseRhs = 32
+};
 void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
                         int out_role, int flags, cudaStream_t st, int fuse = 0);
 // split count of the float-float Gamma' product (its partials' layout)

@@ -578,10 +578,12 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
         }
 }
 
-// Gamma' w from the split partials: one warp per output.
+// Gamma' w from the split partials: one warp per output.  With rhs (one
+// vector, the corrector's Gamma' w) the warp also writes the right-hand side
+// b = -r_d + Gamma' w + w_u of that output.
 template <int NV>
 __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, int o1_role, int flags,
-                                   int splits) {
+                                   int splits, int rhs) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
@@ -589,7 +591,10 @@ __global__ void k_gamma_tmv_ff_sum(const Inst* __restrict__ insts, int o0_role, 
     for (int q = blockIdx.x * wpb + (threadIdx.x >> 5); q < NV * n; q += gridDim.x * wpb) {
         const int vec = q / n, j = q % n;
         const double s = gamma_tmv_ff_gather(I, NV, vec, j, splits);
-        if (lane == 0) (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
+        if (lane == 0) {
+            (vec == 0 ? role_ptr(I, o0_role) : role_ptr(I, o1_role))[j] = s;
+            if (NV == 1 && rhs) I.b[j] = -I.rd[j] + s + I.wxu[j];
+        }
     }
 }
 
@@ -747,11 +752,13 @@ void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, 
         LQ_LAUNCH(lq_pdl(k_ff_prep_w, dim3(npre, count), 256, 0, st, d_insts, w0_role, w1_role, scale0, flags));
     if (NV == 2) {
         LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff<2>, dim3(tiles * splits, count), kFfThreads, 0, st, d_insts, w0_role, w1_role, scale0, flags, splits));
-        LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<2>, dim3(nb, count), 64, 0, st, d_insts, o0_role, o1_role, flags, splits));
+        LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<2>, dim3(nb, count), 64, 0, st, d_insts, o0_role, o1_role, flags, splits,
+                         0));
     } else {
         LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff<1>, dim3(tiles * splits, count), kFfThreads, 0, st, d_insts, w0_role, R_NONE, scale0, flags, splits));
         if (!(fuse & kFuseNoSum))
-            LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<1>, dim3(nb, count), 64, 0, st, d_insts, o0_role, R_NONE, flags, splits));
+            LQ_LAUNCH(lq_pdl(k_gamma_tmv_ff_sum<1>, dim3(nb, count), 64, 0, st, d_insts, o0_role, R_NONE, flags, splits,
+                             (fuse & kFuseRhs) ? 1 : 0));
     }
 }
 

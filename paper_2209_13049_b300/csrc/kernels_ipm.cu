@@ -302,26 +302,23 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
     double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
     v = block_reduce<0>(s4, red); put_part(I, 4, v);
     v = block_reduce<0>(s5, red); put_part(I, 5, v);
-}
-
-// alpha_aff = min(1, max step); mu_aff; sigma = (mu_aff/mu)^3 (Mehrotra).
-__global__ void k_aff_fin(const Inst* __restrict__ insts, int nb) {
-    pdl_wait();
-    __shared__ double red[32];
-    const Inst& I = insts[blockIdx.y];
+    if (!last_arrival(I.sc)) return;
+    // The instance's last CTA: alpha_aff = min(1, max step); mu_aff; sigma =
+    // (mu_aff/mu)^3 (Mehrotra).  Slot 1 (sum s.z) is k_resid's, launched on
+    // the same grid; the partials of the other CTAs are read past L1.
     Scal* S = I.sc;
-    if (S->done) return;
-    double a = INFINITY, sz = 0, s4 = 0, s5 = 0;
+    const int nb = gridDim.x;
+    double a = INFINITY, sz = 0, s4p = 0, s5p = 0;
     for (int p = threadIdx.x; p < nb; p += blockDim.x) {
-        a = fmin(a, I.part[3 * kMaxParts + p]);
-        sz += I.part[1 * kMaxParts + p];
-        s4 += I.part[4 * kMaxParts + p];
-        s5 += I.part[5 * kMaxParts + p];
+        a = fmin(a, __ldcg(I.part + 3 * kMaxParts + p));
+        sz += __ldcg(I.part + 1 * kMaxParts + p);
+        s4p += __ldcg(I.part + 4 * kMaxParts + p);
+        s5p += __ldcg(I.part + 5 * kMaxParts + p);
     }
     a = block_reduce<2>(a, red);
     sz = block_reduce<0>(sz, red);
-    s4 = block_reduce<0>(s4, red);
-    s5 = block_reduce<0>(s5, red);
+    s4 = block_reduce<0>(s4p, red);
+    s5 = block_reduce<0>(s5p, red);
     if (threadIdx.x == 0) {
         double al = fmin(1.0, a);
         double mu_aff = S->m > 0 ? (sz + al * s4 + al * al * s5) / S->m : 0.0;
@@ -369,10 +366,10 @@ __global__ void k_rhs(const Inst* __restrict__ insts) {
 
 // Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with r_c from the
 // stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.  This
-// and the rest of the step (k_step_fin, k_update, k_iter_inc) skip an
+// and the update (k_update) skip an
 // instance whose KKT solve of the iteration failed unseen (Scal::spec_fail):
 // the iterate stays as it was and the host repeats the iteration.
-__global__ void k_step(const Inst* __restrict__ insts) {
+__global__ void k_step(const Inst* __restrict__ insts, int trace_on) {
     pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
@@ -400,17 +397,12 @@ __global__ void k_step(const Inst* __restrict__ insts) {
         *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
     }
     double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
-}
-
-// alpha = min(1, tau * max step); trace; iteration count.
-__global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on) {
-    pdl_wait();
-    __shared__ double red[32];
-    const Inst& I = insts[blockIdx.y];
+    if (!last_arrival(I.sc)) return;
+    // The instance's last CTA: alpha = min(1, tau * max step); trace; the
+    // iteration count (k_update reads alpha only).
     Scal* S = I.sc;
-    if (S->done || S->spec_fail) return;
     double a = INFINITY;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) a = fmin(a, I.part[3 * kMaxParts + p]);
+    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) a = fmin(a, __ldcg(I.part + 3 * kMaxParts + p));
     a = block_reduce<2>(a, red);
     if (threadIdx.x == 0) {
         double al = fmin(1.0, S->tau * a);
@@ -420,6 +412,7 @@ __global__ void k_step_fin(const Inst* __restrict__ insts, int nb, int trace_on)
             t[3] = S->alpha_aff; t[4] = S->sigma; t[5] = al;
             t[6] = S->refine_iter; t[7] = S->prec_cur;
         }
+        S->iter += 1;
     }
 }
 
@@ -438,12 +431,6 @@ __global__ void k_update(const Inst* __restrict__ insts) {
         *r.s_u += al * (*r.ds_u); *r.z_u += al * (*r.dz_u);
         *r.s_l += al * (*r.ds_l); *r.z_l += al * (*r.dz_l);
     }
-}
-
-__global__ void k_iter_inc(const Inst* __restrict__ insts) {
-    pdl_wait();
-    const Inst& I = insts[blockIdx.y];
-    if (threadIdx.x == 0 && !I.sc->done && !I.sc->spec_fail) I.sc->iter += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -483,7 +470,6 @@ void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
     LQ_LAUNCH(lq_pdl(k_aff, dim3(nb, count), 256, 0, st, d_insts));
-    LQ_LAUNCH(lq_pdl(k_aff_fin, dim3(1, count), 256, 0, st, d_insts, nb));
 }
 
 void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
@@ -497,10 +483,8 @@ void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
 void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
                         cudaStream_t st) {
     int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(lq_pdl(k_step, dim3(nb, count), 256, 0, st, d_insts));
-    LQ_LAUNCH(lq_pdl(k_step_fin, dim3(1, count), 256, 0, st, d_insts, nb, trace_on));
+    LQ_LAUNCH(lq_pdl(k_step, dim3(nb, count), 256, 0, st, d_insts, trace_on));
     LQ_LAUNCH(lq_pdl(k_update, dim3(nb, count), 256, 0, st, d_insts));
-    LQ_LAUNCH(lq_pdl(k_iter_inc, dim3(1, count), 32, 0, st, d_insts));
 }
 
 }  // namespace lqmpc

@@ -492,7 +492,7 @@ void seg_run(const Batch& b, int key, F&& body) {
     if (cudaGraphLaunch(g.exec, b.st) == cudaSuccess) note_launches((int)g.kernels);
 }
 
-// The conjugate-gradient loop as one graph: the start (`first`, ending with a
+// The conjugate-gradient loop as one graph: the start (`first`, followed by a
 // loop-control launch that restarts the pass count) and a while node whose
 // body is `pass` (two steps) plus the loop control, which stops when no
 // selected instance is still refining or after `cap` passes.  The host reads
@@ -930,25 +930,34 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
         if (!with_next) return;
         prec(R_RHO, R_DCORR, selr, 2);
     };
-    // With graphs the whole loop runs on the device (a while node, two steps
-    // per pass) and the host reads the flags once at the end; otherwise the
-    // host looks at them after the start and after every second step, and
-    // stops launching once every unfinished instance has converged or failed
-    // (the last read leaves each h_scal holding the outcome).
+    // The start and one step, then two steps at a time.  (Most solves of a
+    // mixed-precision run take no step or one: with the first step ahead of
+    // the loop a one-step solve enters no pass, and a pass's second step
+    // idles only for even counts.)  With graphs the whole loop runs on the
+    // device (the passes in a while node) and the host reads the flags once
+    // at the end; otherwise the host looks at them after the first step and
+    // after every second step, and stops launching once every unfinished
+    // instance has converged or failed (the last read leaves each h_scal
+    // holding the outcome).
+    auto first_step = [&]() {
+        first();
+        step(true);
+    };
+    const int cap = refine_max / 2;   // 1 + 2 cap >= refine_max steps (the budgets stop them first)
     if (is_capturing(b.st)) {   // part of an iteration captured whole
-        if (!pcg_loop_inline(b, selr, (refine_max + 1) / 2, prec64 ? 1 : 0, first, [&]() { step(true); step(true); }))
+        if (!pcg_loop_inline(b, selr, cap, prec64 ? 1 : 0, first_step, [&]() { step(true); step(true); }))
             b.capture_failed = true;
         return LQMPC_OK;
     }
     {
         const int key = SEG_PCG_LOOP + kp, slot = prec64 ? 1 : 0;
-        if (pcg_loop_graph(b, key, selr, (refine_max + 1) / 2, slot, first, [&]() { step(true); step(true); })) {
+        if (pcg_loop_graph(b, key, selr, cap, slot, first_step, [&]() { step(true); step(true); })) {
             b.pass_kernels[slot] = b.gc->segs[2 * key + (b.ff ? 1 : 0)].pass_kernels;
             if (unseen) return LQMPC_OK;   // the outcome is read with the iteration's end
             return read_scals(b);
         }
     }
-    seg_run(b, SEG_PCG0 + kp, first);
+    seg_run(b, SEG_PCG0 + kp, first_step);
     auto pending = [&]() {
         for (auto* c : b.ctxs)
             if (host_selected(*c->h_scal, selr) && !c->h_scal->info) return true;
@@ -956,7 +965,7 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     };
     lqmpc_status st = read_scals(b);
     if (st != LQMPC_OK) return st;
-    for (int s = 0; s < refine_max && pending();) {
+    for (int s = 1; s < refine_max && pending();) {
         if (s + 2 <= refine_max) {
             seg_run(b, SEG_PCG2 + kp, [&]() { step(true); step(true); });
             s += 2;
@@ -1312,8 +1321,12 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
                 // affine step, sigma, corrector right-hand side
                 launch_aff(b.d_insts, b.count, b.max_total, b.st);
                 launch_corr(b.d_insts, b.count, b.max_total, b.st);
-                gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
-                launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+                if (b.ff) {
+                    gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE, kFuseRhs);
+                } else {
+                    gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
+                    launch_rhs(b.d_insts, b.count, b.max_n, b.st);
+                }
             });
             // corrector: same factor
             st = kkt_step(b, o, true, &tm, polish, unseen);

@@ -61,8 +61,9 @@ def test_graph_replay_equals_direct_launches():
     for key in ("fp64", "bf16", "fp32"):
         assert on[key]["u"] == off[key]["u"], key
         # with graphs the conjugate-gradient loop runs on the device: the same
-        # kernels plus one loop-control launch at its start and one per pass
-        # of two steps (one per KKT solve and per two steps), the next
+        # kernels plus one loop-control launch after its start and first step
+        # and one per pass of two steps (one per KKT solve and per two
+        # steps), the next
         # iteration's head queued behind the host's read once more after the
         # last iteration, and any iteration repeated after a solve that failed
         # unseen (the BF16 tier, whose refinements are meant to fail over to
