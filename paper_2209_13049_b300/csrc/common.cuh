@@ -134,7 +134,8 @@ struct Inst {
     double *wz, *wx;                  // SX: vectors for Gamma' products
     double *wzu, *wxu;                // n
     double *gz, *gw;                  // n: Gamma' outputs
-    double *rd, *b, *du, *dx, *du_aff, *dx_aff;
+    double *rd, *b, *du;              // n: r_d, right-hand side, the latest KKT solve's du
+    double* du_aff;                   // n: a warm start's guess, staged
     double *ds1, *dz1, *ds2, *dz2;    // SX
     double *ds3, *dz3, *ds4, *dz4;    // n
     double* M64; float* M32;          // n x n
@@ -178,8 +179,7 @@ struct Inst {
 // Vectors addressed by role, so one launch can name "the same vector" of
 // every instance of a batch.
 enum Role : int {
-    R_U = 0, R_X, R_Y, R_H, R_TMPX, R_WZ, R_WX, R_GZ, R_GW, R_DU, R_DX, R_DU_AFF, R_DX_AFF,
-    R_RHO, R_DCORR, R_B, R_RD, R_MV, R_P, R_Q, R_DXS, R_NONE
+    R_U = 0, R_X, R_Y, R_H, R_TMPX, R_WZ, R_WX, R_GZ, R_GW, R_DU, R_RHO, R_DCORR, R_B, R_RD, R_MV, R_P, R_Q, R_DXS, R_NONE
 };
 
 __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
@@ -187,8 +187,7 @@ __device__ __forceinline__ double* role_ptr(const Inst& I, int r) {
         case R_U: return I.u;        case R_X: return I.x;        case R_Y: return I.y;
         case R_H: return I.h;        case R_TMPX: return I.tmpx;  case R_WZ: return I.wz;
         case R_WX: return I.wx;      case R_GZ: return I.gz;      case R_GW: return I.gw;
-        case R_DU: return I.du;      case R_DX: return I.dx;      case R_DU_AFF: return I.du_aff;
-        case R_DX_AFF: return I.dx_aff; case R_RHO: return I.rho; case R_DCORR: return I.dcorr;
+        case R_DU: return I.du;      case R_RHO: return I.rho;    case R_DCORR: return I.dcorr;
         case R_B: return I.b;        case R_RD: return I.rd;      case R_MV: return I.mv;
         case R_P: return I.pp;       case R_Q: return I.qq;       case R_DXS: return I.dxs;
         default: return nullptr;

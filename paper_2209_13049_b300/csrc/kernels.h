@@ -17,11 +17,13 @@ void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, i
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
                        double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0 = 0.0,
                        double smin = 1.0);
-// rd_parts (with do_rd): 1 r_d and the right-hand side, 2 the stop test, 3 both
+// rd_parts (with do_rd): 1 r_d and the right-hand side, 2 the stop test, 3 both;
+// split_w: k_resid also splits wz and wx for a float-float Gamma' product
+// launched with kFuseInSplit (k_corr likewise wx)
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
-                        cudaStream_t st, bool do_resid, bool do_rd, int rd_parts = 3);
+                        cudaStream_t st, bool do_resid, bool do_rd, int rd_parts = 3, bool split_w = false);
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st);
-void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st);
+void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st, bool split_w = false);
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st);
 void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on, cudaStream_t st);
 

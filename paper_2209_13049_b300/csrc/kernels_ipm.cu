@@ -14,6 +14,7 @@
 // Reductions are deterministic: every block writes one partial per slot and a
 // one-block finaliser combines them in block order.
 #include "common.cuh"
+#include "gamma_ff.cuh"
 #include "kernels.h"
 
 namespace lqmpc {
@@ -155,10 +156,12 @@ __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double to
 //   r_p per family; Sigma_x = z1/s1 + z2/s2 per state row, Sigma_u likewise;
 //   wz = z1 - z2 (for the Gamma' z term of r_d);
 //   predictor w_i = z_i - Sigma_i r_p,i, combined wx = w1 - w2 (for Gamma').
-// Partials: slot 0 max|r_p|, slot 1 sum s.z.
+// Partials: slot 0 max|r_p|, slot 1 sum s.z.  With split, also the
+// float-float split of wz and wx for the float-float Gamma' product of both
+// (hi0, lo0, hi1, lo1 in ffw: no split launch).
 // ---------------------------------------------------------------------------
 
-__global__ void k_resid(const Inst* __restrict__ insts) {
+__global__ void k_resid(const Inst* __restrict__ insts, int split) {
     pdl_wait();
     __shared__ double red[32];
     const Inst& I = insts[blockIdx.y];
@@ -184,6 +187,14 @@ __global__ void k_resid(const Inst* __restrict__ insts) {
         if (k < I.SX) {
             I.sigx[k] = sgu + sgl; I.sigx32[(size_t)(k / I.ns) * I.ldg + k % I.ns] = (float)(sgu + sgl);
             I.wz[k] = wz; I.wx[k] = wx;
+            if (split) {
+                const size_t SX = I.SX;
+                float h, l;
+                split_ff(wz, h, l);
+                I.ffw[k] = h; I.ffw[SX + k] = l;
+                split_ff(wx, h, l);
+                I.ffw[2 * SX + k] = h; I.ffw[3 * SX + k] = l;
+            }
         } else {
             int j = k - I.SX;
             I.sigu[j] = sgu + sgl; I.wzu[j] = wz; I.wxu[j] = wx;
@@ -282,7 +293,7 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
     double s4 = 0.0, s5 = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
-        double d = k < I.SX ? I.dx_aff[k] : I.du_aff[k - I.SX];
+        double d = k < I.SX ? I.dxs[k] : I.du[k - I.SX];   // the predictor's solve: du, Gamma du
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
         if (r.fu) {
@@ -329,8 +340,9 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
 }
 
 // Corrector: r_c = s.z + ds_aff.dz_aff - sigma mu; w = (r_c - z r_p)/s per
-// family; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).
-__global__ void k_corr(const Inst* __restrict__ insts) {
+// family; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).  With
+// split, also the float-float split of wx (hi0, lo0 in ffw).
+__global__ void k_corr(const Inst* __restrict__ insts, int split) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
@@ -350,8 +362,16 @@ __global__ void k_corr(const Inst* __restrict__ insts) {
             double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
             wl = (rc - zl * rp) / sl;
         }
-        if (k < I.SX) I.wx[k] = wu - wl;
-        else I.wxu[k - I.SX] = wu - wl;
+        if (k < I.SX) {
+            I.wx[k] = wu - wl;
+            if (split) {
+                float h, l;
+                split_ff(wu - wl, h, l);
+                I.ffw[k] = h; I.ffw[(size_t)I.SX + k] = l;
+            }
+        } else {
+            I.wxu[k - I.SX] = wu - wl;
+        }
     }
 }
 
@@ -379,7 +399,7 @@ __global__ void k_step(const Inst* __restrict__ insts, int trace_on) {
     StepMin am;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
-        double d = k < I.SX ? I.dx[k] : I.du[k - I.SX];
+        double d = k < I.SX ? I.dxs[k] : I.du[k - I.SX];   // the corrector's solve: du, Gamma du
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
         if (r.fu) {
@@ -426,7 +446,7 @@ __global__ void k_update(const Inst* __restrict__ insts) {
     const int total = I.SX + I.n;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
-        if (k < I.SX) I.x[k] += al * I.dx[k];
+        if (k < I.SX) I.x[k] += al * I.dxs[k];
         else I.u[k - I.SX] += al * I.du[k - I.SX];
         *r.s_u += al * (*r.ds_u); *r.z_u += al * (*r.dz_u);
         *r.s_l += al * (*r.ds_l); *r.z_l += al * (*r.dz_l);
@@ -455,9 +475,9 @@ void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, i
 }
 
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
-                        cudaStream_t st, bool do_resid, bool do_rd, int rd_parts) {
+                        cudaStream_t st, bool do_resid, bool do_rd, int rd_parts, bool split_w) {
     int nb1 = ew_blocks(max_total, 256);
-    if (do_resid) LQ_LAUNCH(lq_pdl(k_resid, dim3(nb1, count), 256, 0, st, d_insts));
+    if (do_resid) LQ_LAUNCH(lq_pdl(k_resid, dim3(nb1, count), 256, 0, st, d_insts, split_w ? 1 : 0));
     int wpb = 8;
     int nb2 = (max_n + wpb - 1) / wpb;
     nb2 = nb2 > kMaxParts ? kMaxParts : nb2;
@@ -472,8 +492,8 @@ void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st) 
     LQ_LAUNCH(lq_pdl(k_aff, dim3(nb, count), 256, 0, st, d_insts));
 }
 
-void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
-    LQ_LAUNCH(lq_pdl(k_corr, dim3(ew_blocks(max_total, 256), count), 256, 0, st, d_insts));
+void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st, bool split_w) {
+    LQ_LAUNCH(lq_pdl(k_corr, dim3(ew_blocks(max_total, 256), count), 256, 0, st, d_insts, split_w ? 1 : 0));
 }
 
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {

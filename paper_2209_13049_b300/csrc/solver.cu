@@ -281,7 +281,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto wzu = c.take<double>(n); auto wxu = c.take<double>(n);
     auto gz = c.take<double>(n); auto gw = c.take<double>(n);
     auto rd = c.take<double>(n); auto b = c.take<double>(n); auto du = c.take<double>(n);
-    auto dx = c.take<double>(SX); auto du_aff = c.take<double>(n); auto dx_aff = c.take<double>(SX);
+    auto du_aff = c.take<double>(n);
     auto ds1 = c.take<double>(SX); auto dz1 = c.take<double>(SX);
     auto ds2 = c.take<double>(SX); auto dz2 = c.take<double>(SX);
     auto ds3 = c.take<double>(n); auto dz3 = c.take<double>(n);
@@ -321,7 +321,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
         I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32; I.sgu = sgu; I.sgl = sgl;
         I.wz = wz; I.wx = wx; I.wzu = wzu; I.wxu = wxu; I.gz = gz; I.gw = gw;
-        I.rd = rd; I.b = b; I.du = du; I.dx = dx; I.du_aff = du_aff; I.dx_aff = dx_aff;
+        I.rd = rd; I.b = b; I.du = du; I.du_aff = du_aff;
         I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;
         I.ds3 = ds3; I.dz3 = dz3; I.ds4 = ds4; I.dz4 = dz4;
         I.M64 = M64; I.M32 = M32; I.Xinv32 = Xinv32; I.Tinv32 = Tinv32; I.XinvT32 = XinvT32; I.rho = rho; I.dcorr = dcorr; I.mv = mv; I.tmpx = tmpx;
@@ -650,13 +650,15 @@ void gtmv(const Batch& b, int w0, int w1, int o0, int o1, int scale0, int flags,
 // waits for the side stream and runs the stop test (which may finish an
 // instance: no kernel of the formation may see that change mid-launch).
 void head_fork(Batch& b) {
-    seg_run(b, SEG_HEAD_R, [&]() { launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false); });
+    seg_run(b, SEG_HEAD_R, [&]() {
+        launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false, 3, b.ff);
+    });
     cudaEventRecord(b.ev_fork, b.st);
     cudaStreamWaitEvent(b.side, b.ev_fork, 0);
     Batch bs = b;
     bs.st = b.side;
     seg_run(bs, SEG_HEAD_SIDE, [&]() {
-        gtmv(bs, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
+        gtmv(bs, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE, kFuseInSplit);   // split by k_resid
         launch_resid_check(bs.d_insts, bs.count, bs.max_total, bs.max_n, 1, bs.st, false, true, 1);
     });
     cudaEventRecord(b.ev_join, b.side);
@@ -1282,8 +1284,8 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             head_fork(b);
         } else {
             seg_run(b, SEG_HEAD, [&]() {
-                launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false);
-                gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE);
+                launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, true, false, 3, b.ff);
+                gtmv(b, R_WZ, R_WX, R_GZ, R_GW, 0, F_NONE, kFuseInSplit);   // split by k_resid
                 launch_resid_check(b.d_insts, b.count, b.max_total, b.max_n, 1, b.st, false, true);
             });
         }
@@ -1316,13 +1318,12 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             lqmpc_status st = kkt_step(b, o, false, &tm, polish, unseen);
             if (st != LQMPC_OK) return st;
             seg_run(b, SEG_PRED_TAIL, [&]() {
-                launch_vec_copy(b.d_insts, b.count, b.max_n, R_DU, R_DU_AFF, 1, F_NONE, b.st);
-                launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX_AFF, 0, F_NONE, b.st);
-                // affine step, sigma, corrector right-hand side
+                // affine step (from the solve's du and Gamma du), sigma,
+                // corrector right-hand side
                 launch_aff(b.d_insts, b.count, b.max_total, b.st);
-                launch_corr(b.d_insts, b.count, b.max_total, b.st);
+                launch_corr(b.d_insts, b.count, b.max_total, b.st, b.ff);
                 if (b.ff) {
-                    gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE, kFuseRhs);
+                    gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE, kFuseRhs | kFuseInSplit);   // split by k_corr
                 } else {
                     gtmv(b, R_WX, R_NONE, R_GW, R_NONE, 0, F_NONE);
                     launch_rhs(b.d_insts, b.count, b.max_n, b.st);
@@ -1331,7 +1332,6 @@ lqmpc_status run_ipm(Batch& b, const lqmpc_options& o, double* t_total, double* 
             // corrector: same factor
             st = kkt_step(b, o, true, &tm, polish, unseen);
             if (st != LQMPC_OK) return st;
-            launch_vec_copy(b.d_insts, b.count, b.max_sx, R_DXS, R_DX, 0, F_NONE, b.st);
             rec_event(c0->ev[3], b.st);
             seg_run(b, SEG_CORR_TAIL, [&]() { launch_step_update(b.d_insts, b.count, b.max_total, 1, b.st); });
             return LQMPC_OK;
