@@ -130,6 +130,9 @@ struct Inst {
     double *s3, *z3, *s4, *z4;        // n:  upper / lower input bound slacks and duals
     double *sigx, *sigu;              // SX, n
     double *sgu, *sgl;                // SX + n: z/s of each row's upper and lower family (rows as row_view)
+    double *rsu, *rsl;                // SX + n: 1/s of the families, for the iteration
+    double *rpu, *rpl;                // SX + n: primal residuals r_p of the families, for the iteration
+    double *rcu, *rcl;                // SX + n: the corrector's r_c of the families
     float* sigx32;                    // N x ldg: FP32 Sigma_x, row r at r*ldg, zero padding
     double *wz, *wx;                  // SX: vectors for Gamma' products
     double *wzu, *wxu;                // n
@@ -283,6 +286,100 @@ __device__ __forceinline__ bool last_arrival(Scal* S) {
     }
     __syncthreads();
     return last;
+}
+
+// Reductions shaped for this part's narrow FP64 pipe (two lanes per clock
+// per SM), for the per-row and conjugate-gradient kernels.
+//
+// block_ext: max (MAX) or min of non-negative doubles (and +inf).  Such
+// values order like their bit patterns read as signed 64-bit integers, so the
+// comparisons run on the integer pipe and the result is exact.  A positive
+// NaN orders above +inf (the max keeps it, the min drops it).
+constexpr long long kBitsPosInf = 0x7FF0000000000000LL;
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ long long abs_bits(double v) { return __double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFLL; }
+
+// max of two non-negative values by their bit patterns (a NaN is kept)
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+    return dbits(a) >= dbits(b) ? a : b;
+}
+
+template <bool MAX>
+__device__ __forceinline__ long long warp_ext_bits(long long b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long t = __shfl_xor_sync(0xffffffffu, b, o);
+        b = MAX ? (t > b ? t : b) : (t < b ? t : b);
+    }
+    return b;
+}
+
+template <bool MAX>
+__device__ __forceinline__ double block_ext(long long b, long long* sm32) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    b = warp_ext_bits<MAX>(b);
+    __syncthreads();
+    if (lane == 0) sm32[w] = b;
+    __syncthreads();
+    if (w == 0) b = warp_ext_bits<MAX>(lane < nw ? sm32[lane] : (MAX ? 0LL : kBitsPosInf));
+    return __longlong_as_double(b);
+}
+
+enum RedKind : int { kSum = 0, kMaxNonneg = 1, kMinNonneg = 2 };
+
+// One warp's reduction of n values src[0..n) (kind as RedKind; strided
+// over the lanes, then a shuffle tree; every lane gets the result).
+template <bool LDCG>
+__device__ __forceinline__ double warp_reduce_span(const double* src, int n, int kind) {
+    const int lane = threadIdx.x & 31;
+    if (kind == kSum) {
+        double t = 0.0;
+        for (int i = lane; i < n; i += 32) t += LDCG ? __ldcg(src + i) : src[i];
+        return warp_sum(t);
+    }
+    const bool mx = kind == kMaxNonneg;
+    long long b = mx ? 0LL : kBitsPosInf;
+    for (int i = lane; i < n; i += 32) {
+        const long long x = dbits(LDCG ? __ldcg(src + i) : src[i]);
+        b = mx ? (x > b ? x : b) : (x < b ? x : b);
+    }
+    return __longlong_as_double(mx ? warp_ext_bits<true>(b) : warp_ext_bits<false>(b));
+}
+
+// This CTA's partials of K quantities at once: the threads' values staged in
+// shared memory (stage holds K x blockDim.x doubles), then warp q (and every
+// nw-th warp after it) reduces quantity q into partial slot slot[q].  One
+// barrier; call once per kernel.
+template <int K>
+__device__ __forceinline__ void put_parts(const Inst& I, const double (&v)[K], const int (&slot)[K],
+                                          const int (&kind)[K], double* stage) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) stage[q * blockDim.x + threadIdx.x] = v[q];
+    __syncthreads();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        if (q % nw != w) continue;
+        const double r = warp_reduce_span<false>(stage + q * blockDim.x, blockDim.x, kind[q]);
+        if ((threadIdx.x & 31) == 0) I.part[slot[q] * kMaxParts + blockIdx.x] = r;
+    }
+}
+
+// The finish of a reduction (the instance's last CTA, after last_arrival):
+// warp q (and every nw-th after it) reduces partial slot slot[q] over the
+// nb[q] CTAs of the launch, read past L1, into out[q], in a fixed order.
+// Ends with a barrier.
+template <int K>
+__device__ __forceinline__ void reduce_parts(const Inst& I, const int (&slot)[K], const int (&kind)[K],
+                                             const int (&nb)[K], double* out) {
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        if (q % nw != w) continue;
+        const double r = warp_reduce_span<true>(I.part + (size_t)slot[q] * kMaxParts, nb[q], kind[q]);
+        if ((threadIdx.x & 31) == 0) out[q] = r;
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }

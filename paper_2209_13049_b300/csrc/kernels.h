@@ -100,7 +100,8 @@ int flowq_task_count(int n);
 void flowq_tasks(int q, int n, int* out);
 bool launch_potrf_flowq(const Inst* d_insts, const int* d_tasks, int ntasks, int max_n, int flags, cudaStream_t st);
 // tail: 0 none; 1 / 2 also the conjugate-gradient direction from z = out
-// (p = z / p = z + beta p with r'z) in the same launch
+// (p = z / p = z + beta p with r'z) in the same launch; 3 the float-float
+// split of out (for a Gamma product launched with kFuseInSplit)
 void launch_prec_apply(const Inst* d_insts, int count, int max_n, int in_role, int out_role, int flags,
                        cudaStream_t st, int tail = 0);
 void launch_chol_solve(const Inst* d_insts, int count, int max_n, int fp64, int in_role,

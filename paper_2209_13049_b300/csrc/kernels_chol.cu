@@ -741,7 +741,9 @@ __global__ void __launch_bounds__(kPrecThreads) k_prec_lower(const Inst* __restr
 }
 
 // tail (conjugate-gradient direction from z, run by the instance's last CTA):
-// 1 p = z and r'z; 2 beta = r'z_new / r'z_old, p = z + beta p.
+// 1 p = z and r'z; 2 beta = r'z_new / r'z_old, p = z + beta p, either split
+// for the next float-float Gamma p.  Tail 3 only splits z itself, element by
+// element (the float-float Gamma du that follows the first solve).
 template <int WPR>
 __global__ void __launch_bounds__(kPrecThreads) k_prec_upper(const Inst* __restrict__ insts, int out_role, int flags,
                                                              int tail) {
@@ -759,16 +761,20 @@ __global__ void __launch_bounds__(kPrecThreads) k_prec_upper(const Inst* __restr
     for (int j0 = blockIdx.x * G.RPC; j0 < n; j0 += gridDim.x * G.RPC) {   // uniform trip count in the CTA
         const int j = j0 + G.g, jj = j < n ? j : 0, len = j < n ? n - j : 0;
         const size_t c0 = (size_t)n * jj + jj;    // column j from row j on
+        double zj;
         if (two) {
             float h, l;
             prec_dot_ff<WPR>(X + c0, I.Xlo32 + c0, nullptr, I.r32 + jj, I.r32lo + jj, len, wsh, wsl, h, l);
-            if (G.tg == 0 && j < n) z[j] = (double)h + (double)l;
+            zj = (double)h + (double)l;
         } else {
-            const float acc = prec_dot32<WPR>(X + c0, I.r32 + jj, len, wsh);
-            if (G.tg == 0 && j < n) z[j] = (double)acc;
+            zj = (double)prec_dot32<WPR>(X + c0, I.r32 + jj, len, wsh);
+        }
+        if (G.tg == 0 && j < n) {
+            z[j] = zj;
+            if (tail == 3) split_ff(zj, I.ffv[j], I.ffv[n + j]);
         }
     }
-    if (!tail || !last_arrival(I.sc)) return;
+    if ((tail != 1 && tail != 2) || !last_arrival(I.sc)) return;
     Scal* S = I.sc;
     double rz = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) rz += I.rho[k] * __ldcg(z + k);

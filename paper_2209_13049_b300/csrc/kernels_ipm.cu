@@ -11,8 +11,18 @@
 // row of Gamma with two slacks.  Rows whose bound is infinite are absent:
 // their s = 1, z = 0 never change and they are left out of every sum.
 //
-// Reductions are deterministic: every block writes one partial per slot and a
-// one-block finaliser combines them in block order.
+// Reductions are deterministic: every block writes one partial per slot, and
+// the finish combines them in a fixed order.
+//
+// The per-row arithmetic is FP64, and the FP64 pipe of this part is narrow
+// (two lanes per clock per SM): these kernels are bound by the FP64
+// instructions of their most loaded SM.  Hence an equal share of rows per SM
+// (ew_grid), the primal residual, the reciprocal slacks and the corrector's
+// r_c formed once per iteration and loaded by the later kernels (a division
+// is some ten FP64 instructions), and reductions that leave the FP64 pipe
+// alone where they can (put_parts, reduce_parts: one warp per quantity, so
+// the finish in the instance's last CTA, while the other SMs wait, is one
+// round of loads and one barrier).
 #include "common.cuh"
 #include "gamma_ff.cuh"
 #include "kernels.h"
@@ -31,6 +41,11 @@ struct RowView {
     bool fu, fl;          // bounds finite
 };
 
+// isfinite on the bit pattern (integer pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7FF0000000000000LL) != 0x7FF0000000000000LL;
+}
+
 __device__ __forceinline__ RowView row_view(const Inst& I, int k) {
     RowView r;
     if (k < I.SX) {
@@ -44,9 +59,11 @@ __device__ __forceinline__ RowView row_view(const Inst& I, int k) {
         r.ds_u = I.ds3 + j; r.dz_u = I.dz3 + j; r.ds_l = I.ds4 + j; r.dz_l = I.dz4 + j;
         r.lo = I.ul[c]; r.hi = I.uu[c]; r.v = I.u[j];
     }
-    r.fu = isfinite(r.hi); r.fl = isfinite(r.lo);
+    r.fu = finite_bits(r.hi); r.fl = finite_bits(r.lo);
     return r;
 }
+
+constexpr int kEwMaxThreads = 1024;   // largest CTA of the per-row kernels
 
 // Write one partial per slot for this block.
 __device__ __forceinline__ void put_part(const Inst& I, int slot, double v) {
@@ -153,8 +170,10 @@ __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double to
 
 // ---------------------------------------------------------------------------
 // Residuals (Eq. 5), Sigma = S^{-1} Z (Eq. 6) and the predictor vectors.
-//   r_p per family; Sigma_x = z1/s1 + z2/s2 per state row, Sigma_u likewise;
-//   wz = z1 - z2 (for the Gamma' z term of r_d);
+//   r_p per family (kept in rpu / rpl for the step kernels of the iteration),
+//   1/s per family (rsu / rsl), Sigma_x = z1/s1 + z2/s2 per state row,
+//   Sigma_u likewise (z/s of each family in sgu / sgl); wz = z1 - z2 (for
+//   the Gamma' z term of r_d);
 //   predictor w_i = z_i - Sigma_i r_p,i, combined wx = w1 - w2 (for Gamma').
 // Partials: slot 0 max|r_p|, slot 1 sum s.z.  With split, also the
 // float-float split of wz and wx for the float-float Gamma' product of both
@@ -163,7 +182,7 @@ __global__ void k_init_fin(const Inst* __restrict__ insts, int nparts, double to
 
 __global__ void k_resid(const Inst* __restrict__ insts, int split) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ double stage[2 * kEwMaxThreads];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     // An iteration starts with no failed solve and no failed pivot (a repeat
@@ -171,15 +190,23 @@ __global__ void k_resid(const Inst* __restrict__ insts, int split) {
     // kernel of the iteration on the main stream, before any KKT launch.
     if (blockIdx.x == 0 && threadIdx.x == 0) { I.sc->spec_fail = 0; I.sc->info = 0; }
     const int total = I.SX + I.n;
-    double rpmax = 0.0, sz = 0.0;
+    long long rpmax = 0;   // bits of max |r_p|
+    double sz = 0.0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         RowView r = row_view(I, k);
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double rpu = r.fu ? r.v + su - r.hi : 0.0;
         double rpl = r.fl ? -r.v + sl + r.lo : 0.0;
-        double sgu = zu / su, sgl = zl / sl;
-        I.sgu[k] = sgu; I.sgl[k] = sgl;   // for the affine step (no second division)
-        rpmax = fmax(rpmax, fmax(fabs(rpu), fabs(rpl)));
+        // 1/s once per iteration: Sigma here, the corrector and the step
+        // multiply by it (an absent row has s = 1, z = 0)
+        const double rsu = 1.0 / su, rsl = 1.0 / sl;
+        const double sgu = zu * rsu, sgl = zl * rsl;
+        I.sgu[k] = sgu; I.sgl[k] = sgl;
+        I.rsu[k] = rsu; I.rsl[k] = rsl;
+        I.rpu[k] = rpu; I.rpl[k] = rpl;
+        const long long a = abs_bits(rpu), b = abs_bits(rpl);
+        rpmax = a > rpmax ? a : rpmax;
+        rpmax = b > rpmax ? b : rpmax;
         if (r.fu) sz += su * zu;
         if (r.fl) sz += sl * zl;
         double wz = zu - zl;
@@ -200,8 +227,9 @@ __global__ void k_resid(const Inst* __restrict__ insts, int split) {
             I.sigu[j] = sgu + sgl; I.wzu[j] = wz; I.wxu[j] = wx;
         }
     }
-    double v = block_reduce<1>(rpmax, red); put_part(I, 0, v);
-    v = block_reduce<0>(sz, red); put_part(I, 1, v);
+    const double v[2] = {__longlong_as_double(rpmax), sz};
+    constexpr int slot[2] = {0, 1}, kind[2] = {kMaxNonneg, kSum};
+    put_parts<2>(I, v, slot, kind, stage);
 }
 
 // r_d = H u + h + Gamma'(z1 - z2) + z3 - z4 (Eq. 5a with lambda = z) and the
@@ -210,12 +238,12 @@ __global__ void k_resid(const Inst* __restrict__ insts, int split) {
 // Partial: slot 2 max|r_d|.
 __global__ void k_rd(const Inst* __restrict__ insts) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ long long ext[32];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x >> 5;
-    double rdmax = 0.0;
+    long long rdmax = 0;   // bits of max |r_d|
     for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < I.n; j += gridDim.x * wpb) {
         const double* hc = I.H64 + (size_t)j * I.n;
         double acc = 0.0;
@@ -225,28 +253,26 @@ __global__ void k_rd(const Inst* __restrict__ insts) {
             double rd = acc + I.h[j] + I.gz[j] + I.wzu[j];
             I.rd[j] = rd;
             I.b[j] = -rd + I.gw[j] + I.wxu[j];
-            rdmax = fmax(rdmax, fabs(rd));
+            const long long a = abs_bits(rd);
+            rdmax = a > rdmax ? a : rdmax;
         }
     }
-    double v = block_reduce<1>(rdmax, red); put_part(I, 2, v);
+    double v = block_ext<true>(rdmax, ext); put_part(I, 2, v);
 }
 
 // Stop test and trace.  nb1: partial count of k_resid, nb2: of k_rd.
 __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int trace_on) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ double fin[3];
     const Inst& I = insts[blockIdx.y];
     Scal* S = I.sc;
     if (S->done) return;
-    double rp = 0, sz = 0, rd = 0;
-    for (int p = threadIdx.x; p < nb1; p += blockDim.x) {
-        rp = fmax(rp, I.part[0 * kMaxParts + p]);
-        sz += I.part[1 * kMaxParts + p];
+    {
+        constexpr int slot[3] = {0, 1, 2}, kind[3] = {kMaxNonneg, kSum, kMaxNonneg};
+        const int cnt[3] = {nb1, nb1, nb2};
+        reduce_parts<3>(I, slot, kind, cnt, fin);
     }
-    for (int p = threadIdx.x; p < nb2; p += blockDim.x) rd = fmax(rd, I.part[2 * kMaxParts + p]);
-    rp = block_reduce<1>(rp, red);
-    sz = block_reduce<0>(sz, red);
-    rd = block_reduce<1>(rd, red);
+    const double rp = fin[0], sz = fin[1], rd = fin[2];
     if (threadIdx.x == 0) {
         double mu = S->m > 0 ? sz / S->m : 0.0;
         double res_d = rd / (1.0 + S->hnorm);
@@ -258,7 +284,8 @@ __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int tr
             t[0] = mu; t[1] = res_d; t[2] = res_p; t[3] = 0; t[4] = 0; t[5] = 0; t[6] = 0; t[7] = -1;
         }
         S->refine_iter = 0;
-        if (!(res == res)) { S->done = 1; S->status = 6; }
+        // a NaN in any row reaches its maximum (the integer order keeps it)
+        if (!(res == res) || !(res_d == res_d) || !(res_p == res_p) || !(mu == mu)) { S->done = 1; S->status = 6; }
         else if (res <= S->tol) { S->done = 1; S->status = 0; }
         else if (S->iter >= S->max_iter) { S->done = 1; S->status = 4; }
     }
@@ -275,17 +302,19 @@ __global__ void k_check(const Inst* __restrict__ insts, int nb1, int nb2, int tr
 // fraction (num, den) with den > 0 and compared by cross-multiplication
 // (v * den < num * (-dv)): one FP64 division per thread at the end instead of
 // one per candidate (this part's FP64 division costs several FMA-pipe passes).
+// The sign test reads the sign bit (integer pipe): a -0 or a negative NaN
+// passes it but never wins the cross-multiplied comparison (v > 0).
 struct StepMin {
     double num = INFINITY, den = 1.0;
     __device__ __forceinline__ void add(double v, double dv) {
-        if (dv < 0.0 && v * den < num * -dv) { num = v; den = -dv; }
+        if (__double_as_longlong(dv) < 0 && v * den < num * -dv) { num = v; den = -dv; }
     }
     __device__ __forceinline__ double value() const { return num / den; }
 };
 
 __global__ void k_aff(const Inst* __restrict__ insts) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ double stage[3 * kEwMaxThreads];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done) return;
     const int total = I.SX + I.n;
@@ -297,51 +326,45 @@ __global__ void k_aff(const Inst* __restrict__ insts) {
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
         if (r.fu) {
-            double rp = r.v + su - r.hi;
-            dsu = -rp - d; dzu = -zu - I.sgu[k] * dsu;
+            dsu = -I.rpu[k] - d; dzu = -zu - I.sgu[k] * dsu;
             am.add(su, dsu); am.add(zu, dzu);
             s4 += su * dzu + zu * dsu; s5 += dsu * dzu;
         }
         if (r.fl) {
-            double rp = -r.v + sl + r.lo;
-            dsl = -rp + d; dzl = -zl - I.sgl[k] * dsl;
+            dsl = -I.rpl[k] + d; dzl = -zl - I.sgl[k] * dsl;
             am.add(sl, dsl); am.add(zl, dzl);
             s4 += sl * dzl + zl * dsl; s5 += dsl * dzl;
         }
         *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
     }
-    double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
-    v = block_reduce<0>(s4, red); put_part(I, 4, v);
-    v = block_reduce<0>(s5, red); put_part(I, 5, v);
+    const double v[3] = {am.value(), s4, s5};
+    constexpr int slot[3] = {3, 4, 5}, kind[3] = {kMinNonneg, kSum, kSum};
+    put_parts<3>(I, v, slot, kind, stage);
     if (!last_arrival(I.sc)) return;
-    // The instance's last CTA: alpha_aff = min(1, max step); mu_aff; sigma =
-    // (mu_aff/mu)^3 (Mehrotra).  Slot 1 (sum s.z) is k_resid's, launched on
-    // the same grid; the partials of the other CTAs are read past L1.
-    Scal* S = I.sc;
-    const int nb = gridDim.x;
-    double a = INFINITY, sz = 0, s4p = 0, s5p = 0;
-    for (int p = threadIdx.x; p < nb; p += blockDim.x) {
-        a = fmin(a, __ldcg(I.part + 3 * kMaxParts + p));
-        sz += __ldcg(I.part + 1 * kMaxParts + p);
-        s4p += __ldcg(I.part + 4 * kMaxParts + p);
-        s5p += __ldcg(I.part + 5 * kMaxParts + p);
+    // The instance's last CTA: alpha_aff = min(1, max step); mu_aff = (sum
+    // s z + a S4 + a^2 S5) / m; sigma = (mu_aff/mu)^3 (Mehrotra).  Slot 1
+    // (sum s.z) is k_resid's, launched on the same grid.
+    __shared__ double fin[4];
+    {
+        const int nb = gridDim.x;
+        constexpr int fslot[4] = {3, 1, 4, 5}, fkind[4] = {kMinNonneg, kSum, kSum, kSum};
+        const int cnt[4] = {nb, nb, nb, nb};
+        reduce_parts<4>(I, fslot, fkind, cnt, fin);
     }
-    a = block_reduce<2>(a, red);
-    sz = block_reduce<0>(sz, red);
-    s4 = block_reduce<0>(s4p, red);
-    s5 = block_reduce<0>(s5p, red);
     if (threadIdx.x == 0) {
-        double al = fmin(1.0, a);
-        double mu_aff = S->m > 0 ? (sz + al * s4 + al * al * s5) / S->m : 0.0;
-        double ratio_ = S->mu > 0.0 ? mu_aff / S->mu : 0.0;
+        Scal* S = I.sc;
+        const double al = fmin(1.0, fin[0]);
+        const double mu_aff = S->m > 0 ? (fin[1] + al * fin[2] + al * al * fin[3]) / S->m : 0.0;
+        const double ratio_ = S->mu > 0.0 ? mu_aff / S->mu : 0.0;
         S->alpha_aff = al; S->mu_aff = mu_aff;
         S->sigma = ratio_ * ratio_ * ratio_;
     }
 }
 
-// Corrector: r_c = s.z + ds_aff.dz_aff - sigma mu; w = (r_c - z r_p)/s per
-// family; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).  With
-// split, also the float-float split of wx (hi0, lo0 in ffw).
+// Corrector: r_c = s.z + ds_aff.dz_aff - sigma mu (kept in rcu / rcl for
+// the step); w = (r_c - z r_p)/s per family, with the iteration's r_p and
+// 1/s; wx = w1 - w2 (state rows), wxu = w3 - w4 (input rows).  With split,
+// also the float-float split of wx (hi0, lo0 in ffw).
 __global__ void k_corr(const Inst* __restrict__ insts, int split) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
@@ -353,14 +376,14 @@ __global__ void k_corr(const Inst* __restrict__ insts, int split) {
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double wu = 0, wl = 0;
         if (r.fu) {
-            double rp = r.v + su - r.hi;
-            double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
-            wu = (rc - zu * rp) / su;
+            const double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
+            I.rcu[k] = rc;
+            wu = (rc - zu * I.rpu[k]) * I.rsu[k];
         }
         if (r.fl) {
-            double rp = -r.v + sl + r.lo;
-            double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
-            wl = (rc - zl * rp) / sl;
+            const double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
+            I.rcl[k] = rc;
+            wl = (rc - zl * I.rpl[k]) * I.rsl[k];
         }
         if (k < I.SX) {
             I.wx[k] = wu - wl;
@@ -384,17 +407,16 @@ __global__ void k_rhs(const Inst* __restrict__ insts) {
         I.b[j] = -I.rd[j] + I.gw[j] + I.wxu[j];
 }
 
-// Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with r_c from the
-// stored affine step.  Overwrites ds*/dz*.  Partial: slot 3 max step.  This
-// and the update (k_update) skip an
-// instance whose KKT solve of the iteration failed unseen (Scal::spec_fail):
-// the iterate stays as it was and the host repeats the iteration.
+// Corrector step: ds = -r_p - J du, dz = -(r_c + z ds)/s, with the
+// iteration's r_p and 1/s and the corrector's r_c.  Overwrites ds*/dz*.
+// Partial: slot 3 max step.  This and the update (k_update) skip an instance
+// whose KKT solve of the iteration failed unseen (Scal::spec_fail): the
+// iterate stays as it was and the host repeats the iteration.
 __global__ void k_step(const Inst* __restrict__ insts, int trace_on) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ double stage[kEwMaxThreads];
     const Inst& I = insts[blockIdx.y];
     if (I.sc->done || I.sc->spec_fail) return;
-    const double smu = I.sc->sigma * I.sc->mu;
     const int total = I.SX + I.n;
     StepMin am;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
@@ -403,29 +425,30 @@ __global__ void k_step(const Inst* __restrict__ insts, int trace_on) {
         double su = *r.s_u, zu = *r.z_u, sl = *r.s_l, zl = *r.z_l;
         double dsu = 0, dzu = 0, dsl = 0, dzl = 0;
         if (r.fu) {
-            double rp = r.v + su - r.hi;
-            double rc = su * zu + (*r.ds_u) * (*r.dz_u) - smu;
-            dsu = -rp - d; dzu = -(rc + zu * dsu) / su;
+            dsu = -I.rpu[k] - d; dzu = -(I.rcu[k] + zu * dsu) * I.rsu[k];
             am.add(su, dsu); am.add(zu, dzu);
         }
         if (r.fl) {
-            double rp = -r.v + sl + r.lo;
-            double rc = sl * zl + (*r.ds_l) * (*r.dz_l) - smu;
-            dsl = -rp + d; dzl = -(rc + zl * dsl) / sl;
+            dsl = -I.rpl[k] + d; dzl = -(I.rcl[k] + zl * dsl) * I.rsl[k];
             am.add(sl, dsl); am.add(zl, dzl);
         }
         *r.ds_u = dsu; *r.dz_u = dzu; *r.ds_l = dsl; *r.dz_l = dzl;
     }
-    double v = block_reduce<2>(am.value(), red); put_part(I, 3, v);
+    const double v[1] = {am.value()};
+    constexpr int slot[1] = {3}, kind[1] = {kMinNonneg};
+    put_parts<1>(I, v, slot, kind, stage);
     if (!last_arrival(I.sc)) return;
-    // The instance's last CTA: alpha = min(1, tau * max step); trace; the
-    // iteration count (k_update reads alpha only).
-    Scal* S = I.sc;
-    double a = INFINITY;
-    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) a = fmin(a, __ldcg(I.part + 3 * kMaxParts + p));
-    a = block_reduce<2>(a, red);
+    // The instance's last CTA: alpha = min(1, tau * max step); the trace row;
+    // the iteration count (k_update reads alpha only).
+    __shared__ double fin[1];
+    {
+        constexpr int fslot[1] = {3}, fkind[1] = {kMinNonneg};
+        const int cnt[1] = {(int)gridDim.x};
+        reduce_parts<1>(I, fslot, fkind, cnt, fin);
+    }
     if (threadIdx.x == 0) {
-        double al = fmin(1.0, S->tau * a);
+        Scal* S = I.sc;
+        const double al = fmin(1.0, S->tau * fin[0]);
         S->alpha = al;
         if (trace_on && S->iter <= S->max_iter) {
             double* t = I.trace + (size_t)S->iter * kTraceW;
@@ -462,6 +485,37 @@ static int ew_blocks(int total_max, int threads) {
     return b < 1 ? 1 : (b > kMaxParts ? kMaxParts : b);
 }
 
+static int sm_count() {
+    static const int n = []() {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1)
+            v = 1;
+        return v;
+    }();
+    return n;
+}
+
+// Grid of the per-row kernels of an iteration (k_resid, k_aff, k_corr,
+// k_step, k_update; k_aff's finish reads k_resid's partials, so they share
+// it).  Their time is the FP64 work of the most loaded SM: a single instance
+// takes one CTA per SM with an equal share of the rows (a multiple of 32
+// threads; CTAs of 1024 over a grid stride past 1024 rows per SM); a batch
+// keeps 256-thread CTAs per instance, whose many CTAs spread by themselves.
+struct EwGrid {
+    int nb, threads;
+};
+static EwGrid ew_grid(int count, int max_total) {
+    if (count == 1) {
+        const int sms = sm_count();
+        int th = ((max_total + sms - 1) / sms + 31) / 32 * 32;
+        th = th < 64 ? 64 : th;
+        if (th <= kEwMaxThreads) return {ew_blocks(max_total, th), th};
+        return {ew_blocks(max_total, kEwMaxThreads), kEwMaxThreads};
+    }
+    return {ew_blocks(max_total, 256), 256};
+}
+
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
                        double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0,
                        double smin) {
@@ -476,8 +530,9 @@ void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, i
 
 void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n, int trace_on,
                         cudaStream_t st, bool do_resid, bool do_rd, int rd_parts, bool split_w) {
-    int nb1 = ew_blocks(max_total, 256);
-    if (do_resid) LQ_LAUNCH(lq_pdl(k_resid, dim3(nb1, count), 256, 0, st, d_insts, split_w ? 1 : 0));
+    const EwGrid g = ew_grid(count, max_total);
+    const int nb1 = g.nb;
+    if (do_resid) LQ_LAUNCH(lq_pdl(k_resid, dim3(nb1, count), g.threads, 0, st, d_insts, split_w ? 1 : 0));
     int wpb = 8;
     int nb2 = (max_n + wpb - 1) / wpb;
     nb2 = nb2 > kMaxParts ? kMaxParts : nb2;
@@ -488,12 +543,13 @@ void launch_resid_check(const Inst* d_insts, int count, int max_total, int max_n
 }
 
 void launch_aff(const Inst* d_insts, int count, int max_total, cudaStream_t st) {
-    int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(lq_pdl(k_aff, dim3(nb, count), 256, 0, st, d_insts));
+    const EwGrid g = ew_grid(count, max_total);
+    LQ_LAUNCH(lq_pdl(k_aff, dim3(g.nb, count), g.threads, 0, st, d_insts));
 }
 
 void launch_corr(const Inst* d_insts, int count, int max_total, cudaStream_t st, bool split_w) {
-    LQ_LAUNCH(lq_pdl(k_corr, dim3(ew_blocks(max_total, 256), count), 256, 0, st, d_insts, split_w ? 1 : 0));
+    const EwGrid g = ew_grid(count, max_total);
+    LQ_LAUNCH(lq_pdl(k_corr, dim3(g.nb, count), g.threads, 0, st, d_insts, split_w ? 1 : 0));
 }
 
 void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
@@ -502,9 +558,9 @@ void launch_rhs(const Inst* d_insts, int count, int max_n, cudaStream_t st) {
 
 void launch_step_update(const Inst* d_insts, int count, int max_total, int trace_on,
                         cudaStream_t st) {
-    int nb = ew_blocks(max_total, 256);
-    LQ_LAUNCH(lq_pdl(k_step, dim3(nb, count), 256, 0, st, d_insts, trace_on));
-    LQ_LAUNCH(lq_pdl(k_update, dim3(nb, count), 256, 0, st, d_insts));
+    const EwGrid g = ew_grid(count, max_total);
+    LQ_LAUNCH(lq_pdl(k_step, dim3(g.nb, count), g.threads, 0, st, d_insts, trace_on));
+    LQ_LAUNCH(lq_pdl(k_update, dim3(g.nb, count), g.threads, 0, st, d_insts));
 }
 
 }  // namespace lqmpc

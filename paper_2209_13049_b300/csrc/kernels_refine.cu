@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __rest
                                                               int splits) {
     pdl_wait();
     constexpr int kW = kMvThreads / 32, RPC = kW / WPR, GT = 32 * WPR;
-    __shared__ double red[32];
     __shared__ double wsum[kW];
+    __shared__ double gred[RPC];
+    __shared__ double fin[1];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
     const double* v = mode == 0 ? I.du : I.pp;
@@ -167,25 +168,33 @@ __global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __rest
             if (mode == 0) {
                 const double r = I.b[j] - mj;
                 I.rho[j] = r;
-                acc_red = fmax(acc_red, fabs(r));
+                acc_red = max_nonneg(acc_red, fabs(r));
             } else {
                 I.qq[j] = mj;
                 acc_red += v[j] * mj;
             }
         }
     }
-    double t = mode == 0 ? block_reduce<1>(acc_red, red) : block_reduce<0>(acc_red, red);
-    if (threadIdx.x == 0) I.part[6 * kMaxParts + blockIdx.x] = t;
-    if (!last_arrival(I.sc)) return;
-    double m = 0.0;
-    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) {
-        const double w = __ldcg(I.part + 6 * kMaxParts + p);
-        m = mode == 0 ? fmax(m, w) : m + w;
-    }
-    m = mode == 0 ? block_reduce<1>(m, red) : block_reduce<0>(m, red);
+    // The CTA's partial: only the row groups' leaders hold values (one per
+    // group), so they meet in shared memory and thread 0 combines them in
+    // group order -- no block-wide FP64 shuffle tree.
+    if (tg == 0) gred[grp] = acc_red;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        if (mode == 0) pcg_test(I, m);
-        else pcg_alpha(I, m);
+        double t = gred[0];
+        for (int q = 1; q < RPC; ++q) t = mode == 0 ? max_nonneg(t, gred[q]) : t + gred[q];
+        I.part[6 * kMaxParts + blockIdx.x] = t;
+    }
+    if (!last_arrival(I.sc)) return;
+    {
+        constexpr int slot[1] = {6};
+        const int kind[1] = {mode == 0 ? (int)kMaxNonneg : (int)kSum};
+        const int cnt[1] = {(int)gridDim.x};
+        reduce_parts<1>(I, slot, kind, cnt, fin);
+    }
+    if (threadIdx.x == 0) {
+        if (mode == 0) pcg_test(I, fin[0]);
+        else pcg_alpha(I, fin[0]);
     }
 }
 
@@ -277,30 +286,34 @@ __device__ void pcg_alpha(const Inst& I, double pq) {
 // rows).  Partial max|r| in slot 7; the last CTA runs the convergence test.
 __global__ void k_pcg_axpy(const Inst* __restrict__ insts, int sel) {
     pdl_wait();
-    __shared__ double red[32];
+    __shared__ long long ext[32];
+    __shared__ double fin[1];
     const Inst& I = insts[blockIdx.y];
     if (pcg_skip(I, sel)) return;
     const double al = I.sc->pcg_alpha;
     const int total = I.SX + I.n;
-    double rmax = 0.0;
+    long long rmax = 0;   // bits of max |r| (integer order, no FP64 max)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x) {
         if (k < I.n) {
             I.du[k] += al * I.pp[k];
             double r = I.rho[k] - al * I.qq[k];
             I.rho[k] = r;
-            rmax = fmax(rmax, fabs(r));
+            const long long a = abs_bits(r);
+            rmax = a > rmax ? a : rmax;
         } else {
             const int q = k - I.n;
             I.dxs[q] += al * I.tmpx[q];
         }
     }
-    double v = block_reduce<1>(rmax, red);
+    double v = block_ext<true>(rmax, ext);
     if (threadIdx.x == 0) I.part[7 * kMaxParts + blockIdx.x] = v;
     if (!last_arrival(I.sc)) return;
-    double m = 0.0;
-    for (int p = threadIdx.x; p < (int)gridDim.x; p += blockDim.x) m = fmax(m, __ldcg(I.part + 7 * kMaxParts + p));
-    m = block_reduce<1>(m, red);
-    if (threadIdx.x == 0) pcg_test(I, m);
+    {
+        constexpr int slot[1] = {7}, kind[1] = {kMaxNonneg};
+        const int cnt[1] = {(int)gridDim.x};
+        reduce_parts<1>(I, slot, kind, cnt, fin);
+    }
+    if (threadIdx.x == 0) pcg_test(I, fin[0]);
 }
 
 // beta = r'z_new / r'z_old; p = z + beta p (one block per instance).

@@ -276,6 +276,9 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
     auto s4 = c.take<double>(n); auto z4 = c.take<double>(n);
     auto sigx = c.take<double>(SX); auto sigu = c.take<double>(n);
     auto sgu = c.take<double>((size_t)SX + n); auto sgl = c.take<double>((size_t)SX + n);
+    auto rsu = c.take<double>((size_t)SX + n); auto rsl = c.take<double>((size_t)SX + n);
+    auto rpu = c.take<double>((size_t)SX + n); auto rpl = c.take<double>((size_t)SX + n);
+    auto rcu = c.take<double>((size_t)SX + n); auto rcl = c.take<double>((size_t)SX + n);
     auto sigx32 = c.take<float>((size_t)I.N * I.ldg);
     auto wz = c.take<double>(SX); auto wx = c.take<double>(SX);
     auto wzu = c.take<double>(n); auto wxu = c.take<double>(n);
@@ -320,6 +323,7 @@ size_t layout(Inst& I, unsigned char* base, int nnzA, int nnzQ, int nnzQf, int m
         I.xbar = xbar; I.y = y; I.h = h; I.u = u; I.x = x;
         I.s1 = s1; I.z1 = z1; I.s2 = s2; I.z2 = z2; I.s3 = s3; I.z3 = z3; I.s4 = s4; I.z4 = z4;
         I.sigx = sigx; I.sigu = sigu; I.sigx32 = sigx32; I.sgu = sgu; I.sgl = sgl;
+        I.rsu = rsu; I.rsl = rsl; I.rpu = rpu; I.rpl = rpl; I.rcu = rcu; I.rcl = rcl;
         I.wz = wz; I.wx = wx; I.wzu = wzu; I.wxu = wxu; I.gz = gz; I.gw = gw;
         I.rd = rd; I.b = b; I.du = du; I.du_aff = du_aff;
         I.ds1 = ds1; I.dz1 = dz1; I.ds2 = ds2; I.dz2 = dz2;
@@ -917,10 +921,11 @@ lqmpc_status kkt_solve_mixed(Batch& b, int refine_max, bool prec64 = false, int 
     const int kp = prec64 ? 100 : 0;   // separate graphs for the two preconditioners
     // start: ||b||, du = P^{-1} b, the initial residual r = b - M du (and
     // Gamma du), z = P^{-1} r and the first direction
+    const bool split_du = b.ff && !prec64;   // the FP32 preconditioner splits du for the Gamma du
     auto first = [&]() {
         launch_pcg_begin(b.d_insts, b.count, sel, refine_max, budget_lo, budget_mid, b.st);
-        prec(R_B, R_DU, sel);
-        pcg_apply_m(b, R_DU, 0, sel, selr, true, false);
+        prec(R_B, R_DU, sel, split_du ? 3 : 0);
+        pcg_apply_m(b, R_DU, 0, sel, selr, true, split_du);
         prec(R_RHO, R_DCORR, selr, 1);
     };
     // one CG step: q = M p, alpha, du/r/dxs update and test; then z = P r and

@@ -189,7 +189,8 @@ def test_warm_start_from_stored_guess_takes_the_oracle_warm_iterates(warm_gold):
     at 1e-2, duals mu0 / s) against the oracle started from the same stored
     guess: the FP64 path takes the oracle's warm iterates (same count, mu_k);
     the FP32 tier, single and batched, stops within 1e-6 of the oracle's warm
-    stop point; both at 1e-11 within the usual bars."""
+    stop point; at 1e-11 the FP64 path stops within the degenerate optimum's
+    band of the oracle's and meets the KKT conditions."""
     g, xt = warm_gold
     p = inputs.heat2d(32, 10, 50)
     s = binding.Solver(p, precision="fp64")
@@ -199,13 +200,23 @@ def test_warm_start_from_stored_guess_takes_the_oracle_warm_iterates(warm_gold):
         assert st["iters"] == len(g[f"v{j}_trace8"]) - 1, j
         np.testing.assert_allclose(s.get_trace()[:, 0], g[f"v{j}_trace8"][:, 0], rtol=1e-6)
         assert rel(u, g[f"v{j}_u8"]) <= 1e-8, j
-    # both run on to 1e-11: the same iterates in exact arithmetic, but at
+    # Both run on to 1e-11: the same iterates in exact arithmetic, but at
     # mu ~ 1e-11 the rounding of each Newton step is amplified by
-    # cond(M) ~ 1/mu; the bar is one decade above the cold start's
+    # cond(M) ~ 1/mu, and the warm start of held-out x0 3 meets a degenerate
+    # optimum (a pair of inputs moves by +-2.6e-6 along a direction the cost
+    # does not see to first order): the oracle's own 1e-11 stop lies 2.45e-6
+    # from where it stalls at 1e-12 and 1e-13.  So the stop is compared
+    # within sqrt(tol), and the result must satisfy the optimality
+    # conditions on its own (the stop test bounds the mean complementarity).
     s.set_options(tol=1e-11)
     for j in range(len(xt)):
         u, _ = s.solve_warm(xt[j], g[f"v{j}_guess"])
-        assert rel(u, g[f"v{j}_u12"]) <= 1e-9, j
+        assert rel(u, g[f"v{j}_u12"]) <= np.sqrt(1e-11), j
+        kc = oracle.kkt_check(p, xt[j], u, s.get_duals())
+        assert kc["primal_violation"] <= 1e-9, j
+        assert kc["dual_min"] >= 0.0, j
+        assert kc["stationarity"] <= 1e-8, j
+        assert kc["complementarity_mean"] <= 1.01e-11, j
     m = binding.Solver(p, precision="fp32")
     for j in range(len(xt)):
         u, st = m.solve_warm(xt[j], g[f"v{j}_guess"])
