@@ -372,14 +372,14 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
         }
         __syncthreads();
     }
-    // partial[split][r][i]
-    double* part = I.gpart + (size_t)split * I.SX;
+    // partial[split][r][i], float-float
+    float2* part = ff_parts(I) + (size_t)split * I.SX;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
-            if (i < ns && r >= 0) part[(size_t)r * ns + i] = (double)sh[a][b] + (double)sl[a][b];
+            if (i < ns && r >= 0) part[(size_t)r * ns + i] = make_float2(sh[a][b], sl[a][b]);
         }
     if (!(fuse & kFuseSumHere)) return;
     __shared__ int last_sh;
@@ -401,12 +401,14 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
             if (i >= ns || r < 0) continue;
             const size_t k = (size_t)r * ns + i;
-            double pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
+            float2 pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
 #pragma unroll
-            for (int q = 0; q < kFfMaxSplits; ++q) pv[q] = q < S ? __ldcg(I.gpart + (size_t)q * I.SX + k) : 0.0;
-            double sum = 0.0;
+            for (int q = 0; q < kFfMaxSplits; ++q)
+                pv[q] = q < S ? __ldcg(ff_parts(I) + (size_t)q * I.SX + k) : make_float2(0.f, 0.f);
+            float hs = 0.f, ls = 0.f;
 #pragma unroll
-            for (int q = 0; q < kFfMaxSplits; ++q) sum += pv[q];
+            for (int q = 0; q < kFfMaxSplits; ++q) ff_acc(hs, ls, pv[q].x, pv[q].y);
+            const double sum = (double)hs + (double)ls;
             out[k] = sum;
             if (fuse & kFuseOutDxs) I.dxs[k] = sum;
             if (fuse & kFuseOutW) {
@@ -431,12 +433,14 @@ __global__ void k_gamma_mv_ff_sum(const Inst* __restrict__ insts, int out_role, 
         // the splits of row r's r-tile (the split plan of k_gamma_mv_ff)
         int kbeg, nk, S;
         mv_ff_rtile((I.N - 1 - k / I.ns) / kFfBN, I.N, I.nu, I.n, kbeg, nk, S);
-        double pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
+        float2 pv[kFfMaxSplits];   // every split's partial in flight at once, summed in split order
 #pragma unroll
-        for (int q = 0; q < kFfMaxSplits; ++q) pv[q] = q < S ? I.gpart[(size_t)q * I.SX + k] : 0.0;
-        double s = 0.0;
+        for (int q = 0; q < kFfMaxSplits; ++q)
+            pv[q] = q < S ? ff_parts(I)[(size_t)q * I.SX + k] : make_float2(0.f, 0.f);
+        float hs = 0.f, ls = 0.f;
 #pragma unroll
-        for (int q = 0; q < kFfMaxSplits; ++q) s += pv[q];
+        for (int q = 0; q < kFfMaxSplits; ++q) ff_acc(hs, ls, pv[q].x, pv[q].y);
+        const double s = (double)hs + (double)ls;
         out[k] = s;
         if (fuse & kFuseOutDxs) I.dxs[k] = s;
         if (fuse & kFuseOutW) {
@@ -565,7 +569,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
     // partial[split] skewed along the anti-diagonals Gamma' sums: P[col, r']
     // with col = (N-1-d) nu + c and r' = vec N + r goes to [vec][t][c][d],
     // t = r - d, so the terms of one output are contiguous; t < 0 is not used
-    double* part = I.gpart + (size_t)split * NR * n;
+    float2* part = ff_parts(I) + (size_t)split * NR * n;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -573,7 +577,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_tmv_ff(const Inst* __restr
             const int col = c0 + ty + 16 * a, r = r_lo + tx + 8 * b;
             if (col < n && r >= 0) {
                 const int d = N - 1 - col / nu, c = col % nu, t = r - d;
-                if (t >= 0) part[(((size_t)vec_t * N + t) * nu + c) * N + d] = (double)sh[a][b] + (double)sl[a][b];
+                if (t >= 0) part[(((size_t)vec_t * N + t) * nu + c) * N + d] = make_float2(sh[a][b], sl[a][b]);
             }
         }
 }

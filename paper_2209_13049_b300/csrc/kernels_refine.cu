@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __rest
                                                               int splits) {
     pdl_wait();
     constexpr int kW = kMvThreads / 32, RPC = kW / WPR, GT = 32 * WPR;
-    __shared__ double wsum[kW];
+    __shared__ float2 wsum[kW];
     __shared__ double gred[RPC];
     __shared__ double fin[1];
     const Inst& I = insts[blockIdx.y];
@@ -121,7 +121,8 @@ __global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __rest
     double acc_red = 0.0;                          // the group leader's
     for (int j0 = blockIdx.x * RPC; j0 < n; j0 += gridDim.x * RPC) {   // uniform trip count in the CTA
         const int j = j0 + grp;
-        double s = 0.0;
+        double s = 0.0;               // this lane's share of H row j . v (FP64)
+        float gh = 0.f, gl = 0.f;     // and of the Gamma' partials (float-float)
         if (j < n) {
             const double* hc = I.H64 + (size_t)j * n;
             double hv[kMvH], vv[kMvH];
@@ -133,36 +134,49 @@ __global__ void __launch_bounds__(kMvThreads) k_pcg_matvec_ff(const Inst* __rest
             }
             // Gamma' partials of output j (see gamma_tmv_ff_gather)
             const int t = j / nu, c = j % nu, nd = N - t;
-            const double* base = I.gpart + ((size_t)t * nu + c) * N;
+            const float2* base = ff_parts(I) + ((size_t)t * nu + c) * N;
             constexpr int QS = kFfMaxSplits / WPR;
-            double g[2 * QS];
+            float2 g[2 * QS];
 #pragma unroll
             for (int q = 0; q < QS; ++q) {
                 const int sp = wg + WPR * q;
-                const double* src = base + (size_t)sp * stride;
-                g[2 * q] = (sp < splits && lane < nd) ? src[lane] : 0.0;
-                g[2 * q + 1] = (sp < splits && lane + 32 < nd) ? src[lane + 32] : 0.0;
+                const float2* src = base + (size_t)sp * stride;
+                g[2 * q] = (sp < splits && lane < nd) ? src[lane] : make_float2(0.f, 0.f);
+                g[2 * q + 1] = (sp < splits && lane + 32 < nd) ? src[lane + 32] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < kMvH; ++u) s = fma(hv[u], vv[u], s);
             for (int k = tg + GT * kMvH; k < n; k += GT) s = fma(hc[k], v[k], s);
 #pragma unroll
-            for (int q = 0; q < 2 * QS; ++q) s += g[q];
+            for (int q = 0; q < 2 * QS; ++q) ff_acc(gh, gl, g[q].x, g[q].y);
             for (int sp = wg; sp < splits; sp += WPR)
-                for (int d = lane + 64; d < nd; d += 32) s += base[(size_t)sp * stride + d];
+                for (int d = lane + 64; d < nd; d += 32) {
+                    const float2 p = base[(size_t)sp * stride + d];
+                    ff_acc(gh, gl, p.x, p.y);
+                }
         }
-        s = warp_sum(s);
+        // the lane's H v share joins the float-float sum, and the lanes' and
+        // warps' sums meet on the FP32 pipe (FP64 adds issue at two lanes per
+        // clock per SM); one conversion back to FP64 per row
+        {
+            float h, l;
+            split_ff(s, h, l);
+            ff_acc(gh, gl, h, l);
+        }
+        warp_sum_ff(gh, gl);
         if (WPR > 1) {
-            if (lane == 0) wsum[warp] = s;
+            if (lane == 0) wsum[warp] = make_float2(gh, gl);
             __syncthreads();
             if (tg == 0) {
-                double m = 0.0;
+                float mh = 0.f, ml = 0.f;
 #pragma unroll
-                for (int w = 0; w < WPR; ++w) m += wsum[grp * WPR + w];
-                s = m;
+                for (int w = 0; w < WPR; ++w) ff_acc(mh, ml, wsum[grp * WPR + w].x, wsum[grp * WPR + w].y);
+                gh = mh;
+                gl = ml;
             }
             __syncthreads();
         }
+        s = (double)gh + (double)gl;
         if (tg == 0 && j < n) {
             const double mj = s + I.sigu[j] * v[j];
             if (mode == 0) {
