@@ -499,9 +499,10 @@ static int sm_count() {
 // Grid of the per-row kernels of an iteration (k_resid, k_aff, k_corr,
 // k_step, k_update; k_aff's finish reads k_resid's partials, so they share
 // it).  Their time is the FP64 work of the most loaded SM: a single instance
-// takes one CTA per SM with an equal share of the rows (a multiple of 32
-// threads; CTAs of 1024 over a grid stride past 1024 rows per SM); a batch
-// keeps 256-thread CTAs per instance, whose many CTAs spread by themselves.
+// of up to 1024 rows per SM takes one CTA per SM with an equal share of the
+// rows (a multiple of 32 threads).  Larger instances and batches keep
+// 256-thread CTAs over a grid stride, whose many CTAs spread by themselves
+// (1024-thread CTAs of 56 registers would fit one per SM, in ragged waves).
 struct EwGrid {
     int nb, threads;
 };
@@ -511,7 +512,6 @@ static EwGrid ew_grid(int count, int max_total) {
         int th = ((max_total + sms - 1) / sms + 31) / 32 * 32;
         th = th < 64 ? 64 : th;
         if (th <= kEwMaxThreads) return {ew_blocks(max_total, th), th};
-        return {ew_blocks(max_total, kEwMaxThreads), kEwMaxThreads};
     }
     return {ew_blocks(max_total, 256), 256};
 }

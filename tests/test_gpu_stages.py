@@ -76,6 +76,32 @@ def test_gamma_products_match_oracle(case, arith, rel):
     s.set_options(precision="fp64")
 
 
+@pytest.mark.parametrize("arith,rel", [("fp64", 1e-12), ("fp32", 1e-11)])
+def test_gamma_products_full_size_heat2d_32(arith, rel):
+    """Both products at the bench's plant (ns = 1024, nu = 10, N = 50, n = 500)
+    in the launch configuration a solve uses: 16 K-splits and anti-diagonal
+    sums of up to 50 terms for the float-float Gamma' w, 10 splits for
+    Gamma v.  Bars, normwise against the largest absolute sum:
+      fp32 (float-float products, float-float split-K partials and sums):
+        a few 2^-44 per term (the float-float words), plus one 2^-47 rounding
+        per float-float addition in a CTA's 64-term partial and in the sum of
+        up to 16 splits x 50 terms (<= 864 additions): <= 8e-12;
+      fp64: blocked FP64 sums, (terms per block + blocks) 2^-53 <= 1.2e-13
+      with a margin for the block plan."""
+    p = inputs.heat2d(32, 10, 50)
+    Gam, _, _, _ = oracle.condensed(p, np.zeros(p.ns))
+    s = binding.Solver(p, precision=arith)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        v = rng.standard_normal(p.n)
+        w = rng.standard_normal(p.ns * p.N)
+        gv = s.gamma_mv(v)
+        assert np.max(np.abs(gv - Gam @ v)) <= rel * np.max(np.abs(Gam) @ np.abs(v))
+        gw = s.gamma_tmv(w)
+        assert np.max(np.abs(gw - Gam.T @ w)) <= rel * np.max(np.abs(Gam).T @ np.abs(w))
+    s.close()
+
+
 def _sigmas(p, seed, spread=2.0):
     rng = np.random.default_rng(seed)
     sigx = 10.0 ** rng.uniform(-spread, spread, p.ns * p.N)
