@@ -288,7 +288,8 @@ __host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kb
 
 // Gamma v: block (r-tile, m-tile of states, split of the column range).  G
 // tiles stream through a double-buffered shared-memory ring (cp.async); the
-// input comes split into float-float by k_ff_prep_v.  Each block leaves its
+// input comes split into float-float (by k_ff_prep_v, or by the kernel that
+// formed it: kFuseInSplit).  Each block leaves its
 // split's partial tile.  With kFuseSumHere (batches) the last of the tile's
 // splits to arrive (a counter per tile, acquire-release like last_arrival)
 // sums them in split order, as k_gamma_mv_ff_sum does for one instance, and
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     __shared__ __align__(16) float Gs[2][2][kFfBK][kFfBM];          // [buffer][hi, lo][col][state]
     __shared__ float Vs[2][2][kFfBK][kFfBN + 1];                   // [buffer][hi, lo][col][r]
     (void)v;
-    const float* vsp = I.ffv;                                       // the input, split by k_ff_prep_v
+    const float* vsp = I.ffv;                                       // the input, split into float-float
     auto load = [&](int kt, int buf) {
         const int c0 = kbeg + kt * kFfBK;
         for (int e = threadIdx.x; e < kFfBK * (kFfBM / 4); e += kFfThreads) {
