@@ -13,6 +13,8 @@ namespace lqmpc {
 struct Inst;
 
 // kernels_ipm.cu
+// SMs of the current device (queried once per process; 1 if the query fails)
+int device_sm_count();
 void launch_set_u0(const Inst* d_insts, int count, int max_n, cudaStream_t st, int warm = 0);
 void launch_init_point(const Inst* d_insts, int count, int max_total, int max_n, double tol,
                        double tau, int max_iter, double refine_tol, int prec, cudaStream_t st, double mu0 = 0.0,

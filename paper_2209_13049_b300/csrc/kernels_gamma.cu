@@ -704,7 +704,7 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
 }
 
 static int ff_splits(int tiles, int nk) {
-    int s = (4 * 148 + tiles - 1) / (tiles > 0 ? tiles : 1);   // about four CTAs per SM
+    int s = (4 * device_sm_count() + tiles - 1) / (tiles > 0 ? tiles : 1);   // about four CTAs per SM
     if (s > nk) s = nk;
     if (s > kFfMaxSplits) s = kFfMaxSplits;
     return s < 1 ? 1 : s;

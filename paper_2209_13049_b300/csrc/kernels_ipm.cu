@@ -485,7 +485,7 @@ static int ew_blocks(int total_max, int threads) {
     return b < 1 ? 1 : (b > kMaxParts ? kMaxParts : b);
 }
 
-static int sm_count() {
+int device_sm_count() {
     static const int n = []() {
         int dev = 0, v = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -508,7 +508,7 @@ struct EwGrid {
 };
 static EwGrid ew_grid(int count, int max_total) {
     if (count == 1) {
-        const int sms = sm_count();
+        const int sms = device_sm_count();
         int th = ((max_total + sms - 1) / sms + 31) / 32 * 32;
         th = th < 64 ? 64 : th;
         if (th <= kEwMaxThreads) return {ew_blocks(max_total, th), th};

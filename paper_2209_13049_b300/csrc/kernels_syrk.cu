@@ -183,7 +183,7 @@ int syrk_cc_splits(int ns, int nu, int N) {
     int n = nu * N;
     int tiles = syrk_cc_tiles(n);
     long long chunks = (long long)N * ((ns + kKc - 1) / kKc);
-    int s = (148 * 4 + tiles - 1) / tiles;
+    int s = (device_sm_count() * 4 + tiles - 1) / tiles;
     if (s > chunks) s = (int)chunks;
     if (s > 64) s = 64;
     return s < 1 ? 1 : s;

@@ -394,21 +394,10 @@ int syrk_tc_tiles(int n) {
 int syrk_tc_splits(int ns, int nu, int N) {
     int tiles = syrk_tc_tiles(nu * N);
     long long chunks = (long long)N * ((ns + 63) / 64);
-    int s = (148 + tiles - 1) / tiles;
+    int s = (device_sm_count() + tiles - 1) / tiles;
     if (s > chunks) s = (int)chunks;
     if (s > 128) s = 128;
     return s < 1 ? 1 : s;
-}
-
-static int g_sms = 0;
-static int sm_count() {
-    if (!g_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_sms < 1)
-            g_sms = 148;
-    }
-    return g_sms;
 }
 
 // Split-K plan of the tensor-core SYRK: lower tile t of the 128-tiling gets
@@ -427,7 +416,7 @@ std::vector<int> syrk_tc_make_plan(int ns, int nu, int N) {
         ch[t] = (long long)(N - rmin) * nkc;
         C += ch[t];
     }
-    const int G = sm_count();
+    const int G = device_sm_count();
     std::vector<int> plan(2 * (size_t)ntiles + 2, 0);
     int off = 0;
     for (int t = 0; t < ntiles; ++t) {
