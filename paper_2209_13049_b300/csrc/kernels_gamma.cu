@@ -279,11 +279,12 @@ __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0
 // (aligned to the horizon's end), needs the columns from kbeg on (nk K-tiles
 // of 32) and gives them to S = min(nk, kFfMaxSplits) CTAs, so that every CTA
 // of the launch gets one K-tile (two past 512 columns) whatever its r-tile.
-__host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kbeg, int& nk, int& S) {
+__host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kbeg, int& nk, int& S,
+                                            int cap = kFfMaxSplits) {
     const int r1 = N - kFfBN * t;
     kbeg = ((N - r1) * nu) / kFfBK * kFfBK;
     nk = (n - kbeg + kFfBK - 1) / kFfBK;
-    S = nk < kFfMaxSplits ? nk : kFfMaxSplits;
+    S = nk < cap ? nk : cap;
 }
 
 // Gamma v: block (r-tile, m-tile of states, split of the column range).  G
@@ -298,7 +299,7 @@ __host__ __device__ inline void mv_ff_rtile(int t, int N, int nu, int n, int& kb
 // took longer than the separate sum launch it saves (C2: 15.7 -> 17.3 ms);
 // a batch has many more tiles (256 instances: 845 -> 833 ms).
 __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restrict__ insts, int in_role,
-                                                            int out_role, int flags, int fuse) {
+                                                            int out_role, int flags, int fuse, int cap) {
     pdl_wait();
     const Inst& I = insts[blockIdx.y];
     if (skip_instance(I, flags)) return;
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     int rem = blockIdx.x, t = 0, kbeg = 0, nk = 0, S = 1;
     for (;; ++t) {
         if (t >= nt) return;
-        mv_ff_rtile(t, N, nu, n, kbeg, nk, S);
+        mv_ff_rtile(t, N, nu, n, kbeg, nk, S, cap);
         if (rem < mt * S) break;
         rem -= mt * S;
     }
@@ -373,6 +374,31 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
         }
         __syncthreads();
     }
+    // the output and its fused uses from a tile's float-float sum
+    auto emit = [&](size_t k, float hs, float ls) {
+        const double sum = (double)hs + (double)ls;
+        role_ptr(I, out_role)[k] = sum;
+        if (fuse & kFuseOutDxs) I.dxs[k] = sum;
+        if (fuse & kFuseOutW) {
+            float h, l;
+            split_ff(sum * I.sigx[k], h, l);
+            I.ffw[k] = h;
+            I.ffw[(size_t)I.SX + k] = l;
+        }
+    };
+    if ((fuse & kFuseSumHere) && S == 1) {   // the tile's only split: no partial, no count
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                const int i = m0 + ty + 16 * a, r = r0 + tx + 8 * b;
+                if (i >= ns || r < 0) continue;
+                float hs = 0.f, ls = 0.f;
+                ff_acc(hs, ls, sh[a][b], sl[a][b]);
+                emit((size_t)r * ns + i, hs, ls);
+            }
+        return;
+    }
     // partial[split][r][i], float-float
     float2* part = ff_parts(I) + (size_t)split * I.SX;
 #pragma unroll
@@ -394,7 +420,6 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
     }
     __syncthreads();
     if (!last_sh) return;
-    double* out = role_ptr(I, out_role);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -409,15 +434,7 @@ __global__ void __launch_bounds__(kFfThreads) k_gamma_mv_ff(const Inst* __restri
             float hs = 0.f, ls = 0.f;
 #pragma unroll
             for (int q = 0; q < kFfMaxSplits; ++q) ff_acc(hs, ls, pv[q].x, pv[q].y);
-            const double sum = (double)hs + (double)ls;
-            out[k] = sum;
-            if (fuse & kFuseOutDxs) I.dxs[k] = sum;
-            if (fuse & kFuseOutW) {
-                float h, l;
-                split_ff(sum * I.sigx[k], h, l);
-                I.ffw[k] = h;
-                I.ffw[(size_t)I.SX + k] = l;
-            }
+            emit(k, hs, ls);
         }
 }
 
@@ -713,9 +730,13 @@ static int ff_splits(int tiles, int nk) {
 void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int in_role,
                         int out_role, int flags, cudaStream_t st, int fuse) {
     // CTAs: sum over r-tiles of m-tiles x splits (exact for one instance; for
-    // a batch a bound over its instances, the surplus CTAs return at once)
+    // a batch a bound over its instances, the surplus CTAs return at once).
+    // One instance splits K up to kFfMaxSplits ways to fill the SMs; a batch
+    // has tiles enough across its instances, so its split count is capped at
+    // what makes about four CTAs per SM (one at 256 instances: 16-way splits
+    // had launched half a million CTAs, nearly all returning at once).
     const int mt = (max_ns + kFfBM - 1) / kFfBM, nt = (max_N + kFfBN - 1) / kFfBN;
-    int ctas = 0;
+    int ctas = 0, cap = kFfMaxSplits;
     if (count == 1) {
         for (int t = 0; t < nt; ++t) {
             int kbeg, nk, S;
@@ -723,16 +744,21 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
             ctas += mt * S;
         }
     } else {
+        const long long tiles = (long long)count * mt * nt;
+        const long long want = 4LL * device_sm_count();
+        cap = (int)((want + tiles - 1) / tiles);
+        cap = cap < 1 ? 1 : (cap > kFfMaxSplits ? kFfMaxSplits : cap);
         const int nkmax = (max_n + kFfBK - 1) / kFfBK;
-        ctas = mt * nt * (nkmax < kFfMaxSplits ? nkmax : kFfMaxSplits);
+        ctas = mt * nt * (nkmax < cap ? nkmax : cap);
     }
     if (!(fuse & kFuseInSplit))
         LQ_LAUNCH(lq_pdl(k_ff_prep_v, dim3((max_n + 255) / 256, count), 256, 0, st, d_insts, in_role, flags));
     if (count > 1) {   // the split-K sum by the last split of each tile
         LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags,
-                         fuse | kFuseSumHere));
+                         fuse | kFuseSumHere, cap));
     } else {
-        LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags, fuse));
+        LQ_LAUNCH(lq_pdl(k_gamma_mv_ff, dim3(ctas, count), kFfThreads, 0, st, d_insts, in_role, out_role, flags, fuse,
+                         cap));
         const int nb = (max_ns * max_N + 255) / 256;
         LQ_LAUNCH(lq_pdl(k_gamma_mv_ff_sum, dim3(nb > 4096 ? 4096 : nb, count), 256, 0, st, d_insts, out_role, flags,
                          0, fuse));
