@@ -720,6 +720,12 @@ void launch_gamma_tmv(const Inst* d_insts, int count, int max_ns, int max_N, int
     }
 }
 
+// A CTA's K range is kept to kFfMaxKt K-tiles at most: in a batch the SMs are
+// full of tiles anyway, and the largest instances' CTAs would otherwise run
+// the whole range (63 K-tiles at ns = 2000) well after the rest.  256-instance
+// batch: 688 ms unbounded, 657 / 643 / 677 ms with 32 / 16 / 8.
+constexpr int kFfMaxKt = 16;
+
 static int ff_splits(int tiles, int nk) {
     int s = (4 * device_sm_count() + tiles - 1) / (tiles > 0 ? tiles : 1);   // about four CTAs per SM
     if (s > nk) s = nk;
@@ -747,8 +753,9 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
         const long long tiles = (long long)count * mt * nt;
         const long long want = 4LL * device_sm_count();
         cap = (int)((want + tiles - 1) / tiles);
+        const int nkmax = (max_n + kFfBK - 1) / kFfBK, cap_len = (nkmax + kFfMaxKt - 1) / kFfMaxKt;
+        cap = cap > cap_len ? cap : cap_len;
         cap = cap < 1 ? 1 : (cap > kFfMaxSplits ? kFfMaxSplits : cap);
-        const int nkmax = (max_n + kFfBK - 1) / kFfBK;
         ctas = mt * nt * (nkmax < cap ? nkmax : cap);
     }
     if (!(fuse & kFuseInSplit))
@@ -767,7 +774,9 @@ void launch_gamma_mv_ff(const Inst* d_insts, int count, int max_ns, int max_N, i
 
 int gamma_tmv_ff_splits(int count, int max_ns, int max_N, int max_n, int NV) {
     const int tiles = ((max_n + kFfBM - 1) / kFfBM) * (NV * ((max_N + kFfBN - 1) / kFfBN));
-    return ff_splits(tiles * count / 2, (max_ns + kFfBK - 1) / kFfBK);
+    const int nk = (max_ns + kFfBK - 1) / kFfBK;
+    const int s = ff_splits(tiles * count / 2, nk), s_len = (nk + kFfMaxKt - 1) / kFfMaxKt;
+    return s > s_len ? s : (s_len > kFfMaxSplits ? kFfMaxSplits : s_len);
 }
 
 void launch_gamma_tmv_ff(const Inst* d_insts, int count, int max_ns, int max_N, int max_n, int w0_role,
