@@ -161,6 +161,30 @@ def dist_setup(args):
     return world, rank, local
 
 
+def replica_seeds(rank: int, count: int) -> list:
+    """x0 seeds of one replica's warm-up and timed solves: ranks draw from
+    disjoint ranges, so N replicas solve N x count distinct problems."""
+    return [rank * 100000 + i for i in range(count)]
+
+
+def max_over_ranks(values, device="cpu") -> list:
+    """Element-wise maximum of per-rank floats over the process group (the
+    slowest replica's time decides the whole job's); unchanged without one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(world: int, steps: int, max_ms: float) -> float:
+    """Solves/s of the whole job: every replica's `steps` solves over the
+    slowest replica's total time (weak scaling: per-GPU work is fixed)."""
+    return world * steps / (max_ms / 1e3)
+
+
 def oracle_baseline():
     """The oracle as it stands, single-threaded, on one full solve of the
     workload (seed 0): about 20 s on one host core."""
@@ -607,7 +631,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     plant = inputs.heat2d(32, 10, 50)
     K, W = args.steps, args.warmup
-    seeds = [rank * 100000 + i for i in range(W + K)]
+    seeds = replica_seeds(rank, W + K)
     x0_host = [inputs.x0_gaussians(32, s) for s in seeds]
     x0_dev = [torch.tensor(x, dtype=torch.float64, device=dev) for x in x0_host]
     u_dev = [torch.zeros(plant.n, dtype=torch.float64, device=dev) for _ in seeds]
@@ -650,16 +674,9 @@ def run_ours(args):
     t_e2e, _ = timed_solves(mixed, range(W, W + K), use_host=True)
     barrier()
 
-    total_ms = float(sum(t_mixed))
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms, float(sum(t_e2e))], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, e2e_ms = float(tt[0]), float(tt[1])
-    else:
-        e2e_ms = float(sum(t_e2e))
-    value = world * K / (total_ms / 1e3)
-    e2e_value = world * K / (e2e_ms / 1e3)
+    total_ms, e2e_ms = max_over_ranks([sum(t_mixed), sum(t_e2e)], dev)
+    value = whole_job_rate(world, K, total_ms)
+    e2e_value = whole_job_rate(world, K, e2e_ms)
 
     # parity against the stored oracle results for x0 seed 0: both stopped by
     # the metric's 1e-8 test, and both run to 1e-11
