@@ -12,6 +12,8 @@ outside the timed events.
 
 The same JSON line carries one block per further workload (single-GPU runs
 only; --blocks selects them):
+  c1     1-D heat plant, ns = 50, nu = 5, N = 10 (n = 50): latency in
+         microseconds per iteration and kernel launches per iteration;
   c3     2-D heat plant of a 100 x 100 grid (ns = 10000, nu = 20, N = 50;
          M is 1000 x 1000): mixed and FP64 solves, formation and Cholesky
          rooflines, parity with the stored oracle solution;
@@ -57,7 +59,7 @@ NS, NU, N = 1024, 10, 50
 L2_NOTE = "flushed between steps (512 MB write, outside the timed events)"
 # DRAM bytes (read + write) of one k_potrf_flow launch on this workload from the
 # ncu capture summarised in profiles/ (None until captured for this kernel version)
-POTRF_FLOW_TRAFFIC = 765696
+POTRF_FLOW_TRAFFIC = 765184
 DTYPES = {
     "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, two-level "
             "FP32 tier near the end, FP64-accurate refinement, FP64 fallback",
@@ -322,6 +324,46 @@ def _potrf_roofline(st_list, n, sm_mhz, traffic, kernel):
                            f"sampled during the timed region); latency-bound (one diagonal block after another)",
             "flops_per_launch": flops, "executed_flops_per_launch": 2.0 * n ** 3 / 3.0,
             "launches": npf, "avg_launch_us": (tpf / max(1, npf) * 1e3) if npf else None}
+
+
+def block_c1(args, torch, binding, stream, flush):
+    """ns = 50, nu = 5, N = 10 (n = 50): a latency workload, whose matrices
+    fit in a few SMs' shared memory.  It is reported in microseconds per
+    solve and per iteration and in kernel launches per iteration (no roofline
+    fraction), mixed and FP64, with parity against the stored oracle solutions
+    of x0 seeds 0-3."""
+    p = inputs.heat1d(50, 5, 10)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K, W = args.c1_steps, 3
+    x0_dev = [torch.tensor(inputs.x0_uniform(50, s), dtype=torch.float64, device=dev) for s in range(W + K)]
+    u_dev = torch.zeros(p.n, dtype=torch.float64, device=dev)
+    out = {"workload": f"heat1d ns=50, nu=5, N=10 (n=50), x0 ~ U(-0.8, 0.8) seeds 0..{W + K - 1}, tol 1e-8",
+           "l2": L2_NOTE}
+    solvers = {"mixed": binding.Solver(p, precision=args.precision, stream=stream),
+               "fp64": binding.Solver(p, precision="fp64", stream=stream)}
+    for name, s in solvers.items():
+        fn = (lambda i, s=s: s.solve_device(x0_dev[i], u_dev, check=False))
+        _event_times(torch, stream, fn, range(W), flush)
+        l0 = binding.kernel_launches()
+        t, st = _event_times(torch, stream, fn, range(W, W + K), flush)
+        launches = binding.kernel_launches() - l0
+        iters = sum(x["iters"] for x in st)
+        out[name] = _summary(t, st)
+        out[name]["us_per_iter"] = sum(t) * 1e3 / max(1, iters)
+        out[name]["launches_per_iter"] = launches / max(1, iters)
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    gold = os.path.join(GOLDDIR, "heat1d_ns50_nu5_N10.npz")
+    if os.path.exists(gold):
+        g = np.load(gold)
+        errs = {}
+        for name, s in solvers.items():
+            e = [rel_err(s.solve(g[f"heat1d_50_s{k}_x0"], check=False)[0], g[f"heat1d_50_s{k}_u8"])
+                 for k in range(4)]
+            errs[f"{name}_vs_oracle_at_1e-8_stop_max"] = max(e)
+        out["u_rel_err_vs_oracle"] = errs
+    for s in solvers.values():
+        s.close()
+    return out
 
 
 def block_c3(args, torch, binding, stream, flush, peaks, which):
@@ -738,7 +780,9 @@ def run_ours(args):
         for b in blocks:
             t0 = time.perf_counter()
             try:
-                if b == "c3":
+                if b == "c1":
+                    line["c1"] = block_c1(args, torch, binding, stream, flush)
+                elif b == "c3":
                     line["c3"] = block_c3(args, torch, binding, stream, flush, peaks, which)
                 elif b == "batch":
                     line["batch"] = block_batch(args, torch, binding)
@@ -770,8 +814,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--blocks", default="c3,batch,warm",
-                    help="comma-separated further workloads on one GPU: c3, batch, warm, cube ('' for none)")
+    ap.add_argument("--blocks", default="c1,c3,batch,warm",
+                    help="comma-separated further workloads on one GPU: c1, c3, batch, warm, cube ('' for none)")
+    ap.add_argument("--c1-steps", type=int, default=20)
     ap.add_argument("--c3-steps", type=int, default=5)
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=3)

@@ -32,7 +32,9 @@
 //     L2, X2   = FP32 Cholesky + inverse of M32
 //     S2a + S2b = Y = X2 X1           k_x2_trimul  (float-float, lower)
 //     Xinv32 / Xlo32 = Y, XinvT32 / XloT32 = Y'    k_x2_copy
-// Scratch: S1 = Tinv32 (n^2 floats), S2a / S2b = the two halves of M64 (free
+// Scratch: S1 = Xlo32 (n^2 floats; free until k_x2_copy writes Y's low plane
+// there, after the last read of S1; not Tinv32, which the grid-cooperative
+// Cholesky uses for its inverse), S2a / S2b = the two halves of M64 (free
 // once E is formed).
 #include <algorithm>
 
@@ -45,7 +47,7 @@ namespace {
 
 constexpr int kXb = 32;          // tile edge (and K step) of every kernel here
 
-__device__ __forceinline__ float* x2_s1(const Inst& I) { return I.Tinv32; }
+__device__ __forceinline__ float* x2_s1(const Inst& I) { return I.Xlo32; }
 __device__ __forceinline__ float* x2_s2a(const Inst& I) { return reinterpret_cast<float*>(I.M64); }
 __device__ __forceinline__ float* x2_s2b(const Inst& I) {
     return reinterpret_cast<float*>(I.M64) + (size_t)I.n * I.n;

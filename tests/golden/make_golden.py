@@ -139,7 +139,7 @@ def group_warm(procs):
 
 
 # (grid points per dimension, horizon) of the stored cube solutions
-CUBE_CASES = ((4, 50), (5, 50), (6, 50), (4, 150))
+CUBE_CASES = ((4, 50), (5, 50), (6, 50), (4, 150), (4, 250), (4, 500))
 
 
 def group_cube(procs):
