@@ -304,3 +304,17 @@ def test_cube_plant_matches_oracle(g, T):
         u, st = s.solve(x0)
         assert st["status"] == 0, precision
         assert rel(u, CUBE[f"{tag}_u12"]) <= bar, precision
+
+
+@pytest.mark.parametrize("g,T", [(4, 250), (4, 500)], ids=["g4_T250", "g4_T500"])
+def test_cube_two_level_tier_past_n1024_matches_oracle(g, T):
+    """Solves started in the two-level FP32 tier at n = 1500 and 3000, where
+    the grid-cooperative Cholesky factors (both of the tier's factorisations):
+    no escalation to FP64 and the oracle's optimum at the 1e-8 stop."""
+    p, x0 = inputs.heat3d_cube(g, T), inputs.x0_cube(g)
+    tag = f"g{g}_T{T}"
+    s = binding.Solver(p, precision="fp32x2")
+    u, st = s.solve(x0)
+    assert st["status"] == 0
+    assert st["fallbacks"] == 0, st["fallbacks"]
+    assert rel(u, CUBE[f"{tag}_u8"]) <= 1e-6
