@@ -60,6 +60,8 @@ L2_NOTE = "flushed between steps (512 MB write, outside the timed events)"
 # DRAM bytes (read + write) of one k_potrf_flow launch on this workload from the
 # ncu capture summarised in profiles/ (None until captured for this kernel version)
 POTRF_FLOW_TRAFFIC = 765184
+# the same for one k_potrf_flowq launch of the 100 x 100 plant (n = 1000)
+POTRF_FLOWQ_C3_TRAFFIC = 2405120
 DTYPES = {
     "fp32": "mixed: FP32-accurate formation on tcgen05 (split TF32, FP32 accumulate), FP32 Cholesky, two-level "
             "FP32 tier near the end, FP64-accurate refinement, FP64 fallback",
@@ -393,7 +395,7 @@ def block_c3(args, torch, binding, stream, flush, peaks, which):
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
     sm_mhz = res["mixed"][2].get("sm_mhz") or 2032.0
     out["roofline_tensor_syrk"] = _tc_roofline(res["mixed"][1], p.ns, p.nu, p.N, peaks, which)
-    out["roofline_potrf"] = _potrf_roofline(res["mixed"][1], p.n, sm_mhz, None,
+    out["roofline_potrf"] = _potrf_roofline(res["mixed"][1], p.n, sm_mhz, POTRF_FLOWQ_C3_TRAFFIC,
                                             "k_potrf_flowq (queued dataflow FP32 Cholesky + inverse, n = 1000)")
     n64 = sum(s["syrk_fp64_launches"] for s in res["fp64"][1])
     t64 = sum(s["t_syrk_fp64_ms"] for s in res["fp64"][1])
