@@ -313,9 +313,9 @@ lqmpc_status lqmpc_form_kkt(lqmpc_ctx* ctx, const double* sigx, const double* si
  *
  * The first call on a device sets that device up, with it current: it loads
  * this entry point's two kernels onto the device (under CUDA's default lazy
- * module loading, that is when the driver places the 16 MiB array in device
- * memory, and it may synchronise the device), looks up the array's address
- * (cudaGetSymbolAddress) and reads the SM count.  Make that first call
+ * module loading, that is when the CUDA driver places the 16 MiB array in
+ * device memory, and it may synchronise the device), looks up the array's
+ * address (cudaGetSymbolAddress) and reads the SM count.  Make that first call
  * during set-up, before the loop that must not allocate, and outside any
  * stream capture (with CUDA_MODULE_LOADING=EAGER the array is placed when the
  * CUDA context is created instead).  All calls on a device share the array, so

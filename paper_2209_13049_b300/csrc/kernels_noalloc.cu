@@ -111,7 +111,7 @@ __global__ void k_kkt_scratch_reduce(const double* __restrict__ ws, int splits, 
 
 // Per-device set-up, done once per device by the first call (the device must
 // be current): force this module's two kernels onto the device (with lazy
-// module loading that is also when the driver places the scratch array),
+// module loading that is also when the CUDA driver places the scratch array),
 // look up the array's device address and read the SM count.  nullptr with
 // *err set if any step fails.
 struct NaDevice {
