@@ -5,7 +5,8 @@ GPUs run N independent replicas: disjoint x0 seeds, no collective in the data
 path, and one all-reduce of the per-rank times after the timed region.  These
 tests run that host logic with world_size 2 over gloo; the reference arm's
 rank rule (rank 0 alone works and prints) is checked by launching bench.py as
-rank 1.
+rank 1, and its JSON line (the CPU oracle on a bounded sample) against the
+headline's metric, unit and config.
 """
 import os
 import socket
@@ -74,3 +75,24 @@ def test_reference_arm_other_ranks_exit_without_work():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_line_keeps_the_contract():
+    """The reference arm (the CPU oracle on a bounded sample) prints one JSON
+    line with the headline's metric, unit and config, so the two arms'
+    lines compare like for like."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "solves/s"
+    assert d["config"] == bench.config_dict(1, "fp32")
+    assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0 and d["n_gpus"] == 1
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
